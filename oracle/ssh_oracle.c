@@ -1,0 +1,305 @@
+/*
+ * ssh_oracle.c -- plain FP64 CPU oracle for the SSH index and query path
+ * (Luo & Shrivastava, arXiv:1610.07328).
+ *
+ * TEST INFRASTRUCTURE: used only by tests/, the smoke check and the benchmark's
+ * CPU-baseline leg. It shares no code with the CUDA library. Each function
+ * follows the paper's definition step by step; see ssh_oracle.h for the
+ * sections, equations and readings each one follows.
+ *
+ * Compile with -ffp-contract=off (no fused multiply-add).
+ */
+#include "ssh_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ---------------------------------------------------------------- Philox */
+
+/* Published constants of Philox4x32 (Salmon et al., SC'11, Sec. 5). */
+#define PHILOX_MUL_A 0xD2511F53u
+#define PHILOX_MUL_B 0xCD9E8D57u
+#define PHILOX_WEYL_A 0x9E3779B9u
+#define PHILOX_WEYL_B 0xBB67AE85u
+
+void ssh_oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+    uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) { /* the key is bumped between rounds */
+            k0 += PHILOX_WEYL_A;
+            k1 += PHILOX_WEYL_B;
+        }
+        uint64_t prod_a = (uint64_t)PHILOX_MUL_A * (uint64_t)x0;
+        uint64_t prod_b = (uint64_t)PHILOX_MUL_B * (uint64_t)x2;
+        uint32_t hi_a = (uint32_t)(prod_a >> 32), lo_a = (uint32_t)prod_a;
+        uint32_t hi_b = (uint32_t)(prod_b >> 32), lo_b = (uint32_t)prod_b;
+        uint32_t y0 = hi_b ^ x1 ^ k0;
+        uint32_t y1 = lo_b;
+        uint32_t y2 = hi_a ^ x3 ^ k1;
+        uint32_t y3 = lo_a;
+        x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+double ssh_oracle_uniform(uint32_t x) {
+    double top23 = (double)(x >> 9);
+    return (top23 + 0.5) * (1.0 / 8388608.0); /* 2^-23 */
+}
+
+/* Domain tags keep the filter draws and the minhash draws on disjoint counters. */
+#define TAG_FILTER 0x46494C54u /* "FILT" */
+#define TAG_CWS 0x43575331u    /* "CWS1" */
+
+static void seed_key(uint64_t seed, uint32_t key[2]) {
+    key[0] = (uint32_t)(seed & 0xFFFFFFFFu);
+    key[1] = (uint32_t)(seed >> 32);
+}
+
+/* Sec. 4.1, "the entries of r are i.i.d. normal": Box-Muller on two uniforms of
+ * the Philox block with counter (p, 0, FILT, 0); entry 2p takes the cosine
+ * branch, entry 2p+1 the sine branch. */
+void ssh_oracle_filter(uint64_t seed, int W, float* r_out) {
+    uint32_t key[2];
+    seed_key(seed, key);
+    const double two_pi = 6.283185307179586476925286766559;
+    for (int j = 0; j < W; ++j) {
+        uint32_t ctr[4] = {(uint32_t)(j / 2), 0u, TAG_FILTER, 0u};
+        uint32_t blk[4];
+        ssh_oracle_philox4x32_10(ctr, key, blk);
+        double u1 = ssh_oracle_uniform(blk[0]);
+        double u2 = ssh_oracle_uniform(blk[1]);
+        double radius = sqrt(-2.0 * log(u1));
+        double angle = two_pi * u2;
+        double z = (j % 2 == 0) ? radius * cos(angle) : radius * sin(angle);
+        r_out[j] = (float)z;
+    }
+}
+
+/* ---------------------------------------------------------------- Sketch */
+
+int ssh_oracle_num_bits(int m, int W, int delta) {
+    if (W < 1 || delta < 1 || m < W) return 0;
+    return (m - W) / delta + 1;
+}
+
+double ssh_oracle_window_dot(const float* x, const float* r, int W, int start) {
+    double acc = 0.0;
+    for (int j = 0; j < W; ++j) acc = acc + (double)r[j] * (double)x[start + j];
+    return acc;
+}
+
+void ssh_oracle_sketch(const float* x, int m, const float* r, int W, int delta, uint8_t* bits_out) {
+    int nb = ssh_oracle_num_bits(m, W, delta);
+    for (int i = 0; i < nb; ++i) {
+        double dot = ssh_oracle_window_dot(x, r, W, i * delta);
+        bits_out[i] = (dot >= 0.0) ? 1 : 0; /* "+1 : r.X >= 0" */
+    }
+}
+
+/* --------------------------------------------------------------- Shingle */
+
+static int cmp_u32(const void* a, const void* b) {
+    uint32_t x = *(const uint32_t*)a, y = *(const uint32_t*)b;
+    return (x > y) - (x < y);
+}
+
+int ssh_oracle_shingle(const uint8_t* bits, int nb, int n, uint32_t* ids_out, uint32_t* counts_out) {
+    if (n < 1 || n > 32 || nb < n) return 0;
+    int s = nb - n + 1;
+    uint32_t* all = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)s);
+    for (int i = 0; i < s; ++i) {
+        uint32_t id = 0;
+        for (int j = 0; j < n; ++j) id = (id << 1) | (uint32_t)(bits[i + j] & 1u);
+        all[i] = id;
+    }
+    qsort(all, (size_t)s, sizeof(uint32_t), cmp_u32);
+    int nnz = 0;
+    for (int i = 0; i < s; ++i) {
+        if (nnz > 0 && ids_out[nnz - 1] == all[i]) {
+            counts_out[nnz - 1] += 1;
+        } else {
+            ids_out[nnz] = all[i];
+            counts_out[nnz] = 1;
+            nnz += 1;
+        }
+    }
+    free(all);
+    return nnz;
+}
+
+/* --------------------------------------------------- Weighted minhash (ICWS) */
+
+void ssh_oracle_cws_draw(uint64_t seed, uint32_t j, uint32_t k, double* r, double* c, double* beta) {
+    uint32_t key[2];
+    seed_key(seed, key);
+    uint32_t ctr0[4] = {k, j, TAG_CWS, 0u};
+    uint32_t ctr1[4] = {k, j, TAG_CWS, 1u};
+    uint32_t b0[4], b1[4];
+    ssh_oracle_philox4x32_10(ctr0, key, b0);
+    ssh_oracle_philox4x32_10(ctr1, key, b1);
+    double u1 = ssh_oracle_uniform(b0[0]);
+    double u2 = ssh_oracle_uniform(b0[1]);
+    double u3 = ssh_oracle_uniform(b0[2]);
+    double u4 = ssh_oracle_uniform(b0[3]);
+    double u5 = ssh_oracle_uniform(b1[0]);
+    *r = -log(u1 * u2);    /* Gamma(2,1) as the sum of two Exp(1) */
+    *c = -log(u3 * u4);    /* Gamma(2,1) */
+    *beta = u5;            /* U(0,1) */
+}
+
+double ssh_oracle_cws_log_a(double r, double c, double beta, uint32_t S, double* t_out) {
+    double ln_s = log((double)S);
+    double t = floor(ln_s / r + beta);
+    double ln_a = log(c) - r * ((t - beta) + 1.0);
+    *t_out = t;
+    return ln_a;
+}
+
+void ssh_oracle_cws(uint64_t seed, int nhash, const uint32_t* ids, const uint32_t* counts, int nnz,
+                    uint32_t* kstar, uint32_t* tstar) {
+    for (int j = 0; j < nhash; ++j) {
+        double best = INFINITY;
+        uint32_t best_k = 0, best_t = 0;
+        for (int e = 0; e < nnz; ++e) { /* ids ascending: strict < keeps the smaller k on ties */
+            double r, c, beta, t;
+            ssh_oracle_cws_draw(seed, (uint32_t)j, ids[e], &r, &c, &beta);
+            double ln_a = ssh_oracle_cws_log_a(r, c, beta, counts[e], &t);
+            if (ln_a < best) {
+                best = ln_a;
+                best_k = ids[e];
+                best_t = (uint32_t)t;
+            }
+        }
+        kstar[j] = best_k;
+        tstar[j] = best_t;
+    }
+}
+
+/* ------------------------------------------------------------ Bucket keys */
+
+/* splitmix64 output finalizer (Steele, Lea & Flood, OOPSLA'14; Stafford's mix13). */
+static uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+uint64_t ssh_oracle_bucket_key(uint64_t seed, int l, int K, const uint32_t* kstar, const uint32_t* tstar) {
+    uint64_t h = seed ^ (0x9E3779B97F4A7C15ull * (uint64_t)(l + 1));
+    for (int i = 0; i < K; ++i) {
+        int j = l * K + i;
+        uint64_t v = ((uint64_t)kstar[j] << 32) | (uint64_t)tstar[j];
+        h = mix64(h ^ v);
+    }
+    return h;
+}
+
+int ssh_oracle_hash_series(const float* x, int m, const float* r, int W, int delta, int n,
+                           uint64_t seed, int K, int L, uint32_t* kstar, uint32_t* tstar) {
+    int nb = ssh_oracle_num_bits(m, W, delta);
+    if (nb < n) return -1;
+    uint8_t* bits = (uint8_t*)malloc((size_t)nb);
+    uint32_t* ids = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)nb);
+    uint32_t* counts = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)nb);
+    ssh_oracle_sketch(x, m, r, W, delta, bits);
+    int nnz = ssh_oracle_shingle(bits, nb, n, ids, counts);
+    ssh_oracle_cws(seed, K * L, ids, counts, nnz, kstar, tstar);
+    free(bits);
+    free(ids);
+    free(counts);
+    return nnz;
+}
+
+/* ------------------------------------------------------------------- DTW */
+
+int ssh_oracle_band_radius(float band, int m) {
+    if (!(band > 0.0f)) return 0;
+    double rb = floor((double)band * (double)m);
+    if (rb > (double)(m - 1)) rb = (double)(m - 1);
+    return (int)rb;
+}
+
+double ssh_oracle_dtw(const float* a, const float* b, int m, int rb) {
+    /* Two rows of the m x m table; cells outside the band |i - j| <= rb are +inf. */
+    double* prev = (double*)malloc(sizeof(double) * (size_t)m);
+    double* cur = (double*)malloc(sizeof(double) * (size_t)m);
+    for (int j = 0; j < m; ++j) prev[j] = INFINITY;
+    for (int i = 0; i < m; ++i) {
+        for (int j = 0; j < m; ++j) cur[j] = INFINITY;
+        int j_lo = i - rb < 0 ? 0 : i - rb;
+        int j_hi = i + rb > m - 1 ? m - 1 : i + rb;
+        for (int j = j_lo; j <= j_hi; ++j) {
+            double diff = (double)a[i] - (double)b[j];
+            double cost = diff * diff;
+            if (i == 0 && j == 0) {
+                cur[j] = cost;
+                continue;
+            }
+            double best = INFINITY;
+            if (i > 0 && prev[j] < best) best = prev[j];                 /* D(i-1, j)   */
+            if (j > 0 && cur[j - 1] < best) best = cur[j - 1];           /* D(i, j-1)   */
+            if (i > 0 && j > 0 && prev[j - 1] < best) best = prev[j - 1]; /* D(i-1, j-1) */
+            cur[j] = cost + best;
+        }
+        double* tmp = prev;
+        prev = cur;
+        cur = tmp;
+    }
+    double out = prev[m - 1];
+    free(prev);
+    free(cur);
+    return out;
+}
+
+double ssh_oracle_lb_keogh(const float* q, const float* c, int m, int rb) {
+    double lb = 0.0;
+    for (int i = 0; i < m; ++i) {
+        int lo = i - rb < 0 ? 0 : i - rb;
+        int hi = i + rb > m - 1 ? m - 1 : i + rb;
+        double up = (double)q[lo], low = (double)q[lo];
+        for (int t = lo; t <= hi; ++t) {
+            if ((double)q[t] > up) up = (double)q[t];
+            if ((double)q[t] < low) low = (double)q[t];
+        }
+        double ci = (double)c[i];
+        if (ci > up) {
+            double d = ci - up;
+            lb = lb + d * d;
+        } else if (ci < low) {
+            double d = ci - low;
+            lb = lb + d * d;
+        }
+    }
+    return lb;
+}
+
+/* (d1, id1) < (d2, id2) in lexicographic order; an empty slot (id -1) is last. */
+static int pair_less(double d1, int64_t id1, double d2, int64_t id2) {
+    if (id2 < 0) return 1;
+    if (d1 != d2) return d1 < d2;
+    return id1 < id2;
+}
+
+void ssh_oracle_topk_dtw(const float* q, const float* rows, const int64_t* ids, int64_t n, int m,
+                         int rb, int k, int64_t* out_ids, double* out_d) {
+    for (int s = 0; s < k; ++s) {
+        out_ids[s] = -1;
+        out_d[s] = INFINITY;
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        double d = ssh_oracle_dtw(q, rows + (size_t)i * (size_t)m, m, rb);
+        int64_t id = ids[i];
+        int pos = k; /* insertion into the sorted list of the k best pairs */
+        while (pos > 0 && pair_less(d, id, out_d[pos - 1], out_ids[pos - 1])) pos -= 1;
+        if (pos >= k) continue;
+        for (int s = k - 1; s > pos; --s) {
+            out_d[s] = out_d[s - 1];
+            out_ids[s] = out_ids[s - 1];
+        }
+        out_d[pos] = d;
+        out_ids[pos] = id;
+    }
+}

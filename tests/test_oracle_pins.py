@@ -1,0 +1,459 @@
+"""Pins for the CPU oracle: each test checks the oracle against something other
+than itself -- a worked example printed in the paper, a published known-answer
+vector, a closed form, an invariant, or brute force on tiny inputs.
+
+Paper: Luo & Shrivastava, arXiv:1610.07328 (SSH: Sketch, Shingle & Hash).
+"""
+import itertools
+import math
+import os
+from collections import Counter
+
+import numpy as np
+import pytest
+
+import oracle
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _read_golden(name):
+    vals = {}
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            parts = line.split()
+            vals[parts[0]] = parts[1:]
+            rows.append(parts)
+    return vals, rows
+
+
+# ------------------------------------------------------------------ Sec. 4.1
+
+def test_sketch_worked_example():
+    """Sec. 4.1 Eq. (eq1): X=(1,2,4,1), r=(0.1,-0.1), delta=2 -> (-1, +1)."""
+    g, _ = _read_golden("sketch_worked_example.txt")
+    x = np.array([float(v) for v in g["x"]], np.float32)
+    r = np.array([float(v) for v in g["r"]], np.float32)
+    delta = int(g["delta"][0])
+    dots = [float(v) for v in g["dots"]]
+    bits = [int(v) for v in g["bits"]]
+    assert oracle.num_bits(len(x), len(r), delta) == len(bits)
+    got = oracle.sketch(x, r, delta)
+    assert got.tolist() == bits
+    for i, d in enumerate(dots):
+        assert oracle.window_dot(x, r, i * delta) == pytest.approx(d, abs=1e-6)
+
+
+def test_num_bits_floor_formula():
+    # floor((m - W) / delta) + 1, fixed by the worked example (m=4, W=2, delta=2 -> 2 bits)
+    assert oracle.num_bits(4, 2, 2) == 2
+    assert oracle.num_bits(512, 80, 3) == 145
+    assert oracle.num_bits(1024, 120, 5) == 181
+    assert oracle.num_bits(128, 32, 3) == 33
+    assert oracle.num_bits(2048, 256, 3) == 598
+    assert oracle.num_bits(10, 10, 3) == 1
+    assert oracle.num_bits(9, 10, 3) == 0
+
+
+def test_sketch_trailing_samples_ignored_and_zero_is_plus():
+    # m=7, W=3, delta=2 -> windows start at 0, 2, 4; samples 7.. do not exist
+    r = np.array([1.0, -2.0, 1.0], np.float32)
+    x = np.zeros(7, np.float32)  # every dot product is exactly 0 -> "+1"
+    assert oracle.sketch(x, r, 2).tolist() == [1, 1, 1]
+    x = np.array([0, 0, 5, 0, 0, 0, 0], np.float32)
+    # windows: [0,0,5] -> 5 >= 0 (1); [5,0,0] -> 5 (1); [0,0,0] -> 0 (1)
+    assert oracle.sketch(x, r, 2).tolist() == [1, 1, 1]
+    x = np.array([0, 3, 0, 0, 0, 3, 0], np.float32)
+    # [0,3,0] -> -6 (0); [0,0,0] -> 0 (1); [0,3,0] -> -6 (0)
+    assert oracle.sketch(x, r, 2).tolist() == [0, 1, 0]
+
+
+def test_sketch_shift_by_delta_shifts_bits():
+    rng = np.random.default_rng(3)
+    W, delta = 16, 3
+    r = oracle.filter_r(11, W)
+    x = rng.standard_normal(200).astype(np.float32)
+    b0 = oracle.sketch(x, r, delta)
+    b1 = oracle.sketch(x[delta:], r, delta)
+    assert np.array_equal(b0[1:1 + len(b1)], b1)
+
+
+def test_sketch_matches_direct_sign_of_projection():
+    rng = np.random.default_rng(5)
+    for W, delta, m in [(8, 1, 40), (32, 3, 128), (17, 5, 100)]:
+        r = rng.standard_normal(W).astype(np.float32)
+        x = rng.standard_normal(m).astype(np.float32)
+        nb = (m - W) // delta + 1
+        want = [1 if float(np.dot(r.astype(np.float64), x[i * delta:i * delta + W].astype(np.float64))) >= 0 else 0
+                for i in range(nb)]
+        # signs agree except at ties within rounding; random data has none
+        assert oracle.sketch(x, r, delta).tolist() == want
+
+
+# ------------------------------------------------------------------ Sec. 4.2
+
+def test_shingle_worked_example():
+    """Sec. 4.2: B=(+1,+1,-1,-1,+1,+1), n=2 -> {(+1,+1):2, (+1,-1):1, (-1,+1):1, (-1,-1):1}."""
+    g, _ = _read_golden("shingle_worked_example.txt")
+    bits = [int(v) for v in g["bits"]]
+    n = int(g["n"][0])
+    ids, counts = oracle.shingle(bits, n)
+    assert ids.tolist() == [int(v) for v in g["ids"]]
+    assert counts.tolist() == [int(v) for v in g["counts"]]
+
+
+def test_shingle_brute_force():
+    rng = np.random.default_rng(7)
+    for trial in range(50):
+        nb = int(rng.integers(1, 60))
+        n = int(rng.integers(1, 20))
+        bits = rng.integers(0, 2, size=nb).astype(np.uint8)
+        ids, counts = oracle.shingle(bits, n)
+        if nb < n:
+            assert len(ids) == 0
+            continue
+        grams = Counter(tuple(bits[i:i + n]) for i in range(nb - n + 1))
+        want = sorted((int("".join(str(b) for b in g), 2), c) for g, c in grams.items())
+        assert list(zip(ids.tolist(), counts.tolist())) == want
+        assert counts.sum() == nb - n + 1
+
+
+def test_shingle_first_bit_most_significant():
+    ids, counts = oracle.shingle([1, 0, 0, 1], 3)
+    assert ids.tolist() == [1, 4] and counts.tolist() == [1, 1]  # "100" = 4, "001" = 1
+    ids, _ = oracle.shingle([1] * 40, 32)
+    assert ids.tolist() == [0xFFFFFFFF]
+
+
+# ------------------------------------------------------------ random numbers
+
+def test_philox_known_answers():
+    _, rows = _read_golden("philox4x32_10_kat.txt")
+    assert len(rows) == 3
+    for row in rows:
+        v = [int(h, 16) for h in row]
+        assert oracle.philox4x32_10(v[0:4], v[4:6]).tolist() == v[6:10]
+
+
+def test_uniform_open_interval_and_fp32_exact():
+    for x in [0, 1, 511, 512, 0x7FFFFFFF, 0x80000000, 0xFFFFFE00, 0xFFFFFFFF, 123456789]:
+        u = oracle.uniform(x)
+        assert 0.0 < u < 1.0
+        assert float(np.float32(u)) == u
+    assert oracle.uniform(0) == 2.0 ** -24
+    assert oracle.uniform(0xFFFFFFFF) == 1.0 - 2.0 ** -24
+
+
+def test_filter_is_standard_normal():
+    """Sec. 4.1: r has i.i.d. N(0,1) entries."""
+    from scipy import stats
+    r = oracle.filter_r(0, 200_000).astype(np.float64)
+    assert abs(r.mean()) < 5.0 / math.sqrt(len(r))
+    assert abs(r.var() - 1.0) < 5.0 * math.sqrt(2.0 / len(r))
+    assert stats.kstest(r, "norm").pvalue > 1e-3
+    # even (cosine) and odd (sine) entries of one Box-Muller pair are uncorrelated
+    assert abs(np.corrcoef(r[0::2], r[1::2])[0, 1]) < 5.0 / math.sqrt(len(r) / 2)
+
+
+def test_filter_deterministic_and_prefix_stable():
+    a = oracle.filter_r(42, 80)
+    b = oracle.filter_r(42, 120)
+    c = oracle.filter_r(43, 80)
+    assert np.array_equal(a, b[:80])
+    assert not np.array_equal(a, c)
+
+
+# ------------------------------------------------------ Sec. 4.3 / Sec. 2.3
+
+def _draws(seed, j, k):
+    return oracle.cws_draw(seed, j, k)
+
+
+def test_cws_single_element_set():
+    """A one-element set hashes to that element; t* brackets the weight: y* <= S < y* e^r
+    with y* = exp(r (t* - beta)) (Ioffe 2010, the consistent-sampling interval)."""
+    for seed in range(30):
+        for S in [1, 2, 3, 7, 40, 1000]:
+            k = 12345 + S
+            ks, ts = oracle.cws(seed, 3, [k], [S])
+            assert ks.tolist() == [k] * 3
+            for j in range(3):
+                r, c, beta = _draws(seed, j, k)
+                y = math.exp(r * (int(ts[j]) - beta))
+                assert y <= S * (1 + 1e-12)
+                assert S < y * math.exp(r) * (1 + 1e-12)
+
+
+def test_cws_count_one_has_t_zero():
+    ks, ts = oracle.cws(5, 50, [1, 9, 77], [1, 1, 1])
+    assert (ts == 0).all()
+
+
+def test_cws_draw_distributions():
+    from scipy import stats
+    rs, cs, bs = [], [], []
+    for j in range(4000):
+        r, c, b = _draws(9, j, j * 7 + 1)
+        rs.append(r)
+        cs.append(c)
+        bs.append(b)
+    assert stats.kstest(rs, "gamma", args=(2.0,)).pvalue > 1e-3
+    assert stats.kstest(cs, "gamma", args=(2.0,)).pvalue > 1e-3
+    assert stats.kstest(bs, "uniform").pvalue > 1e-3
+
+
+def test_cws_identical_sets_collide():
+    ids = [3, 10, 999, 40000]
+    counts = [1, 5, 2, 17]
+    a = oracle.cws(1, 64, ids, counts)
+    b = oracle.cws(1, 64, ids, counts)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def _weighted_jaccard(x: dict, y: dict) -> float:
+    keys = set(x) | set(y)
+    num = sum(min(x.get(k, 0), y.get(k, 0)) for k in keys)
+    den = sum(max(x.get(k, 0), y.get(k, 0)) for k in keys)
+    return num / den
+
+
+@pytest.mark.parametrize("x,y", [
+    ({1: 3, 2: 1, 5: 2}, {1: 2, 2: 1, 7: 4}),
+    ({0: 10, 3: 1}, {0: 4, 3: 1, 9: 1}),
+    ({11: 1, 12: 1, 13: 1}, {12: 1, 13: 1, 14: 1, 15: 1}),
+])
+def test_cws_collision_rate_is_weighted_jaccard(x, y):
+    """Eq. (CollProb): Pr[h(x) = h(y)] = J(x, y), over 10^4 seeds, within 3 sigma."""
+    trials = 10_000
+    J = _weighted_jaccard(x, y)
+    xi, xc = zip(*sorted(x.items()))
+    yi, yc = zip(*sorted(y.items()))
+    hits = 0
+    for seed in range(trials):
+        a = oracle.cws(seed, 1, xi, xc)
+        b = oracle.cws(seed, 1, yi, yc)
+        hits += int(a[0][0] == b[0][0] and a[1][0] == b[1][0])
+    sigma = math.sqrt(J * (1 - J) / trials)
+    assert abs(hits / trials - J) <= 3 * sigma, (hits / trials, J, sigma)
+
+
+def test_cws_binary_sets_reduce_to_jaccard():
+    """Sec. 2.3: for 0/1 weights J is |x ∩ y| / |x ∪ y|."""
+    x = set(range(0, 30))
+    y = set(range(20, 45))
+    J = len(x & y) / len(x | y)
+    nh = 10_000
+    a = oracle.cws(3, nh, sorted(x), [1] * len(x))
+    b = oracle.cws(3, nh, sorted(y), [1] * len(y))
+    rate = float(np.mean((a[0] == b[0]) & (a[1] == b[1])))
+    assert abs(rate - J) <= 3 * math.sqrt(J * (1 - J) / nh)
+
+
+def test_cws_samples_elements_in_proportion_to_weight():
+    """Consistent weighted sampling draws element k with probability S_k / sum S."""
+    from scipy import stats
+    ids = [4, 8, 15, 16, 23]
+    counts = [1, 2, 3, 5, 9]
+    nh = 20_000
+    ks, _ = oracle.cws(17, nh, ids, counts)
+    obs = np.array([(ks == k).sum() for k in ids], dtype=np.float64)
+    exp = np.array(counts, dtype=np.float64) / sum(counts) * nh
+    assert stats.chisquare(obs, exp).pvalue > 1e-3
+
+
+def test_cws_tie_goes_to_smaller_id():
+    # the same shingle twice in a list would tie; with distinct ids ties are measure-zero,
+    # so check the rule on the log-a values directly: argmin over ascending ids keeps the first
+    seed, j = 0, 0
+    vals = []
+    for k in range(200):
+        r, c, b = _draws(seed, j, k)
+        vals.append(oracle.cws_log_a(r, c, b, 1)[0])
+    ks, _ = oracle.cws(seed, 1, list(range(200)), [1] * 200)
+    assert ks[0] == int(np.argmin(vals))  # numpy argmin also returns the first minimum
+
+
+def test_bucket_keys_separate_distinct_tuples():
+    rng = np.random.default_rng(0)
+    K, L = 4, 16
+    seen = {}
+    for _ in range(3000):
+        ks = rng.integers(0, 256, size=K * L).astype(np.uint32)
+        ts = rng.integers(0, 4, size=K * L).astype(np.uint32)
+        for l in range(L):
+            key = oracle.bucket_key(0, l, K, ks, ts)
+            tup = (l, tuple(ks[l * K:(l + 1) * K]), tuple(ts[l * K:(l + 1) * K]))
+            assert seen.setdefault(key, tup) == tup
+
+
+# ------------------------------------------------------------------ Sec. 2.1
+
+def _dtw_all_paths(a, b, rb):
+    """Minimum over every monotone warping path inside the band (brute force)."""
+    m = len(a)
+    best = math.inf
+
+    def walk(i, j, acc):
+        nonlocal best
+        if abs(i - j) > rb:
+            return
+        acc += (float(a[i]) - float(b[j])) ** 2
+        if acc >= best:
+            return
+        if i == m - 1 and j == m - 1:
+            best = acc
+            return
+        if i + 1 < m:
+            walk(i + 1, j, acc)
+        if j + 1 < m:
+            walk(i, j + 1, acc)
+        if i + 1 < m and j + 1 < m:
+            walk(i + 1, j + 1, acc)
+
+    walk(0, 0, 0.0)
+    return best
+
+
+def test_dtw_brute_force_paths():
+    rng = np.random.default_rng(1)
+    for _ in range(60):
+        m = int(rng.integers(1, 7))
+        rb = int(rng.integers(0, m))
+        a = rng.standard_normal(m).astype(np.float32)
+        b = rng.standard_normal(m).astype(np.float32)
+        assert oracle.dtw(a, b, rb) == pytest.approx(_dtw_all_paths(a, b, rb), rel=1e-12, abs=1e-12)
+
+
+def test_dtw_hand_computed_3x3():
+    a = np.array([0, 1, 2], np.float32)
+    b = np.array([0, 2, 2], np.float32)
+    # costs: row0 [0,4,4], row1 [1,1,1], row2 [4,0,0]
+    # D row0: 0, 4, 8; row1: 1, 1, 2; row2: 5, 1, 1  -> 1
+    assert oracle.dtw(a, b, 2) == 1.0
+    # band 1 removes (0,2) and (2,0): D row0: 0,4,inf; row1: 1,1,2; row2: inf,1,1 -> 1
+    assert oracle.dtw(a, b, 1) == 1.0
+    # band 0 is the squared Euclidean distance 0 + 1 + 0
+    assert oracle.dtw(a, b, 0) == 1.0
+    a = np.array([1, 2, 3], np.float32)
+    b = np.array([2, 3, 4], np.float32)
+    assert oracle.dtw(a, b, 0) == 3.0
+    # full band: path (0,0)(1,0)(2,1)(2,2): 1 + 0 + 0 + 1 = 2
+    assert oracle.dtw(a, b, 2) == 2.0
+
+
+def test_dtw_identity_symmetry_band0_monotone():
+    rng = np.random.default_rng(2)
+    for _ in range(20):
+        m = int(rng.integers(2, 90))
+        a = rng.standard_normal(m).astype(np.float32)
+        b = rng.standard_normal(m).astype(np.float32)
+        assert oracle.dtw(a, a, m // 3) == 0.0
+        euclid = float(np.sum((a.astype(np.float64) - b.astype(np.float64)) ** 2))
+        assert oracle.dtw(a, b, 0) == pytest.approx(euclid, rel=1e-12)
+        prev = math.inf
+        for rb in range(0, m, max(1, m // 7)):
+            d = oracle.dtw(a, b, rb)
+            assert d == pytest.approx(oracle.dtw(b, a, rb), rel=1e-12)
+            assert d <= prev * (1 + 1e-12)
+            assert d <= euclid * (1 + 1e-12)
+            prev = d
+
+
+def test_band_radius_floor():
+    assert oracle.band_radius(0.05, 128) == 6
+    assert oracle.band_radius(0.05, 512) == 25
+    assert oracle.band_radius(0.10, 1024) == 102
+    assert oracle.band_radius(0.05, 2048) == 102
+    assert oracle.band_radius(0.0, 100) == 0
+    assert oracle.band_radius(5.0, 100) == 99
+
+
+# ------------------------------------------------------------------- Sec. 3
+
+def test_lb_keogh_lower_bounds_dtw():
+    rng = np.random.default_rng(4)
+    for _ in range(200):
+        m = int(rng.integers(2, 70))
+        rb = int(rng.integers(0, m))
+        q = np.cumsum(rng.standard_normal(m)).astype(np.float32)
+        c = np.cumsum(rng.standard_normal(m)).astype(np.float32)
+        assert oracle.lb_keogh(q, c, rb) <= oracle.dtw(q, c, rb) * (1 + 1e-12) + 1e-12
+
+
+def test_lb_keogh_band0_and_self():
+    rng = np.random.default_rng(6)
+    q = rng.standard_normal(50).astype(np.float32)
+    c = rng.standard_normal(50).astype(np.float32)
+    euclid = float(np.sum((q.astype(np.float64) - c.astype(np.float64)) ** 2))
+    assert oracle.lb_keogh(q, c, 0) == pytest.approx(euclid, rel=1e-12)
+    assert oracle.lb_keogh(q, q, 5) == 0.0
+    # a candidate inside the envelope everywhere has LB 0
+    assert oracle.lb_keogh(q, np.clip(c, q.min(), q.max()) * 0 + np.median(q), 49) == 0.0
+
+
+# --------------------------------------------------------- Algorithms 1 and 2
+
+def test_topk_matches_sort():
+    rng = np.random.default_rng(8)
+    m, n, k = 24, 40, 7
+    q = rng.standard_normal(m).astype(np.float32)
+    rows = rng.standard_normal((n, m)).astype(np.float32)
+    ids = rng.permutation(1000)[:n].astype(np.int64)
+    got_ids, got_d = oracle.topk_dtw(q, rows, ids, 3, k)
+    d = np.array([oracle.dtw(q, rows[i], 3) for i in range(n)])
+    order = sorted(range(n), key=lambda i: (d[i], ids[i]))[:k]
+    assert got_ids.tolist() == [int(ids[i]) for i in order]
+    assert np.allclose(got_d, d[order], rtol=0, atol=0)
+    # fewer rows than k: tail is (-1, inf)
+    got_ids, got_d = oracle.topk_dtw(q, rows[:3], ids[:3], 3, 5)
+    assert got_ids[3:].tolist() == [-1, -1] and np.isinf(got_d[3:]).all()
+
+
+def test_index_candidates_equal_pairwise_tuple_matches():
+    from paper_1610_07328_gb300 import synth
+    W, delta, n, K, L = 16, 2, 6, 2, 5
+    idx = oracle.OracleIndex(W, delta, n, K, L, 0.1, 3)
+    db = synth.random_walk(60, 64, seed=0)
+    idx.add(db)
+    qs, _ = synth.perturbed_queries(db, 6, seed=1)
+    for q in qs:
+        qk, qt = idx.hash(q)
+        qt_l = idx.tuples(qk, qt)
+        want = []
+        for i in range(len(db)):
+            xk, xt = idx.hashes[i]
+            if any(a == b for a, b in zip(qt_l, idx.tuples(xk, xt))):
+                want.append(i)
+        assert idx.candidates(q).tolist() == want
+
+
+def test_index_query_is_topk_of_candidates_and_finds_exact_copies():
+    from paper_1610_07328_gb300 import synth
+    idx = oracle.OracleIndex(32, 3, 8, 4, 16, 0.05, 0)
+    db = synth.random_walk(300, 128, seed=0)
+    idx.add(db)
+    qs, _ = synth.perturbed_queries(db, 5, seed=1)
+    for q in qs:
+        ids, d = idx.query(q, 5)
+        cand = idx.candidates(q)
+        assert set(ids[ids >= 0].tolist()) <= set(cand.tolist())
+        assert np.all(np.diff(d[ids >= 0]) >= 0)
+        # every returned distance is no better than the exact top-k over all series
+        e_ids, e_d = idx.exact_topk(q, 5)
+        assert np.all(d >= e_d - 1e-12)
+    # an unperturbed stored series has the same hashes in every table: it is its own top-1
+    for s in [0, 17, 299]:
+        ids, d = idx.query(db[s], 3)
+        assert ids[0] == s and d[0] == 0.0
+
+
+def test_index_rejects_short_series():
+    idx = oracle.OracleIndex(32, 3, 8, 4, 16, 0.05, 0)
+    assert idx.min_length() == 32 + 7 * 3
+    with pytest.raises(ValueError):
+        idx.add([np.zeros(52, np.float32)])
+    idx.add([np.zeros(53, np.float32)])
