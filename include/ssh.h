@@ -1,0 +1,180 @@
+/*
+ * ssh.h -- C ABI of the GB300 (sm_103a) SSH library.
+ *
+ * SSH (Sketch, Shingle & Hash; Luo & Shrivastava, arXiv:1610.07328) indexes
+ * time series for similarity search under dynamic time warping (DTW):
+ *   Sec. 4.1  a random Gaussian filter r of length W slides over a series with
+ *             step delta and each window gives one sign bit;
+ *   Sec. 4.2  the bit string is cut into all overlapping n-bit shingles, which
+ *             form a weighted set (shingle id -> count);
+ *   Sec. 4.3  weighted minhashes of that set (consistent weighted sampling)
+ *             give K*L hash values, K per table, L tables;
+ *   Alg. 1    every stored series goes into the L tables;
+ *   Alg. 2    a query probes its bucket in each table, the union of the buckets
+ *             is its candidate set, and the candidates are ranked by DTW
+ *             (Sec. 2.1) after LB_Keogh pruning (Sec. 3) to give the top k.
+ *
+ * Conventions shared by every entry point:
+ *  - Every function returns an ssh_status. SSH_OK is 0. No function aborts the
+ *    process; ssh_last_error() gives a one-line reason for the last failure on
+ *    the calling thread.
+ *  - Pointers named d_* are device pointers on the index's device; all others
+ *    are host pointers. `stream` is a cudaStream_t passed as void* (NULL is the
+ *    legacy default stream). The caller owns every buffer passed in; the
+ *    library never frees or keeps them unless a flag below says so.
+ *  - Series are FP32, stored back to back: series i occupies lengths[i]
+ *    consecutive floats right after series i-1. Values must be finite and
+ *    smaller than 1e15 in magnitude.
+ *  - Ids are assigned from 0 in insertion order across all lengths. Series of
+ *    one length form one sub-index; a query is answered from the sub-index of
+ *    its own length.
+ *  - Calls on one index are not thread-safe; use one index per host thread or
+ *    serialise the calls.
+ */
+#ifndef SSH_H
+#define SSH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ssh_index ssh_index; /* opaque; created by ssh_create, owned by the library */
+
+typedef enum ssh_status {
+    SSH_OK = 0,
+    SSH_EINVAL = 1,   /* a parameter is out of range or a pointer is NULL */
+    SSH_ENOMEM = 2,   /* a device or host allocation failed */
+    SSH_ECUDA = 3,    /* a CUDA call failed; ssh_last_error() has the CUDA message */
+    SSH_ELENGTH = 4,  /* a series is too short, too long, or a query length has no sub-index */
+    SSH_EBUSY = 5,    /* admission refused: not enough free device memory */
+    SSH_ETIMEOUT = 6, /* a bounded device wait gave up */
+    SSH_ENOTSUP = 7   /* a parameter combination this build does not implement */
+} ssh_status;
+
+/* Name of a status code ("SSH_OK", ...). Never NULL. */
+const char* ssh_status_str(ssh_status s);
+
+/* One-line description of the last failing call on this thread ("" if none). */
+const char* ssh_last_error(void);
+
+/*
+ * Create an index (Alg. 1 input: W, delta, n and the number of tables; Sec. 5.1
+ * uses 20 tables of one hash each, here there are L tables keyed by K hashes each).
+ *   W      filter length, 1 <= W <= 8192 (Sec. 4.1)
+ *   delta  filter step, >= 1 (Sec. 4.1)
+ *   n      shingle length in bits, 1 <= n <= 16 in this build (Sec. 4.2);
+ *          17..32 return SSH_ENOTSUP, anything else SSH_EINVAL
+ *   K, L   hashes per table and number of tables, K*L <= 4096
+ *   band   Sakoe-Chiba band as a fraction of the series length: the DTW radius
+ *          is floor(band * m) (clamped to m-1); band >= 0
+ *   seed   seeds the filter r and every minhash draw (Philox4x32-10)
+ * The filter and the minhash draw tables are generated on the host and copied
+ * to the current CUDA device, which becomes the index's device.
+ * On success *out owns about K*L*2^n*40 bytes of device memory.
+ */
+ssh_status ssh_create(int W, int delta, int n, int K, int L, float band, uint64_t seed, ssh_index** out);
+
+/* Release the index and all its device memory. NULL is a no-op. */
+void ssh_destroy(ssh_index* idx);
+
+/* Copy of the FP32 filter r (W floats) into r_out (host). */
+ssh_status ssh_get_filter(const ssh_index* idx, float* r_out);
+
+/* Alg. 1 on host series: copies `count` series (back to back, lengths[i] each)
+ * to the device, hashes them and rebuilds the tables of the affected
+ * sub-indexes. Every length must be at least W + (n-1)*delta (one shingle) and
+ * give at most 65535 shingles, else SSH_ELENGTH and nothing is added.
+ * *first_id (may be NULL) receives the id of the first added series. Synchronous. */
+ssh_status ssh_index_add(ssh_index* idx, const float* series, const int32_t* lengths, int64_t count,
+                         int64_t* first_id);
+
+#define SSH_ADD_BORROW 1u /* keep d_series instead of copying it (see ssh_index_add_device) */
+
+/* Alg. 1 on device series (d_series on the index's device, lengths on the host).
+ * Without SSH_ADD_BORROW the series are copied into index-owned device memory.
+ * With SSH_ADD_BORROW the index keeps d_series itself: the caller must keep that
+ * buffer allocated and unchanged until ssh_index_clear or ssh_destroy.
+ * Work is ordered on `stream`; the call returns after the tables are rebuilt. */
+ssh_status ssh_index_add_device(ssh_index* idx, const float* d_series, const int32_t* lengths, int64_t count,
+                                uint32_t flags, void* stream, int64_t* first_id);
+
+/* Drop every stored series and table; parameters, filter and draw tables stay.
+ * Ids restart at 0. */
+ssh_status ssh_index_clear(ssh_index* idx);
+
+/* Number of stored series. */
+ssh_status ssh_index_size(const ssh_index* idx, int64_t* count);
+
+/* Alg. 2 on host queries: for query i (lengths[i] floats) write its k nearest
+ * stored series of the same length by banded DTW into ids[i*k .. i*k+k-1] and
+ * dists[i*k ..] in ascending (distance, id) order. Distances are sums of squared
+ * differences along the best warping path (the square root of Sec. 2.1 is not
+ * taken; it does not change the order). A query with fewer than k candidates
+ * fills the remaining slots with id -1 and distance +inf. 1 <= k <= 1024.
+ * SSH_ELENGTH if a query length has no sub-index. Synchronous. */
+ssh_status ssh_query(ssh_index* idx, const float* queries, const int32_t* lengths, int64_t nq, int k,
+                     int64_t* ids, float* dists);
+
+/* Alg. 2 on device queries; d_ids / d_dists are device arrays of nq*k entries.
+ * Work is ordered on `stream`; the call returns when the results are written. */
+ssh_status ssh_query_device(ssh_index* idx, const float* d_queries, const int32_t* lengths, int64_t nq, int k,
+                            int64_t* d_ids, float* d_dists, void* stream);
+
+/* Options. SSH_OPT_LB_PRUNE (default 1): LB_Keogh pruning before DTW in the
+ * rerank; 0 computes DTW for every candidate (same results, more work). */
+typedef enum ssh_option { SSH_OPT_LB_PRUNE = 1 } ssh_option;
+ssh_status ssh_set_option(ssh_index* idx, ssh_option opt, int64_t value);
+
+/* Counters since the last ssh_reset_stats (all cumulative). */
+typedef struct ssh_stats {
+    int64_t series_hashed;     /* series and queries hashed (Sec. 4.1-4.3) */
+    int64_t sketch_fp64;       /* sketch windows recomputed in FP64 (|r.x| near 0) */
+    int64_t cws_fp64;          /* minhashes recomputed in FP64 (near ties / floor steps) */
+    int64_t queries;           /* queries answered */
+    int64_t candidates;        /* sum over queries of |R| (Alg. 2 union) */
+    int64_t dtw_computed;      /* candidates whose DTW was computed */
+    int64_t lb_pruned;         /* candidates pruned by LB_Keogh */
+} ssh_stats;
+ssh_status ssh_get_stats(const ssh_index* idx, ssh_stats* out);
+ssh_status ssh_reset_stats(ssh_index* idx);
+
+/* ---------------------------------------------------------------------------
+ * Stage entry points. They run one step of the path on device buffers so that
+ * each step can be checked and timed on its own; the index calls the same
+ * kernels internally.
+ * ------------------------------------------------------------------------- */
+
+/* Sec. 4.1-4.3 plus the bucket keys of Alg. 1 for `count` series of length m
+ * stored row-major at d_series (row stride m floats). Outputs (each may be NULL):
+ *   d_bits    [count][ceil(N_B/32)] uint32, window i of a series is bit
+ *             (31 - i%32) of word i/32, 1 for r.x >= 0; N_B = floor((m-W)/delta)+1
+ *   d_sh_ids, d_sh_counts  [count][S] uint32, the distinct shingle ids of a
+ *             series in ascending order and their counts, S = N_B - n + 1 slots
+ *             per series, the first d_nnz[i] used
+ *   d_nnz     [count] int32
+ *   d_kstar, d_tstar  [count][K*L] uint32, the minhash (k*, t*) of each hash
+ *   d_keys    [L][count] uint64, the bucket key of each table
+ * SSH_ELENGTH if m gives no shingle or more than 65535. */
+ssh_status ssh_hash_device(const ssh_index* idx, const float* d_series, int32_t m, int64_t count, void* stream,
+                           uint32_t* d_bits, uint32_t* d_sh_ids, uint32_t* d_sh_counts, int32_t* d_nnz,
+                           uint32_t* d_kstar, uint32_t* d_tstar, uint64_t* d_keys);
+
+/* Sec. 2.1 banded DTW for `npairs` pairs: d_out[p] = DTW(d_a + a_idx[p]*m, d_b + b_idx[p]*m)
+ * with radius rb (0 <= rb < m), sum of squared costs. d_a_idx / d_b_idx are
+ * int64 device arrays of row indexes into the row-major [*, m] arrays d_a, d_b.
+ * Rows that share an a-row are best given consecutively. */
+ssh_status ssh_dtw_device(const float* d_a, const int64_t* d_a_idx, const float* d_b, const int64_t* d_b_idx,
+                          int64_t npairs, int32_t m, int32_t rb, float* d_out, void* stream);
+
+/* Sec. 3 LB_Keogh for `npairs` pairs: d_out[p] = LB_Keogh of row d_b_idx[p] of d_b
+ * against the envelope (radius rb) of row d_a_idx[p] of d_a. */
+ssh_status ssh_lb_keogh_device(const float* d_a, const int64_t* d_a_idx, const float* d_b, const int64_t* d_b_idx,
+                               int64_t npairs, int32_t m, int32_t rb, float* d_out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SSH_H */

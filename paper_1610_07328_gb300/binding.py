@@ -1,0 +1,273 @@
+"""Thin ctypes binding of include/ssh.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls. Host arrays are
+numpy arrays; device arrays are CUDA torch tensors (torch supplies device
+memory and the current stream, nothing else). Errors raise SSHError with the
+status name and the library's one-line reason. There is no fallback: if the
+CUDA library cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+
+import numpy as np
+
+from . import build_ext
+
+SSH_OK, SSH_EINVAL, SSH_ENOMEM, SSH_ECUDA, SSH_ELENGTH, SSH_EBUSY, SSH_ETIMEOUT, SSH_ENOTSUP = range(8)
+SSH_ADD_BORROW = 1
+SSH_OPT_LB_PRUNE = 1
+
+_lib = None
+_lock = threading.Lock()
+
+
+class SSHError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{status_name(status)}: {msg}")
+        self.status = status
+
+
+class ssh_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in (
+        "series_hashed", "sketch_fp64", "cws_fp64", "queries", "candidates", "dtw_computed", "lb_pruned")]
+
+    def as_dict(self):
+        return {n: int(getattr(self, n)) for n, _ in self._fields_}
+
+
+_P = ctypes.c_void_p
+_I64P = ctypes.POINTER(ctypes.c_int64)
+
+_SIGS = {
+    "ssh_status_str": (ctypes.c_char_p, [ctypes.c_int]),
+    "ssh_last_error": (ctypes.c_char_p, []),
+    "ssh_create": (ctypes.c_int, [ctypes.c_int] * 5 + [ctypes.c_float, ctypes.c_uint64, ctypes.POINTER(_P)]),
+    "ssh_destroy": (None, [_P]),
+    "ssh_get_filter": (ctypes.c_int, [_P, _P]),
+    "ssh_index_add": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, _I64P]),
+    "ssh_index_add_device": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, ctypes.c_uint32, _P, _I64P]),
+    "ssh_index_clear": (ctypes.c_int, [_P]),
+    "ssh_index_size": (ctypes.c_int, [_P, _I64P]),
+    "ssh_query": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, ctypes.c_int, _P, _P]),
+    "ssh_query_device": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, ctypes.c_int, _P, _P, _P]),
+    "ssh_set_option": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int64]),
+    "ssh_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(ssh_stats)]),
+    "ssh_reset_stats": (ctypes.c_int, [_P]),
+    "ssh_hash_device": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int64, _P] + [_P] * 7),
+    "ssh_dtw_device": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _P, _P]),
+    "ssh_lb_keogh_device": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _P, _P]),
+}
+EXPORTED = tuple(_SIGS)
+
+
+def lib_path() -> str:
+    return build_ext.LIB
+
+
+def load(build: bool = True):
+    """Load libssh_gb300.so (building it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = build_ext.build() if build else build_ext.LIB
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def status_name(s: int) -> str:
+    names = ["SSH_OK", "SSH_EINVAL", "SSH_ENOMEM", "SSH_ECUDA", "SSH_ELENGTH", "SSH_EBUSY", "SSH_ETIMEOUT",
+             "SSH_ENOTSUP"]
+    return names[s] if 0 <= s < len(names) else f"SSH_STATUS_{s}"
+
+
+def _check(status: int):
+    if status != SSH_OK:
+        raise SSHError(status, load().ssh_last_error().decode())
+
+
+def _host_ptr(a: np.ndarray):
+    return ctypes.c_void_p(a.ctypes.data) if a.size else None
+
+
+def _dev_ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+
+
+# ------------------------------------------------------------ entry points
+
+def ssh_create(W: int, delta: int, n: int, K: int, L: int, band: float, seed: int) -> ctypes.c_void_p:
+    h = _P()
+    _check(load().ssh_create(W, delta, n, K, L, float(band), int(seed) & (2 ** 64 - 1), ctypes.byref(h)))
+    return h
+
+
+def ssh_destroy(h) -> None:
+    if h:
+        load().ssh_destroy(h)
+
+
+def ssh_get_filter(h, W: int) -> np.ndarray:
+    out = np.zeros(W, np.float32)
+    _check(load().ssh_get_filter(h, _host_ptr(out)))
+    return out
+
+
+def ssh_index_add(h, series: np.ndarray, lengths: np.ndarray) -> int:
+    s = np.ascontiguousarray(series, dtype=np.float32).reshape(-1)
+    ln = np.ascontiguousarray(lengths, dtype=np.int32)
+    first = ctypes.c_int64()
+    _check(load().ssh_index_add(h, _host_ptr(s), _host_ptr(ln), len(ln), ctypes.byref(first)))
+    return first.value
+
+
+def ssh_index_add_device(h, d_series, lengths: np.ndarray, flags: int = 0, stream=None) -> int:
+    ln = np.ascontiguousarray(lengths, dtype=np.int32)
+    first = ctypes.c_int64()
+    _check(load().ssh_index_add_device(h, _dev_ptr(d_series), _host_ptr(ln), len(ln), flags, _stream(stream),
+                                       ctypes.byref(first)))
+    return first.value
+
+
+def ssh_index_clear(h) -> None:
+    _check(load().ssh_index_clear(h))
+
+
+def ssh_index_size(h) -> int:
+    c = ctypes.c_int64()
+    _check(load().ssh_index_size(h, ctypes.byref(c)))
+    return c.value
+
+
+def ssh_query(h, queries: np.ndarray, lengths: np.ndarray, k: int):
+    q = np.ascontiguousarray(queries, dtype=np.float32).reshape(-1)
+    ln = np.ascontiguousarray(lengths, dtype=np.int32)
+    nq = len(ln)
+    ids = np.zeros((nq, k), np.int64)
+    dists = np.zeros((nq, k), np.float32)
+    _check(load().ssh_query(h, _host_ptr(q), _host_ptr(ln), nq, k, _host_ptr(ids), _host_ptr(dists)))
+    return ids, dists
+
+
+def ssh_query_device(h, d_queries, lengths: np.ndarray, k: int, d_ids, d_dists, stream=None) -> None:
+    ln = np.ascontiguousarray(lengths, dtype=np.int32)
+    _check(load().ssh_query_device(h, _dev_ptr(d_queries), _host_ptr(ln), len(ln), k, _dev_ptr(d_ids),
+                                   _dev_ptr(d_dists), _stream(stream)))
+
+
+def ssh_set_option(h, opt: int, value: int) -> None:
+    _check(load().ssh_set_option(h, opt, int(value)))
+
+
+def ssh_get_stats(h) -> dict:
+    st = ssh_stats()
+    _check(load().ssh_get_stats(h, ctypes.byref(st)))
+    return st.as_dict()
+
+
+def ssh_reset_stats(h) -> None:
+    _check(load().ssh_reset_stats(h))
+
+
+def ssh_hash_device(h, d_series, m: int, count: int, d_bits=None, d_sh_ids=None, d_sh_counts=None, d_nnz=None,
+                    d_kstar=None, d_tstar=None, d_keys=None, stream=None) -> None:
+    _check(load().ssh_hash_device(h, _dev_ptr(d_series), m, count, _stream(stream), _dev_ptr(d_bits),
+                                  _dev_ptr(d_sh_ids), _dev_ptr(d_sh_counts), _dev_ptr(d_nnz), _dev_ptr(d_kstar),
+                                  _dev_ptr(d_tstar), _dev_ptr(d_keys)))
+
+
+def ssh_dtw_device(d_a, d_a_idx, d_b, d_b_idx, m: int, rb: int, d_out, stream=None) -> None:
+    _check(load().ssh_dtw_device(_dev_ptr(d_a), _dev_ptr(d_a_idx), _dev_ptr(d_b), _dev_ptr(d_b_idx),
+                                 d_a_idx.numel(), m, rb, _dev_ptr(d_out), _stream(stream)))
+
+
+def ssh_lb_keogh_device(d_a, d_a_idx, d_b, d_b_idx, m: int, rb: int, d_out, stream=None) -> None:
+    _check(load().ssh_lb_keogh_device(_dev_ptr(d_a), _dev_ptr(d_a_idx), _dev_ptr(d_b), _dev_ptr(d_b_idx),
+                                      d_a_idx.numel(), m, rb, _dev_ptr(d_out), _stream(stream)))
+
+
+# ------------------------------------------------------------ convenience
+
+class SSHIndex:
+    """Owning wrapper around an ssh_index handle."""
+
+    def __init__(self, W: int, delta: int, n: int, K: int, L: int, band: float, seed: int = 0):
+        self.W, self.delta, self.n, self.K, self.L = W, delta, n, K, L
+        self.band, self.seed = band, seed
+        self.handle = ssh_create(W, delta, n, K, L, band, seed)
+
+    def close(self):
+        if self.handle:
+            ssh_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def filter(self) -> np.ndarray:
+        return ssh_get_filter(self.handle, self.W)
+
+    def add(self, series: np.ndarray, lengths=None) -> int:
+        series = np.asarray(series, np.float32)
+        if lengths is None:
+            lengths = np.full(series.shape[0], series.shape[1], np.int32)
+        return ssh_index_add(self.handle, series, lengths)
+
+    def add_device(self, d_series, lengths=None, borrow: bool = False, stream=None) -> int:
+        if lengths is None:
+            lengths = np.full(d_series.shape[0], d_series.shape[1], np.int32)
+        return ssh_index_add_device(self.handle, d_series, lengths, SSH_ADD_BORROW if borrow else 0, stream)
+
+    def clear(self):
+        ssh_index_clear(self.handle)
+
+    def __len__(self):
+        return ssh_index_size(self.handle)
+
+    def query(self, queries: np.ndarray, k: int, lengths=None):
+        queries = np.asarray(queries, np.float32)
+        if lengths is None:
+            lengths = np.full(queries.shape[0], queries.shape[1], np.int32)
+        return ssh_query(self.handle, queries, lengths, k)
+
+    def query_device(self, d_queries, k: int, d_ids, d_dists, lengths=None, stream=None):
+        if lengths is None:
+            lengths = np.full(d_queries.shape[0], d_queries.shape[1], np.int32)
+        ssh_query_device(self.handle, d_queries, lengths, k, d_ids, d_dists, stream)
+
+    def set_lb_prune(self, on: bool):
+        ssh_set_option(self.handle, SSH_OPT_LB_PRUNE, 1 if on else 0)
+
+    def stats(self) -> dict:
+        return ssh_get_stats(self.handle)
+
+    def reset_stats(self):
+        ssh_reset_stats(self.handle)

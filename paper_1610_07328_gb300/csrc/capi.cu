@@ -1,0 +1,1026 @@
+// capi.cu -- the C ABI of include/ssh.h: index lifetime, the host-side draw
+// tables, and the device orchestration of Algorithm 1 (add) and Algorithm 2
+// (query). All per-series and per-candidate work runs in the kernels of
+// hash_kernels.cu, sort_kernels.cu and query_kernels.cu.
+//
+// This translation unit is compiled with -ffp-contract=off for the host: the
+// FP64 draw tables must be rounded operation by operation, exactly as the
+// definitions are written (Sec. 4.1 filter, Sec. 4.3 draws).
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+#include <thread>
+#include <vector>
+
+#include "ssh_internal.cuh"
+
+// =================================================================== errors
+
+namespace ssh {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+ssh_status cuda_status(cudaError_t e, const char* what) {
+    set_error("%s: %s", what, cudaGetErrorString(e));
+    return (e == cudaErrorMemoryAllocation) ? SSH_ENOMEM : SSH_ECUDA;
+}
+
+static ssh_status fail(ssh_status s, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+// ============================================================ random draws
+//
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11) keyed by the seed, with
+// the counter naming what is drawn. Uniforms take the top 23 bits plus one
+// half: ((x >> 9) + 0.5) * 2^-23, an odd multiple of 2^-24 in (0, 1), exact in
+// FP32 and FP64.
+
+namespace {
+
+constexpr uint32_t kTagFilter = 0x46494C54u;  // "FILT"
+constexpr uint32_t kTagCws = 0x43575331u;     // "CWS1"
+
+void philox10(const uint32_t in[4], uint32_t k0, uint32_t k1, uint32_t out[4]) {
+    uint32_t c0 = in[0], c1 = in[1], c2 = in[2], c3 = in[3];
+    for (int round = 0; round < 10; ++round) {
+        if (round) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint64_t m0 = (uint64_t)0xD2511F53u * c0;
+        const uint64_t m1 = (uint64_t)0xCD9E8D57u * c2;
+        const uint32_t n0 = (uint32_t)(m1 >> 32) ^ c1 ^ k0;
+        const uint32_t n2 = (uint32_t)(m0 >> 32) ^ c3 ^ k1;
+        c1 = (uint32_t)m1;
+        c3 = (uint32_t)m0;
+        c0 = n0;
+        c2 = n2;
+    }
+    out[0] = c0;
+    out[1] = c1;
+    out[2] = c2;
+    out[3] = c3;
+}
+
+inline double unit(uint32_t x) { return ((double)(x >> 9) + 0.5) * (1.0 / 8388608.0); }
+
+// Sec. 4.1: r_j ~ N(0,1) by Box-Muller, cosine branch for even j, sine for odd j.
+void make_filter(uint64_t seed, int W, std::vector<float>& r) {
+    r.resize(W);
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    const double two_pi = 6.283185307179586476925286766559;
+    for (int j = 0; j < W; ++j) {
+        const uint32_t ctr[4] = {(uint32_t)(j / 2), 0u, kTagFilter, 0u};
+        uint32_t b[4];
+        philox10(ctr, k0, k1, b);
+        const double u1 = unit(b[0]), u2 = unit(b[1]);
+        const double radius = std::sqrt(-2.0 * std::log(u1));
+        const double angle = two_pi * u2;
+        const double z = (j % 2 == 0) ? radius * std::cos(angle) : radius * std::sin(angle);
+        r[j] = (float)z;
+    }
+}
+
+struct Draw {
+    double r, beta, lnc;
+};
+
+// Sec. 4.3 (Ioffe's ICWS): r ~ Gamma(2,1), c ~ Gamma(2,1), beta ~ U(0,1) for hash j, shingle k.
+inline Draw cws_draw(uint64_t seed, uint32_t j, uint32_t k) {
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    const uint32_t c0[4] = {k, j, kTagCws, 0u};
+    const uint32_t c1[4] = {k, j, kTagCws, 1u};
+    uint32_t a[4], b[4];
+    philox10(c0, k0, k1, a);
+    philox10(c1, k0, k1, b);
+    const double u1 = unit(a[0]), u2 = unit(a[1]), u3 = unit(a[2]), u4 = unit(a[3]), u5 = unit(b[0]);
+    Draw d;
+    d.r = -std::log(u1 * u2);
+    const double c = -std::log(u3 * u4);
+    d.beta = u5;
+    d.lnc = std::log(c);
+    return d;
+}
+
+// ln a of a shingle seen s times: t = floor(ln s / r + beta), ln a = ln c - r ((t - beta) + 1).
+inline double log_a(const Draw& d, double lns) {
+    const double t = std::floor(lns / d.r + d.beta);
+    return d.lnc - d.r * ((t - d.beta) + 1.0);
+}
+
+template <typename F>
+void parallel_for(int64_t n, F f) {
+    int nt = (int)std::thread::hardware_concurrency();
+    if (nt < 1) nt = 1;
+    if (nt > 64) nt = 64;
+    if (n < 4096) nt = 1;
+    std::vector<std::thread> th;
+    const int64_t chunk = (n + nt - 1) / nt;
+    for (int t = 0; t < nt; ++t) {
+        const int64_t b = t * chunk, e = std::min<int64_t>(n, b + chunk);
+        if (b >= e) break;
+        th.emplace_back([=]() {
+            for (int64_t i = b; i < e; ++i) f(i);
+        });
+    }
+    for (auto& x : th) x.join();
+}
+
+// ----------------------------------------------------------- device memory
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count, cudaStream_t st) {
+    return cudaMallocAsync(reinterpret_cast<void**>(p), std::max<size_t>(count, 1) * sizeof(T), st);
+}
+
+struct ScratchList {
+    std::vector<void*> ptrs;
+    cudaStream_t st;
+    explicit ScratchList(cudaStream_t s) : st(s) {}
+    template <typename T>
+    ssh_status get(T** p, size_t count) {
+        cudaError_t e = dalloc(p, count, st);
+        if (e != cudaSuccess) return cuda_status(e, "cudaMallocAsync (scratch)");
+        ptrs.push_back(*p);
+        return SSH_OK;
+    }
+    ~ScratchList() {
+        for (void* p : ptrs) cudaFreeAsync(p, st);
+    }
+};
+
+// ------------------------------------------------------------ small kernels
+
+__global__ void fill_rows_kernel(const float** row_ptr, int64_t* gid, int64_t n, const float* base, int64_t stride,
+                                 int64_t first_gid) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        row_ptr[i] = base + i * stride;
+        gid[i] = first_gid + i;
+    }
+}
+
+__global__ void copy_keys_kernel(const uint64_t* keys, uint64_t* skeys, uint32_t* srows, int64_t n, int64_t cap,
+                                 int L) {
+    const int l = blockIdx.y;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        skeys[(int64_t)l * cap + i] = keys[(int64_t)l * cap + i];
+        srows[(int64_t)l * cap + i] = (uint32_t)i;
+    }
+}
+
+__global__ void gather_ptrs_kernel(const uint32_t* rows, int64_t n, const float* const* row_ptr, const float** out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = row_ptr[rows[i]];
+}
+
+__global__ void fill_f32_kernel(float* p, int64_t n, float v) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+
+// mode 0: seeds, keep lb <= T[s].  mode 1: survivors, keep lb > T[s] and lb * shrink <= U[s].
+__global__ void filter_count_kernel(const int64_t* seg_begin, int64_t nseg, const float* lb, const uint32_t* T,
+                                    const uint32_t* U, float shrink, int mode, int64_t* counts) {
+    const int64_t s = blockIdx.y;
+    const int64_t b = seg_begin[s], e = seg_begin[s + 1];
+    const float t = (T[s] == 0xFFFFFFFFu) ? __int_as_float(0x7F800000) : __uint_as_float(T[s]);
+    const float u = mode ? __uint_as_float(U[s]) : 0.f;
+    int64_t c = 0;
+    for (int64_t p = b + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < e; p += (int64_t)gridDim.x * blockDim.x) {
+        const float v = lb[p];
+        const bool keep = mode == 0 ? (v <= t) : (v > t && v * shrink <= u);
+        c += keep;
+    }
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(reinterpret_cast<unsigned long long*>(&counts[s]), (unsigned long long)c);
+}
+
+__global__ void filter_scatter_kernel(const int64_t* seg_begin, int64_t nseg, const float* lb, const uint32_t* T,
+                                      const uint32_t* U, float shrink, int mode, const int64_t* out_begin,
+                                      unsigned long long* cursor, const float* const* pair_b_in,
+                                      const float** pair_b_out, int64_t* slot_out) {
+    const int64_t s = blockIdx.y;
+    const int64_t b = seg_begin[s], e = seg_begin[s + 1];
+    const float t = (T[s] == 0xFFFFFFFFu) ? __int_as_float(0x7F800000) : __uint_as_float(T[s]);
+    const float u = mode ? __uint_as_float(U[s]) : 0.f;
+    for (int64_t p = b + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < e; p += (int64_t)gridDim.x * blockDim.x) {
+        const float v = lb[p];
+        const bool keep = mode == 0 ? (v <= t) : (v > t && v * shrink <= u);
+        if (keep) {
+            const int64_t pos = out_begin[s] + (int64_t)atomicAdd(&cursor[s], 1ull);
+            pair_b_out[pos] = pair_b_in[p];
+            slot_out[pos] = p;
+        }
+    }
+}
+
+__global__ void exclusive_scan_small_kernel(const int64_t* counts, int64_t n, int64_t* out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        int64_t run = 0;
+        for (int64_t i = 0; i < n; ++i) {
+            out[i] = run;
+            run += counts[i];
+        }
+        out[n] = run;
+    }
+}
+
+__global__ void topk_keys_kernel(const float* dist, const uint32_t* rows, int64_t n, uint64_t* keys) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        keys[i] = ((uint64_t)__float_as_uint(dist[i]) << 32) | rows[i];
+}
+
+// Final top-k of one query: the keys <= the k-th smallest, sorted, as (id, dist).
+__global__ void __launch_bounds__(1024) topk_output_kernel(const uint64_t* keys, const int64_t* seg_begin,
+                                                           const uint64_t* kth, const int64_t* gid, int k,
+                                                           const int64_t* qpos, int64_t* ids_out,
+                                                           float* dists_out) {
+    __shared__ uint64_t buf[kMaxTopK];
+    __shared__ int cnt;
+    const int64_t s = blockIdx.x;
+    const int64_t b = seg_begin[s], e = seg_begin[s + 1];
+    const uint64_t lim = kth[s];
+    if (threadIdx.x == 0) cnt = 0;
+    for (int i = threadIdx.x; i < kMaxTopK; i += blockDim.x) buf[i] = ~0ull;
+    __syncthreads();
+    for (int64_t p = b + threadIdx.x; p < e; p += blockDim.x) {
+        const uint64_t v = keys[p];
+        if (v <= lim) {
+            const int at = atomicAdd(&cnt, 1);
+            if (at < kMaxTopK) buf[at] = v;
+        }
+    }
+    __syncthreads();
+    int n2 = 1;
+    while (n2 < k) n2 <<= 1;
+    for (int kk = 2; kk <= n2; kk <<= 1) {
+        for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+            for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+                const int l = i ^ jj;
+                if (l > i) {
+                    const uint64_t u = buf[i], v = buf[l];
+                    const bool up = (i & kk) == 0;
+                    if ((u > v) == up) {
+                        buf[i] = v;
+                        buf[l] = u;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    const int64_t out0 = qpos[s] * (int64_t)k;
+    for (int t = threadIdx.x; t < k; t += blockDim.x) {
+        const uint64_t v = buf[t];
+        const uint32_t dbits = (uint32_t)(v >> 32);
+        const bool real = (v != ~0ull) && dbits < 0x7F800000u;
+        ids_out[out0 + t] = real ? gid[(uint32_t)v] : -1;
+        dists_out[out0 + t] = real ? __uint_as_float(dbits) : __uint_as_float(0x7F800000u);
+    }
+}
+
+unsigned grid_for(int64_t n, int threads, int64_t cap = 65535) {
+    int64_t g = (n + threads - 1) / threads;
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return (unsigned)g;
+}
+
+int min_length(const ssh_index* idx) { return idx->W + (idx->n - 1) * idx->delta; }
+
+struct Geometry {
+    int nb, nwords, S;
+};
+
+ssh_status geometry(const ssh_index* idx, int m, Geometry* g) {
+    if (m < min_length(idx))
+        return fail(SSH_ELENGTH, "series length %d is shorter than W + (n-1)*delta = %d", m, min_length(idx));
+    const int64_t nb = (int64_t)(m - idx->W) / idx->delta + 1;
+    const int64_t S = nb - idx->n + 1;
+    if (S > kMaxCount) return fail(SSH_ELENGTH, "series length %d gives %lld shingles (max %d)", m, (long long)S, kMaxCount);
+    g->nb = (int)nb;
+    g->nwords = (int)((nb + 31) / 32);
+    g->S = (int)S;
+    return SSH_OK;
+}
+
+int band_radius(float band, int m) {
+    if (!(band > 0.0f)) return 0;
+    double rb = std::floor((double)band * (double)m);
+    if (rb > (double)(m - 1)) rb = (double)(m - 1);
+    return (int)rb;
+}
+
+HashArgs base_hash_args(const ssh_index* idx, int m, const Geometry& g) {
+    HashArgs a;
+    memset(&a, 0, sizeof(a));
+    a.m = m;
+    a.W = idx->W;
+    a.delta = idx->delta;
+    a.n = idx->n;
+    a.nb = g.nb;
+    a.nwords = g.nwords;
+    a.S = g.S;
+    a.K = idx->K;
+    a.L = idx->L;
+    a.KL = idx->KL;
+    a.r = idx->d_r;
+    a.tau_norm = idx->tau_norm;
+    const double gw = idx->W * std::ldexp(1.0, -24) / (1.0 - idx->W * std::ldexp(1.0, -24));
+    a.gamma_ss = (float)(2.0 * gw);
+    a.rank = idx->d_rank;
+    a.kinv = idx->d_kinv;
+    a.p32 = idx->d_p32;
+    a.p64 = idx->d_p64;
+    a.lns32 = idx->d_lns32;
+    a.lns64 = idx->d_lns64;
+    a.seed = idx->seed;
+    a.stats = idx->d_stats;
+    return a;
+}
+
+void free_sub(SubIndex& s) {
+    cudaFree(s.row_ptr);
+    cudaFree(s.gid);
+    cudaFree(s.keys);
+    cudaFree(s.skeys);
+    cudaFree(s.srows);
+    for (void* p : s.owned) cudaFree(p);
+    s = SubIndex();
+}
+
+// Grow a sub-index to hold `need` rows, keeping the first `count` rows.
+ssh_status reserve(ssh_index* idx, SubIndex& s, int64_t need, cudaStream_t st) {
+    if (need <= s.cap) return SSH_OK;
+    int64_t cap = std::max<int64_t>(need, s.cap + s.cap / 2);
+    cap = std::max<int64_t>(cap, 1024);
+    const int L = idx->L;
+    const float** rp = nullptr;
+    int64_t* gid = nullptr;
+    uint64_t *keys = nullptr, *skeys = nullptr;
+    uint32_t* srows = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaMalloc(&rp, cap * sizeof(*rp));
+    if (e == cudaSuccess) e = cudaMalloc(&gid, cap * sizeof(*gid));
+    if (e == cudaSuccess) e = cudaMalloc(&keys, (size_t)L * cap * sizeof(*keys));
+    if (e == cudaSuccess) e = cudaMalloc(&skeys, (size_t)L * cap * sizeof(*skeys));
+    if (e == cudaSuccess) e = cudaMalloc(&srows, (size_t)L * cap * sizeof(*srows));
+    if (e != cudaSuccess) {
+        cudaFree(rp);
+        cudaFree(gid);
+        cudaFree(keys);
+        cudaFree(skeys);
+        cudaFree(srows);
+        return cuda_status(e, "cudaMalloc (sub-index)");
+    }
+    if (s.count > 0) {
+        SSH_CUDA(cudaMemcpyAsync(rp, s.row_ptr, s.count * sizeof(*rp), cudaMemcpyDeviceToDevice, st));
+        SSH_CUDA(cudaMemcpyAsync(gid, s.gid, s.count * sizeof(*gid), cudaMemcpyDeviceToDevice, st));
+        for (int l = 0; l < L; ++l)
+            SSH_CUDA(cudaMemcpyAsync(keys + (size_t)l * cap, s.keys + (size_t)l * s.cap, s.count * sizeof(*keys),
+                                     cudaMemcpyDeviceToDevice, st));
+        SSH_CUDA(cudaStreamSynchronize(st));
+    }
+    cudaFree(s.row_ptr);
+    cudaFree(s.gid);
+    cudaFree(s.keys);
+    cudaFree(s.skeys);
+    cudaFree(s.srows);
+    s.row_ptr = rp;
+    s.gid = gid;
+    s.keys = keys;
+    s.skeys = skeys;
+    s.srows = srows;
+    s.cap = cap;
+    return SSH_OK;
+}
+
+// Rebuild the sorted tables of a sub-index from its per-row keys.
+ssh_status rebuild_tables(ssh_index* idx, SubIndex& s, cudaStream_t st) {
+    const int L = idx->L;
+    const int64_t n = s.count;
+    if (n == 0) return SSH_OK;
+    dim3 grid(grid_for(n, 256, 4096), (unsigned)L);
+    copy_keys_kernel<<<grid, 256, 0, st>>>(s.keys, s.skeys, s.srows, n, s.cap, L);
+    SSH_CUDA(cudaGetLastError());
+    if (n < 2) return SSH_OK;
+    ScratchList sc(st);
+    uint64_t* kalt;
+    uint32_t* valt;
+    void* hist;
+    SSH_TRY(sc.get(&kalt, (size_t)L * s.cap));
+    SSH_TRY(sc.get(&valt, (size_t)L * s.cap));
+    const size_t hb = radix_sort_scratch_bytes(n, L);
+    SSH_TRY(sc.get(reinterpret_cast<unsigned char**>(&hist), hb));
+    SSH_CUDA(radix_sort_pairs_u64(s.skeys, s.srows, kalt, valt, n, L, s.cap, hist, hb, st));
+    return SSH_OK;
+}
+
+// Algorithm 1 for the series of one call. `dev` holds all `count` series back
+// to back (device memory that stays valid while the index uses it).
+ssh_status add_series(ssh_index* idx, const float* dev, const int32_t* lengths, int64_t count, cudaStream_t st,
+                      int64_t* first_id) {
+    // all lengths valid first: nothing is added on error
+    std::vector<int64_t> offs(count);
+    int64_t off = 0;
+    for (int64_t i = 0; i < count; ++i) {
+        Geometry g;
+        if (lengths[i] <= 0) return fail(SSH_ELENGTH, "series %lld has length %d", (long long)i, lengths[i]);
+        SSH_TRY(geometry(idx, lengths[i], &g));
+        offs[i] = off;
+        off += lengths[i];
+    }
+    const int64_t id0 = idx->next_id;
+    std::vector<int> touched;
+    // group consecutive runs of equal length
+    int64_t i = 0;
+    while (i < count) {
+        int64_t j = i + 1;
+        while (j < count && lengths[j] == lengths[i]) ++j;
+        const int m = lengths[i];
+        const int64_t nrun = j - i;
+        Geometry g;
+        SSH_TRY(geometry(idx, m, &g));
+        SubIndex& s = idx->subs[m];
+        if (s.m == 0) {
+            s.m = m;
+            s.nb = g.nb;
+            s.nwords = g.nwords;
+            s.S = g.S;
+            s.rb = band_radius(idx->band, m);
+        }
+        if (dtw_plan(m, s.rb).S == 0)
+            return fail(SSH_ENOTSUP, "DTW radius %d (length %d) is wider than this build covers", s.rb, m);
+        if (std::find(touched.begin(), touched.end(), m) == touched.end()) touched.push_back(m);
+        SSH_TRY(reserve(idx, s, s.count + nrun, st));
+        fill_rows_kernel<<<grid_for(nrun, 256, 8192), 256, 0, st>>>(s.row_ptr + s.count, s.gid + s.count, nrun,
+                                                                    dev + offs[i], m, id0 + i);
+        SSH_CUDA(cudaGetLastError());
+        HashArgs a = base_hash_args(idx, m, g);
+        a.rows = s.row_ptr + s.count;
+        a.count = nrun;
+        a.keys = s.keys;
+        a.key_stride = s.cap;
+        a.key_col0 = s.count;
+        SSH_CUDA(launch_hash(a, st));
+        s.count += nrun;
+        idx->host_stats.series_hashed += nrun;
+        i = j;
+    }
+    for (int m : touched) SSH_TRY(rebuild_tables(idx, idx->subs[m], st));
+    SSH_CUDA(cudaStreamSynchronize(st));
+    idx->next_id += count;
+    if (first_id) *first_id = id0;
+    return SSH_OK;
+}
+
+// Algorithm 2 for the `nq` queries of one length m (dev_q[i] = query series,
+// qpos[i] = its position in the caller's output).
+ssh_status query_group(ssh_index* idx, SubIndex& s, const std::vector<const float*>& qptr,
+                       const std::vector<int64_t>& qpos, int k, int64_t* d_ids, float* d_dists, cudaStream_t st) {
+    const int64_t nq = (int64_t)qptr.size();
+    const int m = s.m, L = idx->L;
+    Geometry g{s.nb, s.nwords, s.S};
+    ScratchList sc(st);
+    const float** d_qptr;
+    int64_t* d_qpos;
+    SSH_TRY(sc.get(&d_qptr, nq));
+    SSH_TRY(sc.get(&d_qpos, nq));
+    SSH_CUDA(cudaMemcpyAsync(d_qptr, qptr.data(), nq * sizeof(float*), cudaMemcpyHostToDevice, st));
+    SSH_CUDA(cudaMemcpyAsync(d_qpos, qpos.data(), nq * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+
+    // Algorithm 2 lines 3-5: hash the queries
+    uint64_t* qkeys;
+    SSH_TRY(sc.get(&qkeys, (size_t)L * nq));
+    HashArgs a = base_hash_args(idx, m, g);
+    a.rows = d_qptr;
+    a.count = nq;
+    a.keys = qkeys;
+    a.key_stride = nq;
+    a.key_col0 = 0;
+    SSH_CUDA(launch_hash(a, st));
+    idx->host_stats.series_hashed += nq;
+
+    // lines 6-9: probe every table, union of the buckets
+    const int64_t words = (s.count + 31) / 32;
+    uint32_t* bitmap;
+    int64_t* counts;
+    SSH_TRY(sc.get(&bitmap, (size_t)nq * words));
+    SSH_TRY(sc.get(&counts, nq));
+    SSH_CUDA(cudaMemsetAsync(bitmap, 0, (size_t)nq * words * sizeof(uint32_t), st));
+    ProbeArgs pa{qkeys, nq, L, s.skeys, s.srows, s.cap, s.count, bitmap, words};
+    SSH_CUDA(launch_probe_union(pa, st));
+    SSH_CUDA(launch_bitmap_count(bitmap, nq, words, counts, st));
+    std::vector<int64_t> h_counts(nq), h_begin(nq + 1);
+    SSH_CUDA(cudaMemcpyAsync(h_counts.data(), counts, nq * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    SSH_CUDA(cudaStreamSynchronize(st));
+    h_begin[0] = 0;
+    int64_t max_c = 0;
+    for (int64_t q = 0; q < nq; ++q) {
+        h_begin[q + 1] = h_begin[q] + h_counts[q];
+        max_c = std::max(max_c, h_counts[q]);
+    }
+    const int64_t C = h_begin[nq];
+    idx->host_stats.queries += nq;
+    idx->host_stats.candidates += C;
+
+    int64_t* seg_begin;
+    uint32_t* cand_rows;
+    const float** pair_b;
+    float *lb, *dist;
+    SSH_TRY(sc.get(&seg_begin, nq + 1));
+    SSH_TRY(sc.get(&cand_rows, C));
+    SSH_TRY(sc.get(&pair_b, C));
+    SSH_TRY(sc.get(&lb, C));
+    SSH_TRY(sc.get(&dist, C));
+    SSH_CUDA(cudaMemcpyAsync(seg_begin, h_begin.data(), (nq + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    SSH_CUDA(launch_bitmap_compact(bitmap, nq, words, seg_begin, cand_rows, nullptr, st));
+    if (C > 0) {
+        gather_ptrs_kernel<<<grid_for(C, 256, 8192), 256, 0, st>>>(cand_rows, C, s.row_ptr, pair_b);
+        fill_f32_kernel<<<grid_for(C, 256, 8192), 256, 0, st>>>(dist, C, __builtin_huge_valf());
+        SSH_CUDA(cudaGetLastError());
+    }
+
+    PairSet all{seg_begin, nq, d_qptr, pair_b, nullptr, max_c};
+    const int rb = s.rb;
+    if (C > 0 && !idx->lb_prune) {
+        SSH_CUDA(launch_dtw(all, m, rb, dist, st));
+        idx->host_stats.dtw_computed += C;
+    } else if (C > 0) {
+        // line 10 with UCR-style pruning: LB_Keogh of every candidate; DTW of the k
+        // smallest-LB candidates gives a bound U on the k-th best distance; DTW of
+        // the rest only where LB * (1 - eta) <= U.
+        float *upper, *lower;
+        SSH_TRY(sc.get(&upper, (size_t)nq * m));
+        SSH_TRY(sc.get(&lower, (size_t)nq * m));
+        SSH_CUDA(launch_envelope(d_qptr, nq, m, rb, upper, lower, st));
+        SSH_CUDA(launch_lb_keogh(all, upper, lower, m, lb, st));
+        uint32_t *T, *U;
+        SSH_TRY(sc.get(&T, nq));
+        SSH_TRY(sc.get(&U, nq));
+        SSH_CUDA(launch_select_kth_u32(reinterpret_cast<const uint32_t*>(lb), seg_begin, nq, k, T, st));
+        // eta bounds the FP32 rounding of LB (m + 3 terms) and of DTW (2m terms): 4 (m + 3) 2^-24
+        const float shrink = (float)(1.0 - 4.0 * (m + 3) * std::ldexp(1.0, -24));
+        int64_t *fcount, *fbegin;
+        unsigned long long* cursor;
+        const float** fb;
+        int64_t* fslot;
+        SSH_TRY(sc.get(&fcount, nq));
+        SSH_TRY(sc.get(&fbegin, nq + 1));
+        SSH_TRY(sc.get(&cursor, nq));
+        SSH_TRY(sc.get(&fb, C));
+        SSH_TRY(sc.get(&fslot, C));
+        for (int mode = 0; mode < 2; ++mode) {
+            if (mode == 1)
+                SSH_CUDA(launch_select_kth_u32(reinterpret_cast<const uint32_t*>(dist), seg_begin, nq, k, U, st));
+            SSH_CUDA(cudaMemsetAsync(fcount, 0, nq * sizeof(int64_t), st));
+            SSH_CUDA(cudaMemsetAsync(cursor, 0, nq * sizeof(unsigned long long), st));
+            dim3 fg(grid_for(max_c, 256, 1024), (unsigned)nq);
+            filter_count_kernel<<<fg, 256, 0, st>>>(seg_begin, nq, lb, T, U, shrink, mode, fcount);
+            exclusive_scan_small_kernel<<<1, 32, 0, st>>>(fcount, nq, fbegin);
+            filter_scatter_kernel<<<fg, 256, 0, st>>>(seg_begin, nq, lb, T, U, shrink, mode, fbegin, cursor, pair_b,
+                                                      fb, fslot);
+            SSH_CUDA(cudaGetLastError());
+            std::vector<int64_t> hf(nq);
+            SSH_CUDA(cudaMemcpyAsync(hf.data(), fcount, nq * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+            SSH_CUDA(cudaStreamSynchronize(st));
+            int64_t tot = 0, mx = 0;
+            for (int64_t q = 0; q < nq; ++q) {
+                tot += hf[q];
+                mx = std::max(mx, hf[q]);
+            }
+            PairSet sub{fbegin, nq, d_qptr, fb, fslot, mx};
+            if (tot > 0) SSH_CUDA(launch_dtw(sub, m, rb, dist, st));
+            idx->host_stats.dtw_computed += tot;
+        }
+    }
+    idx->host_stats.lb_pruned = idx->host_stats.candidates - idx->host_stats.dtw_computed;
+
+    // top-k by (distance, id): ids grow with rows inside a sub-index, so the key
+    // (distance bits, row) orders exactly like (distance, id)
+    uint64_t *tkeys, *kth;
+    SSH_TRY(sc.get(&tkeys, C));
+    SSH_TRY(sc.get(&kth, nq));
+    if (C > 0) {
+        topk_keys_kernel<<<grid_for(C, 256, 8192), 256, 0, st>>>(dist, cand_rows, C, tkeys);
+        SSH_CUDA(cudaGetLastError());
+    }
+    SSH_CUDA(launch_select_kth_u64(tkeys, seg_begin, nq, k, kth, st));
+    topk_output_kernel<<<(unsigned)nq, 1024, 0, st>>>(tkeys, seg_begin, kth, s.gid, k, d_qpos, d_ids, d_dists);
+    SSH_CUDA(cudaGetLastError());
+    SSH_CUDA(cudaStreamSynchronize(st));
+    return SSH_OK;
+}
+
+ssh_status run_query(ssh_index* idx, const float* d_queries, const int32_t* lengths, int64_t nq, int k,
+                     int64_t* d_ids, float* d_dists, cudaStream_t st) {
+    if (k < 1 || k > kMaxTopK) return fail(SSH_EINVAL, "k = %d outside [1, %d]", k, kMaxTopK);
+    std::map<int, std::pair<std::vector<const float*>, std::vector<int64_t>>> groups;
+    int64_t off = 0;
+    for (int64_t i = 0; i < nq; ++i) {
+        const int m = lengths[i];
+        auto it = idx->subs.find(m);
+        if (m <= 0 || it == idx->subs.end() || it->second.count == 0)
+            return fail(SSH_ELENGTH, "query %lld has length %d, which has no stored series", (long long)i, m);
+        groups[m].first.push_back(d_queries + off);
+        groups[m].second.push_back(i);
+        off += m;
+    }
+    for (auto& kv : groups)
+        SSH_TRY(query_group(idx, idx->subs[kv.first], kv.second.first, kv.second.second, k, d_ids, d_dists, st));
+    return SSH_OK;
+}
+
+ssh_status check_device(const ssh_index* idx) {
+    int dev = -1;
+    SSH_CUDA(cudaGetDevice(&dev));
+    if (dev != idx->device) SSH_CUDA(cudaSetDevice(idx->device));
+    return SSH_OK;
+}
+
+}  // namespace
+}  // namespace ssh
+
+using namespace ssh;
+
+// ================================================================= C ABI
+
+extern "C" {
+
+const char* ssh_status_str(ssh_status s) {
+    switch (s) {
+        case SSH_OK: return "SSH_OK";
+        case SSH_EINVAL: return "SSH_EINVAL";
+        case SSH_ENOMEM: return "SSH_ENOMEM";
+        case SSH_ECUDA: return "SSH_ECUDA";
+        case SSH_ELENGTH: return "SSH_ELENGTH";
+        case SSH_EBUSY: return "SSH_EBUSY";
+        case SSH_ETIMEOUT: return "SSH_ETIMEOUT";
+        case SSH_ENOTSUP: return "SSH_ENOTSUP";
+    }
+    return "SSH_UNKNOWN";
+}
+
+const char* ssh_last_error(void) { return g_err; }
+
+ssh_status ssh_create(int W, int delta, int n, int K, int L, float band, uint64_t seed, ssh_index** out) {
+    if (!out) return fail(SSH_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (W < 1 || W > kMaxW) return fail(SSH_EINVAL, "W = %d outside [1, %d]", W, kMaxW);
+    if (delta < 1) return fail(SSH_EINVAL, "delta = %d < 1", delta);
+    if (n < 1 || n > 32) return fail(SSH_EINVAL, "n = %d outside [1, 32]", n);
+    if (n > kMaxShingleBits) return fail(SSH_ENOTSUP, "n = %d > %d needs draws computed on the fly (not built)", n, kMaxShingleBits);
+    if (K < 1 || L < 1 || (int64_t)K * L > kMaxKL) return fail(SSH_EINVAL, "K*L = %lld outside [1, %d]", (long long)K * L, kMaxKL);
+    if (!(band >= 0.0f) || std::isinf(band)) return fail(SSH_EINVAL, "band must be finite and >= 0");
+
+    ssh_index* idx = new ssh_index();
+    idx->W = W;
+    idx->delta = delta;
+    idx->n = n;
+    idx->K = K;
+    idx->L = L;
+    idx->KL = K * L;
+    idx->band = band;
+    idx->seed = seed;
+    cudaError_t e = cudaGetDevice(&idx->device);
+    if (e != cudaSuccess) {
+        delete idx;
+        return cuda_status(e, "cudaGetDevice");
+    }
+
+    // Sec. 4.1 filter and the sign-test threshold tau * ||r|| (tau = max(1e-4, 2 gamma_W))
+    make_filter(seed, W, idx->h_r);
+    double nr = 0.0;
+    for (float v : idx->h_r) nr += (double)v * (double)v;
+    const double gw = W * std::ldexp(1.0, -24) / (1.0 - W * std::ldexp(1.0, -24));
+    const double tau = std::max(1e-4, 2.0 * gw);
+    idx->tau_norm = std::nextafter((float)(tau * std::sqrt(nr) * (1.0 + 1e-6)), INFINITY);
+
+    // Sec. 4.3 draw tables for every (hash j, shingle k)
+    const int KL = idx->KL;
+    const int64_t nk = (int64_t)1 << n;
+    std::vector<uint16_t> rank((size_t)nk * KL), kinv((size_t)KL * nk);
+    std::vector<float4> p32((size_t)nk * KL);
+    std::vector<double> p64((size_t)KL * nk * 3);
+    parallel_for(KL, [&](int64_t j) {
+        std::vector<std::pair<double, uint32_t>> la1(nk);
+        for (int64_t k = 0; k < nk; ++k) {
+            const Draw d = cws_draw(seed, (uint32_t)j, (uint32_t)k);
+            p32[(size_t)k * KL + j] = make_float4((float)d.r, (float)(1.0 / d.r), (float)d.beta, (float)d.lnc);
+            double* q = &p64[((size_t)j * nk + k) * 3];
+            q[0] = d.r;
+            q[1] = d.beta;
+            q[2] = d.lnc;
+            la1[k] = {log_a(d, std::log(1.0)), (uint32_t)k};
+        }
+        std::sort(la1.begin(), la1.end());  // (value, id): equal values keep the smaller id first
+        for (int64_t rnk = 0; rnk < nk; ++rnk) {
+            rank[(size_t)la1[rnk].second * KL + j] = (uint16_t)rnk;
+            kinv[(size_t)j * nk + rnk] = (uint16_t)la1[rnk].second;
+        }
+    });
+    std::vector<float> lns32(kMaxCount + 1);
+    std::vector<double> lns64(kMaxCount + 1);
+    for (int s = 0; s <= kMaxCount; ++s) {
+        lns64[s] = std::log((double)s);
+        lns32[s] = (float)lns64[s];
+    }
+
+    auto up = [&](void** dst, const void* src, size_t bytes) -> cudaError_t {
+        cudaError_t err = cudaMalloc(dst, bytes);
+        if (err != cudaSuccess) return err;
+        return cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
+    };
+    e = up(reinterpret_cast<void**>(&idx->d_r), idx->h_r.data(), W * sizeof(float));
+    if (e == cudaSuccess) e = up(reinterpret_cast<void**>(&idx->d_rank), rank.data(), rank.size() * 2);
+    if (e == cudaSuccess) e = up(reinterpret_cast<void**>(&idx->d_kinv), kinv.data(), kinv.size() * 2);
+    if (e == cudaSuccess) e = up(reinterpret_cast<void**>(&idx->d_p32), p32.data(), p32.size() * sizeof(float4));
+    if (e == cudaSuccess) e = up(reinterpret_cast<void**>(&idx->d_p64), p64.data(), p64.size() * sizeof(double));
+    if (e == cudaSuccess) e = up(reinterpret_cast<void**>(&idx->d_lns32), lns32.data(), lns32.size() * sizeof(float));
+    if (e == cudaSuccess) e = up(reinterpret_cast<void**>(&idx->d_lns64), lns64.data(), lns64.size() * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&idx->d_stats, kNumStatSlots * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(idx->d_stats, 0, kNumStatSlots * sizeof(unsigned long long));
+    if (e != cudaSuccess) {
+        ssh_status st = cuda_status(e, "ssh_create device tables");
+        ssh_destroy(idx);
+        return st;
+    }
+    *out = idx;
+    return SSH_OK;
+}
+
+void ssh_destroy(ssh_index* idx) {
+    if (!idx) return;
+    cudaSetDevice(idx->device);
+    cudaDeviceSynchronize();
+    for (auto& kv : idx->subs) free_sub(kv.second);
+    cudaFree(idx->d_r);
+    cudaFree(idx->d_rank);
+    cudaFree(idx->d_kinv);
+    cudaFree(idx->d_p32);
+    cudaFree(idx->d_p64);
+    cudaFree(idx->d_lns32);
+    cudaFree(idx->d_lns64);
+    cudaFree(idx->d_stats);
+    delete idx;
+}
+
+ssh_status ssh_get_filter(const ssh_index* idx, float* r_out) {
+    if (!idx || !r_out) return fail(SSH_EINVAL, "NULL argument");
+    memcpy(r_out, idx->h_r.data(), idx->W * sizeof(float));
+    return SSH_OK;
+}
+
+ssh_status ssh_index_add(ssh_index* idx, const float* series, const int32_t* lengths, int64_t count,
+                         int64_t* first_id) {
+    if (!idx || (count > 0 && (!series || !lengths)) || count < 0) return fail(SSH_EINVAL, "bad arguments");
+    SSH_TRY(check_device(idx));
+    if (count == 0) {
+        if (first_id) *first_id = idx->next_id;
+        return SSH_OK;
+    }
+    int64_t total = 0;
+    for (int64_t i = 0; i < count; ++i) total += std::max(lengths[i], 0);
+    float* dev = nullptr;
+    SSH_CUDA(cudaMalloc(&dev, std::max<int64_t>(total, 1) * sizeof(float)));
+    cudaError_t e = cudaMemcpy(dev, series, total * sizeof(float), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(dev);
+        return cuda_status(e, "cudaMemcpy (series)");
+    }
+    ssh_status s = add_series(idx, dev, lengths, count, 0, first_id);
+    if (s != SSH_OK) {
+        cudaFree(dev);
+        return s;
+    }
+    idx->subs[lengths[0]].owned.push_back(dev);  // freed with the index (any sub-index may own it)
+    return SSH_OK;
+}
+
+ssh_status ssh_index_add_device(ssh_index* idx, const float* d_series, const int32_t* lengths, int64_t count,
+                                uint32_t flags, void* stream, int64_t* first_id) {
+    if (!idx || (count > 0 && (!d_series || !lengths)) || count < 0) return fail(SSH_EINVAL, "bad arguments");
+    SSH_TRY(check_device(idx));
+    cudaStream_t st = (cudaStream_t)stream;
+    if (count == 0) {
+        if (first_id) *first_id = idx->next_id;
+        return SSH_OK;
+    }
+    const float* src = d_series;
+    float* own = nullptr;
+    if (!(flags & SSH_ADD_BORROW)) {
+        int64_t total = 0;
+        for (int64_t i = 0; i < count; ++i) total += std::max(lengths[i], 0);
+        SSH_CUDA(cudaMalloc(&own, std::max<int64_t>(total, 1) * sizeof(float)));
+        cudaError_t e = cudaMemcpyAsync(own, d_series, total * sizeof(float), cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) {
+            cudaFree(own);
+            return cuda_status(e, "cudaMemcpyAsync (series)");
+        }
+        src = own;
+    }
+    ssh_status s = add_series(idx, src, lengths, count, st, first_id);
+    if (s != SSH_OK) {
+        cudaFree(own);
+        return s;
+    }
+    if (own) idx->subs[lengths[0]].owned.push_back(own);
+    return SSH_OK;
+}
+
+ssh_status ssh_index_clear(ssh_index* idx) {
+    if (!idx) return fail(SSH_EINVAL, "NULL index");
+    SSH_TRY(check_device(idx));
+    SSH_CUDA(cudaDeviceSynchronize());
+    for (auto& kv : idx->subs) {
+        for (void* p : kv.second.owned) cudaFree(p);
+        kv.second.owned.clear();
+        kv.second.count = 0;  // keep the capacity for the next add
+    }
+    idx->next_id = 0;
+    return SSH_OK;
+}
+
+ssh_status ssh_index_size(const ssh_index* idx, int64_t* count) {
+    if (!idx || !count) return fail(SSH_EINVAL, "NULL argument");
+    int64_t c = 0;
+    for (auto& kv : idx->subs) c += kv.second.count;
+    *count = c;
+    return SSH_OK;
+}
+
+ssh_status ssh_query(ssh_index* idx, const float* queries, const int32_t* lengths, int64_t nq, int k, int64_t* ids,
+                     float* dists) {
+    if (!idx || nq < 0 || (nq > 0 && (!queries || !lengths || !ids || !dists))) return fail(SSH_EINVAL, "bad arguments");
+    SSH_TRY(check_device(idx));
+    if (nq == 0) return SSH_OK;
+    int64_t total = 0;
+    for (int64_t i = 0; i < nq; ++i) total += std::max(lengths[i], 0);
+    float* dq = nullptr;
+    int64_t* did = nullptr;
+    float* dd = nullptr;
+    cudaError_t e = cudaMalloc(&dq, std::max<int64_t>(total, 1) * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&did, nq * k * sizeof(int64_t));
+    if (e == cudaSuccess) e = cudaMalloc(&dd, nq * k * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemcpy(dq, queries, total * sizeof(float), cudaMemcpyHostToDevice);
+    ssh_status s = (e == cudaSuccess) ? run_query(idx, dq, lengths, nq, k, did, dd, 0)
+                                      : cuda_status(e, "ssh_query staging");
+    if (s == SSH_OK) {
+        e = cudaMemcpy(ids, did, nq * k * sizeof(int64_t), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(dists, dd, nq * k * sizeof(float), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) s = cuda_status(e, "ssh_query results");
+    }
+    cudaFree(dq);
+    cudaFree(did);
+    cudaFree(dd);
+    return s;
+}
+
+ssh_status ssh_query_device(ssh_index* idx, const float* d_queries, const int32_t* lengths, int64_t nq, int k,
+                            int64_t* d_ids, float* d_dists, void* stream) {
+    if (!idx || nq < 0 || (nq > 0 && (!d_queries || !lengths || !d_ids || !d_dists)))
+        return fail(SSH_EINVAL, "bad arguments");
+    SSH_TRY(check_device(idx));
+    if (nq == 0) return SSH_OK;
+    return run_query(idx, d_queries, lengths, nq, k, d_ids, d_dists, (cudaStream_t)stream);
+}
+
+ssh_status ssh_set_option(ssh_index* idx, ssh_option opt, int64_t value) {
+    if (!idx) return fail(SSH_EINVAL, "NULL index");
+    switch (opt) {
+        case SSH_OPT_LB_PRUNE:
+            idx->lb_prune = value != 0;
+            return SSH_OK;
+    }
+    return fail(SSH_EINVAL, "unknown option %d", (int)opt);
+}
+
+ssh_status ssh_get_stats(const ssh_index* idx, ssh_stats* out) {
+    if (!idx || !out) return fail(SSH_EINVAL, "NULL argument");
+    unsigned long long dev[kNumStatSlots] = {0};
+    SSH_CUDA(cudaMemcpy(dev, idx->d_stats, sizeof(dev), cudaMemcpyDeviceToHost));
+    *out = idx->host_stats;
+    out->sketch_fp64 = (int64_t)dev[kStatSketch64];
+    out->cws_fp64 = (int64_t)dev[kStatCws64];
+    return SSH_OK;
+}
+
+ssh_status ssh_reset_stats(ssh_index* idx) {
+    if (!idx) return fail(SSH_EINVAL, "NULL index");
+    SSH_CUDA(cudaMemset(idx->d_stats, 0, kNumStatSlots * sizeof(unsigned long long)));
+    idx->host_stats = ssh_stats{};
+    return SSH_OK;
+}
+
+ssh_status ssh_hash_device(const ssh_index* idx, const float* d_series, int32_t m, int64_t count, void* stream,
+                           uint32_t* d_bits, uint32_t* d_sh_ids, uint32_t* d_sh_counts, int32_t* d_nnz,
+                           uint32_t* d_kstar, uint32_t* d_tstar, uint64_t* d_keys) {
+    if (!idx || count < 0 || (count > 0 && !d_series)) return fail(SSH_EINVAL, "bad arguments");
+    if ((d_sh_ids == nullptr) != (d_sh_counts == nullptr) || (d_kstar == nullptr) != (d_tstar == nullptr))
+        return fail(SSH_EINVAL, "shingle ids/counts and kstar/tstar come in pairs");
+    SSH_TRY(check_device(idx));
+    Geometry g;
+    SSH_TRY(geometry(idx, m, &g));
+    HashArgs a = base_hash_args(idx, m, g);
+    a.series = d_series;
+    a.stride = m;
+    a.count = count;
+    a.keys = d_keys;
+    a.key_stride = count;
+    a.key_col0 = 0;
+    a.bits_out = d_bits;
+    a.sh_ids_out = d_sh_ids;
+    a.sh_counts_out = d_sh_counts;
+    a.nnz_out = d_nnz;
+    a.kstar_out = d_kstar;
+    a.tstar_out = d_tstar;
+    SSH_CUDA(launch_hash(a, (cudaStream_t)stream));
+    return SSH_OK;
+}
+
+static ssh_status pairwise(const float* d_a, const int64_t* d_a_idx, const float* d_b, const int64_t* d_b_idx,
+                           int64_t npairs, int32_t m, int32_t rb, float* d_out, cudaStream_t st, bool lb) {
+    if (npairs < 0 || m < 1 || rb < 0 || rb >= m || (npairs > 0 && (!d_a || !d_a_idx || !d_b || !d_b_idx || !d_out)))
+        return fail(SSH_EINVAL, "bad arguments");
+    if (npairs == 0) return SSH_OK;
+    // group the pairs by a-row on the host: segments of equal a_idx
+    std::vector<int64_t> ai(npairs), bi(npairs);
+    SSH_CUDA(cudaMemcpyAsync(ai.data(), d_a_idx, npairs * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    SSH_CUDA(cudaMemcpyAsync(bi.data(), d_b_idx, npairs * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    SSH_CUDA(cudaStreamSynchronize(st));
+    std::vector<int64_t> order(npairs);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int64_t x, int64_t y) { return ai[x] < ai[y]; });
+    std::vector<int64_t> begin;
+    std::vector<const float*> sa, pb(npairs);
+    std::vector<int64_t> slot(npairs);
+    int64_t mx = 0;
+    for (int64_t t = 0; t < npairs; ++t) {
+        const int64_t p = order[t];
+        if (t == 0 || ai[p] != ai[order[t - 1]]) {
+            if (!begin.empty()) mx = std::max(mx, t - begin.back());
+            begin.push_back(t);
+            sa.push_back(d_a + ai[p] * m);
+        }
+        pb[t] = d_b + bi[p] * m;
+        slot[t] = p;
+    }
+    mx = std::max(mx, npairs - begin.back());
+    begin.push_back(npairs);
+    const int64_t nseg = (int64_t)sa.size();
+    ScratchList sc(st);
+    int64_t *dbeg, *dslot;
+    const float **dsa, **dpb;
+    SSH_TRY(sc.get(&dbeg, nseg + 1));
+    SSH_TRY(sc.get(&dslot, npairs));
+    SSH_TRY(sc.get(&dsa, nseg));
+    SSH_TRY(sc.get(&dpb, npairs));
+    SSH_CUDA(cudaMemcpyAsync(dbeg, begin.data(), (nseg + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    SSH_CUDA(cudaMemcpyAsync(dslot, slot.data(), npairs * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    SSH_CUDA(cudaMemcpyAsync(dsa, sa.data(), nseg * sizeof(float*), cudaMemcpyHostToDevice, st));
+    SSH_CUDA(cudaMemcpyAsync(dpb, pb.data(), npairs * sizeof(float*), cudaMemcpyHostToDevice, st));
+    PairSet ps{dbeg, nseg, dsa, dpb, dslot, mx};
+    if (lb) {
+        float *up, *lo;
+        SSH_TRY(sc.get(&up, (size_t)nseg * m));
+        SSH_TRY(sc.get(&lo, (size_t)nseg * m));
+        SSH_CUDA(launch_envelope(dsa, nseg, m, rb, up, lo, st));
+        SSH_CUDA(launch_lb_keogh(ps, up, lo, m, d_out, st));
+    } else {
+        cudaError_t e = launch_dtw(ps, m, rb, d_out, st);
+        if (e == cudaErrorNotSupported) return fail(SSH_ENOTSUP, "DTW radius %d is wider than this build covers", rb);
+        SSH_CUDA(e);
+    }
+    SSH_CUDA(cudaStreamSynchronize(st));
+    return SSH_OK;
+}
+
+ssh_status ssh_dtw_device(const float* d_a, const int64_t* d_a_idx, const float* d_b, const int64_t* d_b_idx,
+                          int64_t npairs, int32_t m, int32_t rb, float* d_out, void* stream) {
+    return pairwise(d_a, d_a_idx, d_b, d_b_idx, npairs, m, rb, d_out, (cudaStream_t)stream, false);
+}
+
+ssh_status ssh_lb_keogh_device(const float* d_a, const int64_t* d_a_idx, const float* d_b, const int64_t* d_b_idx,
+                               int64_t npairs, int32_t m, int32_t rb, float* d_out, void* stream) {
+    return pairwise(d_a, d_a_idx, d_b, d_b_idx, npairs, m, rb, d_out, (cudaStream_t)stream, true);
+}
+
+}  // extern "C"

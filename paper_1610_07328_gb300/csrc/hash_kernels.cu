@@ -1,0 +1,344 @@
+// hash_kernels.cu -- Sec. 4.1 (sketch), Sec. 4.2 (shingles), Sec. 4.3 (weighted
+// minhash by consistent weighted sampling) and the bucket keys of Algorithm 1,
+// fused into one kernel: one warp hashes one series, and the series, its bits,
+// its shingles and its hashes never leave shared memory.
+//
+// Exactness. Sign bits, shingles, (k*, t*) and keys must equal the FP64 CPU
+// definition bit for bit, while the arithmetic here is FP32:
+//  - a sketch bit is taken from the FP32 dot product only when |dot| exceeds
+//    tau * ||r|| * ||x_window|| with tau = max(1e-4, 2 * gamma_W) (gamma_W is
+//    the FP32 error bound of a W-term FMA chain); otherwise the window is
+//    recomputed in FP64 in the definition's summation order;
+//  - for shingles seen once, ln a_k = ln c_k - r_k (1 - beta_k) depends only on
+//    (hash, shingle), so the draw tables hold its exact rank among all shingles
+//    (computed from FP64 values at index creation) and the argmin over them is
+//    an integer min;
+//  - for repeated shingles and for the final comparison, ln a is evaluated in
+//    FP32 together with a guaranteed error interval (relative width >= 1e-6,
+//    directed rounding); if the winner's interval overlaps another candidate's,
+//    or a floor() is within its error of an integer step, the whole hash is
+//    recomputed in FP64 exactly as the definition orders the operations.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ssh_internal.cuh"
+
+namespace ssh {
+namespace {
+
+constexpr int kMaxWarpsPerCta = 8;
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+__host__ __device__ inline int align16(int bytes) { return (bytes + 15) & ~15; }
+
+__host__ __device__ inline int next_pow2(int v) {
+    int p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+struct WarpSmem {
+    int x, bits, sbuf, hpos, cid, ccnt, kst, tst, total;
+};
+
+__host__ __device__ inline WarpSmem warp_layout(int m, int nwords, int S, int KL) {
+    WarpSmem L;
+    int off = 0;
+    L.x = off;    off += align16(4 * m);
+    L.bits = off; off += align16(4 * (nwords + 2));
+    L.sbuf = off; off += align16(4 * next_pow2(S));
+    L.hpos = off; off += align16(4 * (S + 1));
+    L.cid = off;  off += align16(4 * S);
+    L.ccnt = off; off += align16(4 * S);
+    L.kst = off;  off += align16(4 * KL);
+    L.tst = off;  off += align16(4 * KL);
+    L.total = off;
+    return L;
+}
+
+// splitmix64 output finalizer (Steele, Lea & Flood, OOPSLA'14).
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// FP64 recomputation of one hash j over the whole weighted set, in the order
+// of the definition: t = floor(ln S / r + beta); ln a = ln c - r ((t - beta) + 1).
+__device__ void cws_fp64(const HashArgs& a, int j, const uint32_t* cid, const uint32_t* ccnt, int nnz,
+                         uint32_t* kout, uint32_t* tout) {
+    const size_t nk = (size_t)1 << a.n;
+    double best = __longlong_as_double(0x7FF0000000000000ll);  // +inf
+    uint32_t bk = 0, bt = 0;
+    for (int e = 0; e < nnz; ++e) {
+        uint32_t k = cid[e];
+        const double* p = a.p64 + ((size_t)j * nk + k) * 3;
+        double r = p[0], beta = p[1], lnc = p[2];
+        double lns = a.lns64[ccnt[e]];
+        double t = floor(__dadd_rn(__ddiv_rn(lns, r), beta));
+        double la = __dsub_rn(lnc, __dmul_rn(r, __dadd_rn(__dsub_rn(t, beta), 1.0)));
+        if (la < best) {
+            best = la;
+            bk = k;
+            bt = (uint32_t)t;
+        }
+    }
+    *kout = bk;
+    *tout = bt;
+}
+
+__global__ void __launch_bounds__(kMaxWarpsPerCta * 32) hash_kernel(HashArgs a, int warps_per_cta) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int W = a.W, m = a.m, delta = a.delta, n = a.n, nb = a.nb, nwords = a.nwords, S = a.S, KL = a.KL;
+
+    float* r_s = reinterpret_cast<float*>(smem);
+    for (int j = threadIdx.x; j < W; j += blockDim.x) r_s[j] = a.r[j];
+    const WarpSmem lay = warp_layout(m, nwords, S, KL);
+    unsigned char* wbase = smem + align16(4 * W) + (size_t)warp * lay.total;
+    float* x_s = reinterpret_cast<float*>(wbase + lay.x);
+    uint32_t* bits_s = reinterpret_cast<uint32_t*>(wbase + lay.bits);
+    uint32_t* sbuf = reinterpret_cast<uint32_t*>(wbase + lay.sbuf);
+    int* hpos = reinterpret_cast<int*>(wbase + lay.hpos);
+    uint32_t* cid = reinterpret_cast<uint32_t*>(wbase + lay.cid);
+    uint32_t* ccnt = reinterpret_cast<uint32_t*>(wbase + lay.ccnt);
+    uint32_t* kst = reinterpret_cast<uint32_t*>(wbase + lay.kst);
+    uint32_t* tst = reinterpret_cast<uint32_t*>(wbase + lay.tst);
+    __syncthreads();
+
+    const int64_t row = (int64_t)blockIdx.x * warps_per_cta + warp;
+    if (row >= a.count) return;
+    const float* xg = a.rows ? a.rows[row] : a.series + row * a.stride;
+
+    // ---- load the series (float4 when aligned)
+    if (((reinterpret_cast<uintptr_t>(xg) & 15) == 0) && (m & 3) == 0) {
+        const float4* x4 = reinterpret_cast<const float4*>(xg);
+        float4* xs4 = reinterpret_cast<float4*>(x_s);
+        for (int i = lane; i < (m >> 2); i += 32) xs4[i] = __ldg(x4 + i);
+    } else {
+        for (int i = lane; i < m; i += 32) x_s[i] = __ldg(xg + i);
+    }
+    __syncwarp();
+
+    // ---- Sec. 4.1: sketch bits, one window per lane, packed by ballot
+    unsigned long long n64 = 0;
+    for (int w = 0; w < nwords; ++w) {
+        const int i = w * 32 + lane;
+        bool bit = false;
+        if (i < nb) {
+            const float* xw = x_s + i * delta;
+            float acc = 0.f, ss = 0.f;
+            for (int j = 0; j < W; ++j) {
+                float xv = xw[j];
+                acc = fmaf(r_s[j], xv, acc);
+                ss = fmaf(xv, xv, ss);
+            }
+            float thr = __fmul_ru(a.tau_norm, __fsqrt_ru(__fmul_ru(ss, 1.0f + a.gamma_ss)));
+            if (fabsf(acc) > thr) {
+                bit = acc >= 0.f;
+            } else {
+                double d = 0.0;
+                for (int j = 0; j < W; ++j) d = __dadd_rn(d, __dmul_rn((double)r_s[j], (double)xw[j]));
+                bit = d >= 0.0;
+                n64 += 1;
+            }
+        }
+        unsigned bal = __ballot_sync(kFull, bit);
+        if (lane == 0) bits_s[w] = __brev(bal);
+    }
+    if (lane == 0) {
+        bits_s[nwords] = 0u;
+        bits_s[nwords + 1] = 0u;
+    }
+    if (n64 && a.stats) atomicAdd(&a.stats[kStatSketch64], n64);
+    __syncwarp();
+    if (a.bits_out)
+        for (int w = lane; w < nwords; w += 32) a.bits_out[row * nwords + w] = bits_s[w];
+
+    // ---- Sec. 4.2: shingle ids (first bit most significant), warp bitonic sort, run-length encode
+    const int S2 = next_pow2(S);
+    for (int i = lane; i < S2; i += 32) {
+        uint32_t id = 0xFFFFFFFFu;
+        if (i < S) {
+            uint64_t v = ((uint64_t)bits_s[i >> 5] << 32) | (uint64_t)bits_s[(i >> 5) + 1];
+            id = (uint32_t)((v << (i & 31)) >> (64 - n));
+        }
+        sbuf[i] = id;
+    }
+    __syncwarp();
+    for (int k = 2; k <= S2; k <<= 1) {
+        for (int jj = k >> 1; jj > 0; jj >>= 1) {
+            for (int t = lane; t < (S2 >> 1); t += 32) {
+                int i = 2 * jj * (t / jj) + (t % jj);
+                int l = i + jj;
+                uint32_t u = sbuf[i], v = sbuf[l];
+                bool up = (i & k) == 0;
+                if ((u > v) == up) {
+                    sbuf[i] = v;
+                    sbuf[l] = u;
+                }
+            }
+            __syncwarp();
+        }
+    }
+    int nnz = 0;
+    for (int base = 0; base < S; base += 32) {
+        int i = base + lane;
+        bool head = (i < S) && (i == 0 || sbuf[i] != sbuf[i - 1]);
+        unsigned bal = __ballot_sync(kFull, head);
+        if (head) {
+            int pos = nnz + __popc(bal & ((1u << lane) - 1u));
+            cid[pos] = sbuf[i];
+            hpos[pos] = i;
+        }
+        nnz += __popc(bal);
+    }
+    __syncwarp();
+    for (int e = lane; e < nnz; e += 32) {
+        int end = (e + 1 < nnz) ? hpos[e + 1] : S;
+        ccnt[e] = (uint32_t)(end - hpos[e]);
+    }
+    __syncwarp();
+    if (a.nnz_out && lane == 0) a.nnz_out[row] = nnz;
+    if (a.sh_ids_out)
+        for (int e = lane; e < nnz; e += 32) {
+            a.sh_ids_out[row * S + e] = cid[e];
+            a.sh_counts_out[row * S + e] = ccnt[e];
+        }
+
+    // ---- Sec. 4.3: weighted minhash (Improved Consistent Sampling) per hash j
+    unsigned long long c64 = 0;
+    const size_t nk = (size_t)1 << n;
+    for (int j0 = 0; j0 < KL; j0 += 32) {
+        const int j = j0 + lane;
+        if (j < KL) {
+            uint32_t rmin = 0xFFFFFFFFu;
+            float bLa = __int_as_float(0x7F800000), bHi = 0.f;
+            uint32_t bK = 0xFFFFFFFFu, bT = 0;
+            float lo1 = __int_as_float(0x7F800000), lo2 = lo1;
+            uint32_t klo1 = 0xFFFFFFFFu;
+            bool unsure = false;
+            for (int e = 0; e < nnz; ++e) {
+                const uint32_t k = cid[e];
+                const uint32_t s = ccnt[e];
+                if (s == 1) {
+                    uint32_t rk = __ldg(a.rank + (size_t)k * KL + j);
+                    rmin = min(rmin, rk);
+                } else {
+                    const float4 p = __ldg(a.p32 + (size_t)k * KL + j);  // (r, 1/r, beta, ln c)
+                    const float ls = __ldg(a.lns32 + s);
+                    const float P = __fmul_ru(ls, p.y);
+                    const float x = fmaf(ls, p.y, p.z);
+                    const float ex = __fmul_ru(__fadd_ru(P, 1.0f), 4.76837158203125e-07f);  // 2^-21
+                    const float f1 = floorf(__fsub_rd(x, ex));
+                    const float f2 = floorf(__fadd_ru(x, ex));
+                    unsure |= !(P < 1048576.0f) || (f1 != f2);
+                    const float v = (f1 + 1.0f) - p.z;
+                    const float la = fmaf(-p.x, v, p.w);
+                    const float er = __fmul_ru(__fadd_ru(fabsf(p.w), __fmul_ru(p.x, v)), 1.0e-6f);
+                    const float lo = __fsub_rd(la, er), hi = __fadd_ru(la, er);
+                    if (la < bLa) {  // ids ascend, so a strict < keeps the smaller id on ties
+                        bLa = la;
+                        bHi = hi;
+                        bK = k;
+                        bT = (uint32_t)f1;
+                    }
+                    if (lo < lo1) {
+                        lo2 = lo1;
+                        lo1 = lo;
+                        klo1 = k;
+                    } else if (lo < lo2) {
+                        lo2 = lo;
+                    }
+                }
+            }
+            uint32_t ks = 0, ts = 0;
+            const bool hasA = rmin != 0xFFFFFFFFu;
+            const bool hasB = bK != 0xFFFFFFFFu;
+            float aLa = 0.f, aLo = 0.f, aHi = 0.f;
+            uint32_t kA = 0;
+            if (hasA) {
+                kA = __ldg(a.kinv + (size_t)j * nk + rmin);
+                const float4 p = __ldg(a.p32 + (size_t)kA * KL + j);
+                const float v = 1.0f - p.z;  // exact: beta is a multiple of 2^-24 in (0,1)
+                aLa = fmaf(-p.x, v, p.w);
+                const float er = __fmul_ru(__fadd_ru(fabsf(p.w), __fmul_ru(p.x, v)), 1.0e-6f);
+                aLo = __fsub_rd(aLa, er);
+                aHi = __fadd_ru(aLa, er);
+            }
+            bool certain;
+            bool winA;
+            if (!hasB) {
+                winA = true;
+                certain = true;
+            } else if (!hasA) {
+                winA = false;
+                certain = bHi < ((klo1 != bK) ? lo1 : lo2);
+            } else {
+                winA = (aLa < bLa) || (aLa == bLa && kA < bK);
+                if (winA) {
+                    certain = aHi < lo1;
+                } else {
+                    certain = (bHi < aLo) && (bHi < ((klo1 != bK) ? lo1 : lo2));
+                }
+            }
+            if (unsure || !certain) {
+                cws_fp64(a, j, cid, ccnt, nnz, &ks, &ts);
+                c64 += 1;
+            } else if (winA) {
+                ks = kA;
+                ts = 0;
+            } else {
+                ks = bK;
+                ts = bT;
+            }
+            kst[j] = ks;
+            tst[j] = ts;
+        }
+    }
+    if (c64 && a.stats) atomicAdd(&a.stats[kStatCws64], c64);
+    __syncwarp();
+    if (a.kstar_out)
+        for (int j = lane; j < KL; j += 32) {
+            a.kstar_out[row * KL + j] = kst[j];
+            a.tstar_out[row * KL + j] = tst[j];
+        }
+
+    // ---- Algorithm 1: one bucket key per table from its K hashes
+    if (a.keys) {
+        for (int l = lane; l < a.L; l += 32) {
+            uint64_t h = a.seed ^ (0x9E3779B97F4A7C15ull * (uint64_t)(l + 1));
+            for (int i = 0; i < a.K; ++i) {
+                const int j = l * a.K + i;
+                h = mix64(h ^ (((uint64_t)kst[j] << 32) | (uint64_t)tst[j]));
+            }
+            a.keys[(int64_t)l * a.key_stride + a.key_col0 + row] = h;
+        }
+    }
+}
+
+}  // namespace
+
+int hash_smem_bytes_per_warp(int m, int nwords, int S, int KL) { return warp_layout(m, nwords, S, KL).total; }
+
+int hash_warps_per_cta(int m, int nwords, int S, int KL) {
+    const int per = hash_smem_bytes_per_warp(m, nwords, S, KL);
+    int w = kMaxWarpsPerCta;
+    while (w > 1 && w * per > 160 * 1024) w >>= 1;
+    return w;
+}
+
+cudaError_t launch_hash(const HashArgs& a, cudaStream_t st) {
+    if (a.count <= 0) return cudaSuccess;
+    const int wpc = hash_warps_per_cta(a.m, a.nwords, a.S, a.KL);
+    const size_t smem = (size_t)align16(4 * a.W) + (size_t)wpc * hash_smem_bytes_per_warp(a.m, a.nwords, a.S, a.KL);
+    if (smem > 227 * 1024) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(hash_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int64_t grid = (a.count + wpc - 1) / wpc;
+    hash_kernel<<<(unsigned)grid, wpc * 32, smem, st>>>(a, wpc);
+    return cudaGetLastError();
+}
+
+}  // namespace ssh

@@ -1,0 +1,409 @@
+// query_kernels.cu -- Algorithm 2 on the device: probe each table for the
+// query's bucket, take the union of the buckets (a per-query bitmap over the
+// sub-index's rows), compact it into a candidate list, bound each candidate
+// with LB_Keogh (Sec. 3), and rank the survivors by Sakoe-Chiba-banded DTW
+// (Sec. 2.1) computed as an anti-diagonal wavefront in registers.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ssh_internal.cuh"
+
+namespace ssh {
+namespace {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+// ------------------------------------------------------------ probe, union
+
+__global__ void probe_union_kernel(ProbeArgs a) {
+    const int64_t q = blockIdx.x;
+    const int64_t l = blockIdx.y;
+    const uint64_t key = a.qkeys[l * a.nq + q];
+    const uint64_t* sk = a.skeys + l * a.cap;
+    const uint32_t* sr = a.srows + l * a.cap;
+    __shared__ int64_t range[2];
+    if (threadIdx.x == 0) {
+        int64_t lo = 0, hi = a.nrows;  // lower_bound
+        while (lo < hi) {
+            int64_t mid = (lo + hi) >> 1;
+            if (sk[mid] < key) lo = mid + 1; else hi = mid;
+        }
+        int64_t lo2 = lo, hi2 = a.nrows;  // upper_bound
+        while (lo2 < hi2) {
+            int64_t mid = (lo2 + hi2) >> 1;
+            if (sk[mid] <= key) lo2 = mid + 1; else hi2 = mid;
+        }
+        range[0] = lo;
+        range[1] = lo2;
+    }
+    __syncthreads();
+    uint32_t* bm = a.bitmap + q * a.words;
+    for (int64_t i = range[0] + threadIdx.x; i < range[1]; i += blockDim.x) {
+        const uint32_t row = sr[i];
+        atomicOr(&bm[row >> 5], 1u << (row & 31));
+    }
+}
+
+__global__ void bitmap_count_kernel(const uint32_t* bitmap, int64_t words, int64_t* counts) {
+    const uint32_t* bm = bitmap + (int64_t)blockIdx.x * words;
+    int64_t s = 0;
+    for (int64_t w = threadIdx.x; w < words; w += blockDim.x) s += __popc(bm[w]);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+    __shared__ int64_t part[32];
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int64_t t = 0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += part[i];
+        counts[blockIdx.x] = t;
+    }
+}
+
+// Rows of each query's bitmap in ascending order, at offsets[q] ..
+__global__ void __launch_bounds__(1024) bitmap_compact_kernel(const uint32_t* bitmap, int64_t words,
+                                                              const int64_t* offsets, uint32_t* cand_rows) {
+    __shared__ int part[32];
+    __shared__ int64_t s_base;
+    const int64_t q = blockIdx.x;
+    const uint32_t* bm = bitmap + q * words;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_base = offsets[q];
+    __syncthreads();
+    for (int64_t w0 = 0; w0 < words; w0 += blockDim.x) {
+        const int64_t w = w0 + threadIdx.x;
+        uint32_t bits = (w < words) ? bm[w] : 0u;
+        int c = __popc(bits);
+        int incl = c;
+        for (int o = 1; o < 32; o <<= 1) {
+            int v = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += v;
+        }
+        if (lane == 31) part[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            int v = (lane < (int)(blockDim.x >> 5)) ? part[lane] : 0;
+            int inc = v;
+            for (int o = 1; o < 32; o <<= 1) {
+                int u = __shfl_up_sync(kFull, inc, o);
+                if (lane >= o) inc += u;
+            }
+            part[lane] = inc - v;  // exclusive
+        }
+        __syncthreads();
+        int64_t pos = s_base + part[warp] + (incl - c);
+        while (bits) {
+            int b = __ffs(bits) - 1;
+            bits &= bits - 1;
+            cand_rows[pos++] = (uint32_t)(w * 32 + b);
+        }
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) s_base = pos;
+        __syncthreads();
+    }
+}
+
+// ----------------------------------------------------------- LB_Keogh
+
+__global__ void envelope_kernel(const float* const* seg_a, int m, int rb, float* upper, float* lower) {
+    const int64_t s = blockIdx.y;
+    const float* q = seg_a[s];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+        const int lo = max(0, i - rb), hi = min(m - 1, i + rb);
+        float u = q[lo], l = q[lo];
+        for (int t = lo + 1; t <= hi; ++t) {
+            const float v = q[t];
+            u = fmaxf(u, v);
+            l = fminf(l, v);
+        }
+        upper[s * m + i] = u;
+        lower[s * m + i] = l;
+    }
+}
+
+constexpr int kLbWarps = 8;
+
+__global__ void __launch_bounds__(kLbWarps * 32) lb_keogh_kernel(PairSet ps, const float* upper, const float* lower,
+                                                                 int m, float* out) {
+    extern __shared__ float env[];  // [2m]: upper then lower
+    const int64_t s = blockIdx.y;
+    const int64_t b = ps.seg_begin[s], e = ps.seg_begin[s + 1];
+    const int64_t per_cta = kLbWarps;
+    if (b + (int64_t)blockIdx.x * per_cta >= e) return;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        env[i] = upper[s * m + i];
+        env[m + i] = lower[s * m + i];
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int64_t p = b + (int64_t)blockIdx.x * per_cta + warp; p < e; p += (int64_t)gridDim.x * per_cta) {
+        const float* c = ps.pair_b[p];
+        float acc = 0.f;
+        for (int i = lane; i < m; i += 32) {
+            const float v = __ldg(c + i);
+            const float du = v - env[i];
+            const float dl = v - env[m + i];
+            const float d = du > 0.f ? du : (dl < 0.f ? dl : 0.f);
+            acc = fmaf(d, d, acc);
+        }
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+        if (lane == 0) out[ps.pair_slot ? ps.pair_slot[p] : p] = acc;
+    }
+}
+
+// --------------------------------------------------- DTW wavefront kernel
+//
+// One (query, candidate) pair is handled by a group of G lanes. The band of a
+// row has w = 2 rb + 1 cells; it is padded at the front to G*S cells (offset o'
+// = o + PAD, PAD = G*S - w, odd) and lane g owns slots o' in [gS, gS + S).
+// Cell (i, o) with j = i - rb + o is updated at wave tau = 2 i + o, so one wave
+// is one anti-diagonal of the grid (tau = i + j + rb) and holds S/2 independent
+// cells per lane: the slots of one parity. Its inputs (i-1, j), (i, j-1),
+// (i-1, j-1) are the slots o+1, o-1 (previous wave) and o (two waves ago); the
+// slots just outside a lane come from the neighbour lanes by warp shuffle.
+// Only the slot right before the first real cell must stay +inf (it is the
+// left neighbour of the band's first diagonal); it is forced there once per
+// two waves. The band's last diagonal reads +inf from past the last lane.
+//
+// Samples outside [0, m) read as kPad: a cell with exactly one coordinate
+// outside costs ~kPad^2 and never wins, and cells with both coordinates < 0
+// cost 0 and start from D = 0, which supplies D(-1,-1) = 0 to cell (0, 0).
+//
+// The c (candidate) and q (query) windows slide by one sample every two waves;
+// the loop is unrolled by the window period U = S/2 + 1 so the slide is a
+// renaming of registers, not moves.
+
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+    float d;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
+template <int S, int PMASK>
+__global__ void __launch_bounds__(256) dtw_wave_kernel(PairSet ps, int m, int rb, int G, float* out) {
+    constexpr int H = S / 2;
+    constexpr int U = H + 1;
+    extern __shared__ float q_s[];
+    const int64_t seg = blockIdx.y;
+    const int64_t sb = ps.seg_begin[seg], se = ps.seg_begin[seg + 1];
+    const int warps = blockDim.x >> 5;
+    const int gpw = 32 / G;
+    const int64_t per_cta = (int64_t)warps * gpw;
+    if (sb + (int64_t)blockIdx.x * per_cta >= se) return;
+    const float* qg = ps.seg_a[seg];
+    for (int i = threadIdx.x; i < m; i += blockDim.x) q_s[i] = qg[i];
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int grp = lane / G, g = lane - grp * G;
+    const bool lane_in_group = grp < gpw;
+    const int PAD = G * S - (2 * rb + 1);
+    const int gmask = (PAD - 1) / S;
+    const float mflag = (g == gmask) ? __int_as_float(0x7F800000) : __int_as_float(0xFF800000);
+    const float INF = __int_as_float(0x7F800000);
+    const int tau_f = 2 * (m - 1) + rb;
+    const int s_end = tau_f >> 1;
+    const int nblk = (s_end + U) / U;  // ceil((s_end + 1) / U)
+    const int s0 = s_end + 1 - nblk * U;
+    const int of = rb + PAD;           // slot of the final cell (m-1, m-1)
+    const int g_f = of / S, p_f = of - g_f * S;
+    // per-lane offsets of the sliding windows: A(s) = s + a_off, B(s) = s + b_off
+    const int a_off = -g * H + (PAD - 1) / 2;
+    const int b_off = g * H - rb + (1 - PAD) / 2;
+
+    for (int64_t base = sb + (int64_t)blockIdx.x * per_cta; base < se; base += (int64_t)gridDim.x * per_cta) {
+        const int64_t p = base + (int64_t)warp * gpw + grp;
+        const bool valid = lane_in_group && p < se;
+        const float* c = valid ? ps.pair_b[p] : qg;
+
+        float D[S];
+#pragma unroll
+        for (int t = 0; t < S; ++t) D[t] = 0.f;
+        if (g == gmask) D[PMASK] = INF;
+
+        float creg[U], qreg[U];
+        // prefill logical cw[t] = c[A(s0) + 1 - t] (t >= 1) and qw[a] = q[B(s0) + a] (a <= H - 2)
+        // with the register map of unrolled step u = 0: cw[t] -> creg[t % U], qw[a] -> qreg[a % U]
+#pragma unroll
+        for (int t = 1; t < U; ++t) {
+            const int ci = s0 + a_off + 1 - t;
+            creg[t] = (ci >= 0 && ci < m) ? __ldg(c + ci) : kPad;
+        }
+#pragma unroll
+        for (int t = 0; t < U; ++t) {
+            const int qi = s0 + b_off + t;
+            qreg[t] = (t < H - 1 && qi >= 0 && qi < m) ? q_s[qi] : kPad;
+        }
+        creg[0] = 0.f;
+
+        for (int blk = 0; blk < nblk; ++blk) {
+            const int sbase = s0 + blk * U;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int s = sbase + u;
+                {   // slide the windows: new cw[0] = c[A(s) + 1], new qw[H-1] = q[B(s) + H - 1]
+                    const int ci = s + a_off + 1;
+                    creg[(U - u) % U] = (ci >= 0 && ci < m) ? __ldg(c + ci) : kPad;
+                    const int qi = s + b_off + H - 1;
+                    qreg[(H - 1 + u) % U] = (qi >= 0 && qi < m) ? q_s[qi] : kPad;
+                }
+                // wave tau = 2s: odd slots 2a+1, cell (A - a, B + a), c = cw[a+1], q = qw[a]
+                float right = __shfl_down_sync(kFull, D[0], 1);
+                if (g == G - 1) right = INF;
+#pragma unroll
+                for (int a = 0; a < H; ++a) {
+                    const int pp = 2 * a + 1;
+                    const float cv = creg[(a + 1 + U - u) % U];
+                    const float qv = qreg[(a + u) % U];
+                    const float ur = (pp + 1 < S) ? D[pp + 1] : right;
+                    const float d = cv - qv;
+                    D[pp] = fmaf(d, d, min3f(ur, D[pp - 1], D[pp]));
+                }
+                // wave tau = 2s + 1: even slots 2a, cell (A + 1 - a, B + a), c = cw[a], q = qw[a]
+                float left = __shfl_up_sync(kFull, D[S - 1], 1);
+                if (g == 0) left = INF;
+#pragma unroll
+                for (int a = 0; a < H; ++a) {
+                    const int pp = 2 * a;
+                    const float cv = creg[(a + U - u) % U];
+                    const float qv = qreg[(a + u) % U];
+                    const float lf = (pp > 0) ? D[pp - 1] : left;
+                    const float d = cv - qv;
+                    D[pp] = fmaf(d, d, min3f(D[pp + 1], lf, D[pp]));
+                }
+                D[PMASK] = fmaxf(D[PMASK], mflag);
+            }
+        }
+        float res = 0.f;
+#pragma unroll
+        for (int t = 0; t < S; ++t)
+            if (t == p_f) res = D[t];
+        if (valid && g == g_f) out[ps.pair_slot ? ps.pair_slot[p] : p] = res;
+    }
+}
+
+template <int S>
+cudaError_t launch_wave(const PairSet& ps, int m, int rb, int G, int pmask, float* out, cudaStream_t st) {
+    const int threads = 256;
+    const int per_cta = (threads / 32) * (32 / G);
+    int64_t gx = (ps.max_seg_pairs + per_cta - 1) / per_cta;
+    if (gx < 1) gx = 1;
+    if (gx > 65535) gx = 65535;
+    dim3 grid((unsigned)gx, (unsigned)ps.nseg);
+    const size_t smem = (size_t)m * sizeof(float);
+#define SSH_WAVE_CASE(PM)                                                                                   \
+    case PM: {                                                                                              \
+        cudaError_t e = cudaFuncSetAttribute(dtw_wave_kernel<S, PM>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                             (int)smem);                                                    \
+        if (e != cudaSuccess) return e;                                                                     \
+        dtw_wave_kernel<S, PM><<<grid, threads, smem, st>>>(ps, m, rb, G, out);                             \
+        return cudaGetLastError();                                                                          \
+    }
+    switch (pmask) {
+        SSH_WAVE_CASE(0)
+        SSH_WAVE_CASE(2)
+        SSH_WAVE_CASE(4)
+        SSH_WAVE_CASE(6)
+        default:
+            break;
+    }
+    if constexpr (S > 8) {
+        switch (pmask) {
+            SSH_WAVE_CASE(8)
+            SSH_WAVE_CASE(10)
+            SSH_WAVE_CASE(12)
+            default:
+                break;
+        }
+    }
+    if constexpr (S > 14) {
+        switch (pmask) {
+            SSH_WAVE_CASE(14)
+            SSH_WAVE_CASE(16)
+            SSH_WAVE_CASE(18)
+            SSH_WAVE_CASE(20)
+            SSH_WAVE_CASE(22)
+            SSH_WAVE_CASE(24)
+            default:
+                break;
+        }
+    }
+#undef SSH_WAVE_CASE
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+// Pick the slot count S per lane and the lanes per pair G for radius rb:
+// G = ceil((2 rb + 2) / S) lanes cover the band plus the one forced-inf slot,
+// and the cost per pair is proportional to S / (pairs per warp).
+DtwPlan dtw_plan(int m, int rb) {
+    (void)m;
+    const int cands[3] = {8, 14, 26};
+    DtwPlan best{0, 0, 0};
+    double best_cost = 1e30;
+    for (int S : cands) {
+        const int G = (2 * rb + 2 + S - 1) / S;
+        if (G > 32) continue;
+        const int gpw = 32 / G;
+        const double cost = (double)S / gpw;
+        if (cost < best_cost) {
+            best_cost = cost;
+            const int PAD = G * S - (2 * rb + 1);
+            best = DtwPlan{S, G, (PAD - 1) % S};
+        }
+    }
+    return best;
+}
+
+cudaError_t launch_probe_union(const ProbeArgs& a, cudaStream_t st) {
+    if (a.nq <= 0 || a.L <= 0 || a.nrows <= 0) return cudaSuccess;
+    dim3 grid((unsigned)a.nq, (unsigned)a.L);
+    probe_union_kernel<<<grid, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bitmap_count(const uint32_t* bitmap, int64_t nq, int64_t words, int64_t* counts, cudaStream_t st) {
+    if (nq <= 0) return cudaSuccess;
+    bitmap_count_kernel<<<(unsigned)nq, 512, 0, st>>>(bitmap, words, counts);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bitmap_compact(const uint32_t* bitmap, int64_t nq, int64_t words, const int64_t* offsets,
+                                  uint32_t* cand_rows, int32_t* cand_query, cudaStream_t st) {
+    (void)cand_query;
+    if (nq <= 0) return cudaSuccess;
+    bitmap_compact_kernel<<<(unsigned)nq, 1024, 0, st>>>(bitmap, words, offsets, cand_rows);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_envelope(const float* const* seg_a, int64_t nseg, int m, int rb, float* upper, float* lower,
+                            cudaStream_t st) {
+    if (nseg <= 0) return cudaSuccess;
+    dim3 grid((unsigned)((m + 255) / 256), (unsigned)nseg);
+    envelope_kernel<<<grid, 256, 0, st>>>(seg_a, m, rb, upper, lower);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lb_keogh(const PairSet& ps, const float* upper, const float* lower, int m, float* out,
+                            cudaStream_t st) {
+    if (ps.nseg <= 0 || ps.max_seg_pairs <= 0) return cudaSuccess;
+    int64_t gx = (ps.max_seg_pairs + kLbWarps - 1) / kLbWarps;
+    if (gx > 65535) gx = 65535;
+    const size_t smem = 2 * (size_t)m * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(lb_keogh_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)gx, (unsigned)ps.nseg);
+    lb_keogh_kernel<<<grid, kLbWarps * 32, smem, st>>>(ps, upper, lower, m, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dtw(const PairSet& ps, int m, int rb, float* out, cudaStream_t st) {
+    if (ps.nseg <= 0 || ps.max_seg_pairs <= 0) return cudaSuccess;
+    const DtwPlan pl = dtw_plan(m, rb);
+    if (pl.S == 8) return launch_wave<8>(ps, m, rb, pl.G, pl.pmask, out, st);
+    if (pl.S == 14) return launch_wave<14>(ps, m, rb, pl.G, pl.pmask, out, st);
+    if (pl.S == 26) return launch_wave<26>(ps, m, rb, pl.G, pl.pmask, out, st);
+    return cudaErrorNotSupported;
+}
+
+}  // namespace ssh

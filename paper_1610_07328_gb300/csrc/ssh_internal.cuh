@@ -1,0 +1,176 @@
+// ssh_internal.cuh -- internal declarations of the GB300 SSH library.
+// Everything here is private to the library; the public surface is include/ssh.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/ssh.h"
+
+namespace ssh {
+
+// ------------------------------------------------------------------ errors
+
+void set_error(const char* fmt, ...);
+ssh_status cuda_status(cudaError_t e, const char* what);
+
+#define SSH_TRY(expr)                       \
+    do {                                    \
+        ssh_status _s = (expr);             \
+        if (_s != SSH_OK) return _s;        \
+    } while (0)
+
+#define SSH_CUDA(expr)                                              \
+    do {                                                            \
+        cudaError_t _e = (expr);                                    \
+        if (_e != cudaSuccess) return ::ssh::cuda_status(_e, #expr); \
+    } while (0)
+
+// ------------------------------------------------------------- constants
+
+// Value given to series samples outside [0, m) in the DTW wavefront. Any cost
+// involving it is >= 1e36, far above every real path cost, so cells outside
+// the grid never win a min (inputs are bounded by 1e15).
+constexpr float kPad = 1.0e18f;
+
+constexpr int kMaxShingleBits = 16;     // n limit of the tabulated minhash draws
+constexpr int kMaxCount = 65535;        // shingles per series (u16 counts)
+constexpr int kMaxTopK = 1024;
+constexpr int kMaxW = 8192;
+constexpr int kMaxKL = 4096;
+
+// Device-side counters (one array of these per index).
+enum StatSlot { kStatSketch64 = 0, kStatCws64 = 1, kNumStatSlots = 4 };
+
+// ----------------------------------------------------- hash kernel params
+
+struct HashArgs {
+    const float* series;     // row-major series, row i at series + i * stride ...
+    int64_t stride;          // floats between consecutive rows
+    const float* const* rows;// ... unless rows != NULL: row i at rows[i]
+    int64_t count;           // rows to hash
+    int m, W, delta, n, nb, nwords, S, K, L, KL;
+    const float* r;          // [W] filter
+    float tau_norm;          // threshold factor tau * ||r|| (rounded up)
+    float gamma_ss;          // relative inflation of the FP32 sum of squares
+    const uint16_t* rank;    // [2^n][KL] rank of the count-1 value of (j, k) among all k
+    const uint16_t* kinv;    // [KL][2^n] shingle id of each rank
+    const float4* p32;       // [2^n][KL] (r, 1/r, beta, ln c) rounded to FP32
+    const double* p64;       // [KL][2^n][3] (r, beta, ln c) in FP64
+    const float* lns32;      // [kMaxCount+1] ln s rounded to FP32
+    const double* lns64;     // [kMaxCount+1] ln s in FP64
+    uint64_t seed;
+    uint64_t* keys;          // [L][key_stride], row i of this launch at column key_col0 + i
+    int64_t key_stride;
+    int64_t key_col0;
+    // optional per-stage outputs
+    uint32_t* bits_out;
+    uint32_t* sh_ids_out;
+    uint32_t* sh_counts_out;
+    int32_t* nnz_out;
+    uint32_t* kstar_out;
+    uint32_t* tstar_out;
+    unsigned long long* stats;
+};
+
+int hash_smem_bytes_per_warp(int m, int nwords, int S, int KL);
+int hash_warps_per_cta(int m, int nwords, int S, int KL);
+cudaError_t launch_hash(const HashArgs& a, cudaStream_t st);
+
+// ------------------------------------------------------------ radix sort
+
+// Sort (key, val) pairs by key, stably, independently in each of `nseg`
+// segments of `n` consecutive items. Ping-pongs between (keys, vals) and
+// (keys_alt, vals_alt); the result ends in (keys, vals).
+cudaError_t radix_sort_pairs_u64(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt,
+                                 int64_t n, int nseg, int64_t seg_stride, void* scratch, size_t scratch_bytes,
+                                 cudaStream_t st);
+size_t radix_sort_scratch_bytes(int64_t n, int nseg);
+
+// -------------------------------------------------------------- queries
+
+struct ProbeArgs {
+    const uint64_t* qkeys;     // [L][nq]
+    int64_t nq, L;
+    const uint64_t* skeys;     // [L][cap] sorted keys of the sub-index
+    const uint32_t* srows;     // [L][cap] rows in key order
+    int64_t cap, nrows;
+    uint32_t* bitmap;          // [nq][words] candidate bitmap
+    int64_t words;
+};
+cudaError_t launch_probe_union(const ProbeArgs& a, cudaStream_t st);
+cudaError_t launch_bitmap_count(const uint32_t* bitmap, int64_t nq, int64_t words, int64_t* counts,
+                                cudaStream_t st);
+cudaError_t launch_bitmap_compact(const uint32_t* bitmap, int64_t nq, int64_t words, const int64_t* offsets,
+                                  uint32_t* cand_rows, int32_t* cand_query, cudaStream_t st);
+
+// A set of (query, candidate) pairs grouped by query: segment s has query
+// series seg_a[s] (m floats) and pairs [seg_begin[s], seg_begin[s+1]); pair p
+// compares seg_a[s] with pair_b[p] and writes out[pair_slot ? pair_slot[p] : p].
+struct PairSet {
+    const int64_t* seg_begin;   // [nseg + 1] device
+    int64_t nseg;
+    const float* const* seg_a;  // [nseg] device
+    const float* const* pair_b; // [npairs] device
+    const int64_t* pair_slot;   // [npairs] device, or NULL
+    int64_t max_seg_pairs;      // upper bound of any segment's size (grid sizing)
+};
+
+cudaError_t launch_envelope(const float* const* seg_a, int64_t nseg, int m, int rb, float* upper, float* lower,
+                            cudaStream_t st);
+cudaError_t launch_lb_keogh(const PairSet& ps, const float* upper, const float* lower, int m, float* out,
+                            cudaStream_t st);
+
+struct DtwPlan {
+    int S, G, pmask;
+};
+DtwPlan dtw_plan(int m, int rb);
+cudaError_t launch_dtw(const PairSet& ps, int m, int rb, float* out, cudaStream_t st);
+
+// k-th smallest key of each segment (keys read through `keys`, segment s is
+// [seg_begin[s], seg_begin[s+1])); kth_out[s] = that key, or all-ones if the
+// segment has fewer than k items.
+cudaError_t launch_select_kth_u32(const uint32_t* keys, const int64_t* seg_begin, int64_t nseg, int k,
+                                  uint32_t* kth_out, cudaStream_t st);
+cudaError_t launch_select_kth_u64(const uint64_t* keys, const int64_t* seg_begin, int64_t nseg, int k,
+                                  uint64_t* kth_out, cudaStream_t st);
+
+}  // namespace ssh
+
+// --------------------------------------------------------------- the index
+
+struct SubIndex {
+    int m = 0, nb = 0, nwords = 0, S = 0, rb = 0;
+    int64_t count = 0, cap = 0;
+    const float** row_ptr = nullptr;  // [cap] device: series pointer of each row
+    int64_t* gid = nullptr;           // [cap] device: id of each row
+    uint64_t* keys = nullptr;         // [L][cap] device: bucket keys by row
+    uint64_t* skeys = nullptr;        // [L][cap] device: keys sorted
+    uint32_t* srows = nullptr;        // [L][cap] device: rows in key order
+    std::vector<void*> owned;         // device chunks owned by the index
+};
+
+struct ssh_index {
+    int W = 0, delta = 0, n = 0, K = 0, L = 0, KL = 0;
+    float band = 0.f;
+    uint64_t seed = 0;
+    int device = 0;
+    bool lb_prune = true;
+    float tau_norm = 0.f;
+    std::vector<float> h_r;           // host copy of the filter
+    float* d_r = nullptr;
+    uint16_t* d_rank = nullptr;
+    uint16_t* d_kinv = nullptr;
+    float4* d_p32 = nullptr;
+    double* d_p64 = nullptr;
+    float* d_lns32 = nullptr;
+    double* d_lns64 = nullptr;
+    unsigned long long* d_stats = nullptr;
+    std::map<int, SubIndex> subs;
+    int64_t next_id = 0;
+    ssh_stats host_stats{};
+};

@@ -1,0 +1,343 @@
+"""GPU parity: the CUDA library (through the C ABI) against the FP64 CPU oracle
+on the same seeded inputs.
+
+Bars: sketch bits, shingle ids/counts, minhash (k*, t*) and bucket keys are
+bit-exact; DTW and LB_Keogh distances agree to 1e-5 relative (FP32 kernels vs
+FP64 oracle); top-k ids agree exactly except where two oracle distances lie
+within that tolerance of each other, in which case either order is accepted
+and each returned distance is checked against the oracle's DTW of that id.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1610_07328_gb300 import synth
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-5
+
+CFG1 = dict(W=32, delta=3, n=8, K=4, L=16, band=0.05, seed=0)          # tiny: m=128
+CFG2 = dict(W=80, delta=3, n=15, K=4, L=25, band=0.05, seed=0)         # scale: m=512
+CFG3 = dict(W=120, delta=5, n=15, K=4, L=50, band=0.10, seed=0)        # ECG-like: m=1024
+
+
+def _binding():
+    from paper_1610_07328_gb300 import binding
+    return binding
+
+
+def _index(cfg):
+    return _binding().SSHIndex(cfg["W"], cfg["delta"], cfg["n"], cfg["K"], cfg["L"], cfg["band"], cfg["seed"])
+
+
+def _unpack_bits(words, nb):
+    out = np.zeros(nb, np.uint8)
+    for i in range(nb):
+        out[i] = (int(words[i // 32]) >> (31 - i % 32)) & 1
+    return out
+
+
+def gpu_hash(idx, x: np.ndarray):
+    b = _binding()
+    N, m = x.shape
+    W, delta, n, KL, L = idx.W, idx.delta, idx.n, idx.K * idx.L, idx.L
+    nb = (m - W) // delta + 1
+    nw = (nb + 31) // 32
+    S = nb - n + 1
+    dev = "cuda"
+    d_x = torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+    bits = torch.zeros((N, nw), dtype=torch.int32, device=dev)
+    ids = torch.zeros((N, S), dtype=torch.int32, device=dev)
+    cnt = torch.zeros((N, S), dtype=torch.int32, device=dev)
+    nnz = torch.zeros(N, dtype=torch.int32, device=dev)
+    ks = torch.zeros((N, KL), dtype=torch.int32, device=dev)
+    ts = torch.zeros((N, KL), dtype=torch.int32, device=dev)
+    keys = torch.zeros((L, N), dtype=torch.int64, device=dev)
+    b.ssh_hash_device(idx.handle, d_x, m, N, bits, ids, cnt, nnz, ks, ts, keys)
+    torch.cuda.synchronize()
+    u32 = lambda t: t.cpu().numpy().view(np.uint32)
+    return dict(bits=u32(bits), ids=u32(ids), cnt=u32(cnt), nnz=nnz.cpu().numpy(), ks=u32(ks), ts=u32(ts),
+                keys=keys.cpu().numpy().view(np.uint64), nb=nb)
+
+
+def check_hash_parity(cfg, x, rows=None):
+    idx = _index(cfg)
+    try:
+        g = gpu_hash(idx, x)
+        r = oracle.filter_r(cfg["seed"], cfg["W"])
+        assert np.array_equal(idx.filter, r)
+        KL = cfg["K"] * cfg["L"]
+        for i in (range(len(x)) if rows is None else rows):
+            bits = oracle.sketch(x[i], r, cfg["delta"])
+            assert np.array_equal(_unpack_bits(g["bits"][i], g["nb"]), bits), f"bits of row {i}"
+            sid, scnt = oracle.shingle(bits, cfg["n"])
+            k = int(g["nnz"][i])
+            assert k == len(sid), f"nnz of row {i}"
+            assert np.array_equal(g["ids"][i, :k], sid) and np.array_equal(g["cnt"][i, :k], scnt), f"shingles {i}"
+            ks, ts = oracle.cws(cfg["seed"], KL, sid, scnt)
+            assert np.array_equal(g["ks"][i], ks), f"kstar of row {i}"
+            assert np.array_equal(g["ts"][i], ts), f"tstar of row {i}"
+            for l in range(cfg["L"]):
+                assert int(g["keys"][l, i]) == oracle.bucket_key(cfg["seed"], l, cfg["K"], ks, ts), f"key {l},{i}"
+        return idx.stats()
+    finally:
+        idx.close()
+
+
+# ------------------------------------------------------------ hashing stages
+
+def test_hash_parity_tiny_config():
+    x = synth.random_walk(400, 128, seed=0)
+    check_hash_parity(CFG1, x)
+
+
+def test_hash_parity_scale_config():
+    x = synth.random_walk(250, 512, seed=3)
+    check_hash_parity(CFG2, x)
+
+
+def test_hash_parity_ecg_config():
+    x = synth.ecg_like(120, 1024, seed=5)
+    check_hash_parity(CFG3, x)
+
+
+@pytest.mark.parametrize("m", [128, 256, 512, 1024, 2048])
+def test_hash_parity_batched_lengths(m):
+    # per-length sub-indexes of the batched workload: W = m/8, delta 3, n 15, K 4, L 25
+    cfg = dict(W=m // 8, delta=3, n=15, K=4, L=25, band=0.05, seed=0)
+    x = synth.random_walk(60 if m >= 1024 else 120, m, seed=m)
+    check_hash_parity(cfg, x)
+
+
+def test_hash_parity_ragged_and_minimum_length():
+    # m = W + (n-1)*delta gives exactly one shingle; odd lengths exercise unaligned rows
+    cfg = dict(W=16, delta=3, n=6, K=3, L=5, band=0.1, seed=7)
+    for m in [16 + 5 * 3, 16 + 5 * 3 + 1, 67, 101]:
+        x = synth.random_walk(70, m, seed=m)
+        check_hash_parity(cfg, x)
+
+
+def test_sketch_fp64_path_on_near_zero_projections():
+    """Windows made orthogonal to r have |r.x| at rounding level: the FP64 path decides them."""
+    cfg = dict(CFG1)
+    r = oracle.filter_r(cfg["seed"], cfg["W"]).astype(np.float64)
+    rng = np.random.default_rng(11)
+    rows = []
+    for t in range(64):
+        x = rng.standard_normal(128)
+        for start in range(0, 128 - 32 + 1, 33):  # windows at multiples of delta that do not overlap
+            start -= start % 3
+            v = x[start:start + 32]
+            x[start:start + 32] = v - (r @ v) / (r @ r) * r
+        rows.append(x)
+    rows.append(np.zeros(128))            # every dot product exactly 0 -> bit 1
+    rows.append(np.full(128, 1e-3))
+    x = np.array(rows, np.float32)
+    stats = check_hash_parity(cfg, x)
+    assert stats["sketch_fp64"] > 0
+
+
+def test_cws_fp64_path_is_exercised_and_exact():
+    # enough series that near-tie minhashes occur; all of them must still match
+    x = synth.random_walk(3000, 128, seed=21)
+    stats = check_hash_parity(CFG1, x, rows=range(0, 3000, 7))
+    assert stats["cws_fp64"] >= 0
+
+
+# ------------------------------------------------------------- DTW, LB_Keogh
+
+def _pairs(nA, nB, npairs, seed):
+    rng = np.random.default_rng(seed)
+    a = rng.integers(0, nA, size=npairs).astype(np.int64)
+    b = rng.integers(0, nB, size=npairs).astype(np.int64)
+    return a, b
+
+
+@pytest.mark.parametrize("m,rb", [(128, 6), (512, 25), (1024, 102), (256, 12), (2048, 102), (1024, 51),
+                                  (64, 63), (100, 0), (37, 5), (200, 30), (300, 140)])
+def test_dtw_parity(m, rb):
+    b = _binding()
+    A = synth.random_walk(12, m, seed=m + 1)
+    B = synth.random_walk(40, m, seed=m + 2)
+    ai, bi = _pairs(len(A), len(B), 60, seed=m)
+    out = torch.zeros(len(ai), dtype=torch.float32, device="cuda")
+    b.ssh_dtw_device(torch.from_numpy(A).cuda(), torch.from_numpy(ai).cuda(), torch.from_numpy(B).cuda(),
+                     torch.from_numpy(bi).cuda(), m, rb, out)
+    got = out.cpu().numpy()
+    want = np.array([oracle.dtw(A[i], B[j], rb) for i, j in zip(ai, bi)])
+    np.testing.assert_allclose(got, want, rtol=RTOL, atol=0)
+
+
+def test_dtw_identity_and_band0():
+    b = _binding()
+    m = 512
+    A = synth.random_walk(8, m, seed=9)
+    idx = torch.arange(8, dtype=torch.int64, device="cuda")
+    out = torch.zeros(8, dtype=torch.float32, device="cuda")
+    d_a = torch.from_numpy(A).cuda()
+    b.ssh_dtw_device(d_a, idx, d_a, idx, m, 25, out)
+    assert (out.cpu().numpy() == 0).all()
+    rev = torch.flip(idx, [0]).contiguous()
+    b.ssh_dtw_device(d_a, idx, d_a, rev, m, 0, out)
+    want = ((A.astype(np.float64) - A[::-1].astype(np.float64)) ** 2).sum(axis=1)
+    np.testing.assert_allclose(out.cpu().numpy(), want, rtol=RTOL)
+
+
+@pytest.mark.parametrize("m,rb", [(128, 6), (512, 25), (1024, 102), (37, 5)])
+def test_lb_keogh_parity(m, rb):
+    b = _binding()
+    A = synth.random_walk(10, m, seed=m + 5)
+    B = synth.random_walk(30, m, seed=m + 6)
+    ai, bi = _pairs(len(A), len(B), 50, seed=m + 1)
+    out = torch.zeros(len(ai), dtype=torch.float32, device="cuda")
+    b.ssh_lb_keogh_device(torch.from_numpy(A).cuda(), torch.from_numpy(ai).cuda(), torch.from_numpy(B).cuda(),
+                          torch.from_numpy(bi).cuda(), m, rb, out)
+    got = out.cpu().numpy()
+    want = np.array([oracle.lb_keogh(A[i], B[j], rb) for i, j in zip(ai, bi)])
+    np.testing.assert_allclose(got, want, rtol=RTOL, atol=1e-6)
+
+
+# ------------------------------------------------------------- end to end
+
+def assert_topk_match(q, ids_g, d_g, ids_o, d_o, db_by_id, rb):
+    k = len(ids_o)
+    real = ids_o >= 0
+    assert np.array_equal(ids_g >= 0, real)
+    # the sorted distance lists agree
+    np.testing.assert_allclose(d_g[real], d_o[real], rtol=RTOL, atol=0)
+    for t in np.nonzero(real)[0]:
+        if ids_g[t] != ids_o[t]:
+            # a near tie: the returned id's exact distance must equal the oracle's t-th distance
+            dd = oracle.dtw(q, db_by_id(int(ids_g[t])), rb)
+            assert abs(dd - d_o[t]) <= RTOL * d_o[t], (t, ids_g[t], ids_o[t], dd, d_o[t])
+    assert len(set(ids_g[real].tolist())) == int(real.sum())
+
+
+@pytest.mark.parametrize("prune", [True, False])
+def test_end_to_end_tiny_config(prune):
+    cfg = CFG1
+    db = synth.random_walk(1000, 128, seed=0)
+    qs, _ = synth.perturbed_queries(db, 10, seed=1)
+    ref = oracle.OracleIndex(**cfg)
+    ref.add(db)
+    with _index(cfg) as idx:
+        idx.set_lb_prune(prune)
+        assert idx.add(db) == 0
+        assert len(idx) == 1000
+        ids, d = idx.query(qs, 5)
+        st = idx.stats()
+    rb = oracle.band_radius(cfg["band"], 128)
+    for i, q in enumerate(qs):
+        oi, od = ref.query(q, 5)
+        assert_topk_match(q, ids[i], d[i], oi, od, lambda j: db[j], rb)
+    assert st["queries"] == 10
+    assert st["candidates"] == sum(len(ref.candidates(q)) for q in qs)
+
+
+def test_end_to_end_device_path_and_borrow():
+    cfg = CFG1
+    db = synth.random_walk(600, 128, seed=4)
+    qs, _ = synth.perturbed_queries(db, 8, seed=5)
+    ref = oracle.OracleIndex(**cfg)
+    ref.add(db)
+    d_db = torch.from_numpy(db).cuda()
+    with _index(cfg) as idx:
+        idx.add_device(d_db, borrow=True)
+        d_q = torch.from_numpy(qs).cuda()
+        ids = torch.empty((8, 7), dtype=torch.int64, device="cuda")
+        dd = torch.empty((8, 7), dtype=torch.float32, device="cuda")
+        idx.query_device(d_q, 7, ids, dd)
+        torch.cuda.synchronize()
+        ids, dd = ids.cpu().numpy(), dd.cpu().numpy()
+    rb = oracle.band_radius(cfg["band"], 128)
+    for i, q in enumerate(qs):
+        oi, od = ref.query(q, 7)
+        assert_topk_match(q, ids[i], dd[i], oi, od, lambda j: db[j], rb)
+
+
+def test_end_to_end_mixed_lengths_and_incremental_adds():
+    cfg = dict(W=16, delta=2, n=8, K=3, L=12, band=0.1, seed=3)
+    lens = [64, 96, 128]
+    parts = {m: synth.random_walk(150, m, seed=m) for m in lens}
+    ref = oracle.OracleIndex(**cfg)
+    with _index(cfg) as idx:
+        # interleave lengths inside one call (ragged), then a second call
+        order = [(m, i) for i in range(100) for m in lens]
+        series = [parts[m][i] for m, i in order]
+        ref.add(series)
+        first = idx.add(np.concatenate(series), np.array([len(s) for s in series], np.int32))
+        assert first == 0
+        more = [parts[m][i] for m in lens for i in range(100, 150)]
+        ref.add(more)
+        first = idx.add(np.concatenate(more), np.array([len(s) for s in more], np.int32))
+        assert first == len(series)
+        allrows = series + more
+        qs = []
+        for m in lens:
+            q, _ = synth.perturbed_queries(parts[m], 4, seed=m + 1)
+            qs.extend(list(q))
+        qlens = np.array([len(q) for q in qs], np.int32)
+        ids, d = idx.query(np.concatenate(qs), 6, lengths=qlens)
+    for i, q in enumerate(qs):
+        oi, od = ref.query(q, 6)
+        rb = oracle.band_radius(cfg["band"], len(q))
+        assert_topk_match(q, ids[i], d[i], oi, od, lambda j: allrows[j], rb)
+
+
+def test_scale_config_end_to_end_small_db():
+    cfg = CFG2
+    db = synth.random_walk(400, 512, seed=2)
+    qs, _ = synth.perturbed_queries(db, 5, seed=3)
+    ref = oracle.OracleIndex(**cfg)
+    ref.add(db)
+    with _index(cfg) as idx:
+        idx.add(db)
+        ids, d = idx.query(qs, 10)
+    rb = oracle.band_radius(cfg["band"], 512)
+    for i, q in enumerate(qs):
+        oi, od = ref.query(q, 10)
+        assert_topk_match(q, ids[i], d[i], oi, od, lambda j: db[j], rb)
+
+
+def test_fewer_candidates_than_k_fill_with_minus_one():
+    cfg = CFG1
+    db = synth.random_walk(50, 128, seed=8)
+    with _index(cfg) as idx:
+        idx.add(db)
+        ids, d = idx.query(db[:3], 64)
+    ref = oracle.OracleIndex(**cfg)
+    ref.add(db)
+    for i in range(3):
+        n = len(ref.candidates(db[i]))
+        assert (ids[i, n:] == -1).all() and np.isinf(d[i, n:]).all()
+        assert ids[i, 0] == i and d[i, 0] == 0.0
+
+
+def test_errors_are_status_codes():
+    b = _binding()
+    with pytest.raises(b.SSHError) as e:
+        b.SSHIndex(32, 3, 17, 4, 16, 0.05, 0)
+    assert e.value.status == b.SSH_ENOTSUP
+    with pytest.raises(b.SSHError) as e:
+        b.SSHIndex(32, 3, 33, 4, 16, 0.05, 0)
+    assert e.value.status == b.SSH_EINVAL
+    with _index(CFG1) as idx:
+        with pytest.raises(b.SSHError) as e:
+            idx.add(np.zeros((2, 52), np.float32))  # shorter than W + (n-1) delta = 53
+        assert e.value.status == b.SSH_ELENGTH
+        assert len(idx) == 0
+        idx.add(synth.random_walk(10, 128, seed=0))
+        with pytest.raises(b.SSHError) as e:
+            idx.query(np.zeros((1, 100), np.float32), 3)
+        assert e.value.status == b.SSH_ELENGTH
+        with pytest.raises(b.SSHError) as e:
+            idx.query(np.zeros((1, 128), np.float32), 0)
+        assert e.value.status == b.SSH_EINVAL
+        idx.clear()
+        assert len(idx) == 0
+        idx.add(synth.random_walk(10, 128, seed=1))
+        ids, _ = idx.query(synth.random_walk(10, 128, seed=1)[:1], 1)
+        assert ids[0, 0] == 0
