@@ -1,0 +1,475 @@
+#!/usr/bin/env python
+"""Benchmark of the SSH index and query path on one GB300 (or N, one per rank).
+
+One step = the whole hot path over one batch: build the index of N resident
+series (sketch, shingle, weighted minhash, bucket keys, table sort) and answer
+the query batch (hash, probe + union, LB_Keogh, banded DTW, top-k). The JSON
+line reports series hashed per second of step time (value), the query-phase
+throughput, recall@10 against exact DTW, single-query latency, the roofline
+of the dominant kernel group, an end-to-end figure through host buffers, and
+the CPU oracle timed on a bounded sample.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ssh|reference] [--small]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1610_07328_gb300 import synth  # noqa: E402
+
+METRIC = "series hashed/s; queries/s at recall@10≥0.9 vs exact DTW; p50/p99 latency"
+
+# Plain SSH at scale: 1M random-walk series of length 512 (z-normalised, FP32),
+# W=80, delta=3, n=15, K=4, L=25, band 5% of m, 100 queries, top-10; recall
+# against brute-force DTW on a 10k-series subset.
+SCALE = dict(name="plain SSH at scale", N=1_000_000, m=512, W=80, delta=3, n=15, K=4, L=25, band=0.05, seed=0,
+             nq=100, k=10, recall_subset=10_000)
+# Plain SSH, tiny (a quick run): 1000 series x 128, W=32, delta=3, n=8, K=4, L=16, 10 queries, top-5.
+TINY = dict(name="plain SSH tiny", N=1000, m=128, W=32, delta=3, n=8, K=4, L=16, band=0.05, seed=0, nq=10, k=5,
+            recall_subset=1000)
+
+FP32_LANES_PER_SM = 128
+NUM_SMS = 152
+MAX_SM_MHZ = 2070.0
+
+
+def workload_desc(w):
+    return (f"{w['name']}: {w['N']:,} random-walk series x {w['m']} (FP32, z-normalised), W={w['W']} "
+            f"delta={w['delta']} n={w['n']} K={w['K']} L={w['L']} band={w['band']} of m, {w['nq']} perturbed "
+            f"queries, top-{w['k']}")
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            p = json.load(f)
+        return dict(hbm_gbs=float(p["hbm_gbs"]), source="measured")
+    return dict(hbm_gbs=6800.0, source="fallback")
+
+
+def fp32_peak_tflops():
+    # 152 SMs x 128 FP32 lanes x 2 FLOP (FMA) x 2.07 GHz maximum SM clock
+    return NUM_SMS * FP32_LANES_PER_SM * 2 * MAX_SM_MHZ * 1e6 / 1e12
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+            os.close(fd)
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+            if self.gpu_id:
+                cmd += ["-i", self.gpu_id]
+            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        for r in rows:
+            for name, val in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"),
+                                 r[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def gpu_bus_id(torch, dev):
+    try:
+        p = torch.cuda.get_device_properties(dev)
+        return f"{p.pci_domain_id:08X}:{p.pci_bus_id:02X}:{p.pci_device_id:02X}.0"
+    except Exception:
+        return None
+
+
+# -------------------------------------------------------------- CPU oracle
+
+def oracle_sample(w, n_sample: int, n_queries: int, row0: int = 0):
+    """Time the oracle on a bounded sample of the workload and extrapolate the
+    step time: N * (hash time per series) + nq * (query time at n_sample) * N / n_sample
+    (the candidate set, hence the rerank, grows in proportion to the index)."""
+    import oracle
+    db = synth.random_walk(row0 + n_sample, w["m"], seed=w["seed"])[row0:]
+    qs, _ = synth.perturbed_queries(db, n_queries, seed=1)
+    idx = oracle.OracleIndex(w["W"], w["delta"], w["n"], w["K"], w["L"], w["band"], w["seed"])
+    t0 = time.perf_counter()
+    idx.add(db)
+    t1 = time.perf_counter()
+    for q in qs:
+        idx.query(q, w["k"])
+    t2 = time.perf_counter()
+    t_hash = (t1 - t0) / n_sample
+    t_query = (t2 - t1) / n_queries
+    step = w["N"] * t_hash + w["nq"] * t_query * (w["N"] / n_sample)
+    return dict(value=w["N"] / step, seconds=t2 - t0, t_hash=t_hash, t_query=t_query,
+                sample=(f"oracle indexed {n_sample} series and answered {n_queries} queries on them; step time "
+                        f"extrapolated as N*t_hash + nq*t_query*N/{n_sample}"))
+
+
+def run_reference(args, w):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    n_sample, n_q = (1000, 2) if not args.small else (200, 2)
+    vals = []
+    secs = 0.0
+    for s in range(args.warmup + args.steps):
+        r = oracle_sample(w, n_sample, n_q, row0=(s % 5) * n_sample)
+        if s >= args.warmup:
+            vals.append(r["value"])
+            secs += r["seconds"]
+    value = statistics.mean(vals)
+    sample = r["sample"] + f"; each step a different {n_sample}-series slice"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "series/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * w["N"] / value,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_desc(w), "parallelism": "single process, CPU oracle"},
+        "cpu_baseline": {"value": value, "unit": "series/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "series/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def source_digest(paths):
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+KERNEL_SOURCES = {
+    "hash_add": ["paper_1610_07328_gb300/csrc/hash_kernels.cu"],
+    "hash_query": ["paper_1610_07328_gb300/csrc/hash_kernels.cu"],
+    "dtw": ["paper_1610_07328_gb300/csrc/query_kernels.cu"],
+    "lb_keogh": ["paper_1610_07328_gb300/csrc/query_kernels.cu"],
+    "probe_union": ["paper_1610_07328_gb300/csrc/query_kernels.cu"],
+    "table_sort": ["paper_1610_07328_gb300/csrc/sort_kernels.cu"],
+    "topk": ["paper_1610_07328_gb300/csrc/sort_kernels.cu", "paper_1610_07328_gb300/csrc/capi.cu"],
+}
+
+
+def traffic_for(group):
+    """DRAM bytes per launch from a committed ncu summary, if taken on the current source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        t = json.load(f)
+    e = t.get(group)
+    if not e or e.get("source_digest") != source_digest(KERNEL_SOURCES[group]):
+        return None
+    return e.get("bytes_per_launch")
+
+
+def kernel_rooflines(w, times, pk):
+    """Achieved vs peak for each kernel group, from the library's CUDA-event times."""
+    m, L = w["m"], w["L"]
+    out = {}
+    total = sum(v["total_ms"] for v in times.values()) or 1.0
+    for name, v in times.items():
+        calls = max(v["calls"], 1)
+        avg_ms = v["total_ms"] / calls
+        units_per_call = v["units"] / calls
+        e = dict(ms_total=v["total_ms"], calls=v["calls"], launches=v["launches"], avg_ms=avg_ms,
+                 share=v["total_ms"] / total)
+        if name in ("hash_add", "hash_query"):
+            # algorithmic bytes: each series read once (4m B) + L keys written (8 B each)
+            bytes_ = units_per_call * (4 * m + 8 * L)
+            e.update(bound="hbm", unit="GB/s", achieved=bytes_ / (avg_ms * 1e-3) / 1e9, peak=pk["hbm_gbs"])
+        elif name == "dtw":
+            # 3 FLOP per cell: difference, square-and-add (FMA); the 3-way min is not counted
+            flops = units_per_call * 3
+            e.update(bound="alu", unit="TFLOP/s", achieved=flops / (avg_ms * 1e-3) / 1e12, peak=fp32_peak_tflops())
+        elif name == "lb_keogh":
+            bytes_ = units_per_call * 4
+            e.update(bound="hbm", unit="GB/s", achieved=bytes_ / (avg_ms * 1e-3) / 1e9, peak=pk["hbm_gbs"])
+        elif name == "table_sort":
+            # one read and one write of (key, row) = 12 B each per entry
+            bytes_ = units_per_call * 24
+            e.update(bound="hbm", unit="GB/s", achieved=bytes_ / (avg_ms * 1e-3) / 1e9, peak=pk["hbm_gbs"])
+        else:
+            e.update(bound=None, unit=None, achieved=None, peak=None)
+        if e.get("achieved") is not None:
+            e["frac"] = e["achieved"] / e["peak"]
+        out[name] = e
+    return out
+
+
+def exact_topk_gpu(binding, torch, d_q, d_db, rows, m, rb, k):
+    """Brute-force DTW top-k of each query over the given rows (parity-checked DTW kernel)."""
+    nq = d_q.shape[0]
+    out_ids = np.zeros((nq, k), np.int64)
+    rows_t = torch.as_tensor(rows, dtype=torch.int64, device="cuda")
+    for i in range(nq):
+        a_idx = torch.full((len(rows),), i, dtype=torch.int64, device="cuda")
+        d = torch.empty(len(rows), dtype=torch.float32, device="cuda")
+        binding.ssh_dtw_device(d_q, a_idx, d_db, rows_t, m, rb, d)
+        dd = d.cpu().numpy().astype(np.float64)
+        order = np.lexsort((rows, dd))[:k]
+        out_ids[i] = np.asarray(rows)[order]
+    return out_ids
+
+
+def recall(ids, exact):
+    r = []
+    for a, b in zip(ids, exact):
+        got = {int(x) for x in a if x >= 0}
+        r.append(sum(1 for x in b if int(x) in got) / len(b))
+    return float(np.mean(r))
+
+
+def run_gpu(args, w):
+    import torch
+
+    from paper_1610_07328_gb300 import binding
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    N, m, nq, k = w["N"], w["m"], w["nq"], w["k"]
+
+    # inputs: each rank holds its own N-series shard (weak scaling), pinned on the host and resident on the GPU
+    t_gen = time.perf_counter()
+    h_db = torch.empty((N, m), dtype=torch.float32, pin_memory=True)
+    synth.random_walk(N, m, seed=w["seed"] + rank, out=h_db.numpy())
+    sub = synth.random_walk(w["recall_subset"], m, seed=w["seed"])  # rank 0's first rows: query sources
+    h_q_np, src = synth.perturbed_queries(sub, nq, seed=1)
+    h_q = torch.from_numpy(h_q_np).pin_memory()
+    d_db = h_db.to(dev, non_blocking=False)
+    d_q = h_q.to(dev)
+    d_ids = torch.empty((nq, k), dtype=torch.int64, device=dev)
+    d_dists = torch.empty((nq, k), dtype=torch.float32, device=dev)
+    gen_s = time.perf_counter() - t_gen
+
+    idx = binding.SSHIndex(w["W"], w["delta"], w["n"], w["K"], w["L"], w["band"], w["seed"])
+    stream = torch.cuda.current_stream()
+
+    def step():
+        idx.clear()
+        idx.add_device(d_db, borrow=True)
+        idx.query_device(d_q, k, d_ids, d_dists)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    idx.reset_stats()
+    idx.set_kernel_timing(True)
+    sampler = ClockSampler(gpu_bus_id(torch, dev))
+    sampler.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3 * args.steps + 2)]
+    ev[0].record(stream)
+    for s in range(args.steps):
+        ev[1 + 3 * s].record(stream)
+        idx.clear()
+        idx.add_device(d_db, borrow=True)
+        ev[2 + 3 * s].record(stream)
+        idx.query_device(d_q, k, d_ids, d_dists)
+        ev[3 + 3 * s].record(stream)
+    ev[-1].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    idx.set_kernel_timing(False)
+    total_ms = ev[0].elapsed_time(ev[-1])
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    index_ms = statistics.mean(ev[1 + 3 * s].elapsed_time(ev[2 + 3 * s]) for s in range(args.steps))
+    query_ms = statistics.mean(ev[2 + 3 * s].elapsed_time(ev[3 + 3 * s]) for s in range(args.steps))
+    stats = idx.stats()
+    times = idx.kernel_times()
+    ms_per_step = total_ms / args.steps
+    value = N * world / (ms_per_step / 1000.0)
+
+    # results of the last timed step, recall against exact DTW (untimed)
+    res_ids = d_ids.cpu().numpy()
+    rb = int(math.floor(np.float32(w["band"]) * np.float64(m)))
+    rb = min(rb, m - 1)
+    subset_rows = np.arange(w["recall_subset"], dtype=np.int64)
+    extra = {}
+    if rank == 0 and not args.no_recall:
+        d_sub = d_db[: w["recall_subset"]] if w["seed"] + rank == w["seed"] else torch.from_numpy(sub).to(dev)
+        with binding.SSHIndex(w["W"], w["delta"], w["n"], w["K"], w["L"], w["band"], w["seed"]) as sidx:
+            sidx.add_device(d_sub.contiguous())
+            s_ids = torch.empty_like(d_ids)
+            s_d = torch.empty_like(d_dists)
+            sidx.query_device(d_q, k, s_ids, s_d)
+            s_ids = s_ids.cpu().numpy()
+        exact_sub = exact_topk_gpu(binding, torch, d_q, d_sub.contiguous(), subset_rows, m, rb, k)
+        extra["recall_at_10"] = recall(s_ids, exact_sub)
+        extra["recall_at_1"] = float(np.mean([s_ids[i, 0] == exact_sub[i, 0] for i in range(nq)]))
+        if not args.fast:
+            n_full = min(nq, 20)
+            exact_full = exact_topk_gpu(binding, torch, d_q[:n_full].contiguous(), d_db,
+                                        np.arange(N, dtype=np.int64), m, rb, k)
+            extra["recall_at_10_full_db"] = recall(res_ids[:n_full], exact_full)
+            extra["recall_full_db_queries"] = n_full
+
+    # single-query latency: the plain one-query-per-call path
+    lat = []
+    one_ids = torch.empty((1, k), dtype=torch.int64, device=dev)
+    one_d = torch.empty((1, k), dtype=torch.float32, device=dev)
+    for i in range(nq):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        idx.query_device(d_q[i:i + 1], k, one_ids, one_d)
+        e1.record(stream)
+        e1.synchronize()
+        lat.append(e0.elapsed_time(e1))
+    lat_sorted = sorted(lat)
+    p50 = lat_sorted[len(lat) // 2]
+    p99 = lat_sorted[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]
+
+    # end to end through the public host API: H2D of the series and queries, D2H of the results
+    h_db_np = h_db.numpy()
+    h_q_np2 = h_q.numpy()
+    lengths = np.full(N, m, np.int32)
+    qlen = np.full(nq, m, np.int32)
+    e2e_steps = max(2, min(args.steps, 5))
+    idx.clear()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        idx.clear()
+        binding.ssh_index_add(idx.handle, h_db_np, lengths)
+        ids_h, dists_h = binding.ssh_query(idx.handle, h_q_np2, qlen, k)
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t0) * 1000.0 / e2e_steps
+    if dist:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    idx.close()
+
+    pk = peaks()
+    roofs = kernel_rooflines(w, times, pk)
+    dominant = max((n for n in roofs if roofs[n].get("achieved") is not None), key=lambda n: roofs[n]["ms_total"])
+    d = roofs[dominant]
+    roofline = {"kernel": dominant, "bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"],
+                "unit": d["unit"], "frac": d["frac"], "traffic": traffic_for(dominant),
+                "peak_source": pk["source"] if d["unit"] == "GB/s" else "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "series/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": workload_desc(w), "N_per_gpu": N, "m": m, "W": w["W"], "delta": w["delta"],
+                   "n": w["n"], "K": w["K"], "L": w["L"], "band": w["band"], "queries": nq, "k": k,
+                   "parallelism": "one index shard per GPU" if world > 1 else "single GPU",
+                   "l2": "inputs larger than L2 (series %.2f GB per step)" % (N * m * 4 / 1e9),
+                   "step": "index build of N series + one batch of nq queries"},
+        "index_ms": index_ms, "query_ms": query_ms,
+        "series_hashed_per_s_index_phase": N * world / (index_ms / 1000.0),
+        "queries_per_s": nq / (query_ms / 1000.0),
+        "latency_ms": {"p50": p50, "p99": p99, "mode": "one query per call on the built index"},
+        "plain_gpu_path_queries_per_s": 1000.0 / statistics.mean(lat),
+        "candidates_per_query": stats["candidates"] / max(stats["queries"], 1),
+        "candidate_fraction": stats["candidates"] / max(stats["queries"], 1) / N,
+        "dtw_per_query": stats["dtw_computed"] / max(stats["queries"], 1),
+        "fp64_fallbacks": {"sketch_windows": stats["sketch_fp64"], "minhashes": stats["cws_fp64"]},
+        "gpu_launches": stats["kernel_launches"],
+        "roofline": roofline,
+        "kernels": roofs,
+        "e2e": {"value": N * world / (e2e_ms / 1000.0), "unit": "series/s",
+                "h2d_bytes_per_step": N * m * 4 + N * 4 + nq * m * 4 + nq * 4,
+                "d2h_bytes_per_step": nq * k * 12, "steps": e2e_steps,
+                "api": "ssh_index_clear + ssh_index_add(host) + ssh_query(host)"},
+        "clocks": clocks,
+        "setup_s": {"inputs": gen_s},
+        **extra,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        n_s = 10000 if not args.small else 300
+        r = oracle_sample(w, n_s, 10 if not args.small else 3)
+        line["cpu_baseline"] = {"value": r["value"], "unit": "series/s", "cores": 1, "kind": "oracle",
+                                "sample": r["sample"], "seconds": r["seconds"]}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ssh", choices=["ssh", "reference"])
+    ap.add_argument("--small", action="store_true", help="the tiny configuration (quick check)")
+    ap.add_argument("--fast", action="store_true", help="skip the full-database recall")
+    ap.add_argument("--no-recall", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    w = TINY if args.small else SCALE
+    if args.impl == "reference":
+        run_reference(args, w)
+    else:
+        run_gpu(args, w)
+
+
+if __name__ == "__main__":
+    main()

@@ -124,8 +124,13 @@ ssh_status ssh_query_device(ssh_index* idx, const float* d_queries, const int32_
                             int64_t* d_ids, float* d_dists, void* stream);
 
 /* Options. SSH_OPT_LB_PRUNE (default 1): LB_Keogh pruning before DTW in the
- * rerank; 0 computes DTW for every candidate (same results, more work). */
-typedef enum ssh_option { SSH_OPT_LB_PRUNE = 1 } ssh_option;
+ * rerank; 0 computes DTW for every candidate (same results, more work).
+ * SSH_OPT_KERNEL_TIMING (default 0): record CUDA events around each kernel
+ * group on the stream it runs on; read them with ssh_get_kernel_times.
+ * SSH_OPT_HASH_KERNEL (default 0): 0 hashes with the kernel specialised for the
+ * index's (W, delta) and series length when one is compiled in, 1 always with
+ * the generic kernel (same results; a diagnostic and test knob). */
+typedef enum ssh_option { SSH_OPT_LB_PRUNE = 1, SSH_OPT_KERNEL_TIMING = 2, SSH_OPT_HASH_KERNEL = 3 } ssh_option;
 ssh_status ssh_set_option(ssh_index* idx, ssh_option opt, int64_t value);
 
 /* Counters since the last ssh_reset_stats (all cumulative). */
@@ -137,9 +142,25 @@ typedef struct ssh_stats {
     int64_t candidates;        /* sum over queries of |R| (Alg. 2 union) */
     int64_t dtw_computed;      /* candidates whose DTW was computed */
     int64_t lb_pruned;         /* candidates pruned by LB_Keogh */
+    int64_t kernel_launches;   /* kernels launched by calls on this index */
 } ssh_stats;
 ssh_status ssh_get_stats(const ssh_index* idx, ssh_stats* out);
 ssh_status ssh_reset_stats(ssh_index* idx);
+
+/* Device time per kernel group since the last ssh_reset_stats, measured with
+ * CUDA events while SSH_OPT_KERNEL_TIMING is on. Groups: "hash_add" and "hash_query" (units: series),
+ * "table_sort" (units: table entries), "probe_union" (queries x tables),
+ * "lb_keogh" (candidate samples read), "dtw" (DTW cells), "topk" (candidates).
+ * Writes up to `cap` records to out and their number to *count; synchronises
+ * on the recorded events. */
+typedef struct ssh_kernel_time {
+    char name[24];
+    int64_t launches;   /* kernel launches in the group */
+    int64_t calls;      /* timed regions (one region may launch several kernels) */
+    double total_ms;    /* summed event time of the regions */
+    double units;       /* work units processed (see above) */
+} ssh_kernel_time;
+ssh_status ssh_get_kernel_times(ssh_index* idx, ssh_kernel_time* out, int cap, int* count);
 
 /* ---------------------------------------------------------------------------
  * Stage entry points. They run one step of the path on device buffers so that

@@ -18,6 +18,8 @@ from . import build_ext
 SSH_OK, SSH_EINVAL, SSH_ENOMEM, SSH_ECUDA, SSH_ELENGTH, SSH_EBUSY, SSH_ETIMEOUT, SSH_ENOTSUP = range(8)
 SSH_ADD_BORROW = 1
 SSH_OPT_LB_PRUNE = 1
+SSH_OPT_KERNEL_TIMING = 2
+SSH_OPT_HASH_KERNEL = 3
 
 _lib = None
 _lock = threading.Lock()
@@ -31,10 +33,16 @@ class SSHError(RuntimeError):
 
 class ssh_stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in (
-        "series_hashed", "sketch_fp64", "cws_fp64", "queries", "candidates", "dtw_computed", "lb_pruned")]
+        "series_hashed", "sketch_fp64", "cws_fp64", "queries", "candidates", "dtw_computed", "lb_pruned",
+        "kernel_launches")]
 
     def as_dict(self):
         return {n: int(getattr(self, n)) for n, _ in self._fields_}
+
+
+class ssh_kernel_time(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_int64), ("calls", ctypes.c_int64),
+                ("total_ms", ctypes.c_double), ("units", ctypes.c_double)]
 
 
 _P = ctypes.c_void_p
@@ -55,6 +63,8 @@ _SIGS = {
     "ssh_set_option": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int64]),
     "ssh_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(ssh_stats)]),
     "ssh_reset_stats": (ctypes.c_int, [_P]),
+    "ssh_get_kernel_times": (ctypes.c_int, [_P, ctypes.POINTER(ssh_kernel_time), ctypes.c_int,
+                                            ctypes.POINTER(ctypes.c_int)]),
     "ssh_hash_device": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int64, _P] + [_P] * 7),
     "ssh_dtw_device": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _P, _P]),
     "ssh_lb_keogh_device": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _P, _P]),
@@ -187,6 +197,17 @@ def ssh_reset_stats(h) -> None:
     _check(load().ssh_reset_stats(h))
 
 
+def ssh_get_kernel_times(h) -> dict:
+    """{group: {"launches", "calls", "total_ms", "units"}} since the last reset."""
+    cap = 32
+    arr = (ssh_kernel_time * cap)()
+    n = ctypes.c_int()
+    _check(load().ssh_get_kernel_times(h, arr, cap, ctypes.byref(n)))
+    return {arr[i].name.decode(): dict(launches=int(arr[i].launches), calls=int(arr[i].calls),
+                                       total_ms=float(arr[i].total_ms), units=float(arr[i].units))
+            for i in range(min(n.value, cap))}
+
+
 def ssh_hash_device(h, d_series, m: int, count: int, d_bits=None, d_sh_ids=None, d_sh_counts=None, d_nnz=None,
                     d_kstar=None, d_tstar=None, d_keys=None, stream=None) -> None:
     _check(load().ssh_hash_device(h, _dev_ptr(d_series), m, count, _stream(stream), _dev_ptr(d_bits),
@@ -265,6 +286,15 @@ class SSHIndex:
 
     def set_lb_prune(self, on: bool):
         ssh_set_option(self.handle, SSH_OPT_LB_PRUNE, 1 if on else 0)
+
+    def set_hash_kernel(self, generic: bool):
+        ssh_set_option(self.handle, SSH_OPT_HASH_KERNEL, 1 if generic else 0)
+
+    def set_kernel_timing(self, on: bool):
+        ssh_set_option(self.handle, SSH_OPT_KERNEL_TIMING, 1 if on else 0)
+
+    def kernel_times(self) -> dict:
+        return ssh_get_kernel_times(self.handle)
 
     def stats(self) -> dict:
         return ssh_get_stats(self.handle)

@@ -25,6 +25,7 @@
 namespace ssh {
 
 static thread_local char g_err[512] = "";
+std::atomic<long long> g_launches{0};
 
 void set_error(const char* fmt, ...) {
     va_list ap;
@@ -166,6 +167,34 @@ struct ScratchList {
         for (void* p : ptrs) cudaFreeAsync(p, st);
     }
 };
+
+// Records CUDA events around a group of kernels when the index's timing
+// option is on; the events are read (and the device time summed) later by
+// ssh_get_kernel_times.
+struct TimedRegion {
+    ssh_index* idx;
+    cudaStream_t st;
+    const char* name;
+    double units;
+    long long launches0;
+    cudaEvent_t start = nullptr;
+    TimedRegion(ssh_index* i, cudaStream_t s, const char* n, double u)
+        : idx(i), st(s), name(n), units(u), launches0(g_launches.load()) {
+        if (idx->timing && cudaEventCreate(&start) == cudaSuccess) cudaEventRecord(start, st);
+    }
+    ~TimedRegion() {
+        if (!start) return;
+        cudaEvent_t stop;
+        if (cudaEventCreate(&stop) != cudaSuccess) {
+            cudaEventDestroy(start);
+            return;
+        }
+        cudaEventRecord(stop, st);
+        idx->pending.push_back(KernelTimer{name, start, stop, (int)(g_launches.load() - launches0), units});
+    }
+};
+
+double dtw_cells(int m, int rb) { return (double)m * (2.0 * rb + 1.0) - (double)rb * (rb + 1.0); }
 
 // ------------------------------------------------------------ small kernels
 
@@ -347,6 +376,8 @@ HashArgs base_hash_args(const ssh_index* idx, int m, const Geometry& g) {
     const double gw = idx->W * std::ldexp(1.0, -24) / (1.0 - idx->W * std::ldexp(1.0, -24));
     a.gamma_ss = (float)(2.0 * gw);
     a.rank = idx->d_rank;
+    a.rank_stride = (idx->KL + 3) & ~3;
+    a.force_generic = idx->hash_kernel == 1;
     a.kinv = idx->d_kinv;
     a.p32 = idx->d_p32;
     a.p64 = idx->d_p64;
@@ -420,6 +451,7 @@ ssh_status rebuild_tables(ssh_index* idx, SubIndex& s, cudaStream_t st) {
     if (n == 0) return SSH_OK;
     dim3 grid(grid_for(n, 256, 4096), (unsigned)L);
     copy_keys_kernel<<<grid, 256, 0, st>>>(s.keys, s.skeys, s.srows, n, s.cap, L);
+    note_launch();
     SSH_CUDA(cudaGetLastError());
     if (n < 2) return SSH_OK;
     ScratchList sc(st);
@@ -473,6 +505,7 @@ ssh_status add_series(ssh_index* idx, const float* dev, const int32_t* lengths, 
         SSH_TRY(reserve(idx, s, s.count + nrun, st));
         fill_rows_kernel<<<grid_for(nrun, 256, 8192), 256, 0, st>>>(s.row_ptr + s.count, s.gid + s.count, nrun,
                                                                     dev + offs[i], m, id0 + i);
+        note_launch();
         SSH_CUDA(cudaGetLastError());
         HashArgs a = base_hash_args(idx, m, g);
         a.rows = s.row_ptr + s.count;
@@ -480,12 +513,18 @@ ssh_status add_series(ssh_index* idx, const float* dev, const int32_t* lengths, 
         a.keys = s.keys;
         a.key_stride = s.cap;
         a.key_col0 = s.count;
-        SSH_CUDA(launch_hash(a, st));
+        {
+            TimedRegion tr(idx, st, "hash_add", (double)nrun);
+            SSH_CUDA(launch_hash(a, st));
+        }
         s.count += nrun;
         idx->host_stats.series_hashed += nrun;
         i = j;
     }
-    for (int m : touched) SSH_TRY(rebuild_tables(idx, idx->subs[m], st));
+    for (int m : touched) {
+        TimedRegion tr(idx, st, "table_sort", (double)idx->subs[m].count * idx->L);
+        SSH_TRY(rebuild_tables(idx, idx->subs[m], st));
+    }
     SSH_CUDA(cudaStreamSynchronize(st));
     idx->next_id += count;
     if (first_id) *first_id = id0;
@@ -516,7 +555,10 @@ ssh_status query_group(ssh_index* idx, SubIndex& s, const std::vector<const floa
     a.keys = qkeys;
     a.key_stride = nq;
     a.key_col0 = 0;
-    SSH_CUDA(launch_hash(a, st));
+    {
+        TimedRegion tr(idx, st, "hash_query", (double)nq);
+        SSH_CUDA(launch_hash(a, st));
+    }
     idx->host_stats.series_hashed += nq;
 
     // lines 6-9: probe every table, union of the buckets
@@ -527,8 +569,11 @@ ssh_status query_group(ssh_index* idx, SubIndex& s, const std::vector<const floa
     SSH_TRY(sc.get(&counts, nq));
     SSH_CUDA(cudaMemsetAsync(bitmap, 0, (size_t)nq * words * sizeof(uint32_t), st));
     ProbeArgs pa{qkeys, nq, L, s.skeys, s.srows, s.cap, s.count, bitmap, words};
-    SSH_CUDA(launch_probe_union(pa, st));
-    SSH_CUDA(launch_bitmap_count(bitmap, nq, words, counts, st));
+    {
+        TimedRegion tr(idx, st, "probe_union", (double)nq * L);
+        SSH_CUDA(launch_probe_union(pa, st));
+        SSH_CUDA(launch_bitmap_count(bitmap, nq, words, counts, st));
+    }
     std::vector<int64_t> h_counts(nq), h_begin(nq + 1);
     SSH_CUDA(cudaMemcpyAsync(h_counts.data(), counts, nq * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     SSH_CUDA(cudaStreamSynchronize(st));
@@ -555,14 +600,19 @@ ssh_status query_group(ssh_index* idx, SubIndex& s, const std::vector<const floa
     SSH_CUDA(launch_bitmap_compact(bitmap, nq, words, seg_begin, cand_rows, nullptr, st));
     if (C > 0) {
         gather_ptrs_kernel<<<grid_for(C, 256, 8192), 256, 0, st>>>(cand_rows, C, s.row_ptr, pair_b);
+        note_launch();
         fill_f32_kernel<<<grid_for(C, 256, 8192), 256, 0, st>>>(dist, C, __builtin_huge_valf());
+        note_launch();
         SSH_CUDA(cudaGetLastError());
     }
 
     PairSet all{seg_begin, nq, d_qptr, pair_b, nullptr, max_c};
     const int rb = s.rb;
     if (C > 0 && !idx->lb_prune) {
-        SSH_CUDA(launch_dtw(all, m, rb, dist, st));
+        {
+            TimedRegion tr(idx, st, "dtw", (double)C * dtw_cells(m, rb));
+            SSH_CUDA(launch_dtw(all, m, rb, dist, st));
+        }
         idx->host_stats.dtw_computed += C;
     } else if (C > 0) {
         // line 10 with UCR-style pruning: LB_Keogh of every candidate; DTW of the k
@@ -571,8 +621,11 @@ ssh_status query_group(ssh_index* idx, SubIndex& s, const std::vector<const floa
         float *upper, *lower;
         SSH_TRY(sc.get(&upper, (size_t)nq * m));
         SSH_TRY(sc.get(&lower, (size_t)nq * m));
-        SSH_CUDA(launch_envelope(d_qptr, nq, m, rb, upper, lower, st));
-        SSH_CUDA(launch_lb_keogh(all, upper, lower, m, lb, st));
+        {
+            TimedRegion tr(idx, st, "lb_keogh", (double)C * m);
+            SSH_CUDA(launch_envelope(d_qptr, nq, m, rb, upper, lower, st));
+            SSH_CUDA(launch_lb_keogh(all, upper, lower, m, lb, st));
+        }
         uint32_t *T, *U;
         SSH_TRY(sc.get(&T, nq));
         SSH_TRY(sc.get(&U, nq));
@@ -595,9 +648,12 @@ ssh_status query_group(ssh_index* idx, SubIndex& s, const std::vector<const floa
             SSH_CUDA(cudaMemsetAsync(cursor, 0, nq * sizeof(unsigned long long), st));
             dim3 fg(grid_for(max_c, 256, 1024), (unsigned)nq);
             filter_count_kernel<<<fg, 256, 0, st>>>(seg_begin, nq, lb, T, U, shrink, mode, fcount);
+            note_launch();
             exclusive_scan_small_kernel<<<1, 32, 0, st>>>(fcount, nq, fbegin);
+            note_launch();
             filter_scatter_kernel<<<fg, 256, 0, st>>>(seg_begin, nq, lb, T, U, shrink, mode, fbegin, cursor, pair_b,
                                                       fb, fslot);
+            note_launch();
             SSH_CUDA(cudaGetLastError());
             std::vector<int64_t> hf(nq);
             SSH_CUDA(cudaMemcpyAsync(hf.data(), fcount, nq * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
@@ -608,7 +664,10 @@ ssh_status query_group(ssh_index* idx, SubIndex& s, const std::vector<const floa
                 mx = std::max(mx, hf[q]);
             }
             PairSet sub{fbegin, nq, d_qptr, fb, fslot, mx};
-            if (tot > 0) SSH_CUDA(launch_dtw(sub, m, rb, dist, st));
+            if (tot > 0) {
+                TimedRegion tr(idx, st, "dtw", (double)tot * dtw_cells(m, rb));
+                SSH_CUDA(launch_dtw(sub, m, rb, dist, st));
+            }
             idx->host_stats.dtw_computed += tot;
         }
     }
@@ -619,13 +678,18 @@ ssh_status query_group(ssh_index* idx, SubIndex& s, const std::vector<const floa
     uint64_t *tkeys, *kth;
     SSH_TRY(sc.get(&tkeys, C));
     SSH_TRY(sc.get(&kth, nq));
-    if (C > 0) {
-        topk_keys_kernel<<<grid_for(C, 256, 8192), 256, 0, st>>>(dist, cand_rows, C, tkeys);
+    {
+        TimedRegion tr(idx, st, "topk", (double)C);
+        if (C > 0) {
+            topk_keys_kernel<<<grid_for(C, 256, 8192), 256, 0, st>>>(dist, cand_rows, C, tkeys);
+            note_launch();
+            SSH_CUDA(cudaGetLastError());
+        }
+        SSH_CUDA(launch_select_kth_u64(tkeys, seg_begin, nq, k, kth, st));
+        topk_output_kernel<<<(unsigned)nq, 1024, 0, st>>>(tkeys, seg_begin, kth, s.gid, k, d_qpos, d_ids, d_dists);
+        note_launch();
         SSH_CUDA(cudaGetLastError());
     }
-    SSH_CUDA(launch_select_kth_u64(tkeys, seg_begin, nq, k, kth, st));
-    topk_output_kernel<<<(unsigned)nq, 1024, 0, st>>>(tkeys, seg_begin, kth, s.gid, k, d_qpos, d_ids, d_dists);
-    SSH_CUDA(cudaGetLastError());
     SSH_CUDA(cudaStreamSynchronize(st));
     return SSH_OK;
 }
@@ -717,7 +781,8 @@ ssh_status ssh_create(int W, int delta, int n, int K, int L, float band, uint64_
     // Sec. 4.3 draw tables for every (hash j, shingle k)
     const int KL = idx->KL;
     const int64_t nk = (int64_t)1 << n;
-    std::vector<uint16_t> rank((size_t)nk * KL), kinv((size_t)KL * nk);
+    const int KLp = (KL + 3) & ~3;
+    std::vector<uint16_t> rank((size_t)nk * KLp, (uint16_t)0xFFFF), kinv((size_t)KL * nk);
     std::vector<float4> p32((size_t)nk * KL);
     std::vector<double> p64((size_t)KL * nk * 3);
     parallel_for(KL, [&](int64_t j) {
@@ -733,7 +798,7 @@ ssh_status ssh_create(int W, int delta, int n, int K, int L, float band, uint64_
         }
         std::sort(la1.begin(), la1.end());  // (value, id): equal values keep the smaller id first
         for (int64_t rnk = 0; rnk < nk; ++rnk) {
-            rank[(size_t)la1[rnk].second * KL + j] = (uint16_t)rnk;
+            rank[(size_t)la1[rnk].second * KLp + j] = (uint16_t)rnk;
             kinv[(size_t)j * nk + rnk] = (uint16_t)la1[rnk].second;
         }
     });
@@ -772,6 +837,10 @@ void ssh_destroy(ssh_index* idx) {
     cudaSetDevice(idx->device);
     cudaDeviceSynchronize();
     for (auto& kv : idx->subs) free_sub(kv.second);
+    for (auto& t : idx->pending) {
+        cudaEventDestroy(t.start);
+        cudaEventDestroy(t.stop);
+    }
     cudaFree(idx->d_r);
     cudaFree(idx->d_rank);
     cudaFree(idx->d_kinv);
@@ -789,8 +858,44 @@ ssh_status ssh_get_filter(const ssh_index* idx, float* r_out) {
     return SSH_OK;
 }
 
+static ssh_status index_add_impl(ssh_index* idx, const float* series, const int32_t* lengths, int64_t count,
+                                 int64_t* first_id);
+static ssh_status index_add_device_impl(ssh_index* idx, const float* d_series, const int32_t* lengths,
+                                        int64_t count, uint32_t flags, void* stream, int64_t* first_id);
+static ssh_status query_impl(ssh_index* idx, const float* queries, const int32_t* lengths, int64_t nq, int k,
+                             int64_t* ids, float* dists);
+
+// Adds the kernel launches made during one public call to the index's counter.
+struct LaunchCount {
+    ssh_stats* st;
+    long long l0;
+    explicit LaunchCount(const ssh_index* idx)
+        : st(idx ? const_cast<ssh_stats*>(&idx->host_stats) : nullptr), l0(g_launches.load()) {}
+    ~LaunchCount() {
+        if (st) st->kernel_launches += g_launches.load() - l0;
+    }
+};
+
 ssh_status ssh_index_add(ssh_index* idx, const float* series, const int32_t* lengths, int64_t count,
                          int64_t* first_id) {
+    LaunchCount lc(idx);
+    return index_add_impl(idx, series, lengths, count, first_id);
+}
+
+ssh_status ssh_index_add_device(ssh_index* idx, const float* d_series, const int32_t* lengths, int64_t count,
+                                uint32_t flags, void* stream, int64_t* first_id) {
+    LaunchCount lc(idx);
+    return index_add_device_impl(idx, d_series, lengths, count, flags, stream, first_id);
+}
+
+ssh_status ssh_query(ssh_index* idx, const float* queries, const int32_t* lengths, int64_t nq, int k, int64_t* ids,
+                     float* dists) {
+    LaunchCount lc(idx);
+    return query_impl(idx, queries, lengths, nq, k, ids, dists);
+}
+
+static ssh_status index_add_impl(ssh_index* idx, const float* series, const int32_t* lengths, int64_t count,
+                                 int64_t* first_id) {
     if (!idx || (count > 0 && (!series || !lengths)) || count < 0) return fail(SSH_EINVAL, "bad arguments");
     SSH_TRY(check_device(idx));
     if (count == 0) {
@@ -815,8 +920,8 @@ ssh_status ssh_index_add(ssh_index* idx, const float* series, const int32_t* len
     return SSH_OK;
 }
 
-ssh_status ssh_index_add_device(ssh_index* idx, const float* d_series, const int32_t* lengths, int64_t count,
-                                uint32_t flags, void* stream, int64_t* first_id) {
+static ssh_status index_add_device_impl(ssh_index* idx, const float* d_series, const int32_t* lengths,
+                                        int64_t count, uint32_t flags, void* stream, int64_t* first_id) {
     if (!idx || (count > 0 && (!d_series || !lengths)) || count < 0) return fail(SSH_EINVAL, "bad arguments");
     SSH_TRY(check_device(idx));
     cudaStream_t st = (cudaStream_t)stream;
@@ -867,8 +972,8 @@ ssh_status ssh_index_size(const ssh_index* idx, int64_t* count) {
     return SSH_OK;
 }
 
-ssh_status ssh_query(ssh_index* idx, const float* queries, const int32_t* lengths, int64_t nq, int k, int64_t* ids,
-                     float* dists) {
+static ssh_status query_impl(ssh_index* idx, const float* queries, const int32_t* lengths, int64_t nq, int k,
+                             int64_t* ids, float* dists) {
     if (!idx || nq < 0 || (nq > 0 && (!queries || !lengths || !ids || !dists))) return fail(SSH_EINVAL, "bad arguments");
     SSH_TRY(check_device(idx));
     if (nq == 0) return SSH_OK;
@@ -900,6 +1005,7 @@ ssh_status ssh_query_device(ssh_index* idx, const float* d_queries, const int32_
         return fail(SSH_EINVAL, "bad arguments");
     SSH_TRY(check_device(idx));
     if (nq == 0) return SSH_OK;
+    LaunchCount lc(idx);
     return run_query(idx, d_queries, lengths, nq, k, d_ids, d_dists, (cudaStream_t)stream);
 }
 
@@ -908,6 +1014,13 @@ ssh_status ssh_set_option(ssh_index* idx, ssh_option opt, int64_t value) {
     switch (opt) {
         case SSH_OPT_LB_PRUNE:
             idx->lb_prune = value != 0;
+            return SSH_OK;
+        case SSH_OPT_KERNEL_TIMING:
+            idx->timing = value != 0;
+            return SSH_OK;
+        case SSH_OPT_HASH_KERNEL:
+            if (value < 0 || value > 1) return fail(SSH_EINVAL, "SSH_OPT_HASH_KERNEL takes 0 or 1");
+            idx->hash_kernel = (int)value;
             return SSH_OK;
     }
     return fail(SSH_EINVAL, "unknown option %d", (int)opt);
@@ -927,6 +1040,45 @@ ssh_status ssh_reset_stats(ssh_index* idx) {
     if (!idx) return fail(SSH_EINVAL, "NULL index");
     SSH_CUDA(cudaMemset(idx->d_stats, 0, kNumStatSlots * sizeof(unsigned long long)));
     idx->host_stats = ssh_stats{};
+    for (auto& t : idx->pending) {
+        cudaEventDestroy(t.start);
+        cudaEventDestroy(t.stop);
+    }
+    idx->pending.clear();
+    idx->totals.clear();
+    return SSH_OK;
+}
+
+ssh_status ssh_get_kernel_times(ssh_index* idx, ssh_kernel_time* out, int cap, int* count) {
+    if (!idx || !count || (cap > 0 && !out)) return fail(SSH_EINVAL, "NULL argument");
+    for (auto& t : idx->pending) {
+        float ms = 0.f;
+        cudaError_t e = cudaEventSynchronize(t.stop);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t.start, t.stop);
+        cudaEventDestroy(t.start);
+        cudaEventDestroy(t.stop);
+        if (e != cudaSuccess) return cuda_status(e, "kernel timing events");
+        KernelTotals& k = idx->totals[t.name];
+        k.launches += t.launches;
+        k.calls += 1;
+        k.ms += ms;
+        k.units += t.units;
+    }
+    idx->pending.clear();
+    int n = 0;
+    for (auto& kv : idx->totals) {
+        if (n < cap) {
+            ssh_kernel_time& o = out[n];
+            memset(&o, 0, sizeof(o));
+            snprintf(o.name, sizeof(o.name), "%s", kv.first.c_str());
+            o.launches = kv.second.launches;
+            o.calls = kv.second.calls;
+            o.total_ms = kv.second.ms;
+            o.units = kv.second.units;
+        }
+        ++n;
+    }
+    *count = n;
     return SSH_OK;
 }
 
@@ -952,6 +1104,7 @@ ssh_status ssh_hash_device(const ssh_index* idx, const float* d_series, int32_t 
     a.nnz_out = d_nnz;
     a.kstar_out = d_kstar;
     a.tstar_out = d_tstar;
+    LaunchCount lc(idx);
     SSH_CUDA(launch_hash(a, (cudaStream_t)stream));
     return SSH_OK;
 }

@@ -1,0 +1,139 @@
+// hash_common.cuh -- device pieces shared by the two hash kernels: the bucket
+// key mix, the certified FP32 evaluation of consistent weighted sampling
+// (Sec. 4.3, Ioffe's ICWS) and its exact FP64 recomputation.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ssh_internal.cuh"
+
+namespace ssh {
+
+// splitmix64 output finalizer (Steele, Lea & Flood, OOPSLA'14).
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Algorithm 1 bucket key of table l from its K (k*, t*) pairs.
+__device__ __forceinline__ uint64_t bucket_key(uint64_t seed, int l, int K, const uint32_t* kst,
+                                               const uint32_t* tst) {
+    uint64_t h = seed ^ (0x9E3779B97F4A7C15ull * (uint64_t)(l + 1));
+    for (int i = 0; i < K; ++i) {
+        const int j = l * K + i;
+        h = mix64(h ^ (((uint64_t)kst[j] << 32) | (uint64_t)tst[j]));
+    }
+    return h;
+}
+
+// FP64 recomputation of one hash j over the whole weighted set (ids ascending),
+// in the order of the definition: t = floor(ln S / r + beta),
+// ln a = ln c - r ((t - beta) + 1); the smallest ln a wins, ties to the smaller id.
+__device__ inline void cws_fp64(const HashArgs& a, int j, const uint32_t* cid, const uint32_t* ccnt, int nnz,
+                                uint32_t* kout, uint32_t* tout) {
+    const size_t nk = (size_t)1 << a.n;
+    double best = __longlong_as_double(0x7FF0000000000000ll);  // +inf
+    uint32_t bk = 0, bt = 0;
+    for (int e = 0; e < nnz; ++e) {
+        const uint32_t k = cid[e];
+        const double* p = a.p64 + ((size_t)j * nk + k) * 3;
+        const double r = p[0], beta = p[1], lnc = p[2];
+        const double lns = a.lns64[ccnt[e]];
+        const double t = floor(__dadd_rn(__ddiv_rn(lns, r), beta));
+        const double la = __dsub_rn(lnc, __dmul_rn(r, __dadd_rn(__dsub_rn(t, beta), 1.0)));
+        if (la < best) {
+            best = la;
+            bk = k;
+            bt = (uint32_t)t;
+        }
+    }
+    *kout = bk;
+    *tout = bt;
+}
+
+constexpr float kTwoPowMinus21 = 4.76837158203125e-07f;  // 8 units in the last place of FP32
+constexpr float kRelWidth = 1.0e-6f;                      // >= 8 ulp: also the 1e-6 relative-gap rule
+
+// FP32 evaluation of one repeated shingle (count s >= 2) for one hash, with an
+// interval that contains the FP64 value of the definition, tracked as a running
+// certified argmin. The interval's half width is 1e-6 * (|ln c| + r (t + 1 - beta)),
+// at least 8 ulp of every operand, so it covers the rounding of ln c, r, 1/r,
+// ln s and of the three FP32 operations against the exact value.
+struct CwsTrack {
+    float la, hi, lo1, lo2;
+    uint32_t k, t, klo1;
+    bool unsure;
+
+    __device__ __forceinline__ void init() {
+        la = __int_as_float(0x7F800000);
+        hi = 0.f;
+        lo1 = la;
+        lo2 = la;
+        k = 0xFFFFFFFFu;
+        t = 0;
+        klo1 = 0xFFFFFFFFu;
+        unsure = false;
+    }
+
+    // p = (r, 1/r, beta, ln c); ls = ln s in FP32; ids arrive in any order
+    __device__ __forceinline__ void add(const float4 p, float ls, uint32_t id) {
+        const float P = __fmul_ru(ls, p.y);
+        const float x = fmaf(ls, p.y, p.z);
+        const float ex = __fmul_ru(__fadd_ru(P, 1.0f), kTwoPowMinus21);
+        const float f1 = floorf(__fsub_rd(x, ex));
+        const float f2 = floorf(__fadd_ru(x, ex));
+        unsure |= !(P < 1048576.0f) || (f1 != f2);
+        const float v = (f1 + 1.0f) - p.z;
+        const float l = fmaf(-p.x, v, p.w);
+        const float er = __fmul_ru(__fadd_ru(fabsf(p.w), __fmul_ru(p.x, v)), kRelWidth);
+        const float lo = __fsub_rd(l, er), h = __fadd_ru(l, er);
+        if (l < la || (l == la && id < k)) {
+            la = l;
+            hi = h;
+            k = id;
+            t = (uint32_t)f1;
+        }
+        if (lo < lo1) {
+            lo2 = lo1;
+            lo1 = lo;
+            klo1 = id;
+        } else if (lo < lo2) {
+            lo2 = lo;
+        }
+    }
+};
+
+// Combine the exact count-1 winner (by rank; kA = its id, pA its draws) with the
+// repeated-shingle track. Returns false when the FP32 decision is not certain.
+__device__ __forceinline__ bool cws_decide(bool hasA, uint32_t kA, float4 pA, const CwsTrack& b, uint32_t* ks,
+                                           uint32_t* ts) {
+    const bool hasB = b.k != 0xFFFFFFFFu;
+    if (!hasB) {
+        *ks = kA;
+        *ts = 0;
+        return hasA;
+    }
+    const float minLoOther = (b.klo1 != b.k) ? b.lo1 : b.lo2;
+    if (!hasA) {
+        *ks = b.k;
+        *ts = b.t;
+        return !b.unsure && b.hi < minLoOther;
+    }
+    const float v = 1.0f - pA.z;  // exact: beta is an odd multiple of 2^-24 in (0,1)
+    const float aLa = fmaf(-pA.x, v, pA.w);
+    const float er = __fmul_ru(__fadd_ru(fabsf(pA.w), __fmul_ru(pA.x, v)), kRelWidth);
+    const float aLo = __fsub_rd(aLa, er), aHi = __fadd_ru(aLa, er);
+    const bool winA = (aLa < b.la) || (aLa == b.la && kA < b.k);
+    if (winA) {
+        *ks = kA;
+        *ts = 0;
+        return !b.unsure && aHi < b.lo1;
+    }
+    *ks = b.k;
+    *ts = b.t;
+    return !b.unsure && b.hi < aLo && b.hi < minLoOther;
+}
+
+}  // namespace ssh

@@ -21,6 +21,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "hash_common.cuh"
 #include "ssh_internal.cuh"
 
 namespace ssh {
@@ -54,37 +55,6 @@ __host__ __device__ inline WarpSmem warp_layout(int m, int nwords, int S, int KL
     L.tst = off;  off += align16(4 * KL);
     L.total = off;
     return L;
-}
-
-// splitmix64 output finalizer (Steele, Lea & Flood, OOPSLA'14).
-__device__ __forceinline__ uint64_t mix64(uint64_t z) {
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
-}
-
-// FP64 recomputation of one hash j over the whole weighted set, in the order
-// of the definition: t = floor(ln S / r + beta); ln a = ln c - r ((t - beta) + 1).
-__device__ void cws_fp64(const HashArgs& a, int j, const uint32_t* cid, const uint32_t* ccnt, int nnz,
-                         uint32_t* kout, uint32_t* tout) {
-    const size_t nk = (size_t)1 << a.n;
-    double best = __longlong_as_double(0x7FF0000000000000ll);  // +inf
-    uint32_t bk = 0, bt = 0;
-    for (int e = 0; e < nnz; ++e) {
-        uint32_t k = cid[e];
-        const double* p = a.p64 + ((size_t)j * nk + k) * 3;
-        double r = p[0], beta = p[1], lnc = p[2];
-        double lns = a.lns64[ccnt[e]];
-        double t = floor(__dadd_rn(__ddiv_rn(lns, r), beta));
-        double la = __dsub_rn(lnc, __dmul_rn(r, __dadd_rn(__dsub_rn(t, beta), 1.0)));
-        if (la < best) {
-            best = la;
-            bk = k;
-            bt = (uint32_t)t;
-        }
-    }
-    *kout = bk;
-    *tout = bt;
 }
 
 __global__ void __launch_bounds__(kMaxWarpsPerCta * 32) hash_kernel(HashArgs a, int warps_per_cta) {
@@ -214,84 +184,28 @@ __global__ void __launch_bounds__(kMaxWarpsPerCta * 32) hash_kernel(HashArgs a, 
         const int j = j0 + lane;
         if (j < KL) {
             uint32_t rmin = 0xFFFFFFFFu;
-            float bLa = __int_as_float(0x7F800000), bHi = 0.f;
-            uint32_t bK = 0xFFFFFFFFu, bT = 0;
-            float lo1 = __int_as_float(0x7F800000), lo2 = lo1;
-            uint32_t klo1 = 0xFFFFFFFFu;
-            bool unsure = false;
+            bool hasA = false;
+            CwsTrack tr;
+            tr.init();
             for (int e = 0; e < nnz; ++e) {
                 const uint32_t k = cid[e];
                 const uint32_t s = ccnt[e];
                 if (s == 1) {
-                    uint32_t rk = __ldg(a.rank + (size_t)k * KL + j);
-                    rmin = min(rmin, rk);
+                    rmin = min(rmin, (uint32_t)__ldg(a.rank + (size_t)k * a.rank_stride + j));
+                    hasA = true;
                 } else {
-                    const float4 p = __ldg(a.p32 + (size_t)k * KL + j);  // (r, 1/r, beta, ln c)
-                    const float ls = __ldg(a.lns32 + s);
-                    const float P = __fmul_ru(ls, p.y);
-                    const float x = fmaf(ls, p.y, p.z);
-                    const float ex = __fmul_ru(__fadd_ru(P, 1.0f), 4.76837158203125e-07f);  // 2^-21
-                    const float f1 = floorf(__fsub_rd(x, ex));
-                    const float f2 = floorf(__fadd_ru(x, ex));
-                    unsure |= !(P < 1048576.0f) || (f1 != f2);
-                    const float v = (f1 + 1.0f) - p.z;
-                    const float la = fmaf(-p.x, v, p.w);
-                    const float er = __fmul_ru(__fadd_ru(fabsf(p.w), __fmul_ru(p.x, v)), 1.0e-6f);
-                    const float lo = __fsub_rd(la, er), hi = __fadd_ru(la, er);
-                    if (la < bLa) {  // ids ascend, so a strict < keeps the smaller id on ties
-                        bLa = la;
-                        bHi = hi;
-                        bK = k;
-                        bT = (uint32_t)f1;
-                    }
-                    if (lo < lo1) {
-                        lo2 = lo1;
-                        lo1 = lo;
-                        klo1 = k;
-                    } else if (lo < lo2) {
-                        lo2 = lo;
-                    }
+                    tr.add(__ldg(a.p32 + (size_t)k * KL + j), __ldg(a.lns32 + s), k);
                 }
             }
-            uint32_t ks = 0, ts = 0;
-            const bool hasA = rmin != 0xFFFFFFFFu;
-            const bool hasB = bK != 0xFFFFFFFFu;
-            float aLa = 0.f, aLo = 0.f, aHi = 0.f;
-            uint32_t kA = 0;
+            uint32_t kA = 0, ks, ts;
+            float4 pA = make_float4(0.f, 0.f, 0.f, 0.f);
             if (hasA) {
                 kA = __ldg(a.kinv + (size_t)j * nk + rmin);
-                const float4 p = __ldg(a.p32 + (size_t)kA * KL + j);
-                const float v = 1.0f - p.z;  // exact: beta is a multiple of 2^-24 in (0,1)
-                aLa = fmaf(-p.x, v, p.w);
-                const float er = __fmul_ru(__fadd_ru(fabsf(p.w), __fmul_ru(p.x, v)), 1.0e-6f);
-                aLo = __fsub_rd(aLa, er);
-                aHi = __fadd_ru(aLa, er);
+                pA = __ldg(a.p32 + (size_t)kA * KL + j);
             }
-            bool certain;
-            bool winA;
-            if (!hasB) {
-                winA = true;
-                certain = true;
-            } else if (!hasA) {
-                winA = false;
-                certain = bHi < ((klo1 != bK) ? lo1 : lo2);
-            } else {
-                winA = (aLa < bLa) || (aLa == bLa && kA < bK);
-                if (winA) {
-                    certain = aHi < lo1;
-                } else {
-                    certain = (bHi < aLo) && (bHi < ((klo1 != bK) ? lo1 : lo2));
-                }
-            }
-            if (unsure || !certain) {
+            if (!cws_decide(hasA, kA, pA, tr, &ks, &ts)) {
                 cws_fp64(a, j, cid, ccnt, nnz, &ks, &ts);
                 c64 += 1;
-            } else if (winA) {
-                ks = kA;
-                ts = 0;
-            } else {
-                ks = bK;
-                ts = bT;
             }
             kst[j] = ks;
             tst[j] = ts;
@@ -306,16 +220,9 @@ __global__ void __launch_bounds__(kMaxWarpsPerCta * 32) hash_kernel(HashArgs a, 
         }
 
     // ---- Algorithm 1: one bucket key per table from its K hashes
-    if (a.keys) {
-        for (int l = lane; l < a.L; l += 32) {
-            uint64_t h = a.seed ^ (0x9E3779B97F4A7C15ull * (uint64_t)(l + 1));
-            for (int i = 0; i < a.K; ++i) {
-                const int j = l * a.K + i;
-                h = mix64(h ^ (((uint64_t)kst[j] << 32) | (uint64_t)tst[j]));
-            }
-            a.keys[(int64_t)l * a.key_stride + a.key_col0 + row] = h;
-        }
-    }
+    if (a.keys)
+        for (int l = lane; l < a.L; l += 32)
+            a.keys[(int64_t)l * a.key_stride + a.key_col0 + row] = bucket_key(a.seed, l, a.K, kst, tst);
 }
 
 }  // namespace
@@ -329,7 +236,7 @@ int hash_warps_per_cta(int m, int nwords, int S, int KL) {
     return w;
 }
 
-cudaError_t launch_hash(const HashArgs& a, cudaStream_t st) {
+cudaError_t launch_hash_generic(const HashArgs& a, cudaStream_t st) {
     if (a.count <= 0) return cudaSuccess;
     const int wpc = hash_warps_per_cta(a.m, a.nwords, a.S, a.KL);
     const size_t smem = (size_t)align16(4 * a.W) + (size_t)wpc * hash_smem_bytes_per_warp(a.m, a.nwords, a.S, a.KL);
@@ -338,7 +245,14 @@ cudaError_t launch_hash(const HashArgs& a, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     const int64_t grid = (a.count + wpc - 1) / wpc;
     hash_kernel<<<(unsigned)grid, wpc * 32, smem, st>>>(a, wpc);
+    note_launch();
     return cudaGetLastError();
+}
+
+cudaError_t launch_hash(const HashArgs& a, cudaStream_t st) {
+    if (a.count <= 0) return cudaSuccess;
+    if (!a.force_generic && hash_fast_supported(a)) return launch_hash_fast(a, st);
+    return launch_hash_generic(a, st);
 }
 
 }  // namespace ssh

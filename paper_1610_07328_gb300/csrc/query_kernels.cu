@@ -296,6 +296,7 @@ cudaError_t launch_wave(const PairSet& ps, int m, int rb, int G, int pmask, floa
                                              (int)smem);                                                    \
         if (e != cudaSuccess) return e;                                                                     \
         dtw_wave_kernel<S, PM><<<grid, threads, smem, st>>>(ps, m, rb, G, out);                             \
+        note_launch();                                                                                      \
         return cudaGetLastError();                                                                          \
     }
     switch (pmask) {
@@ -359,12 +360,14 @@ cudaError_t launch_probe_union(const ProbeArgs& a, cudaStream_t st) {
     if (a.nq <= 0 || a.L <= 0 || a.nrows <= 0) return cudaSuccess;
     dim3 grid((unsigned)a.nq, (unsigned)a.L);
     probe_union_kernel<<<grid, 256, 0, st>>>(a);
+    note_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_bitmap_count(const uint32_t* bitmap, int64_t nq, int64_t words, int64_t* counts, cudaStream_t st) {
     if (nq <= 0) return cudaSuccess;
     bitmap_count_kernel<<<(unsigned)nq, 512, 0, st>>>(bitmap, words, counts);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -373,6 +376,7 @@ cudaError_t launch_bitmap_compact(const uint32_t* bitmap, int64_t nq, int64_t wo
     (void)cand_query;
     if (nq <= 0) return cudaSuccess;
     bitmap_compact_kernel<<<(unsigned)nq, 1024, 0, st>>>(bitmap, words, offsets, cand_rows);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -381,6 +385,7 @@ cudaError_t launch_envelope(const float* const* seg_a, int64_t nseg, int m, int 
     if (nseg <= 0) return cudaSuccess;
     dim3 grid((unsigned)((m + 255) / 256), (unsigned)nseg);
     envelope_kernel<<<grid, 256, 0, st>>>(seg_a, m, rb, upper, lower);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -394,6 +399,7 @@ cudaError_t launch_lb_keogh(const PairSet& ps, const float* upper, const float* 
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)gx, (unsigned)ps.nseg);
     lb_keogh_kernel<<<grid, kLbWarps * 32, smem, st>>>(ps, upper, lower, m, out);
+    note_launch();
     return cudaGetLastError();
 }
 

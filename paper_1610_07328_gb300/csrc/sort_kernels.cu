@@ -179,9 +179,12 @@ cudaError_t radix_sort_pairs_u64(uint64_t* keys, uint32_t* vals, uint64_t* keys_
     dim3 grid((unsigned)ntiles, (unsigned)nseg);
     for (int shift = 0; shift < 64; shift += 8) {
         radix_hist_kernel<<<grid, kSortThreads, 0, st>>>(kin, n, seg_stride, shift, (int)ntiles, counts);
+        note_launch();
         radix_scan_kernel<<<nseg, 1024, 0, st>>>(counts, (int)ntiles);
+        note_launch();
         radix_scatter_kernel<<<grid, kSortThreads, 0, st>>>(kin, vin, kout, vout, n, seg_stride, shift, (int)ntiles,
                                                             counts);
+        note_launch();
         uint64_t* tk = kin; kin = kout; kout = tk;
         uint32_t* tv = vin; vin = vout; vout = tv;
     }
@@ -192,6 +195,7 @@ cudaError_t launch_select_kth_u32(const uint32_t* keys, const int64_t* seg_begin
                                   uint32_t* kth_out, cudaStream_t st) {
     if (nseg <= 0) return cudaSuccess;
     select_kth_kernel<uint32_t><<<(unsigned)nseg, 512, 0, st>>>(keys, seg_begin, k, kth_out);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -201,6 +205,7 @@ cudaError_t launch_select_kth_u64(const uint64_t* keys, const int64_t* seg_begin
     select_kth_kernel<unsigned long long><<<(unsigned)nseg, 512, 0, st>>>(
         reinterpret_cast<const unsigned long long*>(keys), seg_begin, k,
         reinterpret_cast<unsigned long long*>(kth_out));
+    note_launch();
     return cudaGetLastError();
 }
 

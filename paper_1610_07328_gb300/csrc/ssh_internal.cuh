@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <map>
 #include <string>
 #include <vector>
@@ -29,6 +30,10 @@ ssh_status cuda_status(cudaError_t e, const char* what);
         cudaError_t _e = (expr);                                    \
         if (_e != cudaSuccess) return ::ssh::cuda_status(_e, #expr); \
     } while (0)
+
+// Kernel launches made by this library in the calling process (all threads).
+extern std::atomic<long long> g_launches;
+inline void note_launch(int n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 // ------------------------------------------------------------- constants
 
@@ -57,7 +62,9 @@ struct HashArgs {
     const float* r;          // [W] filter
     float tau_norm;          // threshold factor tau * ||r|| (rounded up)
     float gamma_ss;          // relative inflation of the FP32 sum of squares
-    const uint16_t* rank;    // [2^n][KL] rank of the count-1 value of (j, k) among all k
+    const uint16_t* rank;    // [2^n][rank_stride] rank of the count-1 value of (j, k) among all k
+    int rank_stride;         // KL rounded up to a multiple of 4 (row padding holds 0xFFFF)
+    int force_generic;       // 1: use the generic kernel even when a specialised one exists
     const uint16_t* kinv;    // [KL][2^n] shingle id of each rank
     const float4* p32;       // [2^n][KL] (r, 1/r, beta, ln c) rounded to FP32
     const double* p64;       // [KL][2^n][3] (r, beta, ln c) in FP64
@@ -77,6 +84,9 @@ struct HashArgs {
     unsigned long long* stats;
 };
 
+bool hash_fast_supported(const HashArgs& a);
+cudaError_t launch_hash_fast(const HashArgs& a, cudaStream_t st);
+cudaError_t launch_hash_generic(const HashArgs& a, cudaStream_t st);
 int hash_smem_bytes_per_warp(int m, int nwords, int S, int KL);
 int hash_warps_per_cta(int m, int nwords, int S, int KL);
 cudaError_t launch_hash(const HashArgs& a, cudaStream_t st);
@@ -154,12 +164,28 @@ struct SubIndex {
     std::vector<void*> owned;         // device chunks owned by the index
 };
 
+struct KernelTimer {
+    std::string name;
+    cudaEvent_t start, stop;
+    int launches;
+    double units;
+};
+
+struct KernelTotals {
+    int64_t launches = 0, calls = 0;
+    double ms = 0.0, units = 0.0;
+};
+
 struct ssh_index {
     int W = 0, delta = 0, n = 0, K = 0, L = 0, KL = 0;
+    bool timing = false;
+    std::vector<KernelTimer> pending;
+    std::map<std::string, KernelTotals> totals;
     float band = 0.f;
     uint64_t seed = 0;
     int device = 0;
     bool lb_prune = true;
+    int hash_kernel = 0;              // 0: fastest available, 1: always the generic kernel
     float tau_norm = 0.f;
     std::vector<float> h_r;           // host copy of the filter
     float* d_r = nullptr;

@@ -63,9 +63,10 @@ def gpu_hash(idx, x: np.ndarray):
                 keys=keys.cpu().numpy().view(np.uint64), nb=nb)
 
 
-def check_hash_parity(cfg, x, rows=None):
+def check_hash_parity(cfg, x, rows=None, generic=False):
     idx = _index(cfg)
     try:
+        idx.set_hash_kernel(generic)
         g = gpu_hash(idx, x)
         r = oracle.filter_r(cfg["seed"], cfg["W"])
         assert np.array_equal(idx.filter, r)
@@ -89,27 +90,41 @@ def check_hash_parity(cfg, x, rows=None):
 
 # ------------------------------------------------------------ hashing stages
 
-def test_hash_parity_tiny_config():
+KERNELS = pytest.mark.parametrize("generic", [False, True], ids=["specialised", "generic"])
+
+
+@KERNELS
+def test_hash_parity_tiny_config(generic):
     x = synth.random_walk(400, 128, seed=0)
-    check_hash_parity(CFG1, x)
+    check_hash_parity(CFG1, x, generic=generic)
 
 
-def test_hash_parity_scale_config():
+@KERNELS
+def test_hash_parity_scale_config(generic):
     x = synth.random_walk(250, 512, seed=3)
-    check_hash_parity(CFG2, x)
+    check_hash_parity(CFG2, x, generic=generic)
 
 
-def test_hash_parity_ecg_config():
+@KERNELS
+def test_hash_parity_ecg_config(generic):
     x = synth.ecg_like(120, 1024, seed=5)
-    check_hash_parity(CFG3, x)
+    check_hash_parity(CFG3, x, generic=generic)
 
 
+@KERNELS
 @pytest.mark.parametrize("m", [128, 256, 512, 1024, 2048])
-def test_hash_parity_batched_lengths(m):
+def test_hash_parity_batched_lengths(m, generic):
     # per-length sub-indexes of the batched workload: W = m/8, delta 3, n 15, K 4, L 25
     cfg = dict(W=m // 8, delta=3, n=15, K=4, L=25, band=0.05, seed=0)
     x = synth.random_walk(60 if m >= 1024 else 120, m, seed=m)
-    check_hash_parity(cfg, x)
+    check_hash_parity(cfg, x, generic=generic)
+
+
+@KERNELS
+def test_hash_parity_ecg_like_scale_params(generic):
+    # repeated-shingle heavy input (periodic beats): exercises the FP32 interval track
+    x = synth.ecg_like(200, 512, seed=9)
+    check_hash_parity(CFG2, x, generic=generic)
 
 
 def test_hash_parity_ragged_and_minimum_length():
@@ -120,7 +135,8 @@ def test_hash_parity_ragged_and_minimum_length():
         check_hash_parity(cfg, x)
 
 
-def test_sketch_fp64_path_on_near_zero_projections():
+@KERNELS
+def test_sketch_fp64_path_on_near_zero_projections(generic):
     """Windows made orthogonal to r have |r.x| at rounding level: the FP64 path decides them."""
     cfg = dict(CFG1)
     r = oracle.filter_r(cfg["seed"], cfg["W"]).astype(np.float64)
@@ -136,15 +152,16 @@ def test_sketch_fp64_path_on_near_zero_projections():
     rows.append(np.zeros(128))            # every dot product exactly 0 -> bit 1
     rows.append(np.full(128, 1e-3))
     x = np.array(rows, np.float32)
-    stats = check_hash_parity(cfg, x)
+    stats = check_hash_parity(cfg, x, generic=generic)
     assert stats["sketch_fp64"] > 0
 
 
-def test_cws_fp64_path_is_exercised_and_exact():
+@KERNELS
+def test_cws_fp64_path_is_exercised_and_exact(generic):
     # enough series that near-tie minhashes occur; all of them must still match
-    x = synth.random_walk(3000, 128, seed=21)
-    stats = check_hash_parity(CFG1, x, rows=range(0, 3000, 7))
-    assert stats["cws_fp64"] >= 0
+    x = synth.random_walk(3000, 512, seed=21)
+    stats = check_hash_parity(CFG2, x, rows=range(0, 3000, 11), generic=generic)
+    assert stats["cws_fp64"] > 0
 
 
 # ------------------------------------------------------------- DTW, LB_Keogh
