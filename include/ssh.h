@@ -129,8 +129,16 @@ ssh_status ssh_query_device(ssh_index* idx, const float* d_queries, const int32_
  * group on the stream it runs on; read them with ssh_get_kernel_times.
  * SSH_OPT_HASH_KERNEL (default 0): 0 hashes with the kernel specialised for the
  * index's (W, delta) and series length when one is compiled in, 1 always with
- * the generic kernel (same results; a diagnostic and test knob). */
-typedef enum ssh_option { SSH_OPT_LB_PRUNE = 1, SSH_OPT_KERNEL_TIMING = 2, SSH_OPT_HASH_KERNEL = 3 } ssh_option;
+ * the generic kernel (same results; a diagnostic and test knob).
+ * SSH_OPT_CWS_FP64 (default 0): 1 decides every weighted minhash by the FP64
+ * recomputation instead of the FP32 fast path (same results, much slower; a
+ * test knob for the recomputation itself). */
+typedef enum ssh_option {
+    SSH_OPT_LB_PRUNE = 1,
+    SSH_OPT_KERNEL_TIMING = 2,
+    SSH_OPT_HASH_KERNEL = 3,
+    SSH_OPT_CWS_FP64 = 4
+} ssh_option;
 ssh_status ssh_set_option(ssh_index* idx, ssh_option opt, int64_t value);
 
 /* Counters since the last ssh_reset_stats (all cumulative). */

@@ -20,6 +20,7 @@ SSH_ADD_BORROW = 1
 SSH_OPT_LB_PRUNE = 1
 SSH_OPT_KERNEL_TIMING = 2
 SSH_OPT_HASH_KERNEL = 3
+SSH_OPT_CWS_FP64 = 4
 
 _lib = None
 _lock = threading.Lock()
@@ -289,6 +290,9 @@ class SSHIndex:
 
     def set_hash_kernel(self, generic: bool):
         ssh_set_option(self.handle, SSH_OPT_HASH_KERNEL, 1 if generic else 0)
+
+    def set_cws_fp64(self, on: bool):
+        ssh_set_option(self.handle, SSH_OPT_CWS_FP64, 1 if on else 0)
 
     def set_kernel_timing(self, on: bool):
         ssh_set_option(self.handle, SSH_OPT_KERNEL_TIMING, 1 if on else 0)

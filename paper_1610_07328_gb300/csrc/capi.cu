@@ -372,15 +372,19 @@ HashArgs base_hash_args(const ssh_index* idx, int m, const Geometry& g) {
     a.L = idx->L;
     a.KL = idx->KL;
     a.r = idx->d_r;
+    a.r_host = idx->h_r.data();
     a.tau_norm = idx->tau_norm;
     const double gw = idx->W * std::ldexp(1.0, -24) / (1.0 - idx->W * std::ldexp(1.0, -24));
     a.gamma_ss = (float)(2.0 * gw);
     a.rank = idx->d_rank;
     a.rank_stride = (idx->KL + 3) & ~3;
     a.force_generic = idx->hash_kernel == 1;
+    a.force_fp64 = idx->cws_fp64;
     a.kinv = idx->d_kinv;
     a.p32 = idx->d_p32;
     a.p64 = idx->d_p64;
+    a.lav = idx->d_lav;
+    a.tsm = idx->d_tsm;
     a.lns32 = idx->d_lns32;
     a.lns64 = idx->d_lns64;
     a.seed = idx->seed;
@@ -462,7 +466,7 @@ ssh_status rebuild_tables(ssh_index* idx, SubIndex& s, cudaStream_t st) {
     SSH_TRY(sc.get(&valt, (size_t)L * s.cap));
     const size_t hb = radix_sort_scratch_bytes(n, L);
     SSH_TRY(sc.get(reinterpret_cast<unsigned char**>(&hist), hb));
-    SSH_CUDA(radix_sort_pairs_u64(s.skeys, s.srows, kalt, valt, n, L, s.cap, hist, hb, st));
+    SSH_CUDA(radix_sort_pairs_u64(s.skeys, s.srows, kalt, valt, n, L, s.cap, hist, hb, st, kTableSortFirstBit));
     return SSH_OK;
 }
 
@@ -785,6 +789,9 @@ ssh_status ssh_create(int W, int delta, int n, int K, int L, float band, uint64_
     std::vector<uint16_t> rank((size_t)nk * KLp, (uint16_t)0xFFFF), kinv((size_t)KL * nk);
     std::vector<float4> p32((size_t)nk * KL);
     std::vector<double> p64((size_t)KL * nk * 3);
+    // ln a rounded once to FP32 for small counts, and their t (255: compute it in FP64)
+    std::vector<float> lav((size_t)nk * kTabCounts * KLp, 0.f);
+    std::vector<uint8_t> tsm((size_t)nk * (kTabCounts - 1) * KLp, (uint8_t)255);
     parallel_for(KL, [&](int64_t j) {
         std::vector<std::pair<double, uint32_t>> la1(nk);
         for (int64_t k = 0; k < nk; ++k) {
@@ -795,6 +802,15 @@ ssh_status ssh_create(int W, int delta, int n, int K, int L, float band, uint64_
             q[1] = d.beta;
             q[2] = d.lnc;
             la1[k] = {log_a(d, std::log(1.0)), (uint32_t)k};
+            for (int c = 1; c <= kTabCounts; ++c) {
+                const double lns = std::log((double)c);
+                lav[((size_t)k * kTabCounts + (c - 1)) * KLp + j] = (float)log_a(d, lns);
+                if (c >= 2) {
+                    const double t = std::floor(lns / d.r + d.beta);
+                    tsm[((size_t)k * (kTabCounts - 1) + (c - 2)) * KLp + j] =
+                        (t >= 0.0 && t < 255.0) ? (uint8_t)t : (uint8_t)255;
+                }
+            }
         }
         std::sort(la1.begin(), la1.end());  // (value, id): equal values keep the smaller id first
         for (int64_t rnk = 0; rnk < nk; ++rnk) {
@@ -819,6 +835,8 @@ ssh_status ssh_create(int W, int delta, int n, int K, int L, float band, uint64_
     if (e == cudaSuccess) e = up(reinterpret_cast<void**>(&idx->d_kinv), kinv.data(), kinv.size() * 2);
     if (e == cudaSuccess) e = up(reinterpret_cast<void**>(&idx->d_p32), p32.data(), p32.size() * sizeof(float4));
     if (e == cudaSuccess) e = up(reinterpret_cast<void**>(&idx->d_p64), p64.data(), p64.size() * sizeof(double));
+    if (e == cudaSuccess) e = up(reinterpret_cast<void**>(&idx->d_lav), lav.data(), lav.size() * sizeof(float));
+    if (e == cudaSuccess) e = up(reinterpret_cast<void**>(&idx->d_tsm), tsm.data(), tsm.size());
     if (e == cudaSuccess) e = up(reinterpret_cast<void**>(&idx->d_lns32), lns32.data(), lns32.size() * sizeof(float));
     if (e == cudaSuccess) e = up(reinterpret_cast<void**>(&idx->d_lns64), lns64.data(), lns64.size() * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&idx->d_stats, kNumStatSlots * sizeof(unsigned long long));
@@ -846,6 +864,8 @@ void ssh_destroy(ssh_index* idx) {
     cudaFree(idx->d_kinv);
     cudaFree(idx->d_p32);
     cudaFree(idx->d_p64);
+    cudaFree(idx->d_lav);
+    cudaFree(idx->d_tsm);
     cudaFree(idx->d_lns32);
     cudaFree(idx->d_lns64);
     cudaFree(idx->d_stats);
@@ -1017,6 +1037,9 @@ ssh_status ssh_set_option(ssh_index* idx, ssh_option opt, int64_t value) {
             return SSH_OK;
         case SSH_OPT_KERNEL_TIMING:
             idx->timing = value != 0;
+            return SSH_OK;
+        case SSH_OPT_CWS_FP64:
+            idx->cws_fp64 = value != 0;
             return SSH_OK;
         case SSH_OPT_HASH_KERNEL:
             if (value < 0 || value > 1) return fail(SSH_EINVAL, "SSH_OPT_HASH_KERNEL takes 0 or 1");

@@ -36,6 +36,7 @@ __device__ inline void cws_fp64(const HashArgs& a, int j, const uint32_t* cid, c
     const size_t nk = (size_t)1 << a.n;
     double best = __longlong_as_double(0x7FF0000000000000ll);  // +inf
     uint32_t bk = 0, bt = 0;
+#pragma unroll 1
     for (int e = 0; e < nnz; ++e) {
         const uint32_t k = cid[e];
         const double* p = a.p64 + ((size_t)j * nk + k) * 3;
@@ -134,6 +135,60 @@ __device__ __forceinline__ bool cws_decide(bool hasA, uint32_t kA, float4 pA, co
     *ks = b.k;
     *ts = b.t;
     return !b.unsure && b.hi < aLo && b.hi < minLoOther;
+}
+
+// Candidates whose FP32 value is the FP64 ln a of the definition rounded once
+// (tabulated at index creation): rounding is monotone, so a strictly smaller
+// FP32 value means a strictly smaller FP64 value, and only equal FP32 values
+// leave the order open (tie).
+struct ExactMin {
+    float v;
+    uint32_t k, t;
+    bool tie;
+    __device__ __forceinline__ void init() {
+        v = __int_as_float(0x7F800000);
+        k = 0xFFFFFFFFu;
+        t = 0;
+        tie = false;
+    }
+    __device__ __forceinline__ void add(float val, uint32_t id, uint32_t tt) {
+        if (val < v) {
+            v = val;
+            k = id;
+            t = tt;
+            tie = false;
+        } else if (val == v) {
+            tie = true;
+        }
+    }
+};
+
+// Winner among the exact group E and the interval-tracked group C (counts above
+// the tabulated ones). Returns false when the FP32 decision is not certain
+// (then the hash is recomputed in FP64). t = 255 marks a t that was not tabulated.
+__device__ __forceinline__ bool exact_decide(const ExactMin& E, const CwsTrack& C, uint32_t* ks, uint32_t* ts) {
+    const bool hasE = E.k != 0xFFFFFFFFu, hasC = C.k != 0xFFFFFFFFu;
+    if (!hasC) {
+        *ks = E.k;
+        *ts = E.t;
+        return hasE && !E.tie && E.t != 255u;
+    }
+    const float minLoOtherC = (C.klo1 != C.k) ? C.lo1 : C.lo2;
+    if (!hasE) {
+        *ks = C.k;
+        *ts = C.t;
+        return !C.unsure && C.hi < minLoOtherC;
+    }
+    // E's FP64 value lies within half an ulp of E.v: bracket it by the neighbouring floats
+    const float eLo = nextafterf(E.v, __int_as_float(0xFF800000)), eHi = nextafterf(E.v, __int_as_float(0x7F800000));
+    if (E.v < C.la || (E.v == C.la && E.k < C.k)) {
+        *ks = E.k;
+        *ts = E.t;
+        return !E.tie && E.t != 255u && !C.unsure && eHi < C.lo1;
+    }
+    *ks = C.k;
+    *ts = C.t;
+    return !C.unsure && C.hi < eLo && C.hi < minLoOtherC;
 }
 
 }  // namespace ssh

@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerCta * 32) hash_kernel(HashArgs a, 
                 kA = __ldg(a.kinv + (size_t)j * nk + rmin);
                 pA = __ldg(a.p32 + (size_t)kA * KL + j);
             }
-            if (!cws_decide(hasA, kA, pA, tr, &ks, &ts)) {
+            if (!cws_decide(hasA, kA, pA, tr, &ks, &ts) || a.force_fp64) {
                 cws_fp64(a, j, cid, ccnt, nnz, &ks, &ts);
                 c64 += 1;
             }

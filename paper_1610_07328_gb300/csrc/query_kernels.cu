@@ -23,15 +23,17 @@ __global__ void probe_union_kernel(ProbeArgs a) {
     const uint32_t* sr = a.srows + l * a.cap;
     __shared__ int64_t range[2];
     if (threadIdx.x == 0) {
-        int64_t lo = 0, hi = a.nrows;  // lower_bound
+        // the tables are ordered by the upper 32 key bits: find that run
+        const uint32_t hk = (uint32_t)(key >> kTableSortFirstBit);
+        int64_t lo = 0, hi = a.nrows;
         while (lo < hi) {
-            int64_t mid = (lo + hi) >> 1;
-            if (sk[mid] < key) lo = mid + 1; else hi = mid;
+            const int64_t mid = (lo + hi) >> 1;
+            if ((uint32_t)(sk[mid] >> kTableSortFirstBit) < hk) lo = mid + 1; else hi = mid;
         }
-        int64_t lo2 = lo, hi2 = a.nrows;  // upper_bound
+        int64_t lo2 = lo, hi2 = a.nrows;
         while (lo2 < hi2) {
-            int64_t mid = (lo2 + hi2) >> 1;
-            if (sk[mid] <= key) lo2 = mid + 1; else hi2 = mid;
+            const int64_t mid = (lo2 + hi2) >> 1;
+            if ((uint32_t)(sk[mid] >> kTableSortFirstBit) <= hk) lo2 = mid + 1; else hi2 = mid;
         }
         range[0] = lo;
         range[1] = lo2;
@@ -39,6 +41,7 @@ __global__ void probe_union_kernel(ProbeArgs a) {
     __syncthreads();
     uint32_t* bm = a.bitmap + q * a.words;
     for (int64_t i = range[0] + threadIdx.x; i < range[1]; i += blockDim.x) {
+        if (sk[i] != key) continue;  // same upper half, different key
         const uint32_t row = sr[i];
         atomicOr(&bm[row >> 5], 1u << (row & 31));
     }

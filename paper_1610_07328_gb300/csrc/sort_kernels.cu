@@ -167,7 +167,8 @@ size_t radix_sort_scratch_bytes(int64_t n, int nseg) {
 }
 
 cudaError_t radix_sort_pairs_u64(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt, int64_t n,
-                                 int nseg, int64_t seg_stride, void* scratch, size_t scratch_bytes, cudaStream_t st) {
+                                 int nseg, int64_t seg_stride, void* scratch, size_t scratch_bytes, cudaStream_t st,
+                                 int first_bit) {
     if (n <= 1 || nseg <= 0) return cudaSuccess;
     const int64_t ntiles = (n + kSortTile - 1) / kSortTile;
     if (scratch_bytes < radix_sort_scratch_bytes(n, nseg) || ntiles > (1 << 24)) return cudaErrorInvalidValue;
@@ -177,7 +178,8 @@ cudaError_t radix_sort_pairs_u64(uint64_t* keys, uint32_t* vals, uint64_t* keys_
     uint64_t* kout = keys_alt;
     uint32_t* vout = vals_alt;
     dim3 grid((unsigned)ntiles, (unsigned)nseg);
-    for (int shift = 0; shift < 64; shift += 8) {
+    if (first_bit < 0 || first_bit > 56 || (first_bit % 16) != 0) return cudaErrorInvalidValue;
+    for (int shift = first_bit; shift < 64; shift += 8) {
         radix_hist_kernel<<<grid, kSortThreads, 0, st>>>(kin, n, seg_stride, shift, (int)ntiles, counts);
         note_launch();
         radix_scan_kernel<<<nseg, 1024, 0, st>>>(counts, (int)ntiles);
@@ -188,7 +190,7 @@ cudaError_t radix_sort_pairs_u64(uint64_t* keys, uint32_t* vals, uint64_t* keys_
         uint64_t* tk = kin; kin = kout; kout = tk;
         uint32_t* tv = vin; vin = vout; vout = tv;
     }
-    return cudaGetLastError();  // 8 passes: the sorted data is back in (keys, vals)
+    return cudaGetLastError();  // an even number of passes: the sorted data is back in (keys, vals)
 }
 
 cudaError_t launch_select_kth_u32(const uint32_t* keys, const int64_t* seg_begin, int64_t nseg, int k,

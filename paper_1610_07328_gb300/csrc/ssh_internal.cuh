@@ -10,7 +10,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/ssh.h"
+#include "ssh.h"
 
 namespace ssh {
 
@@ -45,6 +45,7 @@ constexpr float kPad = 1.0e18f;
 constexpr int kMaxShingleBits = 16;     // n limit of the tabulated minhash draws
 constexpr int kMaxCount = 65535;        // shingles per series (u16 counts)
 constexpr int kMaxTopK = 1024;
+constexpr int kTabCounts = 8;           // counts whose ln a is tabulated exactly rounded
 constexpr int kMaxW = 8192;
 constexpr int kMaxKL = 4096;
 
@@ -59,15 +60,19 @@ struct HashArgs {
     const float* const* rows;// ... unless rows != NULL: row i at rows[i]
     int64_t count;           // rows to hash
     int m, W, delta, n, nb, nwords, S, K, L, KL;
-    const float* r;          // [W] filter
+    const float* r;          // [W] filter (device)
+    const float* r_host;     // [W] the same filter in host memory
     float tau_norm;          // threshold factor tau * ||r|| (rounded up)
     float gamma_ss;          // relative inflation of the FP32 sum of squares
     const uint16_t* rank;    // [2^n][rank_stride] rank of the count-1 value of (j, k) among all k
     int rank_stride;         // KL rounded up to a multiple of 4 (row padding holds 0xFFFF)
     int force_generic;       // 1: use the generic kernel even when a specialised one exists
+    int force_fp64;          // 1: decide every minhash by the FP64 recomputation (a test knob)
     const uint16_t* kinv;    // [KL][2^n] shingle id of each rank
     const float4* p32;       // [2^n][KL] (r, 1/r, beta, ln c) rounded to FP32
     const double* p64;       // [KL][2^n][3] (r, beta, ln c) in FP64
+    const float* lav;        // [2^n][kTabCounts][rank_stride] ln a of counts 1..kTabCounts, rounded once to FP32
+    const uint8_t* tsm;      // [2^n][kTabCounts-1][rank_stride] t of counts 2..kTabCounts (255: not tabulated)
     const float* lns32;      // [kMaxCount+1] ln s rounded to FP32
     const double* lns64;     // [kMaxCount+1] ln s in FP64
     uint64_t seed;
@@ -93,12 +98,17 @@ cudaError_t launch_hash(const HashArgs& a, cudaStream_t st);
 
 // ------------------------------------------------------------ radix sort
 
-// Sort (key, val) pairs by key, stably, independently in each of `nseg`
-// segments of `n` consecutive items. Ping-pongs between (keys, vals) and
-// (keys_alt, vals_alt); the result ends in (keys, vals).
+// Sort (key, val) pairs stably by key bits [first_bit, 64) (first_bit a multiple
+// of 16), independently in each of `nseg` segments of `n` consecutive items.
+// Ping-pongs between (keys, vals) and (keys_alt, vals_alt); the result ends in
+// (keys, vals).
 cudaError_t radix_sort_pairs_u64(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt,
                                  int64_t n, int nseg, int64_t seg_stride, void* scratch, size_t scratch_bytes,
-                                 cudaStream_t st);
+                                 cudaStream_t st, int first_bit);
+
+// The bucket tables are sorted on the upper 32 key bits only: a probe finds the
+// run of equal upper halves and compares the full 64-bit keys inside it.
+constexpr int kTableSortFirstBit = 32;
 size_t radix_sort_scratch_bytes(int64_t n, int nseg);
 
 // -------------------------------------------------------------- queries
@@ -186,6 +196,7 @@ struct ssh_index {
     int device = 0;
     bool lb_prune = true;
     int hash_kernel = 0;              // 0: fastest available, 1: always the generic kernel
+    int cws_fp64 = 0;                 // 1: every minhash through the FP64 recomputation
     float tau_norm = 0.f;
     std::vector<float> h_r;           // host copy of the filter
     float* d_r = nullptr;
@@ -193,6 +204,8 @@ struct ssh_index {
     uint16_t* d_kinv = nullptr;
     float4* d_p32 = nullptr;
     double* d_p64 = nullptr;
+    float* d_lav = nullptr;
+    uint8_t* d_tsm = nullptr;
     float* d_lns32 = nullptr;
     double* d_lns64 = nullptr;
     unsigned long long* d_stats = nullptr;

@@ -63,10 +63,11 @@ def gpu_hash(idx, x: np.ndarray):
                 keys=keys.cpu().numpy().view(np.uint64), nb=nb)
 
 
-def check_hash_parity(cfg, x, rows=None, generic=False):
+def check_hash_parity(cfg, x, rows=None, generic=False, force_fp64=False):
     idx = _index(cfg)
     try:
         idx.set_hash_kernel(generic)
+        idx.set_cws_fp64(force_fp64)
         g = gpu_hash(idx, x)
         r = oracle.filter_r(cfg["seed"], cfg["W"])
         assert np.array_equal(idx.filter, r)
@@ -157,11 +158,19 @@ def test_sketch_fp64_path_on_near_zero_projections(generic):
 
 
 @KERNELS
-def test_cws_fp64_path_is_exercised_and_exact(generic):
-    # enough series that near-tie minhashes occur; all of them must still match
+def test_cws_many_series_exact(generic):
+    # enough series that near ties in FP32 occur; every hash must still match
     x = synth.random_walk(3000, 512, seed=21)
-    stats = check_hash_parity(CFG2, x, rows=range(0, 3000, 11), generic=generic)
-    assert stats["cws_fp64"] > 0
+    check_hash_parity(CFG2, x, rows=range(0, 3000, 11), generic=generic)
+
+
+@KERNELS
+@pytest.mark.parametrize("data", ["random_walk", "ecg_like"])
+def test_cws_fp64_recomputation_is_exact(generic, data):
+    """Every minhash decided by the FP64 recomputation (the path taken on near ties)."""
+    x = synth.random_walk(150, 512, seed=5) if data == "random_walk" else synth.ecg_like(150, 512, seed=6)
+    stats = check_hash_parity(CFG2, x, generic=generic, force_fp64=True)
+    assert stats["cws_fp64"] == 150 * CFG2["K"] * CFG2["L"]
 
 
 # ------------------------------------------------------------- DTW, LB_Keogh
