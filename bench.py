@@ -186,61 +186,91 @@ def source_digest(paths):
     return h.hexdigest()[:16]
 
 
+CSRC = "paper_1610_07328_gb300/csrc/"
 KERNEL_SOURCES = {
-    "hash_add": ["paper_1610_07328_gb300/csrc/hash_kernels.cu"],
-    "hash_query": ["paper_1610_07328_gb300/csrc/hash_kernels.cu"],
-    "dtw": ["paper_1610_07328_gb300/csrc/query_kernels.cu"],
-    "lb_keogh": ["paper_1610_07328_gb300/csrc/query_kernels.cu"],
-    "probe_union": ["paper_1610_07328_gb300/csrc/query_kernels.cu"],
-    "table_sort": ["paper_1610_07328_gb300/csrc/sort_kernels.cu"],
-    "topk": ["paper_1610_07328_gb300/csrc/sort_kernels.cu", "paper_1610_07328_gb300/csrc/capi.cu"],
+    "sketch": [CSRC + "hash_split.cu"],
+    "sketch_fixup": [CSRC + "hash_split.cu"],
+    "shingle": [CSRC + "hash_split.cu"],
+    "cws": [CSRC + "hash_split.cu", CSRC + "hash_common.cuh"],
+    "hash_generic": [CSRC + "hash_kernels.cu", CSRC + "hash_common.cuh"],
+    "table_sort": [CSRC + "sort_kernels.cu"],
+    "probe_union": [CSRC + "query_kernels.cu"],
+    "lb_keogh": [CSRC + "query_kernels.cu"],
+    "dtw": [CSRC + "query_kernels.cu"],
+    "topk": [CSRC + "sort_kernels.cu", CSRC + "capi.cu"],
 }
 
 
 def traffic_for(group):
     """DRAM bytes per launch from a committed ncu summary, if taken on the current source."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
-    if not os.path.exists(path):
+    stage = group.split(".", 1)[-1]
+    if not os.path.exists(path) or stage not in KERNEL_SOURCES:
         return None
     with open(path) as f:
         t = json.load(f)
     e = t.get(group)
-    if not e or e.get("source_digest") != source_digest(KERNEL_SOURCES[group]):
+    if not e or e.get("source_digest") != source_digest(KERNEL_SOURCES[stage]):
         return None
     return e.get("bytes_per_launch")
 
 
+def algorithmic(w, stage):
+    """(bound, bytes or FLOP per unit) of a kernel group; units are series unless noted."""
+    m, L, W, delta, n = w["m"], w["L"], w["W"], w["delta"], w["n"]
+    nb = (m - W) // delta + 1
+    nwords = (nb + 31) // 32
+    S = nb - n + 1
+    if stage == "sketch":       # series read once, sign bits written
+        return "hbm", 4 * m + 4 * nwords
+    if stage == "shingle":      # bits read, weighted set written (at most S slots)
+        return "hbm", 4 * nwords + 4 * S
+    if stage == "cws":          # weighted set read, L bucket keys written
+        return "hbm", 4 * S + 8 * L
+    if stage == "hash_generic":
+        return "hbm", 4 * m + 8 * L
+    if stage == "table_sort":   # per table entry: one read and one write of (key, row)
+        return "hbm", 24
+    if stage == "lb_keogh":     # per candidate sample read
+        return "hbm", 4
+    if stage == "dtw":          # per DTW cell: difference and fused square-add (3 FLOP)
+        return "alu", 3
+    return None, None
+
+
 def kernel_rooflines(w, times, pk):
     """Achieved vs peak for each kernel group, from the library's CUDA-event times."""
-    m, L = w["m"], w["L"]
     out = {}
     total = sum(v["total_ms"] for v in times.values()) or 1.0
     for name, v in times.items():
+        stage = name.split(".", 1)[-1]
         calls = max(v["calls"], 1)
         avg_ms = v["total_ms"] / calls
         units_per_call = v["units"] / calls
         e = dict(ms_total=v["total_ms"], calls=v["calls"], launches=v["launches"], avg_ms=avg_ms,
-                 share=v["total_ms"] / total)
-        if name in ("hash_add", "hash_query"):
-            # algorithmic bytes: each series read once (4m B) + L keys written (8 B each)
-            bytes_ = units_per_call * (4 * m + 8 * L)
-            e.update(bound="hbm", unit="GB/s", achieved=bytes_ / (avg_ms * 1e-3) / 1e9, peak=pk["hbm_gbs"])
-        elif name == "dtw":
-            # 3 FLOP per cell: difference, square-and-add (FMA); the 3-way min is not counted
-            flops = units_per_call * 3
-            e.update(bound="alu", unit="TFLOP/s", achieved=flops / (avg_ms * 1e-3) / 1e12, peak=fp32_peak_tflops())
-        elif name == "lb_keogh":
-            bytes_ = units_per_call * 4
-            e.update(bound="hbm", unit="GB/s", achieved=bytes_ / (avg_ms * 1e-3) / 1e9, peak=pk["hbm_gbs"])
-        elif name == "table_sort":
-            # one read and one write of (key, row) = 12 B each per entry
-            bytes_ = units_per_call * 24
-            e.update(bound="hbm", unit="GB/s", achieved=bytes_ / (avg_ms * 1e-3) / 1e9, peak=pk["hbm_gbs"])
+                 share=v["total_ms"] / total, units_per_call=units_per_call)
+        bound, per = algorithmic(w, stage)
+        if bound == "hbm":
+            e.update(bound="hbm", unit="GB/s", achieved=units_per_call * per / (avg_ms * 1e-3) / 1e9,
+                     peak=pk["hbm_gbs"])
+        elif bound == "alu":
+            e.update(bound="alu", unit="TFLOP/s", achieved=units_per_call * per / (avg_ms * 1e-3) / 1e12,
+                     peak=fp32_peak_tflops())
         else:
             e.update(bound=None, unit=None, achieved=None, peak=None)
         if e.get("achieved") is not None:
             e["frac"] = e["achieved"] / e["peak"]
         out[name] = e
+    # the hash pipeline of Sec. 4.1-4.3 as a whole: series read once, keys written once
+    parts = [n for n in out if n.startswith("add.") and n.split(".", 1)[1] in
+             ("sketch", "sketch_fixup", "shingle", "cws", "hash_generic")]
+    if parts:
+        ms = sum(out[n]["avg_ms"] for n in parts)
+        units = out[parts[0]]["units_per_call"]
+        ach = units * (4 * w["m"] + 8 * w["L"]) / (ms * 1e-3) / 1e9
+        out["add.hash_pipeline"] = dict(ms_per_call=ms, series_per_call=units, bound="hbm", unit="GB/s",
+                                        achieved=ach, peak=pk["hbm_gbs"], frac=ach / pk["hbm_gbs"],
+                                        series_per_s=units / (ms * 1e-3))
     return out
 
 
@@ -406,7 +436,8 @@ def run_gpu(args, w):
 
     pk = peaks()
     roofs = kernel_rooflines(w, times, pk)
-    dominant = max((n for n in roofs if roofs[n].get("achieved") is not None), key=lambda n: roofs[n]["ms_total"])
+    dominant = max((n for n in roofs if roofs[n].get("achieved") is not None and "ms_total" in roofs[n]),
+                   key=lambda n: roofs[n]["ms_total"])
     d = roofs[dominant]
     roofline = {"kernel": dominant, "bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"],
                 "unit": d["unit"], "frac": d["frac"], "traffic": traffic_for(dominant),

@@ -156,9 +156,11 @@ ssh_status ssh_get_stats(const ssh_index* idx, ssh_stats* out);
 ssh_status ssh_reset_stats(ssh_index* idx);
 
 /* Device time per kernel group since the last ssh_reset_stats, measured with
- * CUDA events while SSH_OPT_KERNEL_TIMING is on. Groups: "hash_add" and "hash_query" (units: series),
- * "table_sort" (units: table entries), "probe_union" (queries x tables),
- * "lb_keogh" (candidate samples read), "dtw" (DTW cells), "topk" (candidates).
+ * CUDA events while SSH_OPT_KERNEL_TIMING is on. Groups (prefix "add." for
+ * ssh_index_add*, "query." for ssh_query*): "sketch", "sketch_fixup", "shingle",
+ * "cws", "hash_generic" (units: series), "table_sort" (table entries),
+ * "probe_union" (queries x tables), "lb_keogh" (candidate samples read),
+ * "dtw" (DTW cells), "topk" (candidates).
  * Writes up to `cap` records to out and their number to *count; synchronises
  * on the recorded events. */
 typedef struct ssh_kernel_time {

@@ -196,6 +196,45 @@ struct TimedRegion {
 
 double dtw_cells(int m, int rb) { return (double)m * (2.0 * rb + 1.0) - (double)rb * (rb + 1.0); }
 
+// Sec. 4.1-4.3 + keys for a.count series, each stage in its own timed region
+// named "<prefix>.<stage>" (units: series).
+ssh_status run_hash(ssh_index* idx, const HashArgs& a, cudaStream_t st, const char* prefix) {
+    if (a.count <= 0) return SSH_OK;
+    static const char* names[2][5] = {{"add.sketch", "add.sketch_fixup", "add.shingle", "add.cws", "add.hash_generic"},
+                                      {"query.sketch", "query.sketch_fixup", "query.shingle", "query.cws",
+                                       "query.hash_generic"}};
+    const int w = (prefix[0] == 'q') ? 1 : 0;
+    const double units = (double)a.count;
+    if (a.force_generic || !hash_fast_supported(a)) {
+        TimedRegion tr(idx, st, names[w][4], units);
+        SSH_CUDA(launch_hash_generic(a, st));
+        return SSH_OK;
+    }
+    void* scratch = nullptr;
+    SSH_CUDA(cudaMallocAsync(&scratch, hash_fast_scratch_bytes(a), st));
+    const FastHashBuffers b = hash_fast_buffers(a, scratch);
+    cudaError_t e;
+    {
+        TimedRegion tr(idx, st, names[w][0], units);
+        e = hash_fast_sketch(a, b, st);
+    }
+    if (e == cudaSuccess) {
+        TimedRegion tr(idx, st, names[w][1], units);
+        e = hash_fast_fixup(a, b, st);
+    }
+    if (e == cudaSuccess) {
+        TimedRegion tr(idx, st, names[w][2], units);
+        e = hash_fast_shingle(a, b, st);
+    }
+    if (e == cudaSuccess) {
+        TimedRegion tr(idx, st, names[w][3], units);
+        e = hash_fast_cws(a, b, st);
+    }
+    cudaFreeAsync(scratch, st);
+    SSH_CUDA(e);
+    return SSH_OK;
+}
+
 // ------------------------------------------------------------ small kernels
 
 __global__ void fill_rows_kernel(const float** row_ptr, int64_t* gid, int64_t n, const float* base, int64_t stride,
@@ -517,16 +556,13 @@ ssh_status add_series(ssh_index* idx, const float* dev, const int32_t* lengths, 
         a.keys = s.keys;
         a.key_stride = s.cap;
         a.key_col0 = s.count;
-        {
-            TimedRegion tr(idx, st, "hash_add", (double)nrun);
-            SSH_CUDA(launch_hash(a, st));
-        }
+        SSH_TRY(run_hash(idx, a, st, "add"));
         s.count += nrun;
         idx->host_stats.series_hashed += nrun;
         i = j;
     }
     for (int m : touched) {
-        TimedRegion tr(idx, st, "table_sort", (double)idx->subs[m].count * idx->L);
+        TimedRegion tr(idx, st, "add.table_sort", (double)idx->subs[m].count * idx->L);
         SSH_TRY(rebuild_tables(idx, idx->subs[m], st));
     }
     SSH_CUDA(cudaStreamSynchronize(st));
@@ -559,10 +595,7 @@ ssh_status query_group(ssh_index* idx, SubIndex& s, const std::vector<const floa
     a.keys = qkeys;
     a.key_stride = nq;
     a.key_col0 = 0;
-    {
-        TimedRegion tr(idx, st, "hash_query", (double)nq);
-        SSH_CUDA(launch_hash(a, st));
-    }
+    SSH_TRY(run_hash(idx, a, st, "query"));
     idx->host_stats.series_hashed += nq;
 
     // lines 6-9: probe every table, union of the buckets
@@ -574,7 +607,7 @@ ssh_status query_group(ssh_index* idx, SubIndex& s, const std::vector<const floa
     SSH_CUDA(cudaMemsetAsync(bitmap, 0, (size_t)nq * words * sizeof(uint32_t), st));
     ProbeArgs pa{qkeys, nq, L, s.skeys, s.srows, s.cap, s.count, bitmap, words};
     {
-        TimedRegion tr(idx, st, "probe_union", (double)nq * L);
+        TimedRegion tr(idx, st, "query.probe_union", (double)nq * L);
         SSH_CUDA(launch_probe_union(pa, st));
         SSH_CUDA(launch_bitmap_count(bitmap, nq, words, counts, st));
     }
@@ -614,7 +647,7 @@ ssh_status query_group(ssh_index* idx, SubIndex& s, const std::vector<const floa
     const int rb = s.rb;
     if (C > 0 && !idx->lb_prune) {
         {
-            TimedRegion tr(idx, st, "dtw", (double)C * dtw_cells(m, rb));
+            TimedRegion tr(idx, st, "query.dtw", (double)C * dtw_cells(m, rb));
             SSH_CUDA(launch_dtw(all, m, rb, dist, st));
         }
         idx->host_stats.dtw_computed += C;
@@ -626,7 +659,7 @@ ssh_status query_group(ssh_index* idx, SubIndex& s, const std::vector<const floa
         SSH_TRY(sc.get(&upper, (size_t)nq * m));
         SSH_TRY(sc.get(&lower, (size_t)nq * m));
         {
-            TimedRegion tr(idx, st, "lb_keogh", (double)C * m);
+            TimedRegion tr(idx, st, "query.lb_keogh", (double)C * m);
             SSH_CUDA(launch_envelope(d_qptr, nq, m, rb, upper, lower, st));
             SSH_CUDA(launch_lb_keogh(all, upper, lower, m, lb, st));
         }
@@ -669,7 +702,7 @@ ssh_status query_group(ssh_index* idx, SubIndex& s, const std::vector<const floa
             }
             PairSet sub{fbegin, nq, d_qptr, fb, fslot, mx};
             if (tot > 0) {
-                TimedRegion tr(idx, st, "dtw", (double)tot * dtw_cells(m, rb));
+                TimedRegion tr(idx, st, "query.dtw", (double)tot * dtw_cells(m, rb));
                 SSH_CUDA(launch_dtw(sub, m, rb, dist, st));
             }
             idx->host_stats.dtw_computed += tot;
@@ -683,7 +716,7 @@ ssh_status query_group(ssh_index* idx, SubIndex& s, const std::vector<const floa
     SSH_TRY(sc.get(&tkeys, C));
     SSH_TRY(sc.get(&kth, nq));
     {
-        TimedRegion tr(idx, st, "topk", (double)C);
+        TimedRegion tr(idx, st, "query.topk", (double)C);
         if (C > 0) {
             topk_keys_kernel<<<grid_for(C, 256, 8192), 256, 0, st>>>(dist, cand_rows, C, tkeys);
             note_launch();

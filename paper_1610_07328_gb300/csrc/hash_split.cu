@@ -606,23 +606,26 @@ FastScratch fast_scratch(const HashArgs& a) {
 
 size_t hash_fast_scratch_bytes(const HashArgs& a) { return fast_scratch(a).total; }
 
-cudaError_t launch_hash_fast_scratch(const HashArgs& a, void* scratch, size_t scratch_bytes, cudaStream_t st) {
+FastHashBuffers hash_fast_buffers(const HashArgs& a, void* scratch) {
     const FastScratch f = fast_scratch(a);
-    if (scratch_bytes < f.total) return cudaErrorInvalidValue;
     unsigned char* p = static_cast<unsigned char*>(scratch);
-    uint32_t* bits = a.bits_out ? a.bits_out : reinterpret_cast<uint32_t*>(p + f.bits);
-    unsigned long long* nfix = reinterpret_cast<unsigned long long*>(p + f.nfix);
-    unsigned long long* fix = reinterpret_cast<unsigned long long*>(p + f.fix);
-    uint32_t* sets = reinterpret_cast<uint32_t*>(p + f.sets);
-    int2* sizes = reinterpret_cast<int2*>(p + f.sizes);
-    const unsigned long long cap = f.fix_cap;
-    cudaError_t e = cudaMemsetAsync(nfix, 0, sizeof(unsigned long long), st);
+    FastHashBuffers b;
+    b.bits = a.bits_out ? a.bits_out : reinterpret_cast<uint32_t*>(p + f.bits);
+    b.nfix = reinterpret_cast<unsigned long long*>(p + f.nfix);
+    b.fix = reinterpret_cast<unsigned long long*>(p + f.fix);
+    b.fix_cap = f.fix_cap;
+    b.sets = reinterpret_cast<uint32_t*>(p + f.sets);
+    b.sizes = reinterpret_cast<int2*>(p + f.sizes);
+    return b;
+}
+
+cudaError_t hash_fast_sketch(const HashArgs& a, const FastHashBuffers& b, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(b.nfix, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
-    e = cudaErrorInvalidValue;
     for (const SketchShape& s : kSketchShapes) {
         if (!sketch_shape_ok(s, a)) continue;
 #define SSH_SKETCH_CASE(W_, D_, R_) \
-    if (s.W == W_ && s.delta == D_ && s.R == R_) e = launch_sketch_t<W_, D_, R_>(a, bits, fix, cap, nfix, st);
+    if (s.W == W_ && s.delta == D_ && s.R == R_) return launch_sketch_t<W_, D_, R_>(a, b.bits, b.fix, b.fix_cap, b.nfix, st);
         SSH_SKETCH_CASE(80, 3, 5)
         SSH_SKETCH_CASE(32, 3, 2)
         SSH_SKETCH_CASE(120, 5, 6)
@@ -631,30 +634,34 @@ cudaError_t launch_hash_fast_scratch(const HashArgs& a, void* scratch, size_t sc
         SSH_SKETCH_CASE(64, 3, 5)
         SSH_SKETCH_CASE(128, 3, 10)
 #undef SSH_SKETCH_CASE
-        break;
     }
-    if (e != cudaSuccess) return e;
-    {
-        // the list length is only known on the device: size the grid for up to
-        // one listed window per 8 series and let surplus blocks exit
-        int64_t g = ((int64_t)(a.count / 8) + 255) / 256;
-        if (g < 1) g = 1;
-        if (g > 8192) g = 8192;
-        sketch_fixup_kernel<<<(unsigned)g, 256, 0, st>>>(a, bits, fix, nfix, cap);
-        note_launch();
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t hash_fast_fixup(const HashArgs& a, const FastHashBuffers& b, cudaStream_t st) {
+    // the list length is only known on the device: size the grid for up to one
+    // listed window per 8 series and let surplus blocks exit
+    int64_t g = ((int64_t)(a.count / 8) + 255) / 256;
+    if (g < 1) g = 1;
+    if (g > 8192) g = 8192;
+    sketch_fixup_kernel<<<(unsigned)g, 256, 0, st>>>(a, b.bits, b.fix, b.nfix, b.fix_cap);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t hash_fast_shingle(const HashArgs& a, const FastHashBuffers& b, cudaStream_t st) {
     switch (cws_e(a.S)) {
-        case 1: e = launch_shingle_t<1>(a, bits, sets, sizes, st); break;
-        case 2: e = launch_shingle_t<2>(a, bits, sets, sizes, st); break;
-        case 4: e = launch_shingle_t<4>(a, bits, sets, sizes, st); break;
-        case 8: e = launch_shingle_t<8>(a, bits, sets, sizes, st); break;
-        case 16: e = launch_shingle_t<16>(a, bits, sets, sizes, st); break;
-        default: e = cudaErrorInvalidValue;
+        case 1: return launch_shingle_t<1>(a, b.bits, b.sets, b.sizes, st);
+        case 2: return launch_shingle_t<2>(a, b.bits, b.sets, b.sizes, st);
+        case 4: return launch_shingle_t<4>(a, b.bits, b.sets, b.sizes, st);
+        case 8: return launch_shingle_t<8>(a, b.bits, b.sets, b.sizes, st);
+        case 16: return launch_shingle_t<16>(a, b.bits, b.sets, b.sizes, st);
+        default: return cudaErrorInvalidValue;
     }
-    if (e != cudaSuccess) return e;
-    return launch_cws(a, sets, sizes, st);
+}
+
+cudaError_t hash_fast_cws(const HashArgs& a, const FastHashBuffers& b, cudaStream_t st) {
+    return launch_cws(a, b.sets, b.sizes, st);
 }
 
 cudaError_t launch_hash_fast(const HashArgs& a, cudaStream_t st) {
@@ -662,7 +669,11 @@ cudaError_t launch_hash_fast(const HashArgs& a, cudaStream_t st) {
     void* scratch = nullptr;
     cudaError_t e = cudaMallocAsync(&scratch, bytes, st);
     if (e != cudaSuccess) return e;
-    e = launch_hash_fast_scratch(a, scratch, bytes, st);
+    const FastHashBuffers b = hash_fast_buffers(a, scratch);
+    e = hash_fast_sketch(a, b, st);
+    if (e == cudaSuccess) e = hash_fast_fixup(a, b, st);
+    if (e == cudaSuccess) e = hash_fast_shingle(a, b, st);
+    if (e == cudaSuccess) e = hash_fast_cws(a, b, st);
     cudaError_t f = cudaFreeAsync(scratch, st);
     return e != cudaSuccess ? e : f;
 }

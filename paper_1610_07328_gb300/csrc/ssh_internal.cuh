@@ -91,6 +91,23 @@ struct HashArgs {
 
 bool hash_fast_supported(const HashArgs& a);
 cudaError_t launch_hash_fast(const HashArgs& a, cudaStream_t st);
+
+// The specialised hash path in stages (sketch -> FP64 fix-up -> shingle -> CWS)
+// over one scratch block of hash_fast_scratch_bytes(a) bytes.
+struct FastHashBuffers {
+    uint32_t* bits;
+    unsigned long long* nfix;
+    unsigned long long* fix;
+    unsigned long long fix_cap;
+    uint32_t* sets;
+    int2* sizes;
+};
+size_t hash_fast_scratch_bytes(const HashArgs& a);
+FastHashBuffers hash_fast_buffers(const HashArgs& a, void* scratch);
+cudaError_t hash_fast_sketch(const HashArgs& a, const FastHashBuffers& b, cudaStream_t st);
+cudaError_t hash_fast_fixup(const HashArgs& a, const FastHashBuffers& b, cudaStream_t st);
+cudaError_t hash_fast_shingle(const HashArgs& a, const FastHashBuffers& b, cudaStream_t st);
+cudaError_t hash_fast_cws(const HashArgs& a, const FastHashBuffers& b, cudaStream_t st);
 cudaError_t launch_hash_generic(const HashArgs& a, cudaStream_t st);
 int hash_smem_bytes_per_warp(int m, int nwords, int S, int KL);
 int hash_warps_per_cta(int m, int nwords, int S, int KL);
