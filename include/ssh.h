@@ -193,6 +193,36 @@ ssh_status ssh_hash_device(const ssh_index* idx, const float* d_series, int32_t 
                            uint32_t* d_bits, uint32_t* d_sh_ids, uint32_t* d_sh_counts, int32_t* d_nnz,
                            uint32_t* d_kstar, uint32_t* d_tstar, uint64_t* d_keys);
 
+/* Size of the fixed device scratch used by ssh_hash_device_noalloc (16 MiB).
+ * Every GPU on which the library's device code is loaded holds it until the
+ * process exits. */
+#define SSH_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/* ssh_hash_device without any device allocation. The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc, such as a
+ * process whose device memory is all handed out by another framework's pool
+ * (an extra cudaMalloc could fail or fragment that pool), or a latency-bound
+ * loop that must not pay for, or fail on, a device allocation while it runs.
+ *
+ * Arguments, outputs and results are those of ssh_hash_device. The working
+ * buffers of the sketch / fix-up / shingle / minhash kernels live in one static
+ * device array of SSH_NOALLOC_SCRATCH_BYTES bytes instead of memory allocated
+ * per call. That limits how many series one call may hash (about 27,000 series
+ * of length 512 with W = 80, delta = 3, n = 15): a larger count returns
+ * SSH_EINVAL with the limit in ssh_last_error(), and nothing runs. Shapes for
+ * which no specialised kernels are compiled run the single-kernel path, which
+ * needs no scratch at all. The call makes no cudaMalloc, cudaFree or other
+ * allocating call.
+ *
+ * The first call on a device looks up the array's device address (the CUDA
+ * symbol lookup, with that device current); make that first call before any
+ * stream capture. Every call on a device uses the same array, which keeps the
+ * previous call's contents, so calls whose work overlaps on the GPU (other
+ * streams, other host threads) race and must be serialised by the caller. */
+ssh_status ssh_hash_device_noalloc(const ssh_index* idx, const float* d_series, int32_t m, int64_t count,
+                                   void* stream, uint32_t* d_bits, uint32_t* d_sh_ids, uint32_t* d_sh_counts,
+                                   int32_t* d_nnz, uint32_t* d_kstar, uint32_t* d_tstar, uint64_t* d_keys);
+
 /* Sec. 2.1 banded DTW for `npairs` pairs: d_out[p] = DTW(d_a + a_idx[p]*m, d_b + b_idx[p]*m)
  * with radius rb (0 <= rb < m), sum of squared costs. d_a_idx / d_b_idx are
  * int64 device arrays of row indexes into the row-major [*, m] arrays d_a, d_b.

@@ -67,6 +67,7 @@ _SIGS = {
     "ssh_get_kernel_times": (ctypes.c_int, [_P, ctypes.POINTER(ssh_kernel_time), ctypes.c_int,
                                             ctypes.POINTER(ctypes.c_int)]),
     "ssh_hash_device": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int64, _P] + [_P] * 7),
+    "ssh_hash_device_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int64, _P] + [_P] * 7),
     "ssh_dtw_device": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _P, _P]),
     "ssh_lb_keogh_device": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _P, _P]),
 }
@@ -214,6 +215,14 @@ def ssh_hash_device(h, d_series, m: int, count: int, d_bits=None, d_sh_ids=None,
     _check(load().ssh_hash_device(h, _dev_ptr(d_series), m, count, _stream(stream), _dev_ptr(d_bits),
                                   _dev_ptr(d_sh_ids), _dev_ptr(d_sh_counts), _dev_ptr(d_nnz), _dev_ptr(d_kstar),
                                   _dev_ptr(d_tstar), _dev_ptr(d_keys)))
+
+
+def ssh_hash_device_noalloc(h, d_series, m: int, count: int, d_bits=None, d_sh_ids=None, d_sh_counts=None,
+                            d_nnz=None, d_kstar=None, d_tstar=None, d_keys=None, stream=None) -> None:
+    """ssh_hash_device with its scratch in the library's fixed device array (no allocation)."""
+    _check(load().ssh_hash_device_noalloc(h, _dev_ptr(d_series), m, count, _stream(stream), _dev_ptr(d_bits),
+                                          _dev_ptr(d_sh_ids), _dev_ptr(d_sh_counts), _dev_ptr(d_nnz),
+                                          _dev_ptr(d_kstar), _dev_ptr(d_tstar), _dev_ptr(d_keys)))
 
 
 def ssh_dtw_device(d_a, d_a_idx, d_b, d_b_idx, m: int, rb: int, d_out, stream=None) -> None:

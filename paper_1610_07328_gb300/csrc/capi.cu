@@ -758,6 +758,15 @@ ssh_status check_device(const ssh_index* idx) {
 }
 
 }  // namespace
+
+ssh_status prepare_hash_args(const ssh_index* idx, int m, HashArgs* a) {
+    SSH_TRY(check_device(idx));
+    Geometry g;
+    SSH_TRY(geometry(idx, m, &g));
+    *a = base_hash_args(idx, m, g);
+    return SSH_OK;
+}
+
 }  // namespace ssh
 
 using namespace ssh;

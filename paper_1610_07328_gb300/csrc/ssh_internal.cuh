@@ -12,6 +12,8 @@
 
 #include "ssh.h"
 
+struct ssh_index;
+
 namespace ssh {
 
 // ------------------------------------------------------------------ errors
@@ -110,6 +112,10 @@ cudaError_t hash_fast_shingle(const HashArgs& a, const FastHashBuffers& b, cudaS
 cudaError_t hash_fast_cws(const HashArgs& a, const FastHashBuffers& b, cudaStream_t st);
 cudaError_t launch_hash_generic(const HashArgs& a, cudaStream_t st);
 int hash_smem_bytes_per_warp(int m, int nwords, int S, int KL);
+
+// Hash arguments of an index for series of length m (filter, draw tables,
+// geometry); SSH_ELENGTH if m gives no shingle or too many.
+ssh_status prepare_hash_args(const ssh_index* idx, int m, HashArgs* a);
 int hash_warps_per_cta(int m, int nwords, int S, int KL);
 cudaError_t launch_hash(const HashArgs& a, cudaStream_t st);
 
