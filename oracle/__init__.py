@@ -291,7 +291,7 @@ class OracleIndex:
         return first
 
     def candidates(self, q) -> np.ndarray:
-        """Algorithm 2 lines 6-9: the union R of the probed buckets (ids ascending)."""
+        """Algorithm 2: the union R of the buckets probed in every table (ids ascending)."""
         q = _f32(q)
         ks, ts = self.hash(q)
         found = set()

@@ -586,7 +586,7 @@ ssh_status query_group(ssh_index* idx, SubIndex& s, const std::vector<const floa
     SSH_CUDA(cudaMemcpyAsync(d_qptr, qptr.data(), nq * sizeof(float*), cudaMemcpyHostToDevice, st));
     SSH_CUDA(cudaMemcpyAsync(d_qpos, qpos.data(), nq * sizeof(int64_t), cudaMemcpyHostToDevice, st));
 
-    // Algorithm 2 lines 3-5: hash the queries
+    // Algorithm 2: hash the queries as the stored series were hashed
     uint64_t* qkeys;
     SSH_TRY(sc.get(&qkeys, (size_t)L * nq));
     HashArgs a = base_hash_args(idx, m, g);
@@ -598,7 +598,7 @@ ssh_status query_group(ssh_index* idx, SubIndex& s, const std::vector<const floa
     SSH_TRY(run_hash(idx, a, st, "query"));
     idx->host_stats.series_hashed += nq;
 
-    // lines 6-9: probe every table, union of the buckets
+    // Algorithm 2: probe every table, union of the buckets
     const int64_t words = (s.count + 31) / 32;
     uint32_t* bitmap;
     int64_t* counts;
@@ -652,7 +652,7 @@ ssh_status query_group(ssh_index* idx, SubIndex& s, const std::vector<const floa
         }
         idx->host_stats.dtw_computed += C;
     } else if (C > 0) {
-        // line 10 with UCR-style pruning: LB_Keogh of every candidate; DTW of the k
+        // Algorithm 2 reporting step with UCR-style pruning: LB_Keogh of every candidate; DTW of the k
         // smallest-LB candidates gives a bound U on the k-th best distance; DTW of
         // the rest only where LB * (1 - eta) <= U.
         float *upper, *lower;
