@@ -329,10 +329,13 @@ def run_gpu(args, w):
     idx = binding.SSHIndex(w["W"], w["delta"], w["n"], w["K"], w["L"], w["band"], w["seed"])
     stream = torch.cuda.current_stream()
 
+    lengths = np.full(N, m, np.int32)
+    qlengths = np.full(nq, m, np.int32)
+
     def step():
         idx.clear()
-        idx.add_device(d_db, borrow=True)
-        idx.query_device(d_q, k, d_ids, d_dists)
+        idx.add_device(d_db, lengths, borrow=True)
+        idx.query_device(d_q, k, d_ids, d_dists, lengths=qlengths)
 
     for _ in range(args.warmup):
         step()
@@ -352,9 +355,9 @@ def run_gpu(args, w):
     for s in range(args.steps):
         ev[1 + 3 * s].record(stream)
         idx.clear()
-        idx.add_device(d_db, borrow=True)
+        idx.add_device(d_db, lengths, borrow=True)
         ev[2 + 3 * s].record(stream)
-        idx.query_device(d_q, k, d_ids, d_dists)
+        idx.query_device(d_q, k, d_ids, d_dists, lengths=qlengths)
         ev[3 + 3 * s].record(stream)
     ev[-1].record(stream)
     torch.cuda.synchronize()
@@ -416,8 +419,7 @@ def run_gpu(args, w):
     # end to end through the public host API: H2D of the series and queries, D2H of the results
     h_db_np = h_db.numpy()
     h_q_np2 = h_q.numpy()
-    lengths = np.full(N, m, np.int32)
-    qlen = np.full(nq, m, np.int32)
+    qlen = qlengths
     e2e_steps = max(2, min(args.steps, 5))
     idx.clear()
     torch.cuda.synchronize()

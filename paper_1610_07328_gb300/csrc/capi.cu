@@ -513,20 +513,17 @@ ssh_status rebuild_tables(ssh_index* idx, SubIndex& s, cudaStream_t st) {
 // to back (device memory that stays valid while the index uses it).
 ssh_status add_series(ssh_index* idx, const float* dev, const int32_t* lengths, int64_t count, cudaStream_t st,
                       int64_t* first_id) {
-    // all lengths valid first: nothing is added on error
-    std::vector<int64_t> offs(count);
-    int64_t off = 0;
+    // all lengths valid first: nothing is added on error (each distinct run checked once)
     for (int64_t i = 0; i < count; ++i) {
+        if (i > 0 && lengths[i] == lengths[i - 1]) continue;
         Geometry g;
         if (lengths[i] <= 0) return fail(SSH_ELENGTH, "series %lld has length %d", (long long)i, lengths[i]);
         SSH_TRY(geometry(idx, lengths[i], &g));
-        offs[i] = off;
-        off += lengths[i];
     }
     const int64_t id0 = idx->next_id;
     std::vector<int> touched;
     // group consecutive runs of equal length
-    int64_t i = 0;
+    int64_t i = 0, run_off = 0;
     while (i < count) {
         int64_t j = i + 1;
         while (j < count && lengths[j] == lengths[i]) ++j;
@@ -547,7 +544,7 @@ ssh_status add_series(ssh_index* idx, const float* dev, const int32_t* lengths, 
         if (std::find(touched.begin(), touched.end(), m) == touched.end()) touched.push_back(m);
         SSH_TRY(reserve(idx, s, s.count + nrun, st));
         fill_rows_kernel<<<grid_for(nrun, 256, 8192), 256, 0, st>>>(s.row_ptr + s.count, s.gid + s.count, nrun,
-                                                                    dev + offs[i], m, id0 + i);
+                                                                    dev + run_off, m, id0 + i);
         note_launch();
         SSH_CUDA(cudaGetLastError());
         HashArgs a = base_hash_args(idx, m, g);
@@ -559,6 +556,7 @@ ssh_status add_series(ssh_index* idx, const float* dev, const int32_t* lengths, 
         SSH_TRY(run_hash(idx, a, st, "add"));
         s.count += nrun;
         idx->host_stats.series_hashed += nrun;
+        run_off += (int64_t)m * nrun;
         i = j;
     }
     for (int m : touched) {
@@ -814,6 +812,15 @@ ssh_status ssh_create(int W, int delta, int n, int K, int L, float band, uint64_
     if (e != cudaSuccess) {
         delete idx;
         return cuda_status(e, "cudaGetDevice");
+    }
+    {
+        // scratch comes from the device's default stream-ordered pool: keep freed
+        // blocks in the pool across synchronisations instead of returning them
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, idx->device) == cudaSuccess) {
+            uint64_t keep = UINT64_MAX;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
     }
 
     // Sec. 4.1 filter and the sign-test threshold tau * ||r|| (tau = max(1e-4, 2 gamma_W))

@@ -331,6 +331,155 @@ __global__ void __launch_bounds__(kCwsWarps * 32) shingle_kernel(HashArgs a, con
     }
 }
 
+// Shingles of one series by a warp-level counting sort, for 10 <= n <= 16:
+// every shingle id sets its bit in a shared-memory occupancy bitmap of the 2^n
+// ids (lane l owns the ids [l 2^n/32, (l+1) 2^n/32) and a summary word marking
+// which of its bitmap words are non-zero); walking the lanes' ranges in order
+// gives the distinct ids ascending, and an id whose bit was already set is a
+// repeat that adds to its run count (found by binary search in the sorted ids).
+// Only the touched words are cleared afterwards. Output layout as shingle_kernel.
+constexpr int kMaxShingleIdsPerLane = 32;  // ceil(S / 32) for S <= 1024
+
+struct BitmapLayout {
+    int bm, sum, pid, cid, cnt, total;
+};
+
+__host__ __device__ inline BitmapLayout bitmap_layout(int n, int S) {
+    BitmapLayout L;
+    int off = 0;
+    L.bm = off; off += a16(4 * (1 << (n - 5)));
+    L.sum = off; off += a16(4 * (1 << (n - 10)));
+    L.pid = off; off += a16(4 * S);
+    L.cid = off; off += a16(4 * S);
+    L.cnt = off; off += a16(4 * S);
+    L.total = off;
+    return L;
+}
+
+__global__ void __launch_bounds__(kCwsWarps * 32) shingle_bitmap_kernel(HashArgs a, const uint32_t* gbits,
+                                                                         uint32_t* sets, int2* sizes) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwords = a.nwords, S = a.S, n = a.n;
+    const BitmapLayout lay = bitmap_layout(n, S);
+    unsigned char* wb = smem + (size_t)warp * lay.total;
+    uint32_t* bm = reinterpret_cast<uint32_t*>(wb + lay.bm);
+    uint32_t* sum = reinterpret_cast<uint32_t*>(wb + lay.sum);
+    uint32_t* pid = reinterpret_cast<uint32_t*>(wb + lay.pid);  // the id at each position
+    uint32_t* cid = reinterpret_cast<uint32_t*>(wb + lay.cid);
+    uint32_t* cnt = reinterpret_cast<uint32_t*>(wb + lay.cnt);
+    const int nbm = 1 << (n - 5);         // bitmap words
+    const int wpl = nbm >> 5;             // bitmap words per lane (>= 1 for n >= 10)
+    const int spl = (wpl + 31) >> 5;      // summary words per lane
+    for (int w = lane; w < nbm; w += 32) bm[w] = 0u;
+    for (int w = lane; w < 32 * spl; w += 32) sum[w] = 0u;
+    __syncwarp();
+    const unsigned lt = (1u << lane) - 1u;
+    const int rounds = (S + 31) >> 5;
+    const int64_t nwarps = (int64_t)gridDim.x * kCwsWarps;
+    for (int64_t row = (int64_t)blockIdx.x * kCwsWarps + warp; row < a.count; row += nwarps) {
+        const uint32_t* brow = gbits + row * nwords;
+        uint32_t dup = 0;  // bit t set: position lane + 32 t repeats an earlier id
+        for (int t = 0; t < rounds; ++t) {
+            const int i = lane + 32 * t;
+            if (i < S) {
+                const int w0 = i >> 5;
+                const uint32_t hi = __ldg(brow + w0);
+                const uint32_t lo = (w0 + 1 < nwords) ? __ldg(brow + w0 + 1) : 0u;
+                const uint64_t bb = ((uint64_t)hi << 32) | (uint64_t)lo;
+                const uint32_t id = (uint32_t)((bb << (i & 31)) >> (64 - n));
+                pid[i] = id;
+                const uint32_t bit = 1u << (id & 31);
+                const uint32_t old = atomicOr(&bm[id >> 5], bit);
+                if (old & bit) dup |= 1u << t;
+                else if (old == 0u) atomicOr(&sum[(id >> 5) >> 5], 1u << ((id >> 5) & 31));
+            }
+        }
+        __syncwarp();
+        // sorted distinct ids: count per lane range, warp scan, then emit
+        int mine = 0;
+        for (int q = 0; q < spl; ++q) {
+            uint32_t sw = sum[lane * spl + q];
+            while (sw) {
+                const int b = __ffs(sw) - 1;
+                sw &= sw - 1;
+                mine += __popc(bm[(lane * spl + q) * 32 + b]);
+            }
+        }
+        int incl = mine;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += t;
+        }
+        int pos = incl - mine;
+        const int nnz = __shfl_sync(kFull, incl, 31);
+        for (int q = 0; q < spl; ++q) {
+            const int sidx = lane * spl + q;
+            uint32_t sw = sum[sidx];
+            while (sw) {
+                const int b = __ffs(sw) - 1;
+                sw &= sw - 1;
+                const int w = sidx * 32 + b;
+                uint32_t word = bm[w];
+                while (word) {
+                    const int c = __ffs(word) - 1;
+                    word &= word - 1;
+                    cid[pos] = ((uint32_t)w << 5) | (uint32_t)c;
+                    cnt[pos] = 1u;
+                    ++pos;
+                }
+            }
+        }
+        __syncwarp();
+        // repeats: add to the run of their id
+        for (int t = 0; t < rounds; ++t) {
+            if ((dup >> t) & 1u) {
+                const uint32_t id = pid[lane + 32 * t];
+                int lo = 0, hi = nnz - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (cid[mid] < id) lo = mid + 1; else hi = mid;
+                }
+                atomicAdd(&cnt[lo], 1u);
+            }
+        }
+        __syncwarp();
+        // clear the touched words for the next series
+        for (int i = lane; i < S; i += 32) bm[pid[i] >> 5] = 0u;
+        for (int q = 0; q < spl; ++q) sum[lane * spl + q] = 0u;
+        // the set in two ascending groups: seen once, then seen more than once (id | count << 16)
+        uint32_t* out = sets + row * S;
+        int n1 = 0, nm = 0;
+        for (int e0 = 0; e0 < nnz; e0 += 32) {
+            const int e = e0 + lane;
+            uint32_t c = 0, id = 0;
+            if (e < nnz) {
+                c = cnt[e];
+                id = cid[e];
+                if (a.sh_ids_out) {
+                    a.sh_ids_out[row * S + e] = id;
+                    a.sh_counts_out[row * S + e] = c;
+                }
+            }
+            const bool one = (e < nnz) && c == 1u, more = (e < nnz) && c > 1u;
+            const unsigned b1 = __ballot_sync(kFull, one), bmm = __ballot_sync(kFull, more);
+            __syncwarp();
+            if (one) cid[n1 + __popc(b1 & lt)] = id;                    // in place: n1 <= e0 + lane
+            if (more) cnt[nm + __popc(bmm & lt)] = id | (c << 16);      // in place: nm <= e0 + lane
+            n1 += __popc(b1);
+            nm += __popc(bmm);
+            __syncwarp();
+        }
+        for (int e = lane; e < n1 + nm; e += 32) out[e] = (e < n1) ? cid[e] : cnt[e - n1];
+        if (lane == 0) {
+            sizes[row] = make_int2(n1, nm);
+            if (a.nnz_out) a.nnz_out[row] = nnz;
+        }
+        __syncwarp();
+    }
+}
+
 constexpr int kCwsDepth = 16;  // rank loads in flight per lane
 
 struct CwsLayout {
@@ -399,7 +548,7 @@ __global__ void __launch_bounds__(kCwsWarps * 32, 4) cws_kernel(HashArgs a, cons
                     uint2 rv[kCwsDepth];
 #pragma unroll
                     for (int u = 0; u < kCwsDepth; ++u)
-                        rv[u] = __ldg(reinterpret_cast<const uint2*>(rk + (size_t)set[e + u] * kstride));
+                        rv[u] = __ldg(reinterpret_cast<const uint2*>(rk + set[e + u] * (uint32_t)kstride));
 #pragma unroll
                     for (int u = 0; u < kCwsDepth; ++u) {
                         m01 = __vminu2(m01, rv[u].x);
@@ -408,7 +557,7 @@ __global__ void __launch_bounds__(kCwsWarps * 32, 4) cws_kernel(HashArgs a, cons
                 }
 #pragma unroll 1
                 for (; e < n1; ++e) {
-                    const uint2 r2 = __ldg(reinterpret_cast<const uint2*>(rk + (size_t)set[e] * kstride));
+                    const uint2 r2 = __ldg(reinterpret_cast<const uint2*>(rk + set[e] * (uint32_t)kstride));
                     m01 = __vminu2(m01, r2.x);
                     m23 = __vminu2(m23, r2.y);
                 }
@@ -457,10 +606,10 @@ __global__ void __launch_bounds__(kCwsWarps * 32, 4) cws_kernel(HashArgs a, cons
                     }
                 } else {
                     // counts above the table: certified FP32 intervals
-#pragma unroll 1
+#pragma unroll
                     for (int q = 0; q < 4; ++q) {
                         const int j = j0 + q;
-                        if (j >= KL) break;
+                        if (j >= KL) continue;
                         CwsTrack tr;
                         tr.init();
 #pragma unroll 1
@@ -537,6 +686,23 @@ cudaError_t launch_shingle_t(const HashArgs& a, const uint32_t* bits, uint32_t* 
     const int64_t need = (a.count + kCwsWarps - 1) / kCwsWarps;
     if (grid > need) grid = need;
     shingle_kernel<E><<<(unsigned)grid, kCwsWarps * 32, smem, st>>>(a, bits, sets, sizes);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shingle_bitmap(const HashArgs& a, const uint32_t* bits, uint32_t* sets, int2* sizes,
+                                  cudaStream_t st) {
+    const BitmapLayout lay = bitmap_layout(a.n, a.S);
+    const size_t smem = (size_t)kCwsWarps * lay.total;
+    if (smem > 227 * 1024) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(shingle_bitmap_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, shingle_bitmap_kernel, kCwsWarps * 32, smem);
+    int64_t grid = (int64_t)sms_of_device() * (per_sm > 0 ? per_sm : 1);
+    const int64_t need = (a.count + kCwsWarps - 1) / kCwsWarps;
+    if (grid > need) grid = need;
+    shingle_bitmap_kernel<<<(unsigned)grid, kCwsWarps * 32, smem, st>>>(a, bits, sets, sizes);
     note_launch();
     return cudaGetLastError();
 }
@@ -650,6 +816,7 @@ cudaError_t hash_fast_fixup(const HashArgs& a, const FastHashBuffers& b, cudaStr
 }
 
 cudaError_t hash_fast_shingle(const HashArgs& a, const FastHashBuffers& b, cudaStream_t st) {
+    if (a.n >= 10 && a.S <= 32 * kMaxShingleIdsPerLane) return launch_shingle_bitmap(a, b.bits, b.sets, b.sizes, st);
     switch (cws_e(a.S)) {
         case 1: return launch_shingle_t<1>(a, b.bits, b.sets, b.sizes, st);
         case 2: return launch_shingle_t<2>(a, b.bits, b.sets, b.sizes, st);
