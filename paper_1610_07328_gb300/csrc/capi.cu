@@ -245,15 +245,6 @@ __global__ void fill_rows_kernel(const float** row_ptr, int64_t* gid, int64_t n,
     }
 }
 
-__global__ void copy_keys_kernel(const uint64_t* keys, uint64_t* skeys, uint32_t* srows, int64_t n, int64_t cap,
-                                 int L) {
-    const int l = blockIdx.y;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        skeys[(int64_t)l * cap + i] = keys[(int64_t)l * cap + i];
-        srows[(int64_t)l * cap + i] = (uint32_t)i;
-    }
-}
-
 __global__ void gather_ptrs_kernel(const uint32_t* rows, int64_t n, const float* const* row_ptr, const float** out) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         out[i] = row_ptr[rows[i]];
@@ -437,6 +428,7 @@ void free_sub(SubIndex& s) {
     cudaFree(s.keys);
     cudaFree(s.skeys);
     cudaFree(s.srows);
+    cudaFree(s.bins);
     for (void* p : s.owned) cudaFree(p);
     s = SubIndex();
 }
@@ -487,25 +479,23 @@ ssh_status reserve(ssh_index* idx, SubIndex& s, int64_t need, cudaStream_t st) {
     return SSH_OK;
 }
 
-// Rebuild the sorted tables of a sub-index from its per-row keys.
+// Rebuild the bucket tables of a sub-index from its per-row keys.
 ssh_status rebuild_tables(ssh_index* idx, SubIndex& s, cudaStream_t st) {
     const int L = idx->L;
     const int64_t n = s.count;
-    if (n == 0) return SSH_OK;
-    dim3 grid(grid_for(n, 256, 4096), (unsigned)L);
-    copy_keys_kernel<<<grid, 256, 0, st>>>(s.keys, s.skeys, s.srows, n, s.cap, L);
-    note_launch();
-    SSH_CUDA(cudaGetLastError());
-    if (n < 2) return SSH_OK;
+    const int bits = table_bin_bits(n);
+    if (bits > s.bins_alloc_bits) {
+        cudaFree(s.bins);
+        s.bins = nullptr;
+        s.bins_alloc_bits = 0;
+        SSH_CUDA(cudaMalloc(&s.bins, (size_t)L * (((size_t)1 << bits) + 1) * sizeof(uint32_t)));
+        s.bins_alloc_bits = bits;
+    }
+    s.bin_bits = bits;
     ScratchList sc(st);
-    uint64_t* kalt;
-    uint32_t* valt;
-    void* hist;
-    SSH_TRY(sc.get(&kalt, (size_t)L * s.cap));
-    SSH_TRY(sc.get(&valt, (size_t)L * s.cap));
-    const size_t hb = radix_sort_scratch_bytes(n, L);
-    SSH_TRY(sc.get(reinterpret_cast<unsigned char**>(&hist), hb));
-    SSH_CUDA(radix_sort_pairs_u64(s.skeys, s.srows, kalt, valt, n, L, s.cap, hist, hb, st, kTableSortFirstBit));
+    uint32_t* cursor;
+    SSH_TRY(sc.get(&cursor, (size_t)L * (((size_t)1 << bits) + 1)));
+    SSH_CUDA(build_tables(s.keys, n, L, s.cap, bits, s.bins, cursor, s.skeys, s.srows, st));
     return SSH_OK;
 }
 
@@ -603,7 +593,7 @@ ssh_status query_group(ssh_index* idx, SubIndex& s, const std::vector<const floa
     SSH_TRY(sc.get(&bitmap, (size_t)nq * words));
     SSH_TRY(sc.get(&counts, nq));
     SSH_CUDA(cudaMemsetAsync(bitmap, 0, (size_t)nq * words * sizeof(uint32_t), st));
-    ProbeArgs pa{qkeys, nq, L, s.skeys, s.srows, s.cap, s.count, bitmap, words};
+    ProbeArgs pa{qkeys, nq, L, s.skeys, s.srows, s.bins, s.bin_bits, s.cap, s.count, bitmap, words};
     {
         TimedRegion tr(idx, st, "query.probe_union", (double)nq * L);
         SSH_CUDA(launch_probe_union(pa, st));

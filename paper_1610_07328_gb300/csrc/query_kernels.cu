@@ -21,27 +21,13 @@ __global__ void probe_union_kernel(ProbeArgs a) {
     const uint64_t key = a.qkeys[l * a.nq + q];
     const uint64_t* sk = a.skeys + l * a.cap;
     const uint32_t* sr = a.srows + l * a.cap;
-    __shared__ int64_t range[2];
-    if (threadIdx.x == 0) {
-        // the tables are ordered by the upper 32 key bits: find that run
-        const uint32_t hk = (uint32_t)(key >> kTableSortFirstBit);
-        int64_t lo = 0, hi = a.nrows;
-        while (lo < hi) {
-            const int64_t mid = (lo + hi) >> 1;
-            if ((uint32_t)(sk[mid] >> kTableSortFirstBit) < hk) lo = mid + 1; else hi = mid;
-        }
-        int64_t lo2 = lo, hi2 = a.nrows;
-        while (lo2 < hi2) {
-            const int64_t mid = (lo2 + hi2) >> 1;
-            if ((uint32_t)(sk[mid] >> kTableSortFirstBit) <= hk) lo2 = mid + 1; else hi2 = mid;
-        }
-        range[0] = lo;
-        range[1] = lo2;
-    }
-    __syncthreads();
+    // the key's bin: every row with this key is in it
+    const uint32_t* bn = a.bins + l * ((int64_t(1) << a.bin_bits) + 1);
+    const uint32_t bin = (uint32_t)(key >> (64 - a.bin_bits));
+    const int64_t b0 = bn[bin], b1 = bn[bin + 1];
     uint32_t* bm = a.bitmap + q * a.words;
-    for (int64_t i = range[0] + threadIdx.x; i < range[1]; i += blockDim.x) {
-        if (sk[i] != key) continue;  // same upper half, different key
+    for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
+        if (sk[i] != key) continue;  // same bin, different key
         const uint32_t row = sr[i];
         atomicOr(&bm[row >> 5], 1u << (row & 31));
     }

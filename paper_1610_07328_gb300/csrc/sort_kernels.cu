@@ -1,6 +1,12 @@
-// sort_kernels.cu -- device-resident bucket tables of Algorithm 1 are built by a
-// stable LSD radix sort of (64-bit key, 32-bit row) pairs, one segment per
-// table; the top-k of Algorithm 2 uses a per-segment radix select.
+// sort_kernels.cu -- the device-resident bucket tables of Algorithm 1 and the
+// selections of Algorithm 2.
+//
+// Tables: one most-significant-digit radix pass per table. The top B bits of
+// each 64-bit bucket key pick one of 2^B bins (B chosen so a bin holds about
+// 16 rows); a histogram, an exclusive scan and a scatter place every (key, row)
+// in its bin. Equal keys always share a bin, so a probe scans the query key's
+// bin and compares full keys; the order inside a bin is not used.
+// Selections: per-segment radix select of the k-th smallest key.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -9,111 +15,7 @@
 namespace ssh {
 namespace {
 
-constexpr int kSortThreads = 256;
-constexpr int kSortItems = 16;                       // items per thread
-constexpr int kSortTile = kSortThreads * kSortItems;  // 4096 items per CTA
-constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kRadix = 256;
-constexpr unsigned kFull = 0xFFFFFFFFu;
-
-__global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(const uint64_t* keys, int64_t n, int64_t seg_stride,
-                                                                  int shift, int ntiles, uint32_t* counts) {
-    __shared__ uint32_t h[kRadix];
-    const int seg = blockIdx.y, tile = blockIdx.x;
-    for (int d = threadIdx.x; d < kRadix; d += blockDim.x) h[d] = 0;
-    __syncthreads();
-    const uint64_t* k = keys + (int64_t)seg * seg_stride;
-    const int64_t base = (int64_t)tile * kSortTile;
-    for (int t = threadIdx.x; t < kSortTile; t += blockDim.x) {
-        const int64_t i = base + t;
-        if (i < n) atomicAdd(&h[(uint32_t)(k[i] >> shift) & 0xFFu], 1u);
-    }
-    __syncthreads();
-    uint32_t* c = counts + (int64_t)seg * kRadix * ntiles;
-    for (int d = threadIdx.x; d < kRadix; d += blockDim.x) c[(int64_t)d * ntiles + tile] = h[d];
-}
-
-// Exclusive scan of one segment's digit-major counts (kRadix * ntiles values).
-__global__ void __launch_bounds__(1024) radix_scan_kernel(uint32_t* counts, int ntiles) {
-    __shared__ uint32_t part[1024];
-    const int seg = blockIdx.x;
-    uint32_t* c = counts + (int64_t)seg * kRadix * ntiles;
-    const int64_t total = (int64_t)kRadix * ntiles;
-    const int64_t per = (total + blockDim.x - 1) / blockDim.x;
-    const int64_t b = threadIdx.x * per, e = min(total, b + per);
-    uint32_t s = 0;
-    for (int64_t i = b; i < e; ++i) s += c[i];
-    part[threadIdx.x] = s;
-    __syncthreads();
-    for (int off = 1; off < (int)blockDim.x; off <<= 1) {
-        uint32_t v = threadIdx.x >= (unsigned)off ? part[threadIdx.x - off] : 0u;
-        __syncthreads();
-        part[threadIdx.x] += v;
-        __syncthreads();
-    }
-    uint32_t run = threadIdx.x ? part[threadIdx.x - 1] : 0u;
-    for (int64_t i = b; i < e; ++i) {
-        uint32_t v = c[i];
-        c[i] = run;
-        run += v;
-    }
-}
-
-__global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(const uint64_t* keys_in, const uint32_t* vals_in,
-                                                                     uint64_t* keys_out, uint32_t* vals_out, int64_t n,
-                                                                     int64_t seg_stride, int shift, int ntiles,
-                                                                     const uint32_t* offsets) {
-    __shared__ uint32_t wcnt[kSortWarps][kRadix];
-    const int seg = blockIdx.y, tile = blockIdx.x;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int d = lane; d < kRadix; d += 32) wcnt[warp][d] = 0;
-    __syncwarp();
-    const uint64_t* ki = keys_in + (int64_t)seg * seg_stride;
-    const uint32_t* vi = vals_in + (int64_t)seg * seg_stride;
-    const int64_t wbase = (int64_t)tile * kSortTile + (int64_t)warp * (32 * kSortItems);
-    uint64_t key[kSortItems];
-    uint32_t val[kSortItems];
-    uint32_t loc[kSortItems];
-    const unsigned lt = (1u << lane) - 1u;
-#pragma unroll
-    for (int r = 0; r < kSortItems; ++r) {
-        const int64_t i = wbase + r * 32 + lane;
-        const bool ok = i < n;
-        key[r] = ok ? ki[i] : 0ull;
-        val[r] = ok ? vi[i] : 0u;
-        const uint32_t d = ok ? ((uint32_t)(key[r] >> shift) & 0xFFu) : 0x100u;
-        const unsigned peers = __match_any_sync(kFull, d);
-        const uint32_t before = (d < 0x100u) ? wcnt[warp][d] : 0u;
-        loc[r] = before + __popc(peers & lt);
-        __syncwarp();
-        if (d < 0x100u && (peers & lt) == 0) wcnt[warp][d] = before + __popc(peers);
-        __syncwarp();
-    }
-    __syncthreads();
-    // prefix over warps per digit (warp order = item order within the tile)
-    for (int d = threadIdx.x; d < kRadix; d += blockDim.x) {
-        uint32_t run = 0;
-        for (int w = 0; w < kSortWarps; ++w) {
-            uint32_t v = wcnt[w][d];
-            wcnt[w][d] = run;
-            run += v;
-        }
-    }
-    __syncthreads();
-    const uint32_t* off = offsets + (int64_t)seg * kRadix * ntiles;
-    uint64_t* ko = keys_out + (int64_t)seg * seg_stride;
-    uint32_t* vo = vals_out + (int64_t)seg * seg_stride;
-#pragma unroll
-    for (int r = 0; r < kSortItems; ++r) {
-        const int64_t i = wbase + r * 32 + lane;
-        if (i < n) {
-            const uint32_t d = (uint32_t)(key[r] >> shift) & 0xFFu;
-            const int64_t dst = (int64_t)off[(int64_t)d * ntiles + tile] + wcnt[warp][d] + loc[r];
-            ko[dst] = key[r];
-            vo[dst] = val[r];
-        }
-    }
-}
 
 // ------------------------------------------------------------ radix select
 
@@ -159,38 +61,87 @@ __global__ void __launch_bounds__(512) select_kth_kernel(const T* keys, const in
     if (threadIdx.x == 0) kth_out[seg] = s_prefix;
 }
 
-}  // namespace
+// ---------------------------------------------------- table partition
 
-size_t radix_sort_scratch_bytes(int64_t n, int nseg) {
-    const int64_t ntiles = (n + kSortTile - 1) / kSortTile;
-    return (size_t)nseg * kRadix * (size_t)(ntiles > 0 ? ntiles : 1) * sizeof(uint32_t);
+__global__ void bin_hist_kernel(const uint64_t* keys, int64_t n, int64_t cap, int shift, int nbins,
+                                uint32_t* counts) {
+    const int l = blockIdx.y;
+    const uint64_t* k = keys + (int64_t)l * cap;
+    uint32_t* c = counts + (int64_t)l * (nbins + 1);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&c[(uint32_t)(k[i] >> shift)], 1u);
 }
 
-cudaError_t radix_sort_pairs_u64(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt, int64_t n,
-                                 int nseg, int64_t seg_stride, void* scratch, size_t scratch_bytes, cudaStream_t st,
-                                 int first_bit) {
-    if (n <= 1 || nseg <= 0) return cudaSuccess;
-    const int64_t ntiles = (n + kSortTile - 1) / kSortTile;
-    if (scratch_bytes < radix_sort_scratch_bytes(n, nseg) || ntiles > (1 << 24)) return cudaErrorInvalidValue;
-    uint32_t* counts = static_cast<uint32_t*>(scratch);
-    uint64_t* kin = keys;
-    uint32_t* vin = vals;
-    uint64_t* kout = keys_alt;
-    uint32_t* vout = vals_alt;
-    dim3 grid((unsigned)ntiles, (unsigned)nseg);
-    if (first_bit < 0 || first_bit > 56 || (first_bit % 16) != 0) return cudaErrorInvalidValue;
-    for (int shift = first_bit; shift < 64; shift += 8) {
-        radix_hist_kernel<<<grid, kSortThreads, 0, st>>>(kin, n, seg_stride, shift, (int)ntiles, counts);
-        note_launch();
-        radix_scan_kernel<<<nseg, 1024, 0, st>>>(counts, (int)ntiles);
-        note_launch();
-        radix_scatter_kernel<<<grid, kSortThreads, 0, st>>>(kin, vin, kout, vout, n, seg_stride, shift, (int)ntiles,
-                                                            counts);
-        note_launch();
-        uint64_t* tk = kin; kin = kout; kout = tk;
-        uint32_t* tv = vin; vin = vout; vout = tv;
+// Exclusive scan of one table's bin counts in place (nbins + 1 entries: the
+// last becomes n), and a copy into the scatter cursors.
+__global__ void __launch_bounds__(1024) bin_scan_kernel(uint32_t* counts, uint32_t* cursor, int nbins) {
+    __shared__ uint32_t part[1024];
+    const int l = blockIdx.x;
+    uint32_t* c = counts + (int64_t)l * (nbins + 1);
+    uint32_t* cur = cursor + (int64_t)l * (nbins + 1);
+    const int total = nbins + 1;
+    const int per = (total + blockDim.x - 1) / blockDim.x;
+    const int b = threadIdx.x * per, e = min(total, b + per);
+    uint32_t s = 0;
+    for (int i = b; i < e; ++i) s += c[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int off = 1; off < (int)blockDim.x; off <<= 1) {
+        const uint32_t v = threadIdx.x >= (unsigned)off ? part[threadIdx.x - off] : 0u;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
     }
-    return cudaGetLastError();  // an even number of passes: the sorted data is back in (keys, vals)
+    uint32_t run = threadIdx.x ? part[threadIdx.x - 1] : 0u;
+    for (int i = b; i < e; ++i) {
+        const uint32_t v = c[i];
+        c[i] = run;
+        cur[i] = run;
+        run += v;
+    }
+}
+
+__global__ void bin_scatter_kernel(const uint64_t* keys, int64_t n, int64_t cap, int shift, int nbins,
+                                   uint32_t* cursor, uint64_t* skeys, uint32_t* srows) {
+    const int l = blockIdx.y;
+    const uint64_t* k = keys + (int64_t)l * cap;
+    uint32_t* cur = cursor + (int64_t)l * (nbins + 1);
+    uint64_t* sk = skeys + (int64_t)l * cap;
+    uint32_t* sr = srows + (int64_t)l * cap;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t key = k[i];
+        const uint32_t pos = atomicAdd(&cur[(uint32_t)(key >> shift)], 1u);
+        sk[pos] = key;
+        sr[pos] = (uint32_t)i;
+    }
+}
+
+}  // namespace
+
+int table_bin_bits(int64_t n) {
+    int b = 1;
+    while (b < 30 && ((int64_t)1 << (b + 4)) < n) ++b;  // about 16 rows per bin
+    if (b < 8) b = 8;
+    if (b > 24) b = 24;
+    return b;
+}
+
+cudaError_t build_tables(const uint64_t* keys, int64_t n, int L, int64_t cap, int bin_bits, uint32_t* bins,
+                         uint32_t* cursor, uint64_t* skeys, uint32_t* srows, cudaStream_t st) {
+    const int nbins = 1 << bin_bits;
+    const int shift = 64 - bin_bits;
+    cudaError_t e = cudaMemsetAsync(bins, 0, (size_t)L * (nbins + 1) * sizeof(uint32_t), st);
+    if (e != cudaSuccess || n <= 0) return e;
+    int64_t g = (n + 255) / 256;
+    if (g > 4096) g = 4096;
+    dim3 grid((unsigned)g, (unsigned)L);
+    bin_hist_kernel<<<grid, 256, 0, st>>>(keys, n, cap, shift, nbins, bins);
+    note_launch();
+    bin_scan_kernel<<<(unsigned)L, 1024, 0, st>>>(bins, cursor, nbins);
+    note_launch();
+    bin_scatter_kernel<<<grid, 256, 0, st>>>(keys, n, cap, shift, nbins, cursor, skeys, srows);
+    note_launch();
+    return cudaGetLastError();
 }
 
 cudaError_t launch_select_kth_u32(const uint32_t* keys, const int64_t* seg_begin, int64_t nseg, int k,

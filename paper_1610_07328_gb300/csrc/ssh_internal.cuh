@@ -121,26 +121,21 @@ cudaError_t launch_hash(const HashArgs& a, cudaStream_t st);
 
 // ------------------------------------------------------------ radix sort
 
-// Sort (key, val) pairs stably by key bits [first_bit, 64) (first_bit a multiple
-// of 16), independently in each of `nseg` segments of `n` consecutive items.
-// Ping-pongs between (keys, vals) and (keys_alt, vals_alt); the result ends in
-// (keys, vals).
-cudaError_t radix_sort_pairs_u64(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt,
-                                 int64_t n, int nseg, int64_t seg_stride, void* scratch, size_t scratch_bytes,
-                                 cudaStream_t st, int first_bit);
-
-// The bucket tables are sorted on the upper 32 key bits only: a probe finds the
-// run of equal upper halves and compares the full 64-bit keys inside it.
-constexpr int kTableSortFirstBit = 32;
-size_t radix_sort_scratch_bytes(int64_t n, int nseg);
+// Bucket tables: per table, the (key, row) pairs partitioned into 2^bin_bits
+// bins by the top bin_bits key bits; bins[l][b] .. bins[l][b+1] is bin b.
+int table_bin_bits(int64_t n);
+cudaError_t build_tables(const uint64_t* keys, int64_t n, int L, int64_t cap, int bin_bits, uint32_t* bins,
+                         uint32_t* cursor, uint64_t* skeys, uint32_t* srows, cudaStream_t st);
 
 // -------------------------------------------------------------- queries
 
 struct ProbeArgs {
     const uint64_t* qkeys;     // [L][nq]
     int64_t nq, L;
-    const uint64_t* skeys;     // [L][cap] sorted keys of the sub-index
-    const uint32_t* srows;     // [L][cap] rows in key order
+    const uint64_t* skeys;     // [L][cap] keys of the sub-index grouped by bin
+    const uint32_t* srows;     // [L][cap] rows in the same order
+    const uint32_t* bins;      // [L][2^bin_bits + 1] bin starts
+    int bin_bits;
     int64_t cap, nrows;
     uint32_t* bitmap;          // [nq][words] candidate bitmap
     int64_t words;
@@ -192,8 +187,10 @@ struct SubIndex {
     const float** row_ptr = nullptr;  // [cap] device: series pointer of each row
     int64_t* gid = nullptr;           // [cap] device: id of each row
     uint64_t* keys = nullptr;         // [L][cap] device: bucket keys by row
-    uint64_t* skeys = nullptr;        // [L][cap] device: keys sorted
-    uint32_t* srows = nullptr;        // [L][cap] device: rows in key order
+    uint64_t* skeys = nullptr;        // [L][cap] device: keys grouped by bin
+    uint32_t* srows = nullptr;        // [L][cap] device: rows in the same order
+    uint32_t* bins = nullptr;         // [L][2^bin_bits + 1] device: bin starts
+    int bin_bits = 0, bins_alloc_bits = 0;
     std::vector<void*> owned;         // device chunks owned by the index
 };
 
