@@ -123,6 +123,15 @@ ssh_status ssh_query(ssh_index* idx, const float* queries, const int32_t* length
 ssh_status ssh_query_device(ssh_index* idx, const float* d_queries, const int32_t* lengths, int64_t nq, int k,
                             int64_t* d_ids, float* d_dists, void* stream);
 
+/* Alg. 2 over several indexes at once, for collections whose filter length W
+ * depends on the series length (one index per (length, W)): query i goes to the
+ * first handle in handles[0..nh) that stores series of length lengths[i], and
+ * d_which[i] (device int32, may be NULL) receives that handle's position; ids
+ * are that handle's ids. Results as in ssh_query_device. SSH_ELENGTH if no
+ * handle stores a query's length. All handles must live on the current device. */
+ssh_status ssh_group_query_device(ssh_index* const* handles, int nh, const float* d_queries, const int32_t* lengths,
+                                  int64_t nq, int k, int64_t* d_ids, float* d_dists, int32_t* d_which, void* stream);
+
 /* Options. SSH_OPT_LB_PRUNE (default 1): LB_Keogh pruning before DTW in the
  * rerank; 0 computes DTW for every candidate (same results, more work).
  * SSH_OPT_KERNEL_TIMING (default 0): record CUDA events around each kernel

@@ -61,6 +61,7 @@ _SIGS = {
     "ssh_index_size": (ctypes.c_int, [_P, _I64P]),
     "ssh_query": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, ctypes.c_int, _P, _P]),
     "ssh_query_device": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, ctypes.c_int, _P, _P, _P]),
+    "ssh_group_query_device": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_int64, ctypes.c_int, _P, _P, _P, _P]),
     "ssh_set_option": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int64]),
     "ssh_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(ssh_stats)]),
     "ssh_reset_stats": (ctypes.c_int, [_P]),
@@ -183,6 +184,16 @@ def ssh_query_device(h, d_queries, lengths: np.ndarray, k: int, d_ids, d_dists, 
     ln = np.ascontiguousarray(lengths, dtype=np.int32)
     _check(load().ssh_query_device(h, _dev_ptr(d_queries), _host_ptr(ln), len(ln), k, _dev_ptr(d_ids),
                                    _dev_ptr(d_dists), _stream(stream)))
+
+
+def ssh_group_query_device(handles, d_queries, lengths: np.ndarray, k: int, d_ids, d_dists, d_which=None,
+                           stream=None) -> None:
+    """Queries of mixed lengths over several indexes (one per length and filter length)."""
+    arr = (ctypes.c_void_p * len(handles))(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in handles])
+    ln = np.ascontiguousarray(lengths, dtype=np.int32)
+    _check(load().ssh_group_query_device(ctypes.cast(arr, ctypes.c_void_p), len(handles), _dev_ptr(d_queries),
+                                         _host_ptr(ln), len(ln), k, _dev_ptr(d_ids), _dev_ptr(d_dists),
+                                         _dev_ptr(d_which), _stream(stream)))
 
 
 def ssh_set_option(h, opt: int, value: int) -> None:

@@ -738,6 +738,11 @@ ssh_status run_query(ssh_index* idx, const float* d_queries, const int32_t* leng
     return SSH_OK;
 }
 
+__global__ void fill_i32_kernel(int32_t* p, int64_t n, const int64_t* pos, int32_t v) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[pos[i]] = v;
+}
+
 ssh_status check_device(const ssh_index* idx) {
     int dev = -1;
     SSH_CUDA(cudaGetDevice(&dev));
@@ -1066,6 +1071,56 @@ ssh_status ssh_query_device(ssh_index* idx, const float* d_queries, const int32_
     if (nq == 0) return SSH_OK;
     LaunchCount lc(idx);
     return run_query(idx, d_queries, lengths, nq, k, d_ids, d_dists, (cudaStream_t)stream);
+}
+
+ssh_status ssh_group_query_device(ssh_index* const* handles, int nh, const float* d_queries, const int32_t* lengths,
+                                  int64_t nq, int k, int64_t* d_ids, float* d_dists, int32_t* d_which, void* stream) {
+    if (!handles || nh < 1 || nq < 0 || (nq > 0 && (!d_queries || !lengths || !d_ids || !d_dists)))
+        return fail(SSH_EINVAL, "bad arguments");
+    for (int h = 0; h < nh; ++h)
+        if (!handles[h]) return fail(SSH_EINVAL, "handle %d is NULL", h);
+    if (k < 1 || k > kMaxTopK) return fail(SSH_EINVAL, "k = %d outside [1, %d]", k, kMaxTopK);
+    if (nq == 0) return SSH_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    // route every query to the first handle holding series of its length
+    std::map<std::pair<int, int>, std::pair<std::vector<const float*>, std::vector<int64_t>>> groups;
+    int64_t off = 0;
+    for (int64_t i = 0; i < nq; ++i) {
+        const int m = lengths[i];
+        int owner = -1;
+        for (int h = 0; h < nh && owner < 0; ++h) {
+            auto it = handles[h]->subs.find(m);
+            if (it != handles[h]->subs.end() && it->second.count > 0) owner = h;
+        }
+        if (m <= 0 || owner < 0)
+            return fail(SSH_ELENGTH, "query %lld has length %d, which no handle stores", (long long)i, m);
+        auto& g = groups[{owner, m}];
+        g.first.push_back(d_queries + off);
+        g.second.push_back(i);
+        off += m;
+    }
+    for (auto& kv : groups) {
+        ssh_index* idx = handles[kv.first.first];
+        SSH_TRY(check_device(idx));
+        LaunchCount lc(idx);
+        SSH_TRY(query_group(idx, idx->subs[kv.first.second], kv.second.first, kv.second.second, k, d_ids, d_dists, st));
+        if (d_which) {
+            const std::vector<int64_t>& pos = kv.second.second;
+            int64_t* d_pos = nullptr;
+            SSH_CUDA(cudaMallocAsync(&d_pos, pos.size() * sizeof(int64_t), st));
+            cudaError_t e = cudaMemcpyAsync(d_pos, pos.data(), pos.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess) {
+                fill_i32_kernel<<<grid_for((int64_t)pos.size(), 256, 1024), 256, 0, st>>>(d_which, (int64_t)pos.size(),
+                                                                                       d_pos, kv.first.first);
+                note_launch();
+                e = cudaGetLastError();
+            }
+            cudaFreeAsync(d_pos, st);
+            SSH_CUDA(e);
+        }
+    }
+    SSH_CUDA(cudaStreamSynchronize(st));
+    return SSH_OK;
 }
 
 ssh_status ssh_set_option(ssh_index* idx, ssh_option opt, int64_t value) {

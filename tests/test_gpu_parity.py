@@ -367,3 +367,47 @@ def test_errors_are_status_codes():
         idx.add(synth.random_walk(10, 128, seed=1))
         ids, _ = idx.query(synth.random_walk(10, 128, seed=1)[:1], 1)
         assert ids[0, 0] == 0
+
+
+def test_group_query_routes_mixed_lengths_to_per_length_indexes():
+    """Per-length filter W = m/8 (one index per length); queries of mixed lengths in one call."""
+    b = _binding()
+    lens = [128, 256, 512]
+    dbs = {m: synth.random_walk(150, m, seed=m + 3) for m in lens}
+    idxs, refs = [], {}
+    try:
+        for m in lens:
+            cfg = dict(W=m // 8, delta=3, n=15, K=4, L=25, band=0.05, seed=0)
+            ix = _index(cfg)
+            ix.add(dbs[m])
+            idxs.append(ix)
+            refs[m] = oracle.OracleIndex(**cfg)
+            refs[m].add(dbs[m])
+        qs, qlens = [], []
+        rng = np.random.default_rng(0)
+        for t in range(12):
+            m = lens[int(rng.integers(0, 3))]
+            q, _ = synth.perturbed_queries(dbs[m], 1, seed=100 + t)
+            qs.append(q[0])
+            qlens.append(m)
+        k = 5
+        d_q = torch.from_numpy(np.concatenate(qs)).cuda()
+        ids = torch.empty((len(qs), k), dtype=torch.int64, device="cuda")
+        dd = torch.empty((len(qs), k), dtype=torch.float32, device="cuda")
+        which = torch.full((len(qs),), -1, dtype=torch.int32, device="cuda")
+        b.ssh_group_query_device([ix.handle for ix in idxs], d_q, np.array(qlens, np.int32), k, ids, dd, which)
+        torch.cuda.synchronize()
+        ids, dd, which = ids.cpu().numpy(), dd.cpu().numpy(), which.cpu().numpy()
+        for i, (q, m) in enumerate(zip(qs, qlens)):
+            assert which[i] == lens.index(m)
+            oi, od = refs[m].query(q, k)
+            assert_topk_match(q, ids[i], dd[i], oi, od, lambda j: dbs[m][j], oracle.band_radius(0.05, m))
+        bad_ids = torch.empty((1, k), dtype=torch.int64, device="cuda")
+        bad_d = torch.empty((1, k), dtype=torch.float32, device="cuda")
+        with pytest.raises(b.SSHError) as e:
+            b.ssh_group_query_device([ix.handle for ix in idxs], torch.zeros((1, 100), device="cuda"),
+                                     np.array([100], np.int32), k, bad_ids, bad_d)
+        assert e.value.status == b.SSH_ELENGTH
+    finally:
+        for ix in idxs:
+            ix.close()
