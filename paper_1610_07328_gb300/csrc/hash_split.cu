@@ -12,12 +12,14 @@
 //    word (window i -> bit 31 - i%32 of word i/32) into global memory.
 //  sketch_fixup_kernel: one thread per listed window recomputes the dot product
 //    in FP64 in the definition's order and sets the bit when it is >= 0.
-//  shingle_cws_kernel<E>: one warp per series: the S = N_B - n + 1 shingle ids
-//    (first bit most significant) are sorted by a bitonic network over 32E
-//    registers with warp shuffles and run-length encoded with a ballot scan;
-//    each lane then owns 4 consecutive hash functions: one 64-bit load brings
-//    the 4 exact count-1 ranks of a shingle and SIMD u16 mins keep the minima,
-//    repeated shingles go through the certified FP32 interval track, and an
+//  shingle_kernel: one warp per series: the S = N_B - n + 1 shingle ids (first
+//    bit most significant) go into a per-warp open-addressing table in shared
+//    memory that counts repeats; the owners of the distinct ids write the
+//    weighted set, ids seen once first.
+//  cws_kernel: one warp per series; each lane owns 4 consecutive hash
+//    functions: one 64-bit load brings the 4 exact count-1 ranks of a shingle
+//    and SIMD u16 mins keep the minima, repeated shingles go through the
+//    tabulated exact values or the certified FP32 interval track, and an
 //    uncertain hash is recomputed in FP64 (hash_common.cuh). Its shared memory
 //    is small, so many warps per SM hide the L2 latency of the rank lookups.
 #include <cuda_runtime.h>
@@ -31,7 +33,6 @@ namespace {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
 constexpr int kSketchWarps = 8;
-constexpr int kCwsWarps = 8;
 
 __host__ __device__ inline int a16(int b) { return (b + 15) & ~15; }
 
@@ -197,284 +198,150 @@ __global__ void sketch_fixup_kernel(HashArgs a, uint32_t* bits, const unsigned l
 }
 
 // Per-series weighted set as written by shingle_kernel: S slots of u32, the n1
-// shingles seen once first (id), then the nm repeated ones (id | count << 16),
-// each group in ascending id order; sizes[row] = (n1, nm).
+// shingles seen once first (id), then the nm repeated ones (id | count << 16);
+// sizes[row] = (n1, nm). Within a group the order is that of first occurrence:
+// every consumer takes an argmin with an explicit tie rule, so the order of a
+// set does not matter.
 __device__ __forceinline__ uint32_t set_id(uint32_t v) { return v & 0xFFFFu; }
 __device__ __forceinline__ uint32_t set_count(uint32_t v) { return v >> 16; }
 
+// Shared memory of one shingle warp: an open-addressing table of 2^tbits slots
+// (2^tbits >= 2S, so at most half full), the slot of each position (bit 31: the
+// position inserted the id first), and, when the caller asked for the sorted
+// set, the set itself for ranking.
 struct ShingleLayout {
-    int bits, hpos, cid, total;
+    int tbits, tab, pos, cid, total;
 };
 
-__host__ __device__ inline ShingleLayout shingle_layout(int nwords, int S) {
+__host__ __device__ inline ShingleLayout shingle_layout(int S, bool sorted_out) {
     ShingleLayout L;
+    L.tbits = 6;
+    while ((1 << L.tbits) < 2 * S) ++L.tbits;
     int off = 0;
-    L.bits = off; off += a16(4 * (nwords + 2));
-    L.hpos = off; off += a16(4 * (S + 1));
-    L.cid = off; off += a16(4 * S);
+    L.tab = off; off += a16(4 << L.tbits);
+    L.pos = off; off += a16(4 * S);
+    L.cid = off; off += sorted_out ? a16(4 * S) : 0;
     L.total = off;
     return L;
 }
 
-template <int E>
-__global__ void __launch_bounds__(kCwsWarps * 32) shingle_kernel(HashArgs a, const uint32_t* gbits, uint32_t* sets,
-                                                                  int2* sizes) {
+// Shingles of one series (Sec. 4.2) by hashing instead of sorting: position
+// i = lane + 32 t reads sketch bits i .. i+n-1 (first bit most significant),
+// which lie in words t and t+1, so every lane of a round reads the same two
+// words. Each id is inserted into the warp's table (slot word = count << 16 |
+// id; 0 is empty since counts start at 1): the lane whose compare-and-swap
+// fills an empty slot owns the id, a lane that meets its id adds 1 to the
+// count, any other id in the slot moves it on to the next slot. The owners
+// then write the set, count-1 ids first, and clear their slots.
+__global__ void __launch_bounds__(256) shingle_kernel(HashArgs a, const uint32_t* gbits, uint32_t* sets,
+                                                      int2* sizes) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
     const int nwords = a.nwords, S = a.S, n = a.n;
-    const ShingleLayout lay = shingle_layout(nwords, S);
+    const bool sorted_out = a.sh_ids_out != nullptr;
+    const ShingleLayout lay = shingle_layout(S, sorted_out);
     unsigned char* wb = smem + (size_t)warp * lay.total;
-    uint32_t* bits = reinterpret_cast<uint32_t*>(wb + lay.bits);
-    int* hpos = reinterpret_cast<int*>(wb + lay.hpos);
+    uint32_t* tab = reinterpret_cast<uint32_t*>(wb + lay.tab);
+    uint32_t* pos = reinterpret_cast<uint32_t*>(wb + lay.pos);
     uint32_t* cid = reinterpret_cast<uint32_t*>(wb + lay.cid);
-    const int64_t nwarps = (int64_t)gridDim.x * kCwsWarps;
-    for (int64_t row = (int64_t)blockIdx.x * kCwsWarps + warp; row < a.count; row += nwarps) {
-        for (int w = lane; w < nwords + 2; w += 32) bits[w] = (w < nwords) ? __ldg(gbits + row * nwords + w) : 0u;
-        __syncwarp();
-        int nnz;
-        {
-            uint32_t v[E];
-#pragma unroll
-            for (int e = 0; e < E; ++e) {
-                const int i = lane * E + e;
-                uint32_t id = 0xFFFFFFFFu;
-                if (i < S) {
-                    const uint64_t bb = ((uint64_t)bits[i >> 5] << 32) | (uint64_t)bits[(i >> 5) + 1];
-                    id = (uint32_t)((bb << (i & 31)) >> (64 - n));
-                }
-                v[e] = id;
-            }
-            // bitonic sort, ascending; element index i = lane*E + e (blocked layout)
-#pragma unroll
-            for (int k = 2; k <= 32 * E; k <<= 1) {
-#pragma unroll
-                for (int j = k >> 1; j > 0; j >>= 1) {
-                    if (j < E) {
-#pragma unroll
-                        for (int e = 0; e < E; ++e) {
-                            const int p = e ^ j;
-                            if (p > e) {
-                                const bool up = (((lane * E + e) & k) == 0);
-                                const uint32_t lo = min(v[e], v[p]), hi = max(v[e], v[p]);
-                                v[e] = up ? lo : hi;
-                                v[p] = up ? hi : lo;
-                            }
-                        }
-                    } else {
-                        const int lm = j / E;
-                        const bool lower = (lane & lm) == 0;
-#pragma unroll
-                        for (int e = 0; e < E; ++e) {
-                            const uint32_t o = __shfl_xor_sync(kFull, v[e], lm);
-                            const bool up = (((lane * E + e) & k) == 0);
-                            v[e] = (up == lower) ? min(v[e], o) : max(v[e], o);
-                        }
-                    }
-                }
-            }
-            // run-length encoding: run heads and their positions by a warp scan
-            const uint32_t prev = __shfl_up_sync(kFull, v[E - 1], 1);
-            int nh = 0;
-            bool head[E];
-#pragma unroll
-            for (int e = 0; e < E; ++e) {
-                const int i = lane * E + e;
-                head[e] = (i < S) && (i == 0 || v[e] != ((e == 0) ? prev : v[e - 1]));
-                nh += head[e];
-            }
-            int incl = nh;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int t = __shfl_up_sync(kFull, incl, o);
-                if (lane >= o) incl += t;
-            }
-            int pos = incl - nh;
-            nnz = __shfl_sync(kFull, incl, 31);
-#pragma unroll
-            for (int e = 0; e < E; ++e)
-                if (head[e]) {
-                    cid[pos] = v[e];
-                    hpos[pos] = lane * E + e;
-                    ++pos;
-                }
-        }
-        __syncwarp();
-        // counts, then the set in two ascending groups: seen once, seen more than once
-        uint32_t* out = sets + row * S;
-        int n1 = 0, nm = 0;
-        for (int e0 = 0; e0 < nnz; e0 += 32) {
-            const int e = e0 + lane;
-            uint32_t c = 0, id = 0;
-            if (e < nnz) {
-                c = (uint32_t)(((e + 1 < nnz) ? hpos[e + 1] : S) - hpos[e]);
-                id = cid[e];
-                if (a.sh_ids_out) {
-                    a.sh_ids_out[row * S + e] = id;
-                    a.sh_counts_out[row * S + e] = c;
-                }
-            }
-            const bool one = (e < nnz) && c == 1u, more = (e < nnz) && c > 1u;
-            const unsigned b1 = __ballot_sync(kFull, one), bm = __ballot_sync(kFull, more);
-            const unsigned lt = (1u << lane) - 1u;
-            if (one) cid[n1 + __popc(b1 & lt)] = id;              // in place: n1 <= e0 + lane
-            if (more) hpos[nm + __popc(bm & lt)] = (int)(id | (c << 16));
-            n1 += __popc(b1);
-            nm += __popc(bm);
-            __syncwarp();
-        }
-        for (int e = lane; e < n1 + nm; e += 32) out[e] = (e < n1) ? cid[e] : (uint32_t)hpos[e - n1];
-        if (lane == 0) {
-            sizes[row] = make_int2(n1, nm);
-            if (a.nnz_out) a.nnz_out[row] = nnz;
-        }
-        __syncwarp();
-    }
-}
-
-// Shingles of one series by a warp-level counting sort, for 10 <= n <= 16:
-// every shingle id sets its bit in a shared-memory occupancy bitmap of the 2^n
-// ids (lane l owns the ids [l 2^n/32, (l+1) 2^n/32) and a summary word marking
-// which of its bitmap words are non-zero); walking the lanes' ranges in order
-// gives the distinct ids ascending, and an id whose bit was already set is a
-// repeat that adds to its run count (found by binary search in the sorted ids).
-// Only the touched words are cleared afterwards. Output layout as shingle_kernel.
-constexpr int kMaxShingleIdsPerLane = 32;  // ceil(S / 32) for S <= 1024
-
-struct BitmapLayout {
-    int bm, sum, pid, cid, cnt, total;
-};
-
-__host__ __device__ inline BitmapLayout bitmap_layout(int n, int S) {
-    BitmapLayout L;
-    int off = 0;
-    L.bm = off; off += a16(4 * (1 << (n - 5)));
-    L.sum = off; off += a16(4 * (1 << (n - 10)));
-    L.pid = off; off += a16(4 * S);
-    L.cid = off; off += a16(4 * S);
-    L.cnt = off; off += a16(4 * S);
-    L.total = off;
-    return L;
-}
-
-__global__ void __launch_bounds__(kCwsWarps * 32) shingle_bitmap_kernel(HashArgs a, const uint32_t* gbits,
-                                                                         uint32_t* sets, int2* sizes) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nwords = a.nwords, S = a.S, n = a.n;
-    const BitmapLayout lay = bitmap_layout(n, S);
-    unsigned char* wb = smem + (size_t)warp * lay.total;
-    uint32_t* bm = reinterpret_cast<uint32_t*>(wb + lay.bm);
-    uint32_t* sum = reinterpret_cast<uint32_t*>(wb + lay.sum);
-    uint32_t* pid = reinterpret_cast<uint32_t*>(wb + lay.pid);  // the id at each position
-    uint32_t* cid = reinterpret_cast<uint32_t*>(wb + lay.cid);
-    uint32_t* cnt = reinterpret_cast<uint32_t*>(wb + lay.cnt);
-    const int nbm = 1 << (n - 5);         // bitmap words
-    const int wpl = nbm >> 5;             // bitmap words per lane (>= 1 for n >= 10)
-    const int spl = (wpl + 31) >> 5;      // summary words per lane
-    for (int w = lane; w < nbm; w += 32) bm[w] = 0u;
-    for (int w = lane; w < 32 * spl; w += 32) sum[w] = 0u;
+    const uint32_t tmask = (1u << lay.tbits) - 1u;
+    const int tshift = 32 - lay.tbits;
+    constexpr uint32_t kOwner = 0x80000000u;
+    for (uint32_t w = lane; w <= tmask; w += 32) tab[w] = 0u;
     __syncwarp();
     const unsigned lt = (1u << lane) - 1u;
     const int rounds = (S + 31) >> 5;
-    const int64_t nwarps = (int64_t)gridDim.x * kCwsWarps;
-    for (int64_t row = (int64_t)blockIdx.x * kCwsWarps + warp; row < a.count; row += nwarps) {
+    const int64_t nwarps = (int64_t)gridDim.x * wpb;
+    for (int64_t row = (int64_t)blockIdx.x * wpb + warp; row < a.count; row += nwarps) {
         const uint32_t* brow = gbits + row * nwords;
-        uint32_t dup = 0;  // bit t set: position lane + 32 t repeats an earlier id
+        uint32_t hi = __ldg(brow);
         for (int t = 0; t < rounds; ++t) {
+            const uint32_t lo = (t + 1 < nwords) ? __ldg(brow + t + 1) : 0u;
             const int i = lane + 32 * t;
             if (i < S) {
-                const int w0 = i >> 5;
-                const uint32_t hi = __ldg(brow + w0);
-                const uint32_t lo = (w0 + 1 < nwords) ? __ldg(brow + w0 + 1) : 0u;
                 const uint64_t bb = ((uint64_t)hi << 32) | (uint64_t)lo;
-                const uint32_t id = (uint32_t)((bb << (i & 31)) >> (64 - n));
-                pid[i] = id;
-                const uint32_t bit = 1u << (id & 31);
-                const uint32_t old = atomicOr(&bm[id >> 5], bit);
-                if (old & bit) dup |= 1u << t;
-                else if (old == 0u) atomicOr(&sum[(id >> 5) >> 5], 1u << ((id >> 5) & 31));
-            }
-        }
-        __syncwarp();
-        // sorted distinct ids: count per lane range, warp scan, then emit
-        int mine = 0;
-        for (int q = 0; q < spl; ++q) {
-            uint32_t sw = sum[lane * spl + q];
-            while (sw) {
-                const int b = __ffs(sw) - 1;
-                sw &= sw - 1;
-                mine += __popc(bm[(lane * spl + q) * 32 + b]);
-            }
-        }
-        int incl = mine;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(kFull, incl, o);
-            if (lane >= o) incl += t;
-        }
-        int pos = incl - mine;
-        const int nnz = __shfl_sync(kFull, incl, 31);
-        for (int q = 0; q < spl; ++q) {
-            const int sidx = lane * spl + q;
-            uint32_t sw = sum[sidx];
-            while (sw) {
-                const int b = __ffs(sw) - 1;
-                sw &= sw - 1;
-                const int w = sidx * 32 + b;
-                uint32_t word = bm[w];
-                while (word) {
-                    const int c = __ffs(word) - 1;
-                    word &= word - 1;
-                    cid[pos] = ((uint32_t)w << 5) | (uint32_t)c;
-                    cnt[pos] = 1u;
-                    ++pos;
+                const uint32_t id = (uint32_t)((bb << lane) >> (64 - n));
+                uint32_t h = (id * 0x9E3779B1u) >> tshift;
+                uint32_t own = 0u;
+                // at most S distinct ids in 2S slots: an empty slot or the id itself
+                // is met within tmask + 1 probes
+                for (uint32_t probe = 0; probe <= tmask; ++probe) {
+                    const uint32_t old = atomicCAS(&tab[h], 0u, id | 0x10000u);
+                    if (old == 0u) {
+                        own = kOwner;
+                        break;
+                    }
+                    if ((old & 0xFFFFu) == id) {
+                        atomicAdd(&tab[h], 0x10000u);
+                        break;
+                    }
+                    h = (h + 1u) & tmask;
                 }
+                pos[i] = h | own;
             }
+            hi = lo;
         }
         __syncwarp();
-        // repeats: add to the run of their id
-        for (int t = 0; t < rounds; ++t) {
-            if ((dup >> t) & 1u) {
-                const uint32_t id = pid[lane + 32 * t];
-                int lo = 0, hi = nnz - 1;
-                while (lo < hi) {
-                    const int mid = (lo + hi) >> 1;
-                    if (cid[mid] < id) lo = mid + 1; else hi = mid;
-                }
-                atomicAdd(&cnt[lo], 1u);
-            }
-        }
-        __syncwarp();
-        // clear the touched words for the next series
-        for (int i = lane; i < S; i += 32) bm[pid[i] >> 5] = 0u;
-        for (int q = 0; q < spl; ++q) sum[lane * spl + q] = 0u;
-        // the set in two ascending groups: seen once, then seen more than once (id | count << 16)
-        uint32_t* out = sets + row * S;
         int n1 = 0, nm = 0;
-        for (int e0 = 0; e0 < nnz; e0 += 32) {
-            const int e = e0 + lane;
-            uint32_t c = 0, id = 0;
-            if (e < nnz) {
-                c = cnt[e];
-                id = cid[e];
-                if (a.sh_ids_out) {
-                    a.sh_ids_out[row * S + e] = id;
-                    a.sh_counts_out[row * S + e] = c;
+        for (int t = 0; t < rounds; ++t) {
+            const int i = lane + 32 * t;
+            bool one = false, more = false;
+            if (i < S) {
+                const uint32_t p = pos[i];
+                if (p & kOwner) {
+                    one = set_count(tab[p & ~kOwner]) == 1u;
+                    more = !one;
                 }
             }
-            const bool one = (e < nnz) && c == 1u, more = (e < nnz) && c > 1u;
-            const unsigned b1 = __ballot_sync(kFull, one), bmm = __ballot_sync(kFull, more);
-            __syncwarp();
-            if (one) cid[n1 + __popc(b1 & lt)] = id;                    // in place: n1 <= e0 + lane
-            if (more) cnt[nm + __popc(bmm & lt)] = id | (c << 16);      // in place: nm <= e0 + lane
-            n1 += __popc(b1);
-            nm += __popc(bmm);
-            __syncwarp();
+            n1 += __popc(__ballot_sync(kFull, one));
+            nm += __popc(__ballot_sync(kFull, more));
         }
-        for (int e = lane; e < n1 + nm; e += 32) out[e] = (e < n1) ? cid[e] : cnt[e - n1];
+        uint32_t* out = sets + row * S;
+        int o1 = 0, om = n1;
+        for (int t = 0; t < rounds; ++t) {
+            const int i = lane + 32 * t;
+            bool one = false, more = false;
+            uint32_t v = 0u;
+            if (i < S) {
+                const uint32_t p = pos[i];
+                if (p & kOwner) {
+                    v = tab[p & ~kOwner];
+                    one = set_count(v) == 1u;
+                    more = !one;
+                }
+            }
+            const unsigned b1 = __ballot_sync(kFull, one), bm = __ballot_sync(kFull, more);
+            const int e = one ? o1 + __popc(b1 & lt) : om + __popc(bm & lt);
+            if (one || more) {
+                out[e] = one ? set_id(v) : v;
+                if (sorted_out) cid[e] = v;
+            }
+            o1 += __popc(b1);
+            om += __popc(bm);
+        }
+        __syncwarp();
+        const int nnz = n1 + nm;
+        if (sorted_out) {
+            // the sorted (id, count) list: the rank of an id among the distinct ids
+            for (int e = lane; e < nnz; e += 32) {
+                const uint32_t v = cid[e], id = set_id(v);
+                int rank = 0;
+#pragma unroll 1
+                for (int f = 0; f < nnz; ++f) rank += set_id(cid[f]) < id;
+                a.sh_ids_out[row * S + rank] = id;
+                a.sh_counts_out[row * S + rank] = set_count(v);
+            }
+        }
         if (lane == 0) {
             sizes[row] = make_int2(n1, nm);
             if (a.nnz_out) a.nnz_out[row] = nnz;
+        }
+        for (int t = 0; t < rounds; ++t) {
+            const int i = lane + 32 * t;
+            if (i < S) {
+                const uint32_t p = pos[i];
+                if (p & kOwner) tab[p & ~kOwner] = 0u;
+            }
         }
         __syncwarp();
     }
@@ -520,9 +387,9 @@ __device__ inline void cws_fp64_set(const HashArgs& a, int j, const uint32_t* se
     *tout = bt;
 }
 
-__global__ void __launch_bounds__(kCwsWarps * 32, 4) cws_kernel(HashArgs a, const uint32_t* sets, const int2* sizes) {
+__global__ void __launch_bounds__(256, 4) cws_kernel(HashArgs a, const uint32_t* sets, const int2* sizes) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
     const int S = a.S, KL = a.KL;
     const CwsLayout lay = cws_layout(S, KL);
     unsigned char* wb = smem + (size_t)warp * lay.total;
@@ -532,8 +399,8 @@ __global__ void __launch_bounds__(kCwsWarps * 32, 4) cws_kernel(HashArgs a, cons
     const size_t nk = (size_t)1 << a.n;
     const int kstride = a.rank_stride;
     unsigned long long n64c = 0;
-    const int64_t nwarps = (int64_t)gridDim.x * kCwsWarps;
-    for (int64_t row = (int64_t)blockIdx.x * kCwsWarps + warp; row < a.count; row += nwarps) {
+    const int64_t nwarps = (int64_t)gridDim.x * wpb;
+    for (int64_t row = (int64_t)blockIdx.x * wpb + warp; row < a.count; row += nwarps) {
         const int2 sz = __ldg(sizes + row);
         const int n1 = sz.x, nm = sz.y;
         for (int e = lane; e < n1 + nm; e += 32) set[e] = __ldg(sets + row * S + e);
@@ -673,52 +540,44 @@ cudaError_t launch_sketch_t(const HashArgs& a, uint32_t* bits, unsigned long lon
     return cudaGetLastError();
 }
 
-template <int E>
-cudaError_t launch_shingle_t(const HashArgs& a, const uint32_t* bits, uint32_t* sets, int2* sizes, cudaStream_t st) {
-    const ShingleLayout lay = shingle_layout(a.nwords, a.S);
-    const size_t smem = (size_t)kCwsWarps * lay.total;
-    if (smem > 227 * 1024) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(shingle_kernel<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, shingle_kernel<E>, kCwsWarps * 32, smem);
-    int64_t grid = (int64_t)sms_of_device() * (per_sm > 0 ? per_sm : 1);
-    const int64_t need = (a.count + kCwsWarps - 1) / kCwsWarps;
-    if (grid > need) grid = need;
-    shingle_kernel<E><<<(unsigned)grid, kCwsWarps * 32, smem, st>>>(a, bits, sets, sizes);
-    note_launch();
-    return cudaGetLastError();
+// Warps per block for a kernel whose warps each take `per_warp` bytes of shared
+// memory (8, fewer when they do not fit; 0 when one warp does not fit).
+int warps_for(size_t per_warp) {
+    int w = 8;
+    while (w > 0 && (size_t)w * per_warp > 227 * 1024) --w;
+    return w;
 }
 
-cudaError_t launch_shingle_bitmap(const HashArgs& a, const uint32_t* bits, uint32_t* sets, int2* sizes,
-                                  cudaStream_t st) {
-    const BitmapLayout lay = bitmap_layout(a.n, a.S);
-    const size_t smem = (size_t)kCwsWarps * lay.total;
-    if (smem > 227 * 1024) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(shingle_bitmap_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+cudaError_t launch_shingle(const HashArgs& a, const uint32_t* bits, uint32_t* sets, int2* sizes, cudaStream_t st) {
+    const ShingleLayout lay = shingle_layout(a.S, a.sh_ids_out != nullptr);
+    const int wpb = warps_for((size_t)lay.total);
+    if (wpb < 1) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)wpb * lay.total;
+    cudaError_t e = cudaFuncSetAttribute(shingle_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, shingle_bitmap_kernel, kCwsWarps * 32, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, shingle_kernel, wpb * 32, smem);
     int64_t grid = (int64_t)sms_of_device() * (per_sm > 0 ? per_sm : 1);
-    const int64_t need = (a.count + kCwsWarps - 1) / kCwsWarps;
+    const int64_t need = (a.count + wpb - 1) / wpb;
     if (grid > need) grid = need;
-    shingle_bitmap_kernel<<<(unsigned)grid, kCwsWarps * 32, smem, st>>>(a, bits, sets, sizes);
+    shingle_kernel<<<(unsigned)grid, wpb * 32, smem, st>>>(a, bits, sets, sizes);
     note_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_cws(const HashArgs& a, const uint32_t* sets, const int2* sizes, cudaStream_t st) {
     const CwsLayout lay = cws_layout(a.S, a.KL);
-    const size_t smem = (size_t)kCwsWarps * lay.total;
-    if (smem > 227 * 1024) return cudaErrorInvalidValue;
+    const int wpb = warps_for((size_t)lay.total);
+    if (wpb < 1) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)wpb * lay.total;
     cudaError_t e = cudaFuncSetAttribute(cws_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cws_kernel, kCwsWarps * 32, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cws_kernel, wpb * 32, smem);
     int64_t grid = (int64_t)sms_of_device() * (per_sm > 0 ? per_sm : 1);
-    const int64_t need = (a.count + kCwsWarps - 1) / kCwsWarps;
+    const int64_t need = (a.count + wpb - 1) / wpb;
     if (grid > need) grid = need;
-    cws_kernel<<<(unsigned)grid, kCwsWarps * 32, smem, st>>>(a, sets, sizes);
+    cws_kernel<<<(unsigned)grid, wpb * 32, smem, st>>>(a, sets, sizes);
     note_launch();
     return cudaGetLastError();
 }
@@ -734,19 +593,13 @@ bool sketch_shape_ok(const SketchShape& s, const HashArgs& a) {
     return s.W == a.W && s.delta == a.delta && a.nb <= 32 * s.R && a.nb > 32 * (s.R - 1) && a.nb < 65536;
 }
 
-int cws_e(int S) {
-    for (int E = 1; E <= 32; E <<= 1)
-        if (S <= 32 * E) return E;
-    return 0;
-}
-
 }  // namespace
 
 bool hash_fast_supported(const HashArgs& a) {
     bool ok = false;
     for (const SketchShape& s : kSketchShapes) ok |= sketch_shape_ok(s, a);
-    const int E = cws_e(a.S);
-    return ok && E >= 1 && E <= 16 && a.n <= 16;
+    return ok && a.n <= 16 && a.S >= 1 && warps_for((size_t)shingle_layout(a.S, true).total) >= 1 &&
+           warps_for((size_t)cws_layout(a.S, a.KL).total) >= 1;
 }
 
 // Scratch of the split hash path: bits [count][nwords], the fix-up counter and
@@ -816,15 +669,7 @@ cudaError_t hash_fast_fixup(const HashArgs& a, const FastHashBuffers& b, cudaStr
 }
 
 cudaError_t hash_fast_shingle(const HashArgs& a, const FastHashBuffers& b, cudaStream_t st) {
-    if (a.n >= 10 && a.S <= 32 * kMaxShingleIdsPerLane) return launch_shingle_bitmap(a, b.bits, b.sets, b.sizes, st);
-    switch (cws_e(a.S)) {
-        case 1: return launch_shingle_t<1>(a, b.bits, b.sets, b.sizes, st);
-        case 2: return launch_shingle_t<2>(a, b.bits, b.sets, b.sizes, st);
-        case 4: return launch_shingle_t<4>(a, b.bits, b.sets, b.sizes, st);
-        case 8: return launch_shingle_t<8>(a, b.bits, b.sets, b.sizes, st);
-        case 16: return launch_shingle_t<16>(a, b.bits, b.sets, b.sizes, st);
-        default: return cudaErrorInvalidValue;
-    }
+    return launch_shingle(a, b.bits, b.sets, b.sizes, st);
 }
 
 cudaError_t hash_fast_cws(const HashArgs& a, const FastHashBuffers& b, cudaStream_t st) {
