@@ -410,7 +410,7 @@ HashArgs base_hash_args(const ssh_index* idx, int m, const Geometry& g) {
     a.rank_stride = (idx->KL + 3) & ~3;
     a.force_generic = idx->hash_kernel == 1;
     a.force_fp64 = idx->cws_fp64;
-    a.kinv = idx->d_kinv;
+    a.kla = idx->d_kla;
     a.p32 = idx->d_p32;
     a.p64 = idx->d_p64;
     a.lav = idx->d_lav;
@@ -830,7 +830,8 @@ ssh_status ssh_create(int W, int delta, int n, int K, int L, float band, uint64_
     const int KL = idx->KL;
     const int64_t nk = (int64_t)1 << n;
     const int KLp = (KL + 3) & ~3;
-    std::vector<uint16_t> rank((size_t)nk * KLp, (uint16_t)0xFFFF), kinv((size_t)KL * nk);
+    std::vector<uint16_t> rank((size_t)nk * KLp, (uint16_t)0xFFFF);
+    std::vector<uint2> kla((size_t)KL * nk);  // per rank: (shingle id, fl32 ln a at count 1)
     std::vector<float4> p32((size_t)nk * KL);
     std::vector<double> p64((size_t)KL * nk * 3);
     // ln a rounded once to FP32 for small counts, and their t (255: compute it in FP64)
@@ -859,7 +860,11 @@ ssh_status ssh_create(int W, int delta, int n, int K, int L, float band, uint64_
         std::sort(la1.begin(), la1.end());  // (value, id): equal values keep the smaller id first
         for (int64_t rnk = 0; rnk < nk; ++rnk) {
             rank[(size_t)la1[rnk].second * KLp + j] = (uint16_t)rnk;
-            kinv[(size_t)j * nk + rnk] = (uint16_t)la1[rnk].second;
+            const uint32_t k = la1[rnk].second;
+            float v = lav[(size_t)k * kTabCounts * KLp + j];
+            uint32_t bitsv;
+            memcpy(&bitsv, &v, 4);
+            kla[(size_t)j * nk + rnk] = make_uint2(k, bitsv);
         }
     });
     std::vector<float> lns32(kMaxCount + 1);
@@ -876,7 +881,7 @@ ssh_status ssh_create(int W, int delta, int n, int K, int L, float band, uint64_
     };
     e = up(reinterpret_cast<void**>(&idx->d_r), idx->h_r.data(), W * sizeof(float));
     if (e == cudaSuccess) e = up(reinterpret_cast<void**>(&idx->d_rank), rank.data(), rank.size() * 2);
-    if (e == cudaSuccess) e = up(reinterpret_cast<void**>(&idx->d_kinv), kinv.data(), kinv.size() * 2);
+    if (e == cudaSuccess) e = up(reinterpret_cast<void**>(&idx->d_kla), kla.data(), kla.size() * sizeof(uint2));
     if (e == cudaSuccess) e = up(reinterpret_cast<void**>(&idx->d_p32), p32.data(), p32.size() * sizeof(float4));
     if (e == cudaSuccess) e = up(reinterpret_cast<void**>(&idx->d_p64), p64.data(), p64.size() * sizeof(double));
     if (e == cudaSuccess) e = up(reinterpret_cast<void**>(&idx->d_lav), lav.data(), lav.size() * sizeof(float));
@@ -905,7 +910,7 @@ void ssh_destroy(ssh_index* idx) {
     }
     cudaFree(idx->d_r);
     cudaFree(idx->d_rank);
-    cudaFree(idx->d_kinv);
+    cudaFree(idx->d_kla);
     cudaFree(idx->d_p32);
     cudaFree(idx->d_p64);
     cudaFree(idx->d_lav);

@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerCta * 32) hash_kernel(HashArgs a, 
             uint32_t kA = 0, ks, ts;
             float4 pA = make_float4(0.f, 0.f, 0.f, 0.f);
             if (hasA) {
-                kA = __ldg(a.kinv + (size_t)j * nk + rmin);
+                kA = __ldg(a.kla + (size_t)j * nk + rmin).x;
                 pA = __ldg(a.p32 + (size_t)kA * KL + j);
             }
             if (!cws_decide(hasA, kA, pA, tr, &ks, &ts) || a.force_fp64) {

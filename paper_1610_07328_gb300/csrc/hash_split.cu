@@ -25,6 +25,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "hash_common.cuh"
 #include "ssh_internal.cuh"
 
@@ -435,8 +437,8 @@ __global__ void __launch_bounds__(256, 4) cws_kernel(HashArgs a, const uint32_t*
                 for (int q = 0; q < 4; ++q) {
                     ex[q].init();
                     if (n1 > 0 && j0 + q < KL) {
-                        const uint32_t kA = __ldg(a.kinv + (size_t)(j0 + q) * nk + rmin[q]);
-                        ex[q].add(__ldg(a.lav + (size_t)kA * kTabCounts * kstride + j0 + q), kA, 0u);
+                        const uint2 w = __ldg(a.kla + (size_t)(j0 + q) * nk + rmin[q]);
+                        ex[q].add(__uint_as_float(w.y), w.x, 0u);
                     }
                 }
                 int nlarge = 0;
@@ -571,6 +573,10 @@ cudaError_t launch_cws(const HashArgs& a, const uint32_t* sets, const int2* size
     if (wpb < 1) return cudaErrorInvalidValue;
     const size_t smem = (size_t)wpb * lay.total;
     cudaError_t e = cudaFuncSetAttribute(cws_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    // the rank rows are re-read from L1: ask for no more shared memory than 4 blocks use
+    const int pct = (int)std::min<size_t>(100, (4 * smem * 100 + 228 * 1024 - 1) / (228 * 1024));
+    e = cudaFuncSetAttribute(cws_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cws_kernel, wpb * 32, smem);

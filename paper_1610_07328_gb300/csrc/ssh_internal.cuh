@@ -70,7 +70,7 @@ struct HashArgs {
     int rank_stride;         // KL rounded up to a multiple of 4 (row padding holds 0xFFFF)
     int force_generic;       // 1: use the generic kernel even when a specialised one exists
     int force_fp64;          // 1: decide every minhash by the FP64 recomputation (a test knob)
-    const uint16_t* kinv;    // [KL][2^n] shingle id of each rank
+    const uint2* kla;        // [KL][2^n] per rank: (shingle id, ln a at count 1 rounded once to FP32, as bits)
     const float4* p32;       // [2^n][KL] (r, 1/r, beta, ln c) rounded to FP32
     const double* p64;       // [KL][2^n][3] (r, beta, ln c) in FP64
     const float* lav;        // [2^n][kTabCounts][rank_stride] ln a of counts 1..kTabCounts, rounded once to FP32
@@ -221,7 +221,7 @@ struct ssh_index {
     std::vector<float> h_r;           // host copy of the filter
     float* d_r = nullptr;
     uint16_t* d_rank = nullptr;
-    uint16_t* d_kinv = nullptr;
+    uint2* d_kla = nullptr;
     float4* d_p32 = nullptr;
     double* d_p64 = nullptr;
     float* d_lav = nullptr;
