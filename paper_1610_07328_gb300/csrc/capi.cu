@@ -407,7 +407,7 @@ HashArgs base_hash_args(const ssh_index* idx, int m, const Geometry& g) {
     const double gw = idx->W * std::ldexp(1.0, -24) / (1.0 - idx->W * std::ldexp(1.0, -24));
     a.gamma_ss = (float)(2.0 * gw);
     a.rank = idx->d_rank;
-    a.rank_stride = (idx->KL + 3) & ~3;
+    a.rank_stride = rank_stride_of(idx->KL);
     a.force_generic = idx->hash_kernel == 1;
     a.force_fp64 = idx->cws_fp64;
     a.kla = idx->d_kla;
@@ -829,7 +829,7 @@ ssh_status ssh_create(int W, int delta, int n, int K, int L, float band, uint64_
     // Sec. 4.3 draw tables for every (hash j, shingle k)
     const int KL = idx->KL;
     const int64_t nk = (int64_t)1 << n;
-    const int KLp = (KL + 3) & ~3;
+    const int KLp = rank_stride_of(KL);
     std::vector<uint16_t> rank((size_t)nk * KLp, (uint16_t)0xFFFF);
     std::vector<uint2> kla((size_t)KL * nk);  // per rank: (shingle id, fl32 ln a at count 1)
     std::vector<float4> p32((size_t)nk * KL);

@@ -6,9 +6,9 @@
 //    one is processed). Lane l owns the R consecutive windows [lR, lR + R); the
 //    filter r sits in registers and the loop over the lane's W + (R-1) DELTA
 //    samples is unrolled, so each sample read from shared memory feeds up to R
-//    FMAs. A window whose |r.x| is not above tau ||r|| ||x_series|| is checked
-//    again against its own energy tau ||r|| ||x_window||; if it stays below, it
-//    goes to a fix-up list with a provisional bit 0. Bits are packed 32 per
+//    FMAs and the strip's energy. A window whose |r.x| is not above
+//    tau ||r|| ||x_strip|| (>= tau ||r|| ||x_window||) goes to a fix-up list
+//    with a provisional bit 0. Bits are packed 32 per
 //    word (window i -> bit 31 - i%32 of word i/32) into global memory.
 //  sketch_fixup_kernel: one thread per listed window recomputes the dot product
 //    in FP64 in the definition's order and sets the bit when it is >= 0.
@@ -110,55 +110,44 @@ __global__ void __launch_bounds__(kSketchWarps * 32, 3)
         cp_async_wait1();
         __syncwarp();
         const float* x = xbuf[cur];
-        // series energy: ||x_window||^2 <= sum over the series; the loose test uses it
-        float e = 0.f;
-        for (int i = lane; i < m; i += 32) e = fmaf(x[i], x[i], e);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(kFull, e, o);
-        // e carries at most (m/32 + 5) roundings of relative 2^-24 each; inflate by 2m 2^-24
-        const float e_up = __fmul_ru(e, 1.0f + (float)(2 * m + 64) * 5.9604645e-08f);
-        const float thr_loose = __fmul_ru(a.tau_norm, __fsqrt_ru(__fmul_ru(e_up, 1.0f + a.gamma_ss)));
-
+        // the R dot products and the energy of the lane's strip of STRIP samples,
+        // which holds every window of the lane: ||x_window||^2 <= strip energy
         float acc[R];
 #pragma unroll
         for (int k = 0; k < R; ++k) acc[k] = 0.f;
+        float e = 0.f;
         const float* xs = x + lane * R * DELTA;
 #pragma unroll
         for (int t = 0; t < STRIP; ++t) {
             const float xv = xs[t];
+            e = fmaf(xv, xv, e);
 #pragma unroll
             for (int k = 0; k < R; ++k) {
                 const int j = t - k * DELTA;
                 if (j >= 0 && j < W) acc[k] = fmaf(rp.v[j], xv, acc[k]);
             }
         }
+        // e carries at most STRIP roundings of relative 2^-24 each: inflate it past them
+        const float e_up = __fmul_ru(e, 1.0f + (float)(2 * STRIP + 64) * 5.9604645e-08f);
+        const float thr = __fmul_ru(a.tau_norm, __fsqrt_ru(__fmul_ru(e_up, 1.0f + a.gamma_ss)));
 #pragma unroll
         for (int k = 0; k < R; ++k) {
             const int i = lane * R + k;
             uint8_t bit = 0;
             if (i < nb) {
-                if (fabsf(acc[k]) > thr_loose) {
+                if (fabsf(acc[k]) > thr) {
                     bit = acc[k] >= 0.f;
                 } else {
-                    // the window's own energy (sequential FMAs: at most W roundings)
-                    const float* xw = xs + k * DELTA;
-                    float ss = 0.f;
-#pragma unroll 1
-                    for (int j = 0; j < W; ++j) ss = fmaf(xw[j], xw[j], ss);
-                    const float thr = __fmul_ru(a.tau_norm, __fsqrt_ru(__fmul_ru(ss, 1.0f + a.gamma_ss)));
-                    if (fabsf(acc[k]) > thr) {
-                        bit = acc[k] >= 0.f;
+                    const unsigned long long slot = atomicAdd(nfix, 1ull);
+                    if (slot < fix_cap) {
+                        fix[slot] = ((unsigned long long)row << 16) | (unsigned long long)i;
                     } else {
-                        const unsigned long long slot = atomicAdd(nfix, 1ull);
-                        if (slot < fix_cap) {
-                            fix[slot] = ((unsigned long long)row << 16) | (unsigned long long)i;
-                        } else {
-                            double d = 0.0;  // list full: the definition's FP64 order, in place
+                        const float* xw = xs + k * DELTA;
+                        double d = 0.0;  // list full: the definition's FP64 order, in place
 #pragma unroll 1
-                            for (int j = 0; j < W; ++j) d = fma((double)r_s[j], (double)xw[j], d);
-                            bit = d >= 0.0;
-                            n_inplace += 1;
-                        }
+                        for (int j = 0; j < W; ++j) d = fma((double)r_s[j], (double)xw[j], d);
+                        bit = d >= 0.0;
+                        n_inplace += 1;
                     }
                 }
             }

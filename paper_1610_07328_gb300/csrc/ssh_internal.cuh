@@ -46,6 +46,9 @@ constexpr float kPad = 1.0e18f;
 
 constexpr int kMaxShingleBits = 16;     // n limit of the tabulated minhash draws
 constexpr int kMaxCount = 65535;        // shingles per series (u16 counts)
+// Row stride (in hashes) of the per-shingle draw tables: K L rounded up to 4, so
+// a lane's 4 consecutive hashes are one aligned 8-byte (ranks) or 16-byte load.
+inline int rank_stride_of(int KL) { return (KL + 3) & ~3; }
 constexpr int kMaxTopK = 1024;
 constexpr int kTabCounts = 8;           // counts whose ln a is tabulated exactly rounded
 constexpr int kMaxW = 8192;
