@@ -421,6 +421,12 @@ def run_gpu(args, w):
     h_q_np2 = h_q.numpy()
     qlen = qlengths
     e2e_steps = max(2, min(args.steps, 5))
+    # warm-up: the first host add allocates the index's 2 GB staging copy, later
+    # adds reuse it (ssh_index_clear keeps the buffer for the next add)
+    for _ in range(max(1, min(args.warmup, 2))):
+        idx.clear()
+        binding.ssh_index_add(idx.handle, h_db_np, lengths)
+        binding.ssh_query(idx.handle, h_q_np2, qlen, k)
     idx.clear()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -467,8 +473,8 @@ def run_gpu(args, w):
         "roofline": roofline,
         "kernels": roofs,
         "e2e": {"value": N * world / (e2e_ms / 1000.0), "unit": "series/s",
-                "h2d_bytes_per_step": N * m * 4 + N * 4 + nq * m * 4 + nq * 4,
-                "d2h_bytes_per_step": nq * k * 12, "steps": e2e_steps,
+                "h2d_bytes_per_step": N * m * 4 + nq * m * 4,
+                "d2h_bytes_per_step": nq * k * 12, "steps": e2e_steps, "warmup": max(1, min(args.warmup, 2)),
                 "api": "ssh_index_clear + ssh_index_add(host) + ssh_query(host)"},
         "clocks": clocks,
         "setup_s": {"inputs": gen_s},

@@ -429,7 +429,6 @@ void free_sub(SubIndex& s) {
     cudaFree(s.skeys);
     cudaFree(s.srows);
     cudaFree(s.bins);
-    for (void* p : s.owned) cudaFree(p);
     s = SubIndex();
 }
 
@@ -499,24 +498,47 @@ ssh_status rebuild_tables(ssh_index* idx, SubIndex& s, cudaStream_t st) {
     return SSH_OK;
 }
 
-// Algorithm 1 for the series of one call. `dev` holds all `count` series back
-// to back (device memory that stays valid while the index uses it).
-ssh_status add_series(ssh_index* idx, const float* dev, const int32_t* lengths, int64_t count, cudaStream_t st,
-                      int64_t* first_id) {
-    // all lengths valid first: nothing is added on error (each distinct run checked once)
-    for (int64_t i = 0; i < count; ++i) {
-        if (i > 0 && lengths[i] == lengths[i - 1]) continue;
+// End of the run of equal lengths that starts at i: the first j > i with
+// lengths[j] != lengths[i], or count. Whole chunks are tested with an OR of
+// XORs (a loop the compiler vectorises), so a call of one length costs a
+// fraction of a scalar compare loop.
+int64_t run_end(const int32_t* lengths, int64_t i, int64_t count) {
+    const uint32_t v = (uint32_t)lengths[i];
+    int64_t j = i + 1;
+    constexpr int64_t kChunk = 256;
+    while (j + kChunk <= count) {
+        uint32_t diff = 0;
+        for (int64_t q = 0; q < kChunk; ++q) diff |= (uint32_t)lengths[j + q] ^ v;
+        if (diff) break;
+        j += kChunk;
+    }
+    while (j < count && (uint32_t)lengths[j] == v) ++j;
+    return j;
+}
+
+// Every length of a call must be valid before anything is added (each run of
+// equal lengths is checked once).
+ssh_status validate_lengths(ssh_index* idx, const int32_t* lengths, int64_t count) {
+    for (int64_t i = 0; i < count; i = run_end(lengths, i, count)) {
         Geometry g;
         if (lengths[i] <= 0) return fail(SSH_ELENGTH, "series %lld has length %d", (long long)i, lengths[i]);
         SSH_TRY(geometry(idx, lengths[i], &g));
+        const int rb = band_radius(idx->band, lengths[i]);
+        if (dtw_plan(lengths[i], rb).S == 0)
+            return fail(SSH_ENOTSUP, "DTW radius %d (length %d) is wider than this build covers", rb, lengths[i]);
     }
-    const int64_t id0 = idx->next_id;
-    std::vector<int> touched;
-    // group consecutive runs of equal length
-    int64_t i = 0, run_off = 0;
-    while (i < count) {
-        int64_t j = i + 1;
-        while (j < count && lengths[j] == lengths[i]) ++j;
+    return SSH_OK;
+}
+
+// Algorithm 1 (sketch, shingle, minhash and row keys) for series [i0, i1) of a
+// call whose first id is id0; `dev` points at series i0, the series back to
+// back in device memory that stays valid while the index uses it. The
+// sub-indexes touched are added to `touched`; their tables are rebuilt later.
+ssh_status hash_range(ssh_index* idx, const float* dev, const int32_t* lengths, int64_t i0, int64_t i1, int64_t id0,
+                      cudaStream_t st, std::vector<int>& touched) {
+    int64_t i = i0, run_off = 0;
+    while (i < i1) {
+        const int64_t j = run_end(lengths, i, i1);
         const int m = lengths[i];
         const int64_t nrun = j - i;
         Geometry g;
@@ -529,8 +551,6 @@ ssh_status add_series(ssh_index* idx, const float* dev, const int32_t* lengths, 
             s.S = g.S;
             s.rb = band_radius(idx->band, m);
         }
-        if (dtw_plan(m, s.rb).S == 0)
-            return fail(SSH_ENOTSUP, "DTW radius %d (length %d) is wider than this build covers", s.rb, m);
         if (std::find(touched.begin(), touched.end(), m) == touched.end()) touched.push_back(m);
         SSH_TRY(reserve(idx, s, s.count + nrun, st));
         fill_rows_kernel<<<grid_for(nrun, 256, 8192), 256, 0, st>>>(s.row_ptr + s.count, s.gid + s.count, nrun,
@@ -549,13 +569,53 @@ ssh_status add_series(ssh_index* idx, const float* dev, const int32_t* lengths, 
         run_off += (int64_t)m * nrun;
         i = j;
     }
+    return SSH_OK;
+}
+
+// Rebuild the tables of the touched sub-indexes and wait for the call's work.
+ssh_status finish_add(ssh_index* idx, const std::vector<int>& touched, int64_t count, cudaStream_t st,
+                      int64_t* first_id) {
     for (int m : touched) {
         TimedRegion tr(idx, st, "add.table_sort", (double)idx->subs[m].count * idx->L);
         SSH_TRY(rebuild_tables(idx, idx->subs[m], st));
     }
     SSH_CUDA(cudaStreamSynchronize(st));
+    if (first_id) *first_id = idx->next_id;
     idx->next_id += count;
-    if (first_id) *first_id = id0;
+    return SSH_OK;
+}
+
+// Algorithm 1 for the series of one call, already in device memory.
+ssh_status add_series(ssh_index* idx, const float* dev, const int32_t* lengths, int64_t count, cudaStream_t st,
+                      int64_t* first_id) {
+    SSH_TRY(validate_lengths(idx, lengths, count));
+    std::vector<int> touched;
+    SSH_TRY(hash_range(idx, dev, lengths, 0, count, idx->next_id, st, touched));
+    return finish_add(idx, touched, count, st, first_id);
+}
+
+// A device buffer of at least `bytes` for a copy of series: a spare one left by
+// ssh_index_clear (the smallest that fits) or a new allocation.
+ssh_status take_buffer(ssh_index* idx, size_t bytes, DevBuf* out) {
+    int best = -1;
+    for (int q = 0; q < (int)idx->spare.size(); ++q)
+        if (idx->spare[q].bytes >= bytes && (best < 0 || idx->spare[q].bytes < idx->spare[best].bytes)) best = q;
+    if (best >= 0) {
+        *out = idx->spare[best];
+        idx->spare.erase(idx->spare.begin() + best);
+        return SSH_OK;
+    }
+    DevBuf b;
+    b.bytes = std::max<size_t>(bytes, 256);
+    cudaError_t e = cudaMalloc(&b.p, b.bytes);
+    if (e != cudaSuccess) {
+        // spare buffers too small to use: give their memory back and try once more
+        for (DevBuf& f : idx->spare) cudaFree(f.p);
+        idx->spare.clear();
+        e = cudaMalloc(&b.p, b.bytes);
+        if (e != cudaSuccess) return cuda_status(e, "cudaMalloc (series copy)");
+    }
+    *out = b;
     return SSH_OK;
 }
 
@@ -817,6 +877,14 @@ ssh_status ssh_create(int W, int delta, int n, int K, int L, float band, uint64_
             cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
         }
     }
+    e = cudaStreamCreateWithFlags(&idx->hstream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&idx->cstream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&idx->cevent, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        ssh_status st = cuda_status(e, "ssh_create streams");
+        ssh_destroy(idx);
+        return st;
+    }
 
     // Sec. 4.1 filter and the sign-test threshold tau * ||r|| (tau = max(1e-4, 2 gamma_W))
     make_filter(seed, W, idx->h_r);
@@ -904,6 +972,11 @@ void ssh_destroy(ssh_index* idx) {
     cudaSetDevice(idx->device);
     cudaDeviceSynchronize();
     for (auto& kv : idx->subs) free_sub(kv.second);
+    for (DevBuf& b : idx->owned) cudaFree(b.p);
+    for (DevBuf& b : idx->spare) cudaFree(b.p);
+    if (idx->cevent) cudaEventDestroy(idx->cevent);
+    if (idx->hstream) cudaStreamDestroy(idx->hstream);
+    if (idx->cstream) cudaStreamDestroy(idx->cstream);
     for (auto& t : idx->pending) {
         cudaEventDestroy(t.start);
         cudaEventDestroy(t.stop);
@@ -928,7 +1001,51 @@ ssh_status ssh_get_filter(const ssh_index* idx, float* r_out) {
 }
 
 static ssh_status index_add_impl(ssh_index* idx, const float* series, const int32_t* lengths, int64_t count,
-                                 int64_t* first_id);
+                                 int64_t* first_id) {
+    if (!idx || (count > 0 && (!series || !lengths)) || count < 0) return fail(SSH_EINVAL, "bad arguments");
+    SSH_TRY(check_device(idx));
+    if (count == 0) {
+        if (first_id) *first_id = idx->next_id;
+        return SSH_OK;
+    }
+    SSH_TRY(validate_lengths(idx, lengths, count));
+    int64_t total = 0;
+    for (int64_t i = 0; i < count; ++i) total += lengths[i];
+    DevBuf buf;
+    SSH_TRY(take_buffer(idx, (size_t)total * sizeof(float), &buf));
+    float* dev = static_cast<float*>(buf.p);
+    // copy in chunks of about kAddChunkBytes on cstream; hashing of a chunk on
+    // hstream waits only for that chunk's copy, so copies and hashing overlap
+    constexpr int64_t kAddChunkBytes = 128ll << 20;
+    cudaStream_t st = idx->hstream, cs = idx->cstream;
+    std::vector<int> touched;
+    ssh_status status = SSH_OK;
+    int64_t i = 0, off = 0;
+    while (i < count && status == SSH_OK) {
+        int64_t j = i, bytes = 0;
+        while (j < count && (j == i || bytes + (int64_t)lengths[j] * 4 <= kAddChunkBytes)) bytes += (int64_t)lengths[j++] * 4;
+        cudaError_t e = cudaMemcpyAsync(dev + off, series + off, bytes, cudaMemcpyHostToDevice, cs);
+        if (e == cudaSuccess) e = cudaEventRecord(idx->cevent, cs);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, idx->cevent, 0);
+        if (e != cudaSuccess) {
+            status = cuda_status(e, "series copy");
+            break;
+        }
+        status = hash_range(idx, dev + off, lengths, i, j, idx->next_id, st, touched);
+        off += bytes / 4;
+        i = j;
+    }
+    if (status == SSH_OK) status = finish_add(idx, touched, count, st, first_id);
+    if (status != SSH_OK) {
+        cudaStreamSynchronize(cs);
+        cudaStreamSynchronize(st);
+        idx->spare.push_back(buf);
+        return status;
+    }
+    idx->owned.push_back(buf);  // referenced by the stored rows until ssh_index_clear
+    return SSH_OK;
+}
+
 static ssh_status index_add_device_impl(ssh_index* idx, const float* d_series, const int32_t* lengths,
                                         int64_t count, uint32_t flags, void* stream, int64_t* first_id);
 static ssh_status query_impl(ssh_index* idx, const float* queries, const int32_t* lengths, int64_t nq, int k,
@@ -963,32 +1080,6 @@ ssh_status ssh_query(ssh_index* idx, const float* queries, const int32_t* length
     return query_impl(idx, queries, lengths, nq, k, ids, dists);
 }
 
-static ssh_status index_add_impl(ssh_index* idx, const float* series, const int32_t* lengths, int64_t count,
-                                 int64_t* first_id) {
-    if (!idx || (count > 0 && (!series || !lengths)) || count < 0) return fail(SSH_EINVAL, "bad arguments");
-    SSH_TRY(check_device(idx));
-    if (count == 0) {
-        if (first_id) *first_id = idx->next_id;
-        return SSH_OK;
-    }
-    int64_t total = 0;
-    for (int64_t i = 0; i < count; ++i) total += std::max(lengths[i], 0);
-    float* dev = nullptr;
-    SSH_CUDA(cudaMalloc(&dev, std::max<int64_t>(total, 1) * sizeof(float)));
-    cudaError_t e = cudaMemcpy(dev, series, total * sizeof(float), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) {
-        cudaFree(dev);
-        return cuda_status(e, "cudaMemcpy (series)");
-    }
-    ssh_status s = add_series(idx, dev, lengths, count, 0, first_id);
-    if (s != SSH_OK) {
-        cudaFree(dev);
-        return s;
-    }
-    idx->subs[lengths[0]].owned.push_back(dev);  // freed with the index (any sub-index may own it)
-    return SSH_OK;
-}
-
 static ssh_status index_add_device_impl(ssh_index* idx, const float* d_series, const int32_t* lengths,
                                         int64_t count, uint32_t flags, void* stream, int64_t* first_id) {
     if (!idx || (count > 0 && (!d_series || !lengths)) || count < 0) return fail(SSH_EINVAL, "bad arguments");
@@ -999,24 +1090,28 @@ static ssh_status index_add_device_impl(ssh_index* idx, const float* d_series, c
         return SSH_OK;
     }
     const float* src = d_series;
-    float* own = nullptr;
+    DevBuf own;
     if (!(flags & SSH_ADD_BORROW)) {
+        SSH_TRY(validate_lengths(idx, lengths, count));
         int64_t total = 0;
-        for (int64_t i = 0; i < count; ++i) total += std::max(lengths[i], 0);
-        SSH_CUDA(cudaMalloc(&own, std::max<int64_t>(total, 1) * sizeof(float)));
-        cudaError_t e = cudaMemcpyAsync(own, d_series, total * sizeof(float), cudaMemcpyDeviceToDevice, st);
+        for (int64_t i = 0; i < count; ++i) total += lengths[i];
+        SSH_TRY(take_buffer(idx, (size_t)total * sizeof(float), &own));
+        cudaError_t e = cudaMemcpyAsync(own.p, d_series, total * sizeof(float), cudaMemcpyDeviceToDevice, st);
         if (e != cudaSuccess) {
-            cudaFree(own);
+            idx->spare.push_back(own);
             return cuda_status(e, "cudaMemcpyAsync (series)");
         }
-        src = own;
+        src = static_cast<const float*>(own.p);
     }
     ssh_status s = add_series(idx, src, lengths, count, st, first_id);
     if (s != SSH_OK) {
-        cudaFree(own);
+        if (own.p) {
+            cudaStreamSynchronize(st);
+            idx->spare.push_back(own);
+        }
         return s;
     }
-    if (own) idx->subs[lengths[0]].owned.push_back(own);
+    if (own.p) idx->owned.push_back(own);
     return SSH_OK;
 }
 
@@ -1024,11 +1119,10 @@ ssh_status ssh_index_clear(ssh_index* idx) {
     if (!idx) return fail(SSH_EINVAL, "NULL index");
     SSH_TRY(check_device(idx));
     SSH_CUDA(cudaDeviceSynchronize());
-    for (auto& kv : idx->subs) {
-        for (void* p : kv.second.owned) cudaFree(p);
-        kv.second.owned.clear();
-        kv.second.count = 0;  // keep the capacity for the next add
-    }
+    for (auto& kv : idx->subs) kv.second.count = 0;  // keep the capacity for the next add
+    // the copies of the cleared series become staging buffers for later adds
+    for (DevBuf& b : idx->owned) idx->spare.push_back(b);
+    idx->owned.clear();
     idx->next_id = 0;
     return SSH_OK;
 }
@@ -1048,23 +1142,26 @@ static ssh_status query_impl(ssh_index* idx, const float* queries, const int32_t
     if (nq == 0) return SSH_OK;
     int64_t total = 0;
     for (int64_t i = 0; i < nq; ++i) total += std::max(lengths[i], 0);
+    cudaStream_t st = idx->hstream;
     float* dq = nullptr;
     int64_t* did = nullptr;
     float* dd = nullptr;
-    cudaError_t e = cudaMalloc(&dq, std::max<int64_t>(total, 1) * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&did, nq * k * sizeof(int64_t));
-    if (e == cudaSuccess) e = cudaMalloc(&dd, nq * k * sizeof(float));
-    if (e == cudaSuccess) e = cudaMemcpy(dq, queries, total * sizeof(float), cudaMemcpyHostToDevice);
-    ssh_status s = (e == cudaSuccess) ? run_query(idx, dq, lengths, nq, k, did, dd, 0)
+    cudaError_t e = cudaMallocAsync(&dq, std::max<int64_t>(total, 1) * sizeof(float), st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&did, nq * k * sizeof(int64_t), st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&dd, nq * k * sizeof(float), st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dq, queries, total * sizeof(float), cudaMemcpyHostToDevice, st);
+    ssh_status s = (e == cudaSuccess) ? run_query(idx, dq, lengths, nq, k, did, dd, st)
                                       : cuda_status(e, "ssh_query staging");
     if (s == SSH_OK) {
-        e = cudaMemcpy(ids, did, nq * k * sizeof(int64_t), cudaMemcpyDeviceToHost);
-        if (e == cudaSuccess) e = cudaMemcpy(dists, dd, nq * k * sizeof(float), cudaMemcpyDeviceToHost);
+        e = cudaMemcpyAsync(ids, did, nq * k * sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dists, dd, nq * k * sizeof(float), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) s = cuda_status(e, "ssh_query results");
     }
-    cudaFree(dq);
-    cudaFree(did);
-    cudaFree(dd);
+    cudaFreeAsync(dq, st);
+    cudaFreeAsync(did, st);
+    cudaFreeAsync(dd, st);
+    cudaStreamSynchronize(st);
     return s;
 }
 

@@ -194,7 +194,6 @@ struct SubIndex {
     uint32_t* srows = nullptr;        // [L][cap] device: rows in the same order
     uint32_t* bins = nullptr;         // [L][2^bin_bits + 1] device: bin starts
     int bin_bits = 0, bins_alloc_bits = 0;
-    std::vector<void*> owned;         // device chunks owned by the index
 };
 
 struct KernelTimer {
@@ -202,6 +201,11 @@ struct KernelTimer {
     cudaEvent_t start, stop;
     int launches;
     double units;
+};
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
 };
 
 struct KernelTotals {
@@ -235,4 +239,12 @@ struct ssh_index {
     std::map<int, SubIndex> subs;
     int64_t next_id = 0;
     ssh_stats host_stats{};
+    // series copies made by the library (host adds, non-borrowed device adds):
+    // `owned` are referenced by stored rows; ssh_index_clear moves them to
+    // `spare`, from which later host adds take their staging buffer
+    std::vector<DevBuf> owned, spare;
+    // host-API calls run on these non-blocking streams: hstream hashes and
+    // queries, cstream copies host series in chunks ahead of the hashing
+    cudaStream_t hstream = nullptr, cstream = nullptr;
+    cudaEvent_t cevent = nullptr;
 };
