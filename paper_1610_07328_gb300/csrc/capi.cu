@@ -693,10 +693,11 @@ ssh_status query_group(ssh_index* idx, SubIndex& s, const std::vector<const floa
 
     PairSet all{seg_begin, nq, d_qptr, pair_b, nullptr, max_c};
     const int rb = s.rb;
+    const DtwPlan dplan = (C > 0) ? dtw_tuned_plan(m, rb, st) : DtwPlan{0, 0, 0};
     if (C > 0 && !idx->lb_prune) {
         {
             TimedRegion tr(idx, st, "query.dtw", (double)C * dtw_cells(m, rb));
-            SSH_CUDA(launch_dtw(all, m, rb, dist, st));
+            SSH_CUDA(launch_dtw_plan(all, m, rb, dplan, dist, st));
         }
         idx->host_stats.dtw_computed += C;
     } else if (C > 0) {
@@ -751,7 +752,7 @@ ssh_status query_group(ssh_index* idx, SubIndex& s, const std::vector<const floa
             PairSet sub{fbegin, nq, d_qptr, fb, fslot, mx};
             if (tot > 0) {
                 TimedRegion tr(idx, st, "query.dtw", (double)tot * dtw_cells(m, rb));
-                SSH_CUDA(launch_dtw(sub, m, rb, dist, st));
+                SSH_CUDA(launch_dtw_plan(sub, m, rb, dplan, dist, st));
             }
             idx->host_stats.dtw_computed += tot;
         }

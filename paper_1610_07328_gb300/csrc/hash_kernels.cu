@@ -77,8 +77,14 @@ __global__ void __launch_bounds__(kMaxWarpsPerCta * 32) hash_kernel(HashArgs a, 
     uint32_t* tst = reinterpret_cast<uint32_t*>(wbase + lay.tst);
     __syncthreads();
 
-    const int64_t row = (int64_t)blockIdx.x * warps_per_cta + warp;
-    if (row >= a.count) return;
+    int64_t row = (int64_t)blockIdx.x * warps_per_cta + warp;
+    if (a.dev_range) {
+        const int64_t r0 = a.dev_range[0], r1 = min(a.dev_range[1], r0 + a.count);
+        row += r0;
+        if (row >= r1) return;
+    } else if (row >= a.count) {
+        return;
+    }
     const float* xg = a.rows ? a.rows[row] : a.series + row * a.stride;
 
     // ---- load the series (float4 when aligned)

@@ -6,6 +6,11 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+#include <vector>
+#include <mutex>
+#include <map>
+
 #include "ssh_internal.cuh"
 
 namespace ssh {
@@ -93,19 +98,22 @@ __global__ void __launch_bounds__(1024) bitmap_compact_kernel(const uint32_t* bi
 
 // ----------------------------------------------------------- LB_Keogh
 
-__global__ void envelope_kernel(const float* const* seg_a, int m, int rb, float* upper, float* lower) {
-    const int64_t s = blockIdx.y;
-    const float* q = seg_a[s];
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
-        const int lo = max(0, i - rb), hi = min(m - 1, i + rb);
-        float u = q[lo], l = q[lo];
-        for (int t = lo + 1; t <= hi; ++t) {
-            const float v = q[t];
-            u = fmaxf(u, v);
-            l = fminf(l, v);
+__global__ void envelope_kernel(const float* const* seg_a, int64_t nseg, int m, int rb, float* upper, float* lower,
+                                const int64_t* seg_range, int64_t env_stride) {
+    const int64_t s_lo = seg_range ? seg_range[0] : 0, s_hi = seg_range ? seg_range[1] : nseg;
+    for (int64_t s = s_lo + blockIdx.y; s < s_hi; s += gridDim.y) {
+        const float* q = seg_a[s];
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+            const int lo = max(0, i - rb), hi = min(m - 1, i + rb);
+            float u = q[lo], l = q[lo];
+            for (int t = lo + 1; t <= hi; ++t) {
+                const float v = q[t];
+                u = fmaxf(u, v);
+                l = fminf(l, v);
+            }
+            upper[s * env_stride + i] = u;
+            lower[s * env_stride + i] = l;
         }
-        upper[s * m + i] = u;
-        lower[s * m + i] = l;
     }
 }
 
@@ -114,28 +122,32 @@ constexpr int kLbWarps = 8;
 __global__ void __launch_bounds__(kLbWarps * 32) lb_keogh_kernel(PairSet ps, const float* upper, const float* lower,
                                                                  int m, float* out) {
     extern __shared__ float env[];  // [2m]: upper then lower
-    const int64_t s = blockIdx.y;
-    const int64_t b = ps.seg_begin[s], e = ps.seg_begin[s + 1];
     const int64_t per_cta = kLbWarps;
-    if (b + (int64_t)blockIdx.x * per_cta >= e) return;
-    for (int i = threadIdx.x; i < m; i += blockDim.x) {
-        env[i] = upper[s * m + i];
-        env[m + i] = lower[s * m + i];
-    }
-    __syncthreads();
+    const int64_t es = ps.env_stride ? ps.env_stride : m;
+    const int64_t s_lo = ps.seg_range ? ps.seg_range[0] : 0, s_hi = ps.seg_range ? ps.seg_range[1] : ps.nseg;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int64_t p = b + (int64_t)blockIdx.x * per_cta + warp; p < e; p += (int64_t)gridDim.x * per_cta) {
-        const float* c = ps.pair_b[p];
-        float acc = 0.f;
-        for (int i = lane; i < m; i += 32) {
-            const float v = __ldg(c + i);
-            const float du = v - env[i];
-            const float dl = v - env[m + i];
-            const float d = du > 0.f ? du : (dl < 0.f ? dl : 0.f);
-            acc = fmaf(d, d, acc);
+    for (int64_t s = s_lo + blockIdx.y; s < s_hi; s += gridDim.y) {
+        const int64_t b = ps.seg_begin[s], e = ps.seg_begin[s + 1];
+        if (b + (int64_t)blockIdx.x * per_cta >= e) continue;  // uniform over the block
+        __syncthreads();  // the previous segment's envelope is no longer read
+        for (int i = threadIdx.x; i < m; i += blockDim.x) {
+            env[i] = upper[s * es + i];
+            env[m + i] = lower[s * es + i];
         }
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
-        if (lane == 0) out[ps.pair_slot ? ps.pair_slot[p] : p] = acc;
+        __syncthreads();
+        for (int64_t p = b + (int64_t)blockIdx.x * per_cta + warp; p < e; p += (int64_t)gridDim.x * per_cta) {
+            const float* c = ps.pair_b[p];
+            float acc = 0.f;
+            for (int i = lane; i < m; i += 32) {
+                const float v = __ldg(c + i);
+                const float du = v - env[i];
+                const float dl = v - env[m + i];
+                const float d = du > 0.f ? du : (dl < 0.f ? dl : 0.f);
+                acc = fmaf(d, d, acc);
+            }
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+            if (lane == 0) out[ps.pair_slot ? ps.pair_slot[p] : p] = acc;
+        }
     }
 }
 
@@ -172,13 +184,15 @@ __global__ void __launch_bounds__(256) dtw_wave_kernel(PairSet ps, int m, int rb
     constexpr int H = S / 2;
     constexpr int U = H + 1;
     extern __shared__ float q_s[];
-    const int64_t seg = blockIdx.y;
-    const int64_t sb = ps.seg_begin[seg], se = ps.seg_begin[seg + 1];
     const int warps = blockDim.x >> 5;
     const int gpw = 32 / G;
     const int64_t per_cta = (int64_t)warps * gpw;
-    if (sb + (int64_t)blockIdx.x * per_cta >= se) return;
+    const int64_t s_lo = ps.seg_range ? ps.seg_range[0] : 0, s_hi = ps.seg_range ? ps.seg_range[1] : ps.nseg;
+    for (int64_t seg = s_lo + blockIdx.y; seg < s_hi; seg += gridDim.y) {
+    const int64_t sb = ps.seg_begin[seg], se = ps.seg_begin[seg + 1];
+    if (sb + (int64_t)blockIdx.x * per_cta >= se) continue;  // uniform over the block
     const float* qg = ps.seg_a[seg];
+    __syncthreads();  // the previous segment's query is no longer read
     for (int i = threadIdx.x; i < m; i += blockDim.x) q_s[i] = qg[i];
     __syncthreads();
 
@@ -268,6 +282,7 @@ __global__ void __launch_bounds__(256) dtw_wave_kernel(PairSet ps, int m, int rb
             if (t == p_f) res = D[t];
         if (valid && g == g_f) out[ps.pair_slot ? ps.pair_slot[p] : p] = res;
     }
+    }
 }
 
 template <int S>
@@ -277,7 +292,7 @@ cudaError_t launch_wave(const PairSet& ps, int m, int rb, int G, int pmask, floa
     int64_t gx = (ps.max_seg_pairs + per_cta - 1) / per_cta;
     if (gx < 1) gx = 1;
     if (gx > 65535) gx = 65535;
-    dim3 grid((unsigned)gx, (unsigned)ps.nseg);
+    dim3 grid((unsigned)gx, (unsigned)std::min<int64_t>(ps.nseg, 65535));
     const size_t smem = (size_t)m * sizeof(float);
 #define SSH_WAVE_CASE(PM)                                                                                   \
     case PM: {                                                                                              \
@@ -319,6 +334,37 @@ cudaError_t launch_wave(const PairSet& ps, int m, int rb, int G, int pmask, floa
     }
 #undef SSH_WAVE_CASE
     return cudaErrorInvalidValue;
+}
+
+// ------------------------------------------------- DTW tiling autotuner
+
+// Random-walk rows for timing: row i is a cumulative sum of uniform steps drawn
+// from a 32-bit mix of (seed, i, t).
+__global__ void tune_walk_kernel(float* x, int64_t rows, int m, uint32_t seed) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows; i += (int64_t)gridDim.x * blockDim.x) {
+        float v = 0.f;
+        for (int t = 0; t < m; ++t) {
+            uint32_t h = seed ^ (uint32_t)(i * 0x9E3779B1u) ^ (uint32_t)(t * 0x85EBCA6Bu);
+            h ^= h >> 16;
+            h *= 0x7FEB352Du;
+            h ^= h >> 15;
+            h *= 0x846CA68Bu;
+            h ^= h >> 16;
+            v += (float)(h >> 8) * (1.0f / 8388608.0f) - 1.0f;
+            x[i * m + t] = v;
+        }
+    }
+}
+
+// Pair p of segment p / per_seg: query row p / per_seg, candidate row p.
+__global__ void tune_pairs_kernel(const float* a, const float* b, int m, int64_t nseg, int64_t per_seg,
+                                  const float** seg_a, const float** pair_b, int64_t* seg_begin) {
+    const int64_t np = nseg * per_seg;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p <= np; p += (int64_t)gridDim.x * blockDim.x) {
+        if (p < np) pair_b[p] = b + p * m;
+        if (p < nseg) seg_a[p] = a + p * m;
+        if (p % per_seg == 0) seg_begin[p / per_seg] = p;
+    }
 }
 
 }  // namespace
@@ -370,10 +416,10 @@ cudaError_t launch_bitmap_compact(const uint32_t* bitmap, int64_t nq, int64_t wo
 }
 
 cudaError_t launch_envelope(const float* const* seg_a, int64_t nseg, int m, int rb, float* upper, float* lower,
-                            cudaStream_t st) {
+                            cudaStream_t st, const int64_t* seg_range, int64_t env_stride) {
     if (nseg <= 0) return cudaSuccess;
-    dim3 grid((unsigned)((m + 255) / 256), (unsigned)nseg);
-    envelope_kernel<<<grid, 256, 0, st>>>(seg_a, m, rb, upper, lower);
+    dim3 grid((unsigned)((m + 255) / 256), (unsigned)std::min<int64_t>(nseg, 65535));
+    envelope_kernel<<<grid, 256, 0, st>>>(seg_a, nseg, m, rb, upper, lower, seg_range, env_stride ? env_stride : m);
     note_launch();
     return cudaGetLastError();
 }
@@ -386,19 +432,99 @@ cudaError_t launch_lb_keogh(const PairSet& ps, const float* upper, const float* 
     const size_t smem = 2 * (size_t)m * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(lb_keogh_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    dim3 grid((unsigned)gx, (unsigned)ps.nseg);
+    dim3 grid((unsigned)gx, (unsigned)std::min<int64_t>(ps.nseg, 65535));
     lb_keogh_kernel<<<grid, kLbWarps * 32, smem, st>>>(ps, upper, lower, m, out);
     note_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_dtw(const PairSet& ps, int m, int rb, float* out, cudaStream_t st) {
+    return launch_dtw_plan(ps, m, rb, dtw_plan(m, rb), out, st);
+}
+
+cudaError_t launch_dtw_plan(const PairSet& ps, int m, int rb, const DtwPlan& pl, float* out, cudaStream_t st) {
     if (ps.nseg <= 0 || ps.max_seg_pairs <= 0) return cudaSuccess;
-    const DtwPlan pl = dtw_plan(m, rb);
     if (pl.S == 8) return launch_wave<8>(ps, m, rb, pl.G, pl.pmask, out, st);
     if (pl.S == 14) return launch_wave<14>(ps, m, rb, pl.G, pl.pmask, out, st);
     if (pl.S == 26) return launch_wave<26>(ps, m, rb, pl.G, pl.pmask, out, st);
     return cudaErrorNotSupported;
+}
+
+// Time every feasible slot count S (lanes per pair G = ceil((2 rb + 2) / S))
+// on random-walk pairs of length m (about 1e9 cells per run, 3 runs, the
+// fastest counts) and keep the fastest tiling for (m, rb) for the process.
+DtwPlan dtw_tuned_plan(int m, int rb, cudaStream_t st) {
+    static std::mutex mu;
+    static std::map<std::pair<int, int>, DtwPlan> cache;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        auto it = cache.find({m, rb});
+        if (it != cache.end()) return it->second;
+    }
+    std::vector<DtwPlan> cands;
+    for (int S : {8, 14, 26}) {
+        const int G = (2 * rb + 2 + S - 1) / S;
+        if (G > 32) continue;
+        const int PAD = G * S - (2 * rb + 1);
+        cands.push_back(DtwPlan{S, G, (PAD - 1) % S});
+    }
+    DtwPlan best = dtw_plan(m, rb);
+    if (cands.size() > 1) {
+        const double cells = (double)m * (2.0 * rb + 1.0) - (double)rb * (rb + 1.0);
+        int64_t np = (int64_t)(1e9 / std::max(cells, 1.0));
+        np = std::max<int64_t>(2048, std::min<int64_t>(np, 262144));
+        const int64_t nseg = 16, per_seg = (np + nseg - 1) / nseg;
+        np = nseg * per_seg;
+        float *a = nullptr, *b = nullptr, *out = nullptr;
+        const float **seg_a = nullptr, **pair_b = nullptr;
+        int64_t* seg_begin = nullptr;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        bool ok = cudaMallocAsync(&a, (size_t)nseg * m * 4, st) == cudaSuccess &&
+                  cudaMallocAsync(&b, (size_t)np * m * 4, st) == cudaSuccess &&
+                  cudaMallocAsync(&out, (size_t)np * 4, st) == cudaSuccess &&
+                  cudaMallocAsync(&seg_a, (size_t)nseg * sizeof(float*), st) == cudaSuccess &&
+                  cudaMallocAsync(&pair_b, (size_t)np * sizeof(float*), st) == cudaSuccess &&
+                  cudaMallocAsync(&seg_begin, (size_t)(nseg + 1) * 8, st) == cudaSuccess &&
+                  cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess;
+        if (ok) {
+            tune_walk_kernel<<<64, 256, 0, st>>>(a, nseg, m, 0x51u);
+            tune_walk_kernel<<<(unsigned)std::min<int64_t>((np + 255) / 256, 4096), 256, 0, st>>>(b, np, m, 0xA7u);
+            tune_pairs_kernel<<<(unsigned)std::min<int64_t>((np + 256) / 256, 4096), 256, 0, st>>>(
+                a, b, m, nseg, per_seg, seg_a, pair_b, seg_begin);
+            note_launch();
+            note_launch();
+            note_launch();
+            PairSet ps{seg_begin, nseg, seg_a, pair_b, nullptr, per_seg};
+            float best_ms = 1e30f;
+            for (const DtwPlan& pl : cands) {
+                float t_min = 1e30f;
+                for (int rep = 0; rep < 4 && ok; ++rep) {
+                    ok = cudaEventRecord(e0, st) == cudaSuccess &&
+                         launch_dtw_plan(ps, m, rb, pl, out, st) == cudaSuccess &&
+                         cudaEventRecord(e1, st) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
+                    float ms = 0.f;
+                    if (ok && rep > 0 && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) t_min = std::min(t_min, ms);
+                }
+                if (ok && t_min < best_ms) {
+                    best_ms = t_min;
+                    best = pl;
+                }
+            }
+        }
+        cudaFreeAsync(a, st);
+        cudaFreeAsync(b, st);
+        cudaFreeAsync(out, st);
+        cudaFreeAsync(seg_a, st);
+        cudaFreeAsync(pair_b, st);
+        cudaFreeAsync(seg_begin, st);
+        cudaStreamSynchronize(st);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        cudaGetLastError();  // a failed timing falls back to the cost model's plan
+    }
+    std::lock_guard<std::mutex> lock(mu);
+    cache[{m, rb}] = best;
+    return best;
 }
 
 }  // namespace ssh

@@ -81,6 +81,9 @@ struct HashArgs {
     const float* lns32;      // [kMaxCount+1] ln s rounded to FP32
     const double* lns64;     // [kMaxCount+1] ln s in FP64
     uint64_t seed;
+    // optional device [2] (first, end): hash rows first .. end-1 of `rows`/`series`
+    // (at most `count` of them; keys at column key_col0 + row). NULL: rows 0 .. count-1.
+    const int64_t* dev_range;
     uint64_t* keys;          // [L][key_stride], row i of this launch at column key_col0 + i
     int64_t key_stride;
     int64_t key_col0;
@@ -159,10 +162,14 @@ struct PairSet {
     const float* const* pair_b; // [npairs] device
     const int64_t* pair_slot;   // [npairs] device, or NULL
     int64_t max_seg_pairs;      // upper bound of any segment's size (grid sizing)
+    // optional device [2] (first, end): process only segments first .. end-1
+    // (the launch then strides over them with its fixed grid). NULL: all nseg.
+    const int64_t* seg_range = nullptr;
+    int64_t env_stride = 0;     // floats between segments' envelopes (0: m)
 };
 
 cudaError_t launch_envelope(const float* const* seg_a, int64_t nseg, int m, int rb, float* upper, float* lower,
-                            cudaStream_t st);
+                            cudaStream_t st, const int64_t* seg_range = nullptr, int64_t env_stride = 0);
 cudaError_t launch_lb_keogh(const PairSet& ps, const float* upper, const float* lower, int m, float* out,
                             cudaStream_t st);
 
@@ -170,7 +177,11 @@ struct DtwPlan {
     int S, G, pmask;
 };
 DtwPlan dtw_plan(int m, int rb);
+// The tiling used for (m, rb): timed once per process over the candidate slot
+// counts (the first call for a (m, rb) runs the timing on `st` and waits for it).
+DtwPlan dtw_tuned_plan(int m, int rb, cudaStream_t st);
 cudaError_t launch_dtw(const PairSet& ps, int m, int rb, float* out, cudaStream_t st);
+cudaError_t launch_dtw_plan(const PairSet& ps, int m, int rb, const DtwPlan& pl, float* out, cudaStream_t st);
 
 // k-th smallest key of each segment (keys read through `keys`, segment s is
 // [seg_begin[s], seg_begin[s+1])); kth_out[s] = that key, or all-ones if the
