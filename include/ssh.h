@@ -132,6 +132,39 @@ ssh_status ssh_query_device(ssh_index* idx, const float* d_queries, const int32_
 ssh_status ssh_group_query_device(ssh_index* const* handles, int nh, const float* d_queries, const int32_t* lengths,
                                   int64_t nq, int k, int64_t* d_ids, float* d_dists, int32_t* d_which, void* stream);
 
+/* ---- batched queries: one CUDA graph per plan ----
+ *
+ * A batch plan answers Algorithm 2 for many queries of mixed lengths over the
+ * nh indexes `handles` at once (a query goes to the first handle that stores
+ * series of its length, as in ssh_group_query_device). Every kernel of the
+ * plan's pipeline runs on a fixed grid and reads the batch's sizes from device
+ * memory, so the pipeline is captured once as a CUDA graph and replayed for
+ * each batch; the first batch of a plan runs directly and the graph is
+ * captured from it. ssh_batch_create allocates every device buffer: room for
+ * max_queries queries (1 .. 65535), top-k with k <= 1024, and max_pairs
+ * (query, candidate) pairs in total (0: max(2^20, 2048 max_queries)); a batch
+ * with more candidates grows the pair buffers and reruns. The DTW tiling of
+ * each (length, band radius) is chosen at creation by timing the candidate
+ * tilings (cached for the process). After an add to or clear of any of the
+ * indexes the next ssh_batch_query rebuilds the plan. The indexes must outlive
+ * the plan; one plan serves one thread at a time.
+ *
+ * ssh_batch_query: queries back to back in device memory (d_queries, lengths
+ * on the host); d_ids/d_dists [nq][k] and d_which [nq] (may be NULL) as in
+ * ssh_group_query_device. It waits for `stream`'s earlier work, and returns
+ * when the results are in place (work is ordered before later work on
+ * `stream`). SSH_ELENGTH for a length no index stores, SSH_EINVAL for
+ * nq > max_queries. ssh_batch_stats: pairs (candidates) and DTW pairs of the
+ * last batch, the pair capacity, and the kernels in the captured graph. */
+typedef struct ssh_batch ssh_batch;
+ssh_status ssh_batch_create(ssh_index* const* handles, int nh, int64_t max_queries, int k, int64_t max_pairs,
+                            ssh_batch** out);
+ssh_status ssh_batch_query(ssh_batch* b, const float* d_queries, const int32_t* lengths, int64_t nq, int64_t* d_ids,
+                           float* d_dists, int32_t* d_which, void* stream);
+ssh_status ssh_batch_stats(const ssh_batch* b, int64_t* pairs, int64_t* dtw, int64_t* pair_capacity,
+                           int32_t* graph_kernels);
+void ssh_batch_destroy(ssh_batch* b);
+
 /* Options. SSH_OPT_LB_PRUNE (default 1): LB_Keogh pruning before DTW in the
  * rerank; 0 computes DTW for every candidate (same results, more work).
  * SSH_OPT_KERNEL_TIMING (default 0): record CUDA events around each kernel

@@ -62,6 +62,11 @@ _SIGS = {
     "ssh_query": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, ctypes.c_int, _P, _P]),
     "ssh_query_device": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, ctypes.c_int, _P, _P, _P]),
     "ssh_group_query_device": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_int64, ctypes.c_int, _P, _P, _P, _P]),
+    "ssh_batch_create": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int64, ctypes.c_int, ctypes.c_int64,
+                                        ctypes.POINTER(_P)]),
+    "ssh_batch_query": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, _P, _P, _P, _P]),
+    "ssh_batch_stats": (ctypes.c_int, [_P, _I64P, _I64P, _I64P, ctypes.POINTER(ctypes.c_int32)]),
+    "ssh_batch_destroy": (None, [_P]),
     "ssh_set_option": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int64]),
     "ssh_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(ssh_stats)]),
     "ssh_reset_stats": (ctypes.c_int, [_P]),
@@ -194,6 +199,65 @@ def ssh_group_query_device(handles, d_queries, lengths: np.ndarray, k: int, d_id
     _check(load().ssh_group_query_device(ctypes.cast(arr, ctypes.c_void_p), len(handles), _dev_ptr(d_queries),
                                          _host_ptr(ln), len(ln), k, _dev_ptr(d_ids), _dev_ptr(d_dists),
                                          _dev_ptr(d_which), _stream(stream)))
+
+
+def ssh_batch_create(handles, max_queries: int, k: int, max_pairs: int = 0):
+    """A batch plan over the indexes `handles` (see include/ssh.h)."""
+    arr = (ctypes.c_void_p * len(handles))(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in handles])
+    out = _P()
+    _check(load().ssh_batch_create(ctypes.cast(arr, ctypes.c_void_p), len(handles), max_queries, k, max_pairs,
+                                   ctypes.byref(out)))
+    return out
+
+
+def ssh_batch_query(b, d_queries, lengths: np.ndarray, d_ids, d_dists, d_which=None, stream=None) -> None:
+    ln = np.ascontiguousarray(lengths, dtype=np.int32)
+    _check(load().ssh_batch_query(b, _dev_ptr(d_queries), _host_ptr(ln), len(ln), _dev_ptr(d_ids), _dev_ptr(d_dists),
+                                  _dev_ptr(d_which), _stream(stream)))
+
+
+def ssh_batch_stats(b) -> dict:
+    pairs, dtw, cap = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    nk = ctypes.c_int32()
+    _check(load().ssh_batch_stats(b, ctypes.byref(pairs), ctypes.byref(dtw), ctypes.byref(cap), ctypes.byref(nk)))
+    return dict(pairs=pairs.value, dtw=dtw.value, pair_capacity=cap.value, graph_kernels=nk.value)
+
+
+def ssh_batch_destroy(b) -> None:
+    if b:
+        load().ssh_batch_destroy(b)
+
+
+class SSHBatch:
+    """Owning wrapper around an ssh_batch plan."""
+
+    def __init__(self, indexes, max_queries: int, k: int, max_pairs: int = 0):
+        self.k = k
+        self.indexes = list(indexes)  # kept alive for the plan's lifetime
+        self.handle = ssh_batch_create([ix.handle for ix in self.indexes], max_queries, k, max_pairs)
+
+    def query(self, d_queries, lengths, d_ids, d_dists, d_which=None, stream=None):
+        ssh_batch_query(self.handle, d_queries, lengths, d_ids, d_dists, d_which, stream)
+
+    def stats(self) -> dict:
+        return ssh_batch_stats(self.handle)
+
+    def close(self):
+        if self.handle:
+            ssh_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 def ssh_set_option(h, opt: int, value: int) -> None:

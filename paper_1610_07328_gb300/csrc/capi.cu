@@ -14,6 +14,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <map>
+#include <mutex>
 #include <numeric>
 #include <thread>
 #include <vector>
@@ -250,111 +252,6 @@ __global__ void gather_ptrs_kernel(const uint32_t* rows, int64_t n, const float*
         out[i] = row_ptr[rows[i]];
 }
 
-__global__ void fill_f32_kernel(float* p, int64_t n, float v) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        p[i] = v;
-}
-
-// mode 0: seeds, keep lb <= T[s].  mode 1: survivors, keep lb > T[s] and lb * shrink <= U[s].
-__global__ void filter_count_kernel(const int64_t* seg_begin, int64_t nseg, const float* lb, const uint32_t* T,
-                                    const uint32_t* U, float shrink, int mode, int64_t* counts) {
-    const int64_t s = blockIdx.y;
-    const int64_t b = seg_begin[s], e = seg_begin[s + 1];
-    const float t = (T[s] == 0xFFFFFFFFu) ? __int_as_float(0x7F800000) : __uint_as_float(T[s]);
-    const float u = mode ? __uint_as_float(U[s]) : 0.f;
-    int64_t c = 0;
-    for (int64_t p = b + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < e; p += (int64_t)gridDim.x * blockDim.x) {
-        const float v = lb[p];
-        const bool keep = mode == 0 ? (v <= t) : (v > t && v * shrink <= u);
-        c += keep;
-    }
-    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
-    if ((threadIdx.x & 31) == 0 && c) atomicAdd(reinterpret_cast<unsigned long long*>(&counts[s]), (unsigned long long)c);
-}
-
-__global__ void filter_scatter_kernel(const int64_t* seg_begin, int64_t nseg, const float* lb, const uint32_t* T,
-                                      const uint32_t* U, float shrink, int mode, const int64_t* out_begin,
-                                      unsigned long long* cursor, const float* const* pair_b_in,
-                                      const float** pair_b_out, int64_t* slot_out) {
-    const int64_t s = blockIdx.y;
-    const int64_t b = seg_begin[s], e = seg_begin[s + 1];
-    const float t = (T[s] == 0xFFFFFFFFu) ? __int_as_float(0x7F800000) : __uint_as_float(T[s]);
-    const float u = mode ? __uint_as_float(U[s]) : 0.f;
-    for (int64_t p = b + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < e; p += (int64_t)gridDim.x * blockDim.x) {
-        const float v = lb[p];
-        const bool keep = mode == 0 ? (v <= t) : (v > t && v * shrink <= u);
-        if (keep) {
-            const int64_t pos = out_begin[s] + (int64_t)atomicAdd(&cursor[s], 1ull);
-            pair_b_out[pos] = pair_b_in[p];
-            slot_out[pos] = p;
-        }
-    }
-}
-
-__global__ void exclusive_scan_small_kernel(const int64_t* counts, int64_t n, int64_t* out) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        int64_t run = 0;
-        for (int64_t i = 0; i < n; ++i) {
-            out[i] = run;
-            run += counts[i];
-        }
-        out[n] = run;
-    }
-}
-
-__global__ void topk_keys_kernel(const float* dist, const uint32_t* rows, int64_t n, uint64_t* keys) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        keys[i] = ((uint64_t)__float_as_uint(dist[i]) << 32) | rows[i];
-}
-
-// Final top-k of one query: the keys <= the k-th smallest, sorted, as (id, dist).
-__global__ void __launch_bounds__(1024) topk_output_kernel(const uint64_t* keys, const int64_t* seg_begin,
-                                                           const uint64_t* kth, const int64_t* gid, int k,
-                                                           const int64_t* qpos, int64_t* ids_out,
-                                                           float* dists_out) {
-    __shared__ uint64_t buf[kMaxTopK];
-    __shared__ int cnt;
-    const int64_t s = blockIdx.x;
-    const int64_t b = seg_begin[s], e = seg_begin[s + 1];
-    const uint64_t lim = kth[s];
-    if (threadIdx.x == 0) cnt = 0;
-    for (int i = threadIdx.x; i < kMaxTopK; i += blockDim.x) buf[i] = ~0ull;
-    __syncthreads();
-    for (int64_t p = b + threadIdx.x; p < e; p += blockDim.x) {
-        const uint64_t v = keys[p];
-        if (v <= lim) {
-            const int at = atomicAdd(&cnt, 1);
-            if (at < kMaxTopK) buf[at] = v;
-        }
-    }
-    __syncthreads();
-    int n2 = 1;
-    while (n2 < k) n2 <<= 1;
-    for (int kk = 2; kk <= n2; kk <<= 1) {
-        for (int jj = kk >> 1; jj > 0; jj >>= 1) {
-            for (int i = threadIdx.x; i < n2; i += blockDim.x) {
-                const int l = i ^ jj;
-                if (l > i) {
-                    const uint64_t u = buf[i], v = buf[l];
-                    const bool up = (i & kk) == 0;
-                    if ((u > v) == up) {
-                        buf[i] = v;
-                        buf[l] = u;
-                    }
-                }
-            }
-            __syncthreads();
-        }
-    }
-    const int64_t out0 = qpos[s] * (int64_t)k;
-    for (int t = threadIdx.x; t < k; t += blockDim.x) {
-        const uint64_t v = buf[t];
-        const uint32_t dbits = (uint32_t)(v >> 32);
-        const bool real = (v != ~0ull) && dbits < 0x7F800000u;
-        ids_out[out0 + t] = real ? gid[(uint32_t)v] : -1;
-        dists_out[out0 + t] = real ? __uint_as_float(dbits) : __uint_as_float(0x7F800000u);
-    }
-}
 
 unsigned grid_for(int64_t n, int threads, int64_t cap = 65535) {
     int64_t g = (n + threads - 1) / threads;
@@ -498,6 +395,7 @@ ssh_status rebuild_tables(ssh_index* idx, SubIndex& s, cudaStream_t st) {
     return SSH_OK;
 }
 
+
 // End of the run of equal lengths that starts at i: the first j > i with
 // lengths[j] != lengths[i], or count. Whole chunks are tested with an OR of
 // XORs (a loop the compiler vectorises), so a call of one length costs a
@@ -582,6 +480,7 @@ ssh_status finish_add(ssh_index* idx, const std::vector<int>& touched, int64_t c
     SSH_CUDA(cudaStreamSynchronize(st));
     if (first_id) *first_id = idx->next_id;
     idx->next_id += count;
+    idx->version += 1;
     return SSH_OK;
 }
 
@@ -686,13 +585,14 @@ ssh_status query_group(ssh_index* idx, SubIndex& s, const std::vector<const floa
     if (C > 0) {
         gather_ptrs_kernel<<<grid_for(C, 256, 8192), 256, 0, st>>>(cand_rows, C, s.row_ptr, pair_b);
         note_launch();
-        fill_f32_kernel<<<grid_for(C, 256, 8192), 256, 0, st>>>(dist, C, __builtin_huge_valf());
-        note_launch();
         SSH_CUDA(cudaGetLastError());
+        SSH_CUDA(launch_fill_f32(dist, C, nullptr, __builtin_huge_valf(), st));
     }
 
     PairSet all{seg_begin, nq, d_qptr, pair_b, nullptr, max_c};
     const int rb = s.rb;
+    unsigned long long* pruned_counts = nullptr;  // pinned: DTW pairs of the seed and survivor passes
+    size_t pruned_slots[2] = {SIZE_MAX, SIZE_MAX};
     const DtwPlan dplan = (C > 0) ? dtw_tuned_plan(m, rb, st) : DtwPlan{0, 0, 0};
     if (C > 0 && !idx->lb_prune) {
         {
@@ -719,64 +619,72 @@ ssh_status query_group(ssh_index* idx, SubIndex& s, const std::vector<const floa
         // eta bounds the FP32 rounding of LB (m + 3 terms) and of DTW (2m terms): 4 (m + 3) 2^-24
         const float shrink = (float)(1.0 - 4.0 * (m + 3) * std::ldexp(1.0, -24));
         int64_t *fcount, *fbegin;
-        unsigned long long* cursor;
+        unsigned long long *cursor, *ftotal;
         const float** fb;
         int64_t* fslot;
         SSH_TRY(sc.get(&fcount, nq));
         SSH_TRY(sc.get(&fbegin, nq + 1));
         SSH_TRY(sc.get(&cursor, nq));
+        SSH_TRY(sc.get(&ftotal, 2));
         SSH_TRY(sc.get(&fb, C));
         SSH_TRY(sc.get(&fslot, C));
-        for (int mode = 0; mode < 2; ++mode) {
+        unsigned long long* h_tot = idx->h_pinned;
+        h_tot[0] = h_tot[1] = 0;
+        ssh_status fst = SSH_OK;
+        size_t tslot[2] = {SIZE_MAX, SIZE_MAX};  // the two DTW timings: cells are known after the sync
+        for (int mode = 0; mode < 2 && fst == SSH_OK; ++mode) {
+            cudaError_t e = cudaSuccess;
             if (mode == 1)
-                SSH_CUDA(launch_select_kth_u32(reinterpret_cast<const uint32_t*>(dist), seg_begin, nq, k, U, st));
-            SSH_CUDA(cudaMemsetAsync(fcount, 0, nq * sizeof(int64_t), st));
-            SSH_CUDA(cudaMemsetAsync(cursor, 0, nq * sizeof(unsigned long long), st));
-            dim3 fg(grid_for(max_c, 256, 1024), (unsigned)nq);
-            filter_count_kernel<<<fg, 256, 0, st>>>(seg_begin, nq, lb, T, U, shrink, mode, fcount);
-            note_launch();
-            exclusive_scan_small_kernel<<<1, 32, 0, st>>>(fcount, nq, fbegin);
-            note_launch();
-            filter_scatter_kernel<<<fg, 256, 0, st>>>(seg_begin, nq, lb, T, U, shrink, mode, fbegin, cursor, pair_b,
-                                                      fb, fslot);
-            note_launch();
-            SSH_CUDA(cudaGetLastError());
-            std::vector<int64_t> hf(nq);
-            SSH_CUDA(cudaMemcpyAsync(hf.data(), fcount, nq * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-            SSH_CUDA(cudaStreamSynchronize(st));
-            int64_t tot = 0, mx = 0;
-            for (int64_t q = 0; q < nq; ++q) {
-                tot += hf[q];
-                mx = std::max(mx, hf[q]);
+                e = launch_select_kth_u32(reinterpret_cast<const uint32_t*>(dist), seg_begin, nq, k, U, st);
+            FilterArgs f{seg_begin, nq, max_c, lb, T, U, shrink, mode, fcount, cursor, fbegin, ftotal + mode, pair_b, fb,
+                         fslot};
+            if (e == cudaSuccess) e = launch_filter(f, st);
+            // every filtered segment is no longer than its candidate segment: size the DTW grid by max_c
+            PairSet sub{fbegin, nq, d_qptr, fb, fslot, max_c};
+            if (e == cudaSuccess) {
+                {
+                    TimedRegion tr(idx, st, "query.dtw", 0.0);
+                    e = launch_dtw_plan(sub, m, rb, dplan, dist, st);
+                }
+                if (idx->timing && !idx->pending.empty()) tslot[mode] = idx->pending.size() - 1;
             }
-            PairSet sub{fbegin, nq, d_qptr, fb, fslot, mx};
-            if (tot > 0) {
-                TimedRegion tr(idx, st, "query.dtw", (double)tot * dtw_cells(m, rb));
-                SSH_CUDA(launch_dtw_plan(sub, m, rb, dplan, dist, st));
-            }
-            idx->host_stats.dtw_computed += tot;
+            if (e != cudaSuccess) fst = cuda_status(e, "rerank");
         }
+        if (fst == SSH_OK) {
+            // read at the end of the query with the results
+            cudaError_t e = cudaMemcpyAsync(h_tot, ftotal, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
+            if (e != cudaSuccess) fst = cuda_status(e, "rerank counts");
+        }
+        if (fst != SSH_OK) {
+            cudaStreamSynchronize(st);
+            return fst;
+        }
+        pruned_counts = h_tot;
+        pruned_slots[0] = tslot[0];
+        pruned_slots[1] = tslot[1];
     }
-    idx->host_stats.lb_pruned = idx->host_stats.candidates - idx->host_stats.dtw_computed;
-
     // top-k by (distance, id): ids grow with rows inside a sub-index, so the key
     // (distance bits, row) orders exactly like (distance, id)
     uint64_t *tkeys, *kth;
     SSH_TRY(sc.get(&tkeys, C));
     SSH_TRY(sc.get(&kth, nq));
+    cudaError_t e = cudaSuccess;
     {
         TimedRegion tr(idx, st, "query.topk", (double)C);
-        if (C > 0) {
-            topk_keys_kernel<<<grid_for(C, 256, 8192), 256, 0, st>>>(dist, cand_rows, C, tkeys);
-            note_launch();
-            SSH_CUDA(cudaGetLastError());
-        }
-        SSH_CUDA(launch_select_kth_u64(tkeys, seg_begin, nq, k, kth, st));
-        topk_output_kernel<<<(unsigned)nq, 1024, 0, st>>>(tkeys, seg_begin, kth, s.gid, k, d_qpos, d_ids, d_dists);
-        note_launch();
-        SSH_CUDA(cudaGetLastError());
+        if (C > 0) e = launch_topk_keys(dist, cand_rows, C, nullptr, tkeys, st);
+        if (e == cudaSuccess) e = launch_select_kth_u64(tkeys, seg_begin, nq, k, kth, st);
+        TopkOut o{d_ids, d_dists, d_qpos, s.gid, nullptr, nullptr, nullptr, nullptr};
+        if (e == cudaSuccess) e = launch_topk_output(o, tkeys, seg_begin, kth, nq, k, st);
     }
-    SSH_CUDA(cudaStreamSynchronize(st));
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess && pruned_counts) {
+        idx->host_stats.dtw_computed += (int64_t)(pruned_counts[0] + pruned_counts[1]);
+        for (int mode = 0; mode < 2; ++mode)
+            if (pruned_slots[mode] != SIZE_MAX)
+                idx->pending[pruned_slots[mode]].units = (double)pruned_counts[mode] * dtw_cells(m, rb);
+    }
+    idx->host_stats.lb_pruned = idx->host_stats.candidates - idx->host_stats.dtw_computed;
+    SSH_CUDA(e);
     return SSH_OK;
 }
 
@@ -804,6 +712,22 @@ __global__ void fill_i32_kernel(int32_t* p, int64_t n, const int64_t* pos, int32
         p[pos[i]] = v;
 }
 
+}  // namespace
+
+cudaError_t ensure_dynamic_smem(const void* fn, size_t bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void*>, size_t> have;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    size_t& cur = have[{dev, fn}];
+    if (bytes <= cur) return cudaSuccess;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) cur = bytes;
+    return e;
+}
+
 ssh_status check_device(const ssh_index* idx) {
     int dev = -1;
     SSH_CUDA(cudaGetDevice(&dev));
@@ -811,7 +735,15 @@ ssh_status check_device(const ssh_index* idx) {
     return SSH_OK;
 }
 
-}  // namespace
+ssh_status fail_status(ssh_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    set_error("%s", buf);
+    return s;
+}
 
 ssh_status prepare_hash_args(const ssh_index* idx, int m, HashArgs* a) {
     SSH_TRY(check_device(idx));
@@ -881,6 +813,7 @@ ssh_status ssh_create(int W, int delta, int n, int K, int L, float band, uint64_
     e = cudaStreamCreateWithFlags(&idx->hstream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&idx->cstream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&idx->cevent, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMallocHost(&idx->h_pinned, 8 * sizeof(unsigned long long));
     if (e != cudaSuccess) {
         ssh_status st = cuda_status(e, "ssh_create streams");
         ssh_destroy(idx);
@@ -976,6 +909,7 @@ void ssh_destroy(ssh_index* idx) {
     for (DevBuf& b : idx->owned) cudaFree(b.p);
     for (DevBuf& b : idx->spare) cudaFree(b.p);
     if (idx->cevent) cudaEventDestroy(idx->cevent);
+    if (idx->h_pinned) cudaFreeHost(idx->h_pinned);
     if (idx->hstream) cudaStreamDestroy(idx->hstream);
     if (idx->cstream) cudaStreamDestroy(idx->cstream);
     for (auto& t : idx->pending) {
@@ -1121,6 +1055,7 @@ ssh_status ssh_index_clear(ssh_index* idx) {
     SSH_TRY(check_device(idx));
     SSH_CUDA(cudaDeviceSynchronize());
     for (auto& kv : idx->subs) kv.second.count = 0;  // keep the capacity for the next add
+    idx->version += 1;
     // the copies of the cleared series become staging buffers for later adds
     for (DevBuf& b : idx->owned) idx->spare.push_back(b);
     idx->owned.clear();

@@ -247,7 +247,7 @@ cudaError_t launch_hash_generic(const HashArgs& a, cudaStream_t st) {
     const int wpc = hash_warps_per_cta(a.m, a.nwords, a.S, a.KL);
     const size_t smem = (size_t)align16(4 * a.W) + (size_t)wpc * hash_smem_bytes_per_warp(a.m, a.nwords, a.S, a.KL);
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(hash_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ensure_dynamic_smem((const void*)hash_kernel, smem);
     if (e != cudaSuccess) return e;
     const int64_t grid = (a.count + wpc - 1) / wpc;
     hash_kernel<<<(unsigned)grid, wpc * 32, smem, st>>>(a, wpc);

@@ -515,8 +515,7 @@ cudaError_t launch_sketch_t(const HashArgs& a, uint32_t* bits, unsigned long lon
     const int xb = sketch_xb(a.m, W, DELTA, R);
     const size_t smem = (size_t)a16(4 * W) + (size_t)kSketchWarps * (2 * a16(4 * xb) + a16(32 * R));
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
-    cudaError_t e =
-        cudaFuncSetAttribute(sketch_kernel<W, DELTA, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ensure_dynamic_smem((const void*)sketch_kernel<W, DELTA, R>, smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sketch_kernel<W, DELTA, R>, kSketchWarps * 32, smem);
@@ -544,7 +543,7 @@ cudaError_t launch_shingle(const HashArgs& a, const uint32_t* bits, uint32_t* se
     const int wpb = warps_for((size_t)lay.total);
     if (wpb < 1) return cudaErrorInvalidValue;
     const size_t smem = (size_t)wpb * lay.total;
-    cudaError_t e = cudaFuncSetAttribute(shingle_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ensure_dynamic_smem((const void*)shingle_kernel, smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, shingle_kernel, wpb * 32, smem);
@@ -561,7 +560,7 @@ cudaError_t launch_cws(const HashArgs& a, const uint32_t* sets, const int2* size
     const int wpb = warps_for((size_t)lay.total);
     if (wpb < 1) return cudaErrorInvalidValue;
     const size_t smem = (size_t)wpb * lay.total;
-    cudaError_t e = cudaFuncSetAttribute(cws_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ensure_dynamic_smem((const void*)cws_kernel, smem);
     if (e != cudaSuccess) return e;
     // the rank rows are re-read from L1: ask for no more shared memory than 4 blocks use
     const int pct = (int)std::min<size_t>(100, (4 * smem * 100 + 228 * 1024 - 1) / (228 * 1024));

@@ -292,12 +292,11 @@ cudaError_t launch_wave(const PairSet& ps, int m, int rb, int G, int pmask, floa
     int64_t gx = (ps.max_seg_pairs + per_cta - 1) / per_cta;
     if (gx < 1) gx = 1;
     if (gx > 65535) gx = 65535;
-    dim3 grid((unsigned)gx, (unsigned)std::min<int64_t>(ps.nseg, 65535));
+    dim3 grid((unsigned)gx, (unsigned)(ps.grid_y ? ps.grid_y : std::min<int64_t>(ps.nseg, 65535)));
     const size_t smem = (size_t)m * sizeof(float);
 #define SSH_WAVE_CASE(PM)                                                                                   \
     case PM: {                                                                                              \
-        cudaError_t e = cudaFuncSetAttribute(dtw_wave_kernel<S, PM>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                             (int)smem);                                                    \
+        cudaError_t e = ensure_dynamic_smem((const void*)dtw_wave_kernel<S, PM>, smem);                    \
         if (e != cudaSuccess) return e;                                                                     \
         dtw_wave_kernel<S, PM><<<grid, threads, smem, st>>>(ps, m, rb, G, out);                             \
         note_launch();                                                                                      \
@@ -334,6 +333,163 @@ cudaError_t launch_wave(const PairSet& ps, int m, int rb, int G, int pmask, floa
     }
 #undef SSH_WAVE_CASE
     return cudaErrorInvalidValue;
+}
+
+// ------------------------------------------ candidate filters and top-k
+
+// p[i] = v for i < n (n read from n_dev when it is given).
+__global__ void fill_f32_kernel(float* p, int64_t n, const int64_t* n_dev, float v) {
+    if (n_dev) n = *n_dev;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+
+// Exclusive prefix sums of counts[0 .. n) into out[0 .. n], one block; with
+// cap > 0 and a total above cap, every count is taken as 0 and *overflow = 1.
+__global__ void __launch_bounds__(1024) scan_kernel(const int64_t* counts, int64_t n, int64_t* out, int64_t cap,
+                                                    unsigned long long* total_out, unsigned long long* overflow) {
+    __shared__ int64_t warp_sums[32];
+    __shared__ int64_t carry;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int pass = 0; pass < 2; ++pass) {
+        if (threadIdx.x == 0) carry = 0;
+        __syncthreads();
+        for (int64_t base = 0; base < n; base += blockDim.x) {
+            const int64_t i = base + threadIdx.x;
+            const int64_t v = (i < n) ? counts[i] : 0;
+            int64_t incl = v;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int64_t u = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o) incl += u;
+            }
+            if (lane == 31) warp_sums[warp] = incl;
+            __syncthreads();
+            if (warp == 0) {
+                const int64_t ws = (lane < nw) ? warp_sums[lane] : 0;
+                int64_t wi = ws;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int64_t u = __shfl_up_sync(kFull, wi, o);
+                    if (lane >= o) wi += u;
+                }
+                if (lane < nw) warp_sums[lane] = wi - ws;
+            }
+            __syncthreads();
+            const int64_t excl = carry + warp_sums[warp] + incl - v;
+            if (pass == 1 && i < n) out[i] = excl;
+            __syncthreads();
+            if (threadIdx.x == blockDim.x - 1) carry = excl + v;
+            __syncthreads();
+        }
+        if (pass == 0) {
+            // the total decides whether the offsets are written as counted or as all zero
+            const int64_t total = carry;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                if (total_out) *total_out = (unsigned long long)total;
+                if (overflow) *overflow = (cap > 0 && total > cap) ? 1ull : 0ull;
+            }
+            if (cap > 0 && total > cap) {
+                for (int64_t i = threadIdx.x; i <= n; i += blockDim.x) out[i] = 0;
+                return;
+            }
+        } else if (threadIdx.x == 0) {
+            out[n] = carry;
+        }
+        __syncthreads();
+    }
+}
+
+// mode 0: seeds, keep lb <= T[s].  mode 1: survivors, keep lb > T[s] and lb * shrink <= U[s].
+__global__ void filter_count_kernel(const int64_t* seg_begin, const float* lb, const uint32_t* T, const uint32_t* U,
+                                    float shrink, int mode, int64_t* counts) {
+    const int64_t s = blockIdx.y;
+    const int64_t b = seg_begin[s], e = seg_begin[s + 1];
+    const float t = (T[s] == 0xFFFFFFFFu) ? __int_as_float(0x7F800000) : __uint_as_float(T[s]);
+    const float u = mode ? __uint_as_float(U[s]) : 0.f;
+    int64_t c = 0;
+    for (int64_t p = b + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < e; p += (int64_t)gridDim.x * blockDim.x) {
+        const float v = lb[p];
+        const bool keep = mode == 0 ? (v <= t) : (v > t && v * shrink <= u);
+        c += keep;
+    }
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(reinterpret_cast<unsigned long long*>(&counts[s]), (unsigned long long)c);
+}
+
+__global__ void filter_scatter_kernel(const int64_t* seg_begin, const float* lb, const uint32_t* T, const uint32_t* U,
+                                      float shrink, int mode, const int64_t* out_begin, unsigned long long* cursor,
+                                      const float* const* pair_b_in, const float** pair_b_out, int64_t* slot_out) {
+    const int64_t s = blockIdx.y;
+    const int64_t b = seg_begin[s], e = seg_begin[s + 1];
+    const float t = (T[s] == 0xFFFFFFFFu) ? __int_as_float(0x7F800000) : __uint_as_float(T[s]);
+    const float u = mode ? __uint_as_float(U[s]) : 0.f;
+    for (int64_t p = b + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < e; p += (int64_t)gridDim.x * blockDim.x) {
+        const float v = lb[p];
+        const bool keep = mode == 0 ? (v <= t) : (v > t && v * shrink <= u);
+        if (keep) {
+            const int64_t pos = out_begin[s] + (int64_t)atomicAdd(&cursor[s], 1ull);
+            pair_b_out[pos] = pair_b_in[p];
+            slot_out[pos] = p;
+        }
+    }
+}
+
+__global__ void topk_keys_kernel(const float* dist, const uint32_t* rows, int64_t n, const int64_t* n_dev,
+                                 uint64_t* keys) {
+    if (n_dev) n = *n_dev;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        keys[i] = ((uint64_t)__float_as_uint(dist[i]) << 32) | rows[i];
+}
+
+// Final top-k of one segment: the keys <= the k-th smallest, sorted, as (id, dist).
+__global__ void __launch_bounds__(1024) topk_output_kernel(TopkOut o, const uint64_t* keys, const int64_t* seg_begin,
+                                                           const uint64_t* kth, int k) {
+    __shared__ uint64_t buf[kMaxTopK];
+    __shared__ int cnt;
+    const int64_t s = blockIdx.x;
+    if (o.nseg_dev && s >= *o.nseg_dev) return;
+    const int64_t b = seg_begin[s], e = seg_begin[s + 1];
+    const uint64_t lim = kth[s];
+    if (threadIdx.x == 0) cnt = 0;
+    for (int i = threadIdx.x; i < kMaxTopK; i += blockDim.x) buf[i] = ~0ull;
+    __syncthreads();
+    for (int64_t p = b + threadIdx.x; p < e; p += blockDim.x) {
+        const uint64_t v = keys[p];
+        if (v <= lim) {
+            const int at = atomicAdd(&cnt, 1);
+            if (at < kMaxTopK) buf[at] = v;
+        }
+    }
+    __syncthreads();
+    int n2 = 1;
+    while (n2 < k) n2 <<= 1;
+    for (int kk = 2; kk <= n2; kk <<= 1) {
+        for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+            for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+                const int l = i ^ jj;
+                if (l > i) {
+                    const uint64_t u = buf[i], v = buf[l];
+                    const bool up = (i & kk) == 0;
+                    if ((u > v) == up) {
+                        buf[i] = v;
+                        buf[l] = u;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    const int64_t* gid = o.seg_gid ? o.seg_gid[s] : o.gid;
+    const int64_t qp = o.qpos[s];
+    const int64_t out0 = qp * (int64_t)k;
+    for (int t = threadIdx.x; t < k; t += blockDim.x) {
+        const uint64_t v = buf[t];
+        const uint32_t dbits = (uint32_t)(v >> 32);
+        const bool real = (v != ~0ull) && dbits < 0x7F800000u;
+        o.ids[out0 + t] = real ? gid[(uint32_t)v] : -1;
+        o.dists[out0 + t] = real ? __uint_as_float(dbits) : __uint_as_float(0x7F800000u);
+    }
+    if (o.which && threadIdx.x == 0) o.which[qp] = o.seg_which[s];
 }
 
 // ------------------------------------------------- DTW tiling autotuner
@@ -430,9 +586,9 @@ cudaError_t launch_lb_keogh(const PairSet& ps, const float* upper, const float* 
     int64_t gx = (ps.max_seg_pairs + kLbWarps - 1) / kLbWarps;
     if (gx > 65535) gx = 65535;
     const size_t smem = 2 * (size_t)m * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(lb_keogh_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ensure_dynamic_smem((const void*)lb_keogh_kernel, smem);
     if (e != cudaSuccess) return e;
-    dim3 grid((unsigned)gx, (unsigned)std::min<int64_t>(ps.nseg, 65535));
+    dim3 grid((unsigned)gx, (unsigned)(ps.grid_y ? ps.grid_y : std::min<int64_t>(ps.nseg, 65535)));
     lb_keogh_kernel<<<grid, kLbWarps * 32, smem, st>>>(ps, upper, lower, m, out);
     note_launch();
     return cudaGetLastError();
@@ -448,6 +604,55 @@ cudaError_t launch_dtw_plan(const PairSet& ps, int m, int rb, const DtwPlan& pl,
     if (pl.S == 14) return launch_wave<14>(ps, m, rb, pl.G, pl.pmask, out, st);
     if (pl.S == 26) return launch_wave<26>(ps, m, rb, pl.G, pl.pmask, out, st);
     return cudaErrorNotSupported;
+}
+
+cudaError_t launch_fill_f32(float* p, int64_t n, const int64_t* n_dev, float v, cudaStream_t st) {
+    if (n <= 0 && !n_dev) return cudaSuccess;
+    const int64_t g = std::max<int64_t>(1, std::min<int64_t>((std::max<int64_t>(n, 1) + 255) / 256, 8192));
+    fill_f32_kernel<<<(unsigned)g, 256, 0, st>>>(p, n, n_dev, v);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan(const int64_t* counts, int64_t n, int64_t* out, int64_t cap, unsigned long long* total_out,
+                        unsigned long long* overflow, cudaStream_t st) {
+    scan_kernel<<<1, 1024, 0, st>>>(counts, n, out, cap, total_out, overflow);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_filter(const FilterArgs& f, cudaStream_t st) {
+    if (f.nseg <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(f.count, 0, f.nseg * sizeof(int64_t), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(f.cursor, 0, f.nseg * sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    const int64_t gx = std::max<int64_t>(1, std::min<int64_t>((f.max_seg + 255) / 256, 1024));
+    const dim3 grid((unsigned)gx, (unsigned)f.nseg);
+    filter_count_kernel<<<grid, 256, 0, st>>>(f.seg_begin, f.lb, f.T, f.U, f.shrink, f.mode, f.count);
+    note_launch();
+    scan_kernel<<<1, 1024, 0, st>>>(f.count, f.nseg, f.begin, 0, f.total, nullptr);
+    note_launch();
+    filter_scatter_kernel<<<grid, 256, 0, st>>>(f.seg_begin, f.lb, f.T, f.U, f.shrink, f.mode, f.begin, f.cursor,
+                                                f.pair_b, f.pair_b_out, f.slot_out);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_topk_keys(const float* dist, const uint32_t* rows, int64_t n, const int64_t* n_dev, uint64_t* keys,
+                             cudaStream_t st) {
+    if (n <= 0 && !n_dev) return cudaSuccess;
+    const int64_t g = std::max<int64_t>(1, std::min<int64_t>((std::max<int64_t>(n, 1) + 255) / 256, 8192));
+    topk_keys_kernel<<<(unsigned)g, 256, 0, st>>>(dist, rows, n, n_dev, keys);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_topk_output(const TopkOut& o, const uint64_t* keys, const int64_t* seg_begin, const uint64_t* kth,
+                               int64_t nseg, int k, cudaStream_t st) {
+    if (nseg <= 0) return cudaSuccess;
+    topk_output_kernel<<<(unsigned)nseg, 1024, 0, st>>>(o, keys, seg_begin, kth, k);
+    note_launch();
+    return cudaGetLastError();
 }
 
 // Time every feasible slot count S (lanes per pair G = ceil((2 rb + 2) / S))

@@ -20,6 +20,10 @@ namespace ssh {
 
 void set_error(const char* fmt, ...);
 ssh_status cuda_status(cudaError_t e, const char* what);
+// set_error(fmt, ...) and return s
+ssh_status fail_status(ssh_status s, const char* fmt, ...);
+// Make the index's device current.
+ssh_status check_device(const ssh_index* idx);
 
 #define SSH_TRY(expr)                       \
     do {                                    \
@@ -166,6 +170,7 @@ struct PairSet {
     // (the launch then strides over them with its fixed grid). NULL: all nseg.
     const int64_t* seg_range = nullptr;
     int64_t env_stride = 0;     // floats between segments' envelopes (0: m)
+    int64_t grid_y = 0;         // blocks striding over the segments (0: one per segment)
 };
 
 cudaError_t launch_envelope(const float* const* seg_a, int64_t nseg, int m, int rb, float* upper, float* lower,
@@ -182,6 +187,55 @@ DtwPlan dtw_plan(int m, int rb);
 DtwPlan dtw_tuned_plan(int m, int rb, cudaStream_t st);
 cudaError_t launch_dtw(const PairSet& ps, int m, int rb, float* out, cudaStream_t st);
 cudaError_t launch_dtw_plan(const PairSet& ps, int m, int rb, const DtwPlan& pl, float* out, cudaStream_t st);
+
+// Raise (never lower) a kernel's dynamic shared memory limit on the current
+// device to `bytes`: a launch captured in a CUDA graph keeps its size, so the
+// limit must not drop below it later.
+cudaError_t ensure_dynamic_smem(const void* fn, size_t bytes);
+
+// Candidate filter of the rerank (one segment per query): mode 0 keeps the
+// pairs with lb <= T[s] (the seeds), mode 1 those with T[s] < lb and
+// lb * shrink <= U[s] (the survivors). Writes the kept pairs' candidate
+// pointers and original slots segment by segment, begin[0 .. nseg] the
+// offsets and *total their number. Grid: max_seg bounds a segment's size.
+struct FilterArgs {
+    const int64_t* seg_begin;
+    int64_t nseg, max_seg;
+    const float* lb;
+    const uint32_t *T, *U;
+    float shrink;
+    int mode;
+    int64_t* count;                 // [nseg] scratch
+    unsigned long long* cursor;     // [nseg] scratch
+    int64_t* begin;                 // [nseg + 1] out
+    unsigned long long* total;      // [1] out (may be NULL)
+    const float* const* pair_b;
+    const float** pair_b_out;
+    int64_t* slot_out;
+};
+cudaError_t launch_filter(const FilterArgs& f, cudaStream_t st);
+cudaError_t launch_fill_f32(float* p, int64_t n, const int64_t* n_dev, float v, cudaStream_t st);
+// Exclusive prefix sums (one block); cap > 0: a total above cap zeroes every
+// offset and sets *overflow.
+cudaError_t launch_scan(const int64_t* counts, int64_t n, int64_t* out, int64_t cap, unsigned long long* total_out,
+                        unsigned long long* overflow, cudaStream_t st);
+cudaError_t launch_topk_keys(const float* dist, const uint32_t* rows, int64_t n, const int64_t* n_dev, uint64_t* keys,
+                             cudaStream_t st);
+// Where the top-k of segment s goes: ids/dists rows qpos[s] (k each), the id of
+// row r is gid[r] (or seg_gid[s][r]); which[qpos[s]] = seg_which[s] when which
+// is given; segments at or past *nseg_dev (when given) are skipped.
+struct TopkOut {
+    int64_t* ids;
+    float* dists;
+    const int64_t* qpos;
+    const int64_t* gid;
+    const int64_t* const* seg_gid;
+    int32_t* which;
+    const int32_t* seg_which;
+    const int64_t* nseg_dev;
+};
+cudaError_t launch_topk_output(const TopkOut& o, const uint64_t* keys, const int64_t* seg_begin, const uint64_t* kth,
+                               int64_t nseg, int k, cudaStream_t st);
 
 // k-th smallest key of each segment (keys read through `keys`, segment s is
 // [seg_begin[s], seg_begin[s+1])); kth_out[s] = that key, or all-ones if the
@@ -258,4 +312,6 @@ struct ssh_index {
     // queries, cstream copies host series in chunks ahead of the hashing
     cudaStream_t hstream = nullptr, cstream = nullptr;
     cudaEvent_t cevent = nullptr;
+    unsigned long long* h_pinned = nullptr;  // small pinned host buffer for per-call device counters
+    uint64_t version = 0;                    // bumped by every add and clear (batch plans check it)
 };

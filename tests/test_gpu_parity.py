@@ -411,3 +411,111 @@ def test_group_query_routes_mixed_lengths_to_per_length_indexes():
     finally:
         for ix in idxs:
             ix.close()
+
+
+# ------------------------------------------------------------- batch plans
+
+def _batch_setup(lens=(128, 256, 512), n=150):
+    dbs = {m: synth.random_walk(n, m, seed=m + 5) for m in lens}
+    cfgs = {m: dict(W=m // 8, delta=3, n=15, K=4, L=25, band=0.05, seed=0) for m in lens}
+    idxs = []
+    for m in lens:
+        ix = _index(cfgs[m])
+        ix.add(dbs[m])
+        idxs.append(ix)
+    return dbs, cfgs, idxs
+
+
+def _mixed_queries(dbs, lens, nq, seed):
+    rng = np.random.default_rng(seed)
+    qs, qlens = [], []
+    for t in range(nq):
+        m = lens[int(rng.integers(0, len(lens)))]
+        q, _ = synth.perturbed_queries(dbs[m], 1, seed=seed * 1000 + t)
+        qs.append(q[0])
+        qlens.append(m)
+    return qs, np.array(qlens, np.int32)
+
+
+def _run_batch(bt, qs, qlens, k):
+    d_q = torch.from_numpy(np.concatenate(qs)).cuda()
+    ids = torch.full((len(qs), k), -7, dtype=torch.int64, device="cuda")
+    dd = torch.zeros((len(qs), k), dtype=torch.float32, device="cuda")
+    which = torch.full((len(qs),), -1, dtype=torch.int32, device="cuda")
+    bt.query(d_q, qlens, ids, dd, which)
+    torch.cuda.synchronize()
+    return ids.cpu().numpy(), dd.cpu().numpy(), which.cpu().numpy()
+
+
+def _run_group(idxs, qs, qlens, k):
+    b = _binding()
+    d_q = torch.from_numpy(np.concatenate(qs)).cuda()
+    ids = torch.empty((len(qs), k), dtype=torch.int64, device="cuda")
+    dd = torch.empty((len(qs), k), dtype=torch.float32, device="cuda")
+    which = torch.full((len(qs),), -1, dtype=torch.int32, device="cuda")
+    b.ssh_group_query_device([ix.handle for ix in idxs], d_q, qlens, k, ids, dd, which)
+    torch.cuda.synchronize()
+    return ids.cpu().numpy(), dd.cpu().numpy(), which.cpu().numpy()
+
+
+def test_batch_plan_matches_oracle_and_replays_graph():
+    """Mixed-length batches through one plan: the first runs directly, later ones replay the captured graph."""
+    b = _binding()
+    lens = (128, 256, 512)
+    dbs, cfgs, idxs = _batch_setup(lens)
+    try:
+        refs = {}
+        for m in lens:
+            refs[m] = oracle.OracleIndex(**cfgs[m])
+            refs[m].add(dbs[m])
+        k = 5
+        with b.SSHBatch(idxs, max_queries=64, k=k) as bt:
+            for rep in range(3):  # rep 0 runs directly, reps 1-2 replay the graph
+                qs, qlens = _mixed_queries(dbs, lens, 20 + 7 * rep, seed=rep + 1)
+                ids, dd, which = _run_batch(bt, qs, qlens, k)
+                for i, (q, m) in enumerate(zip(qs, qlens)):
+                    assert which[i] == lens.index(m)
+                    oi, od = refs[m].query(q, k)
+                    assert_topk_match(q, ids[i], dd[i], oi, od, lambda j: dbs[m][j], oracle.band_radius(0.05, m))
+                # the same kernels answer the per-length group path: identical results
+                gi, gd, gw = _run_group(idxs, qs, qlens, k)
+                assert np.array_equal(ids, gi) and np.array_equal(dd, gd) and np.array_equal(which, gw)
+            st = bt.stats()
+            assert st["graph_kernels"] > 10
+            assert st["pairs"] > 0 and 0 < st["dtw"] <= st["pairs"]
+    finally:
+        for ix in idxs:
+            ix.close()
+
+
+def test_batch_plan_grows_pair_buffers_and_follows_adds():
+    b = _binding()
+    lens = (128, 256)
+    dbs, cfgs, idxs = _batch_setup(lens, n=200)
+    try:
+        k = 4
+        with b.SSHBatch(idxs, max_queries=16, k=k, max_pairs=8) as bt:
+            qs, qlens = _mixed_queries(dbs, lens, 12, seed=9)
+            ids, dd, which = _run_batch(bt, qs, qlens, k)
+            gi, gd, gw = _run_group(idxs, qs, qlens, k)
+            assert np.array_equal(ids, gi) and np.array_equal(dd, gd)
+            assert bt.stats()["pair_capacity"] > 8  # grown past the first capacity
+            # an add to one index: the next batch sees the new rows (the plan is rebuilt)
+            more = synth.random_walk(50, 256, seed=77)
+            first = idxs[1].add(more)
+            q = more[3:4] + np.float32(0.0)
+            ids2, dd2, _ = _run_batch(bt, [q[0]], np.array([256], np.int32), k)
+            assert ids2[0, 0] == first + 3 and dd2[0, 0] == 0.0
+            # errors
+            d_q = torch.zeros((17, 128), device="cuda")
+            bad_ids = torch.empty((17, k), dtype=torch.int64, device="cuda")
+            bad_d = torch.empty((17, k), dtype=torch.float32, device="cuda")
+            with pytest.raises(b.SSHError) as e:
+                bt.query(d_q, np.full(17, 128, np.int32), bad_ids, bad_d)
+            assert e.value.status == b.SSH_EINVAL
+            with pytest.raises(b.SSHError) as e:
+                bt.query(d_q[:1, :100].contiguous(), np.array([100], np.int32), bad_ids[:1], bad_d[:1])
+            assert e.value.status == b.SSH_ELENGTH
+    finally:
+        for ix in idxs:
+            ix.close()
