@@ -297,6 +297,141 @@ def recall(ids, exact):
     return float(np.mean(r))
 
 
+# Parameter sets tried for the recall operating point, from the most to the
+# least selective; the operating point is the fastest one with recall@10 >= 0.9.
+OPERATING_POINTS = [
+    (80, 3, 15, 4, 25), (40, 3, 15, 4, 25), (40, 3, 12, 4, 25), (40, 3, 10, 4, 25),
+    (40, 3, 8, 4, 25), (80, 3, 10, 2, 25), (80, 3, 12, 1, 25), (80, 3, 10, 1, 25),
+]
+
+
+def recall_operating_point(binding, torch, d_sub, d_q, exact, w, k):
+    """recall@10, candidate fraction and queries/s of each parameter set on the recall subset."""
+    n_sub, m, nq = d_sub.shape[0], w["m"], d_q.shape[0]
+    points = []
+    for (W, delta, n, K, L) in OPERATING_POINTS:
+        with binding.SSHIndex(W, delta, n, K, L, w["band"], w["seed"]) as ix:
+            ix.add_device(d_sub)
+            ids = torch.empty((nq, k), dtype=torch.int64, device=d_q.device)
+            dd = torch.empty((nq, k), dtype=torch.float32, device=d_q.device)
+            ix.query_device(d_q, k, ids, dd)  # warm-up (and the DTW tiling's timing)
+            torch.cuda.synchronize()
+            ix.reset_stats()
+            best = float("inf")
+            for _ in range(3):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                ix.query_device(d_q, k, ids, dd)
+                e1.record()
+                e1.synchronize()
+                best = min(best, e0.elapsed_time(e1))
+            st = ix.stats()
+            r10 = recall(ids.cpu().numpy(), exact)
+            one_i = torch.empty((1, k), dtype=torch.int64, device=d_q.device)
+            one_d = torch.empty((1, k), dtype=torch.float32, device=d_q.device)
+            lat = []
+            for i in range(min(nq, 20)):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                ix.query_device(d_q[i:i + 1], k, one_i, one_d)
+                e1.record()
+                e1.synchronize()
+                lat.append(e0.elapsed_time(e1))
+        points.append({"W": W, "delta": delta, "n": n, "K": K, "L": L, "recall_at_10": r10,
+                       "candidate_fraction": st["candidates"] / (3 * nq) / n_sub,
+                       "queries_per_s": nq / (best / 1000.0),
+                       "plain_gpu_path_queries_per_s": 1000.0 / statistics.mean(lat)})
+    ok = [p for p in points if p["recall_at_10"] >= 0.9]
+    chosen = max(ok, key=lambda p: p["queries_per_s"]) if ok else None
+    return {"subset": n_sub, "queries": nq, "points": points, "chosen": chosen}
+
+
+BATCH_LENGTHS = (128, 256, 512, 1024, 2048)
+
+
+def batched_measurement(args, binding, torch, dev):
+    """Mixed-length queries over per-length indexes (W = m/8) through one batch plan (a CUDA graph),
+    against the plain path of one query per call; recall@10 against exact DTW on a sample."""
+    small = args.small
+    N4, nq4, k = (2000, 256, 10) if small else (200_000, 4096, 10)
+    rng = np.random.default_rng(4)
+    t0 = time.perf_counter()
+    hosts = {m: synth.random_walk(N4, m, seed=40 + m) for m in BATCH_LENGTHS}
+    data = {m: torch.from_numpy(hosts[m]).to(dev) for m in BATCH_LENGTHS}
+    qlens = rng.choice(np.array(BATCH_LENGTHS, np.int32), size=nq4)
+    qs = []
+    for i, m in enumerate(qlens):
+        q, _ = synth.perturbed_queries(hosts[m], 1, seed=1000 + i)
+        qs.append(q[0])
+    d_q = torch.from_numpy(np.concatenate(qs)).to(dev)
+    gen_s = time.perf_counter() - t0
+    idxs = [binding.SSHIndex(m // 8, 3, 15, 4, 25, 0.05, 0) for m in BATCH_LENGTHS]
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for ix, m in zip(idxs, BATCH_LENGTHS):
+        ix.add_device(data[m], borrow=True)
+    e1.record()
+    e1.synchronize()
+    build_ms = e0.elapsed_time(e1)
+    ids = torch.empty((nq4, k), dtype=torch.int64, device=dev)
+    dd = torch.empty((nq4, k), dtype=torch.float32, device=dev)
+    which = torch.empty((nq4,), dtype=torch.int32, device=dev)
+    out = {"workload": "5 per-length indexes x %d random walks, m in %s, W = m/8, delta=3, n=15, K=4, L=25, "
+                       "band 5%%; %d queries of uniformly mixed lengths, top-%d" % (N4, list(BATCH_LENGTHS), nq4, k),
+           "index_build_series_per_s": 5 * N4 / (build_ms / 1000.0)}
+    with binding.SSHBatch(idxs, max_queries=nq4, k=k) as bt:
+        for _ in range(2):  # the first batch runs directly and captures the graph
+            bt.query(d_q, qlens, ids, dd, which)
+        torch.cuda.synchronize()
+        steps = max(3, min(args.steps, 5))
+        e0.record()
+        for _ in range(steps):
+            bt.query(d_q, qlens, ids, dd, which)
+        e1.record()
+        e1.synchronize()
+        batch_ms = e0.elapsed_time(e1) / steps
+        st = bt.stats()
+    out.update({"batched_queries_per_s": nq4 / (batch_ms / 1000.0), "ms_per_batch": batch_ms,
+                "graph_kernels": st["graph_kernels"], "candidates_per_query": st["pairs"] / nq4,
+                "dtw_per_query": st["dtw"] / nq4})
+    # plain path: one query per call on the query's own index
+    n_plain = min(nq4, 256)
+    one_i = torch.empty((1, k), dtype=torch.int64, device=dev)
+    one_d = torch.empty((1, k), dtype=torch.float32, device=dev)
+    offs = np.concatenate([[0], np.cumsum(qlens)])
+    for i in range(min(n_plain, 8)):  # warm-up
+        m = int(qlens[i])
+        idxs[BATCH_LENGTHS.index(m)].query_device(d_q[offs[i]:offs[i] + m].view(1, m), k, one_i, one_d)
+    torch.cuda.synchronize()
+    e0.record()
+    for i in range(n_plain):
+        m = int(qlens[i])
+        idxs[BATCH_LENGTHS.index(m)].query_device(d_q[offs[i]:offs[i] + m].view(1, m), k, one_i, one_d)
+    e1.record()
+    e1.synchronize()
+    out["plain_gpu_path_queries_per_s"] = n_plain / (e0.elapsed_time(e1) / 1000.0)
+    out["plain_sample"] = n_plain
+    # recall@10 against exact DTW over the whole per-length collection, a few queries per length
+    res = ids.cpu().numpy()
+    rec = []
+    per_len = 2 if small else 4
+    for m in BATCH_LENGTHS:
+        sel = [i for i in range(nq4) if qlens[i] == m][:per_len]
+        if not sel:
+            continue
+        d_sel = torch.stack([d_q[offs[i]:offs[i] + m] for i in sel]).contiguous()
+        rb = min(int(math.floor(np.float32(0.05) * np.float64(m))), m - 1)
+        ex = exact_topk_gpu(binding, torch, d_sel, data[m], np.arange(N4, dtype=np.int64), m, rb, k)
+        rec.append(recall(res[sel], ex))
+    out["recall_at_10"] = float(np.mean(rec)) if rec else None
+    out["recall_queries"] = per_len * len(BATCH_LENGTHS)
+    out["setup_s"] = gen_s
+    for ix in idxs:
+        ix.close()
+    return out
+
+
 def run_gpu(args, w):
     import torch
 
@@ -394,6 +529,8 @@ def run_gpu(args, w):
         exact_sub = exact_topk_gpu(binding, torch, d_q, d_sub.contiguous(), subset_rows, m, rb, k)
         extra["recall_at_10"] = recall(s_ids, exact_sub)
         extra["recall_at_1"] = float(np.mean([s_ids[i, 0] == exact_sub[i, 0] for i in range(nq)]))
+        extra["recall_operating_point"] = recall_operating_point(binding, torch, d_sub.contiguous(), d_q,
+                                                                 exact_sub, w, k)
         if not args.fast:
             n_full = min(nq, 20)
             exact_full = exact_topk_gpu(binding, torch, d_q[:n_full].contiguous(), d_db,
@@ -480,6 +617,8 @@ def run_gpu(args, w):
         "setup_s": {"inputs": gen_s},
         **extra,
     }
+    if rank == 0 and world == 1 and not args.no_batched:
+        line["batched"] = batched_measurement(args, binding, torch, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         n_s = 10000 if not args.small else 300
         r = oracle_sample(w, n_s, 10 if not args.small else 3)
@@ -502,6 +641,7 @@ def main():
     ap.add_argument("--fast", action="store_true", help="skip the full-database recall")
     ap.add_argument("--no-recall", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the mixed-length batch-plan measurement")
     args = ap.parse_args()
     w = TINY if args.small else SCALE
     if args.impl == "reference":

@@ -580,7 +580,7 @@ struct SketchShape {
     int W, delta, R;
 };
 const SketchShape kSketchShapes[] = {
-    {80, 3, 5},  {32, 3, 2},  {120, 5, 6}, {16, 3, 2}, {32, 3, 3}, {64, 3, 5}, {128, 3, 10},
+    {80, 3, 5},  {32, 3, 2},  {120, 5, 6}, {16, 3, 2}, {32, 3, 3}, {64, 3, 5}, {128, 3, 10}, {256, 3, 19},
 };
 
 bool sketch_shape_ok(const SketchShape& s, const HashArgs& a) {
@@ -646,6 +646,7 @@ cudaError_t hash_fast_sketch(const HashArgs& a, const FastHashBuffers& b, cudaSt
         SSH_SKETCH_CASE(32, 3, 3)
         SSH_SKETCH_CASE(64, 3, 5)
         SSH_SKETCH_CASE(128, 3, 10)
+        SSH_SKETCH_CASE(256, 3, 19)
 #undef SSH_SKETCH_CASE
     }
     return cudaErrorInvalidValue;
