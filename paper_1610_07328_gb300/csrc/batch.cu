@@ -445,6 +445,10 @@ ssh_status enqueue_pipeline(ssh_batch* b) {
         for (int c = 0; c < C; ++c) {
             const ssh_batch::HostClass& hc = b->cls[c];
             PairSet ps{b->fbegin, Q, d.q_ptr, b->fb, b->fslot, kDtwGridPairs, d.cls_begin + c, 0, kGridSegs};
+            if (mode == 1) {  // survivors: stop at the bound U of the seeds' k-th distance
+                ps.abandon = b->U;
+                ps.abandon_shrink = shrink;
+            }
             SSH_CUDA(launch_dtw_plan(ps, hc.m, hc.rb, hc.plan, b->dist, st));
         }
     }

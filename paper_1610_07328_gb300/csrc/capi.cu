@@ -641,6 +641,10 @@ ssh_status query_group(ssh_index* idx, SubIndex& s, const std::vector<const floa
             if (e == cudaSuccess) e = launch_filter(f, st);
             // every filtered segment is no longer than its candidate segment: size the DTW grid by max_c
             PairSet sub{fbegin, nq, d_qptr, fb, fslot, max_c};
+            if (mode == 1) {  // survivors: stop at the bound U of the seeds' k-th distance
+                sub.abandon = U;
+                sub.abandon_shrink = shrink;
+            }
             if (e == cudaSuccess) {
                 {
                     TimedRegion tr(idx, st, "query.dtw", 0.0);

@@ -184,21 +184,12 @@ __global__ void __launch_bounds__(256) dtw_wave_kernel(PairSet ps, int m, int rb
     constexpr int H = S / 2;
     constexpr int U = H + 1;
     extern __shared__ float q_s[];
-    const int warps = blockDim.x >> 5;
+    __shared__ unsigned long long s_next;  // next unclaimed pair of this block's share
+    const int lane = threadIdx.x & 31;
     const int gpw = 32 / G;
-    const int64_t per_cta = (int64_t)warps * gpw;
-    const int64_t s_lo = ps.seg_range ? ps.seg_range[0] : 0, s_hi = ps.seg_range ? ps.seg_range[1] : ps.nseg;
-    for (int64_t seg = s_lo + blockIdx.y; seg < s_hi; seg += gridDim.y) {
-    const int64_t sb = ps.seg_begin[seg], se = ps.seg_begin[seg + 1];
-    if (sb + (int64_t)blockIdx.x * per_cta >= se) continue;  // uniform over the block
-    const float* qg = ps.seg_a[seg];
-    __syncthreads();  // the previous segment's query is no longer read
-    for (int i = threadIdx.x; i < m; i += blockDim.x) q_s[i] = qg[i];
-    __syncthreads();
-
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int grp = lane / G, g = lane - grp * G;
     const bool lane_in_group = grp < gpw;
+    const unsigned gbits = (G == 32) ? 0xFFFFFFFFu : (((1u << G) - 1u) << (grp * G));
     const int PAD = G * S - (2 * rb + 1);
     const int gmask = (PAD - 1) / S;
     const float mflag = (g == gmask) ? __int_as_float(0x7F800000) : __int_as_float(0xFF800000);
@@ -212,34 +203,69 @@ __global__ void __launch_bounds__(256) dtw_wave_kernel(PairSet ps, int m, int rb
     // per-lane offsets of the sliding windows: A(s) = s + a_off, B(s) = s + b_off
     const int a_off = -g * H + (PAD - 1) / 2;
     const int b_off = g * H - rb + (1 - PAD) / 2;
-
-    for (int64_t base = sb + (int64_t)blockIdx.x * per_cta; base < se; base += (int64_t)gridDim.x * per_cta) {
-        const int64_t p = base + (int64_t)warp * gpw + grp;
-        const bool valid = lane_in_group && p < se;
-        const float* c = valid ? ps.pair_b[p] : qg;
-
-        float D[S];
-#pragma unroll
-        for (int t = 0; t < S; ++t) D[t] = 0.f;
-        if (g == gmask) D[PMASK] = INF;
-
-        float creg[U], qreg[U];
-        // prefill logical cw[t] = c[A(s0) + 1 - t] (t >= 1) and qw[a] = q[B(s0) + a] (a <= H - 2)
-        // with the register map of unrolled step u = 0: cw[t] -> creg[t % U], qw[a] -> qreg[a % U]
-#pragma unroll
-        for (int t = 1; t < U; ++t) {
-            const int ci = s0 + a_off + 1 - t;
-            creg[t] = (ci >= 0 && ci < m) ? __ldg(c + ci) : kPad;
+    const int64_t s_lo = ps.seg_range ? ps.seg_range[0] : 0, s_hi = ps.seg_range ? ps.seg_range[1] : ps.nseg;
+    for (int64_t seg = s_lo + blockIdx.y; seg < s_hi; seg += gridDim.y) {
+        const int64_t sb = ps.seg_begin[seg], se = ps.seg_begin[seg + 1];
+        // this block's share of the segment (at least one pair per lane group, so
+        // short segments fill whole blocks); its lane groups claim pairs from it one by one
+        const int64_t per_cta = (int64_t)(blockDim.x >> 5) * gpw;
+        const int64_t share = max(per_cta, (se - sb + gridDim.x - 1) / gridDim.x);
+        const int64_t b0 = sb + (int64_t)blockIdx.x * share;
+        const int64_t b1 = min(se, b0 + share);
+        if (b0 >= b1) continue;  // uniform over the block
+        const float* qg = ps.seg_a[seg];
+        __syncthreads();  // the previous segment's query and counter are no longer used
+        for (int i = threadIdx.x; i < m; i += blockDim.x) q_s[i] = qg[i];
+        if (threadIdx.x == 0) s_next = (unsigned long long)b0;
+        __syncthreads();
+        // early abandoning against the segment's bound (a k-th best distance): the
+        // two waves of a step hold a cell of every warping path, and later cells
+        // only add non-negative costs, so a pair whose band cells all exceed
+        // bound / shrink ends above the bound; it is reported as +inf
+        float bound = INF;
+        if (ps.abandon) {
+            const uint32_t ub = ps.abandon[seg];
+            if (ub != 0xFFFFFFFFu) bound = __uint_as_float(ub);
         }
-#pragma unroll
-        for (int t = 0; t < U; ++t) {
-            const int qi = s0 + b_off + t;
-            qreg[t] = (t < H - 1 && qi >= 0 && qi < m) ? q_s[qi] : kPad;
-        }
-        creg[0] = 0.f;
 
-        for (int blk = 0; blk < nblk; ++blk) {
-            const int sbase = s0 + blk * U;
+        int64_t p = -1;  // the group's pair, -1: none
+        int lblk = 0;    // blocks of U steps the group has done on it
+        const float* c = qg;
+        float D[S], creg[U], qreg[U];
+        bool need = lane_in_group;
+        while (true) {
+            // groups without a pair claim the next one (leader's atomic, shuffled to the group)
+            unsigned long long v = ~0ull;
+            if (need && g == 0) v = atomicAdd(&s_next, 1ull);
+            v = __shfl_sync(kFull, v, lane_in_group ? grp * G : lane);
+            if (need) {
+                p = (v < (unsigned long long)b1) ? (int64_t)v : -1;
+                if (p >= 0) {
+                    c = ps.pair_b[p];
+                    lblk = 0;
+#pragma unroll
+                    for (int t = 0; t < S; ++t) D[t] = 0.f;
+                    if (g == gmask) D[PMASK] = INF;
+                    // prefill logical cw[t] = c[A(s0) + 1 - t] (t >= 1) and qw[a] = q[B(s0) + a]
+                    // (a <= H - 2) with the register map of unrolled step u = 0:
+                    // cw[t] -> creg[t % U], qw[a] -> qreg[a % U]
+#pragma unroll
+                    for (int t = 1; t < U; ++t) {
+                        const int ci = s0 + a_off + 1 - t;
+                        creg[t] = (ci >= 0 && ci < m) ? __ldg(c + ci) : kPad;
+                    }
+#pragma unroll
+                    for (int t = 0; t < U; ++t) {
+                        const int qi = s0 + b_off + t;
+                        qreg[t] = (t < H - 1 && qi >= 0 && qi < m) ? q_s[qi] : kPad;
+                    }
+                    creg[0] = 0.f;
+                } else {
+                    c = qg;  // idle: the steps below run on the query itself and are discarded
+                }
+            }
+            if (!__any_sync(kFull, p >= 0)) break;
+            const int sbase = s0 + lblk * U;
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 const int s = sbase + u;
@@ -275,13 +301,29 @@ __global__ void __launch_bounds__(256) dtw_wave_kernel(PairSet ps, int m, int rb
                 }
                 D[PMASK] = fmaxf(D[PMASK], mflag);
             }
-        }
-        float res = 0.f;
+            ++lblk;
+            bool over = false;
+            if (bound < INF) {  // uniform over the block
+                float lm = INF;
 #pragma unroll
-        for (int t = 0; t < S; ++t)
-            if (t == p_f) res = D[t];
-        if (valid && g == g_f) out[ps.pair_slot ? ps.pair_slot[p] : p] = res;
-    }
+                for (int t = 0; t < S; ++t)
+                    if (g * S + t >= PAD) lm = fminf(lm, D[t]);  // front padding slots are not band cells
+                const unsigned bal = __ballot_sync(kFull, lm * ps.abandon_shrink > bound);
+                over = (bal & gbits) == gbits;
+            }
+            const bool fin = p >= 0 && lblk == nblk;
+            const bool ab = p >= 0 && !fin && over;
+            if (fin || ab) {
+                float res = INF;
+                if (fin) {
+#pragma unroll
+                    for (int t = 0; t < S; ++t)
+                        if (t == p_f) res = D[t];
+                }
+                if (g == g_f) out[ps.pair_slot ? ps.pair_slot[p] : p] = res;
+            }
+            need = lane_in_group && (fin || ab);
+        }
     }
 }
 

@@ -171,6 +171,10 @@ struct PairSet {
     const int64_t* seg_range = nullptr;
     int64_t env_stride = 0;     // floats between segments' envelopes (0: m)
     int64_t grid_y = 0;         // blocks striding over the segments (0: one per segment)
+    // optional [nseg] per-segment bound (float bits; all ones: none): DTW stops a
+    // warp's pairs once all of them certainly exceed it (distance reported +inf)
+    const uint32_t* abandon = nullptr;
+    float abandon_shrink = 1.f; // relative FP32 rounding margin of a path cost (1 - 4 (m + 3) 2^-24)
 };
 
 cudaError_t launch_envelope(const float* const* seg_a, int64_t nseg, int m, int rb, float* upper, float* lower,

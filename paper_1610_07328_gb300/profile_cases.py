@@ -9,6 +9,12 @@
         each (rows of a random-walk table larger than L2) through
         ssh_dtw_device; prints the call time of the fastest repetition.
 
+    python -m paper_1610_07328_gb300.profile_cases batch 50000 1024
+        five per-length indexes (m = 128 .. 2048, W = m/8, delta=3, n=15, K=4,
+        L=25) of 50,000 random walks each and three batches of 1,024 mixed-length
+        queries through one batch plan: the first runs directly, the others
+        replay the captured CUDA graph.
+
 Every input is seeded and synthetic; nothing here is on the library's path.
 """
 from __future__ import annotations
@@ -57,9 +63,35 @@ def _dtw(spec: str, reps: int) -> None:
         print(f"m={m} rb={rb} pairs={100 * cand} call_ms={best:.3f} cells={cells}")
 
 
+def _batch(n: int, nq: int) -> None:
+    import torch
+    from . import binding, synth
+    lens = (128, 256, 512, 1024, 2048)
+    hosts = {m: synth.random_walk(n, m, seed=40 + m) for m in lens}
+    idxs = [binding.SSHIndex(m // 8, 3, 15, 4, 25, 0.05, 0) for m in lens]
+    data = {m: torch.from_numpy(hosts[m]).cuda() for m in lens}
+    for ix, m in zip(idxs, lens):
+        ix.add_device(data[m], borrow=True)
+    rng = np.random.default_rng(4)
+    qlens = rng.choice(np.array(lens, np.int32), size=nq)
+    qs = [synth.perturbed_queries(hosts[m], 1, seed=1000 + i)[0][0] for i, m in enumerate(qlens)]
+    d_q = torch.from_numpy(np.concatenate(qs)).cuda()
+    ids = torch.empty((nq, 10), dtype=torch.int64, device="cuda")
+    dd = torch.empty((nq, 10), dtype=torch.float32, device="cuda")
+    with binding.SSHBatch(idxs, max_queries=nq, k=10) as bt:
+        for _ in range(3):
+            bt.query(d_q, qlens, ids, dd)
+        torch.cuda.synchronize()
+        print("batches done;", bt.stats())
+    for ix in idxs:
+        ix.close()
+
+
 def main(argv: list[str]) -> None:
     if len(argv) >= 2 and argv[0] == "hash":
         _hash(int(argv[1]))
+    elif len(argv) >= 3 and argv[0] == "batch":
+        _batch(int(argv[1]), int(argv[2]))
     elif len(argv) >= 2 and argv[0] == "dtw":
         _dtw(argv[1], int(argv[2]) if len(argv) > 2 else 3)
     else:
