@@ -165,6 +165,55 @@ ssh_status ssh_batch_stats(const ssh_batch* b, int64_t* pairs, int64_t* dtw, int
                            int32_t* graph_kernels);
 void ssh_batch_destroy(ssh_batch* b);
 
+/* ---- serving loop with continuous batching ----
+ *
+ * A server answers queries submitted from any thread while inserts stream in.
+ * One worker thread owns the indexes (callers must not use them while the
+ * server runs) and keeps up to max_slots batch plans ("slots"; as many as fit
+ * while reserve_bytes of device memory stay free, at least one). Whenever a
+ * slot is free and queries wait, it takes up to max_batch of them, copies them
+ * to the device and launches the slot's batch (a replay of its CUDA graph)
+ * without waiting, so batches of several slots run on the GPU at once while
+ * later arrivals queue. Inserts are applied between batches (admission of
+ * queries pauses until the slots drain); the plans follow the grown tables.
+ * A query of a given length gets the same rows whether it is served alone or
+ * in a mix (batching changes neither its candidates nor its DTW).
+ *
+ * ssh_server_submit copies the queries (host, back to back) and returns one
+ * ticket each; arrival_s (may be NULL: now) gives each query's arrival on the
+ * server clock (ssh_server_now, seconds since creation) for latency. SSH_ELENGTH
+ * for a length no index stores. ssh_server_insert copies host series; they are
+ * appended to the index that serves their length (the first storing it, else
+ * the first index) with ids from that index's sequence. ssh_server_wait blocks
+ * until a ticket is done (SSH_ETIMEOUT after timeout_s) and gives its k ids,
+ * distances, handle position and latency in ms; ssh_server_collect takes up to
+ * max_n finished requests in completion order (waiting up to timeout_s for the
+ * first), with ids [n][k], dists [n][k], latency_ms [n] and status [n] (any of
+ * the output arrays may be NULL). ssh_server_flush waits until every submitted
+ * query and insert is done. ssh_server_destroy finishes the queued work first. */
+typedef struct ssh_server ssh_server;
+typedef struct ssh_server_stats {
+    int64_t slots;              /* batch plans admitted at creation */
+    int64_t queries_submitted, queries_done, errors;
+    int64_t batches, max_inflight;
+    double mean_batch;          /* queries per batch */
+    int64_t inserts_submitted, inserts_applied, insert_errors, insert_batches;
+    double insert_latency_ms_sum; /* submit-to-applied time summed over insert calls */
+} ssh_server_stats;
+ssh_status ssh_server_create(ssh_index* const* handles, int nh, int k, int max_batch, int max_slots,
+                             int64_t reserve_bytes, ssh_server** out);
+double ssh_server_now(const ssh_server* s);
+ssh_status ssh_server_submit(ssh_server* s, const float* queries, const int32_t* lengths, int64_t n,
+                             const double* arrival_s, int64_t* tickets);
+ssh_status ssh_server_insert(ssh_server* s, const float* series, const int32_t* lengths, int64_t count);
+ssh_status ssh_server_wait(ssh_server* s, int64_t ticket, double timeout_s, int64_t* ids, float* dists,
+                           int32_t* which, double* latency_ms);
+ssh_status ssh_server_collect(ssh_server* s, int64_t max_n, double timeout_s, int64_t* tickets, int64_t* ids,
+                              float* dists, double* latency_ms, int32_t* status, int64_t* n_out);
+ssh_status ssh_server_flush(ssh_server* s, double timeout_s);
+ssh_status ssh_server_get_stats(ssh_server* s, ssh_server_stats* out);
+void ssh_server_destroy(ssh_server* s);
+
 /* Options. SSH_OPT_LB_PRUNE (default 1): LB_Keogh pruning before DTW in the
  * rerank; 0 computes DTW for every candidate (same results, more work).
  * SSH_OPT_KERNEL_TIMING (default 0): record CUDA events around each kernel

@@ -46,6 +46,17 @@ class ssh_kernel_time(ctypes.Structure):
                 ("total_ms", ctypes.c_double), ("units", ctypes.c_double)]
 
 
+class ssh_server_stats(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int64), ("queries_submitted", ctypes.c_int64), ("queries_done", ctypes.c_int64),
+                ("errors", ctypes.c_int64), ("batches", ctypes.c_int64), ("max_inflight", ctypes.c_int64),
+                ("mean_batch", ctypes.c_double), ("inserts_submitted", ctypes.c_int64),
+                ("inserts_applied", ctypes.c_int64), ("insert_errors", ctypes.c_int64),
+                ("insert_batches", ctypes.c_int64), ("insert_latency_ms_sum", ctypes.c_double)]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
 _P = ctypes.c_void_p
 _I64P = ctypes.POINTER(ctypes.c_int64)
 
@@ -67,6 +78,16 @@ _SIGS = {
     "ssh_batch_query": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, _P, _P, _P, _P]),
     "ssh_batch_stats": (ctypes.c_int, [_P, _I64P, _I64P, _I64P, ctypes.POINTER(ctypes.c_int32)]),
     "ssh_batch_destroy": (None, [_P]),
+    "ssh_server_create": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int64,
+                                         ctypes.POINTER(_P)]),
+    "ssh_server_now": (ctypes.c_double, [_P]),
+    "ssh_server_submit": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, _P, _P]),
+    "ssh_server_insert": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64]),
+    "ssh_server_wait": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_double, _P, _P, _P, _P]),
+    "ssh_server_collect": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_double, _P, _P, _P, _P, _P, _P]),
+    "ssh_server_flush": (ctypes.c_int, [_P, ctypes.c_double]),
+    "ssh_server_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(ssh_server_stats)]),
+    "ssh_server_destroy": (None, [_P]),
     "ssh_set_option": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int64]),
     "ssh_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(ssh_stats)]),
     "ssh_reset_stats": (ctypes.c_int, [_P]),
@@ -245,6 +266,83 @@ class SSHBatch:
     def close(self):
         if self.handle:
             ssh_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class SSHServer:
+    """Owning wrapper around an ssh_server (serving loop with continuous batching)."""
+
+    def __init__(self, indexes, k: int, max_batch: int = 256, max_slots: int = 4, reserve_bytes: int = 1 << 30):
+        self.k = k
+        self.indexes = list(indexes)  # kept alive for the server's lifetime
+        arr = (ctypes.c_void_p * len(self.indexes))(*[ix.handle.value if isinstance(ix.handle, ctypes.c_void_p)
+                                                       else ix.handle for ix in self.indexes])
+        out = _P()
+        _check(load().ssh_server_create(ctypes.cast(arr, ctypes.c_void_p), len(self.indexes), k, max_batch, max_slots,
+                                        reserve_bytes, ctypes.byref(out)))
+        self.handle = out
+
+    def now(self) -> float:
+        return load().ssh_server_now(self.handle)
+
+    def submit(self, queries: np.ndarray, lengths: np.ndarray, arrival_s: np.ndarray | None = None) -> np.ndarray:
+        q = np.ascontiguousarray(queries, dtype=np.float32).reshape(-1)
+        ln = np.ascontiguousarray(lengths, dtype=np.int32)
+        tickets = np.zeros(len(ln), np.int64)
+        arr = None if arrival_s is None else np.ascontiguousarray(arrival_s, dtype=np.float64)
+        _check(load().ssh_server_submit(self.handle, _host_ptr(q), _host_ptr(ln), len(ln),
+                                        None if arr is None else _host_ptr(arr), _host_ptr(tickets)))
+        return tickets
+
+    def insert(self, series: np.ndarray, lengths: np.ndarray) -> None:
+        x = np.ascontiguousarray(series, dtype=np.float32).reshape(-1)
+        ln = np.ascontiguousarray(lengths, dtype=np.int32)
+        _check(load().ssh_server_insert(self.handle, _host_ptr(x), _host_ptr(ln), len(ln)))
+
+    def wait(self, ticket: int, timeout_s: float = 10.0):
+        ids = np.zeros(self.k, np.int64)
+        dists = np.zeros(self.k, np.float32)
+        which = ctypes.c_int32()
+        lat = ctypes.c_double()
+        _check(load().ssh_server_wait(self.handle, int(ticket), timeout_s, _host_ptr(ids), _host_ptr(dists),
+                                      ctypes.byref(which), ctypes.byref(lat)))
+        return ids, dists, which.value, lat.value
+
+    def collect(self, max_n: int = 4096, timeout_s: float = 0.01):
+        tickets = np.zeros(max_n, np.int64)
+        ids = np.zeros((max_n, self.k), np.int64)
+        dists = np.zeros((max_n, self.k), np.float32)
+        lat = np.zeros(max_n, np.float64)
+        status = np.zeros(max_n, np.int32)
+        n = ctypes.c_int64()
+        _check(load().ssh_server_collect(self.handle, max_n, timeout_s, _host_ptr(tickets), _host_ptr(ids),
+                                         _host_ptr(dists), _host_ptr(lat), _host_ptr(status), ctypes.byref(n)))
+        c = n.value
+        return tickets[:c], ids[:c], dists[:c], lat[:c], status[:c]
+
+    def flush(self, timeout_s: float = 60.0) -> None:
+        _check(load().ssh_server_flush(self.handle, timeout_s))
+
+    def stats(self) -> dict:
+        st = ssh_server_stats()
+        _check(load().ssh_server_get_stats(self.handle, ctypes.byref(st)))
+        return st.as_dict()
+
+    def close(self):
+        if self.handle:
+            load().ssh_server_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

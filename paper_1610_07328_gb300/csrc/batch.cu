@@ -202,8 +202,11 @@ struct ssh_batch {
     int Lmax = 1, max_m = 1;
     int64_t max_words = 1;
     cudaStream_t st = nullptr;
-    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_done = nullptr;
     cudaGraphExec_t exec = nullptr;
+    bool eager = false;           // the launched batch ran without the graph (capture after it)
+    int64_t nq = 0;               // queries of the prepared batch
+    std::vector<int> q_class;     // their classes, in caller order
     int graph_kernels = 0;
     // plan (pinned host copy + device copy)
     unsigned char* h_plan = nullptr;
@@ -496,65 +499,59 @@ ssh_status capture(ssh_batch* b) {
 }  // namespace
 }  // namespace ssh
 
-extern "C" {
+namespace ssh {
 
-ssh_status ssh_batch_create(ssh_index* const* handles, int nh, int64_t max_queries, int k, int64_t max_pairs,
-                            ssh_batch** out) {
-    if (!out) return fail_status(SSH_EINVAL, "out is NULL");
-    *out = nullptr;
-    if (!handles || nh < 1) return fail_status(SSH_EINVAL, "no indexes");
-    for (int h = 0; h < nh; ++h)
-        if (!handles[h]) return fail_status(SSH_EINVAL, "handle %d is NULL", h);
-    if (max_queries < 1 || max_queries > 65535)
-        return fail_status(SSH_EINVAL, "max_queries = %lld outside [1, 65535]", (long long)max_queries);
-    if (k < 1 || k > kMaxTopK) return fail_status(SSH_EINVAL, "k = %d outside [1, %d]", k, kMaxTopK);
-    if (max_pairs < 0) return fail_status(SSH_EINVAL, "max_pairs < 0");
-    for (int h = 1; h < nh; ++h)
-        if (handles[h]->device != handles[0]->device)
-            return fail_status(SSH_EINVAL, "the indexes of a batch must be on one device");
-    SSH_TRY(check_device(handles[0]));
-    ssh_batch* b = new ssh_batch();
-    b->handles.assign(handles, handles + nh);
-    b->qcap = max_queries;
-    b->k = k;
-    b->device = handles[0]->device;
-    cudaError_t e = cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaMallocHost(&b->h_status, sizeof(BatchStatus));
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_status, sizeof(BatchStatus));
-    if (e != cudaSuccess) {
-        ssh_status s = cuda_status(e, "ssh_batch_create");
-        ssh_batch_destroy(b);
-        return s;
+// The indexes changed since the plan was built: when the classes are the same
+// and every class still fits the bitmap stride, only the class descriptors
+// (table pointers and sizes) are rewritten and the captured graph stays valid;
+// otherwise the plan is rebuilt (and captured again on its next batch).
+ssh_status batch_refresh(ssh_batch* b) {
+    bool same = true;
+    std::vector<ClassDev> dev(b->cls.size());
+    std::map<int, int> seen;
+    int ncls = 0;
+    for (int h = 0; h < (int)b->handles.size() && same; ++h) {
+        for (auto& kv : b->handles[h]->subs) {
+            const SubIndex& s = kv.second;
+            if (s.count == 0 || seen.count(kv.first)) continue;
+            seen[kv.first] = h;
+            ++ncls;
+            auto it = b->class_of_length.find(kv.first);
+            if (it == b->class_of_length.end() || b->cls[it->second].h != h || (s.count + 31) / 32 > b->max_words ||
+                b->handles[h]->L != b->cls[it->second].L) {
+                same = false;
+                break;
+            }
+            ClassDev& d = dev[it->second];
+            d.skeys = s.skeys;
+            d.srows = s.srows;
+            d.bins = s.bins;
+            d.row_ptr = s.row_ptr;
+            d.cap = s.cap;
+            d.nrows = s.count;
+            d.words = (s.count + 31) / 32;
+            d.bin_bits = s.bin_bits;
+            d.L = b->handles[h]->L;
+        }
     }
-    ssh_status s = build_plan(b);
-    if (s == SSH_OK) {
-        int64_t pc = max_pairs;
-        if (pc == 0) pc = std::max<int64_t>(1 << 20, max_queries * 2048);
-        s = alloc_pairs(b, pc);
-    }
-    if (s != SSH_OK) {
-        ssh_batch_destroy(b);
-        return s;
-    }
-    *out = b;
+    if (!same || ncls != (int)b->cls.size()) return build_plan(b);
+    SSH_CUDA(cudaStreamSynchronize(b->st));
+    SSH_CUDA(cudaMemcpy(b->d_cls, dev.data(), dev.size() * sizeof(ClassDev), cudaMemcpyHostToDevice));
+    for (size_t h = 0; h < b->handles.size(); ++h) b->versions[h] = b->handles[h]->version;
     return SSH_OK;
 }
 
-ssh_status ssh_batch_query(ssh_batch* b, const float* d_queries, const int32_t* lengths, int64_t nq, int64_t* d_ids,
-                           float* d_dists, int32_t* d_which, void* stream) {
-    if (!b || nq < 0 || (nq > 0 && (!d_queries || !lengths || !d_ids || !d_dists)))
-        return fail_status(SSH_EINVAL, "bad arguments");
+// Route the queries (back to back at d_queries) to their classes and write
+// the query table into the plan's pinned copy; rebuild or refresh a stale plan.
+ssh_status batch_prepare(ssh_batch* b, const float* d_queries, const int32_t* lengths, int64_t nq) {
     if (nq > b->qcap) return fail_status(SSH_EINVAL, "%lld queries > the plan's %lld", (long long)nq, (long long)b->qcap);
-    if (nq == 0) return SSH_OK;
     SSH_TRY(check_device(b->handles[0]));
     bool stale = false;
     for (size_t h = 0; h < b->handles.size(); ++h) stale |= b->handles[h]->version != b->versions[h];
-    if (stale) SSH_TRY(build_plan(b));
-    // route and sort the queries by class
+    if (stale) SSH_TRY(batch_refresh(b));
     const int C = (int)b->cls.size();
-    std::vector<int> qc(nq);
+    std::vector<int>& qc = b->q_class;
+    qc.resize(nq);
     std::vector<int64_t> qoff(nq), per(C + 1, 0);
     int64_t off = 0;
     for (int64_t i = 0; i < nq; ++i) {
@@ -582,43 +579,133 @@ ssh_status ssh_batch_query(ssh_batch* b, const float* d_queries, const int32_t* 
         hv.q_gid[s] = b->handles[hc.h]->subs[hc.m].gid;
         hv.q_which[s] = hc.h;
     }
-    cudaStream_t us = (cudaStream_t)stream;
-    SSH_CUDA(cudaEventRecord(b->ev_in, us));
-    SSH_CUDA(cudaStreamWaitEvent(b->st, b->ev_in, 0));
-    for (int attempt = 0; attempt < 2; ++attempt) {
-        const bool eager = b->exec == nullptr;
-        if (eager) {
-            // the first batch of a plan (or of a new pair capacity) runs directly;
-            // the graph is captured from it for the batches that follow
-            SSH_TRY(enqueue_pipeline(b));
-        } else {
-            SSH_CUDA(cudaGraphLaunch(b->exec, b->st));
-            note_launch(b->graph_kernels);
-        }
-        SSH_CUDA(cudaStreamSynchronize(b->st));
-        if (!b->h_status->overflow) {
-            if (eager) SSH_TRY(capture(b));
-            break;
-        }
+    b->nq = nq;
+    return SSH_OK;
+}
+
+// Start the prepared batch on the plan's stream (the captured graph, or the
+// kernels themselves for a plan's first batch); returns without waiting.
+ssh_status batch_launch(ssh_batch* b) {
+    b->eager = b->exec == nullptr;
+    if (b->eager) {
+        SSH_TRY(enqueue_pipeline(b));
+    } else {
+        SSH_CUDA(cudaGraphLaunch(b->exec, b->st));
+        note_launch(b->graph_kernels);
+    }
+    SSH_CUDA(cudaEventRecord(b->ev_done, b->st));
+    return SSH_OK;
+}
+
+bool batch_done(ssh_batch* b) { return cudaEventQuery(b->ev_done) != cudaErrorNotReady; }
+
+// Wait for the launched batch; a batch whose candidates overflowed the pair
+// buffers is run again with grown buffers. Captures the graph after a
+// plan's first (direct) batch. Results: batch_outputs, rows in caller order.
+ssh_status batch_finish(ssh_batch* b) {
+    SSH_CUDA(cudaEventSynchronize(b->ev_done));
+    for (int attempt = 0; b->h_status->overflow; ++attempt) {
         if (attempt == 1) return fail_status(SSH_ENOMEM, "batch candidates exceed the pair buffers");
-        // more candidates than pair capacity: grow it and rerun
         const int64_t need = (int64_t)b->h_status->pairs;
         SSH_TRY(alloc_pairs(b, need + need / 4 + 1024));
         if (b->exec) cudaGraphExecDestroy(b->exec);
         b->exec = nullptr;
+        SSH_TRY(batch_launch(b));
+        SSH_CUDA(cudaEventSynchronize(b->ev_done));
     }
+    if (b->eager) SSH_TRY(capture(b));
+    b->eager = false;
+    for (size_t h = 0; h < b->handles.size(); ++h) {
+        int64_t q_h = 0;
+        for (int64_t i = 0; i < b->nq; ++i) q_h += b->cls[b->q_class[i]].h == (int)h;
+        b->handles[h]->host_stats.queries += q_h;
+    }
+    b->handles[0]->host_stats.candidates += (int64_t)b->h_status->pairs;
+    b->handles[0]->host_stats.dtw_computed += (int64_t)(b->h_status->dtw[0] + b->h_status->dtw[1]);
+    return SSH_OK;
+}
+
+void batch_outputs(const ssh_batch* b, const int64_t** ids, const float** dists, const int32_t** which) {
+    *ids = b->out_ids;
+    *dists = b->out_dists;
+    *which = b->out_which;
+}
+
+cudaStream_t batch_stream(const ssh_batch* b) { return b->st; }
+
+size_t batch_device_bytes(const ssh_batch* b) {
+    const int C = (int)b->cls.size();
+    const size_t Q = (size_t)b->qcap;
+    return plan_view(nullptr, b->qcap, C).bytes + C * sizeof(ClassDev) + (size_t)b->Lmax * Q * 8 +
+           Q * (size_t)b->max_words * 4 + Q * 8 * 6 + Q * (size_t)b->max_m * 8 + Q * 4 * 2 + Q * 8 +
+           Q * (size_t)b->k * 12 + Q * 4 + (size_t)b->pcap * 44;
+}
+
+}  // namespace ssh
+
+extern "C" {
+
+ssh_status ssh_batch_create(ssh_index* const* handles, int nh, int64_t max_queries, int k, int64_t max_pairs,
+                            ssh_batch** out) {
+    if (!out) return fail_status(SSH_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!handles || nh < 1) return fail_status(SSH_EINVAL, "no indexes");
+    for (int h = 0; h < nh; ++h)
+        if (!handles[h]) return fail_status(SSH_EINVAL, "handle %d is NULL", h);
+    if (max_queries < 1 || max_queries > 65535)
+        return fail_status(SSH_EINVAL, "max_queries = %lld outside [1, 65535]", (long long)max_queries);
+    if (k < 1 || k > kMaxTopK) return fail_status(SSH_EINVAL, "k = %d outside [1, %d]", k, kMaxTopK);
+    if (max_pairs < 0) return fail_status(SSH_EINVAL, "max_pairs < 0");
+    for (int h = 1; h < nh; ++h)
+        if (handles[h]->device != handles[0]->device)
+            return fail_status(SSH_EINVAL, "the indexes of a batch must be on one device");
+    SSH_TRY(check_device(handles[0]));
+    ssh_batch* b = new ssh_batch();
+    b->handles.assign(handles, handles + nh);
+    b->qcap = max_queries;
+    b->k = k;
+    b->device = handles[0]->device;
+    cudaError_t e = cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_status, sizeof(BatchStatus));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_status, sizeof(BatchStatus));
+    if (e != cudaSuccess) {
+        ssh_status s = cuda_status(e, "ssh_batch_create");
+        ssh_batch_destroy(b);
+        return s;
+    }
+    ssh_status s = build_plan(b);
+    if (s == SSH_OK) {
+        int64_t pc = max_pairs;
+        if (pc == 0) pc = std::max<int64_t>(1 << 20, max_queries * 2048);
+        s = alloc_pairs(b, pc);
+    }
+    if (s != SSH_OK) {
+        ssh_batch_destroy(b);
+        return s;
+    }
+    *out = b;
+    return SSH_OK;
+}
+
+ssh_status ssh_batch_query(ssh_batch* b, const float* d_queries, const int32_t* lengths, int64_t nq, int64_t* d_ids,
+                           float* d_dists, int32_t* d_which, void* stream) {
+    if (!b || nq < 0 || (nq > 0 && (!d_queries || !lengths || !d_ids || !d_dists)))
+        return fail_status(SSH_EINVAL, "bad arguments");
+    if (nq == 0) return SSH_OK;
+    SSH_TRY(batch_prepare(b, d_queries, lengths, nq));
+    cudaStream_t us = (cudaStream_t)stream;
+    SSH_CUDA(cudaEventRecord(b->ev_in, us));
+    SSH_CUDA(cudaStreamWaitEvent(b->st, b->ev_in, 0));
+    SSH_TRY(batch_launch(b));
+    SSH_TRY(batch_finish(b));
     SSH_CUDA(cudaMemcpyAsync(d_ids, b->out_ids, (size_t)nq * b->k * 8, cudaMemcpyDeviceToDevice, b->st));
     SSH_CUDA(cudaMemcpyAsync(d_dists, b->out_dists, (size_t)nq * b->k * 4, cudaMemcpyDeviceToDevice, b->st));
     if (d_which) SSH_CUDA(cudaMemcpyAsync(d_which, b->out_which, (size_t)nq * 4, cudaMemcpyDeviceToDevice, b->st));
     SSH_CUDA(cudaEventRecord(b->ev_out, b->st));
     SSH_CUDA(cudaStreamWaitEvent(us, b->ev_out, 0));
-    for (size_t h = 0; h < b->handles.size(); ++h) {
-        int64_t q_h = 0;
-        for (int64_t i = 0; i < nq; ++i) q_h += b->cls[qc[i]].h == (int)h;
-        b->handles[h]->host_stats.queries += q_h;
-    }
-    b->handles[0]->host_stats.candidates += (int64_t)b->h_status->pairs;
-    b->handles[0]->host_stats.dtw_computed += (int64_t)(b->h_status->dtw[0] + b->h_status->dtw[1]);
     return SSH_OK;
 }
 
@@ -642,6 +729,7 @@ void ssh_batch_destroy(ssh_batch* b) {
     cudaFree(b->d_status);
     if (b->ev_in) cudaEventDestroy(b->ev_in);
     if (b->ev_out) cudaEventDestroy(b->ev_out);
+    if (b->ev_done) cudaEventDestroy(b->ev_done);
     if (b->st) cudaStreamDestroy(b->st);
     delete b;
 }

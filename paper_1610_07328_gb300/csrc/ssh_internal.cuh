@@ -13,6 +13,7 @@
 #include "ssh.h"
 
 struct ssh_index;
+struct ssh_batch;
 
 namespace ssh {
 
@@ -240,6 +241,19 @@ struct TopkOut {
 };
 cudaError_t launch_topk_output(const TopkOut& o, const uint64_t* keys, const int64_t* seg_begin, const uint64_t* kth,
                                int64_t nseg, int k, cudaStream_t st);
+
+// Batch plans, asynchronously (the server's slots): prepare writes the query
+// table (queries back to back at d_queries), launch starts the batch on the
+// plan's stream, done polls it, finish waits (and reruns an overflowed batch),
+// outputs are the plan's device result rows in caller order.
+ssh_status batch_prepare(ssh_batch* b, const float* d_queries, const int32_t* lengths, int64_t nq);
+ssh_status batch_launch(ssh_batch* b);
+bool batch_done(ssh_batch* b);
+ssh_status batch_finish(ssh_batch* b);
+ssh_status batch_refresh(ssh_batch* b);
+void batch_outputs(const ssh_batch* b, const int64_t** ids, const float** dists, const int32_t** which);
+cudaStream_t batch_stream(const ssh_batch* b);
+size_t batch_device_bytes(const ssh_batch* b);
 
 // k-th smallest key of each segment (keys read through `keys`, segment s is
 // [seg_begin[s], seg_begin[s+1])); kth_out[s] = that key, or all-ones if the
