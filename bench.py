@@ -432,6 +432,141 @@ def batched_measurement(args, binding, torch, dev):
     return out
 
 
+def ecg_like_gpu(torch, N, m, seed, dev, chunk=65536):
+    """The ECG-like recipe of synth.ecg_like generated on the GPU with torch's generator
+    (the serving index is too large for the host generator): beats of P/QRS/T Gaussian bumps
+    (sigma 8/3/12, amplitude 0.15/1.0/0.3 at -0.2/0/+0.3 period), periods uniform 180-260,
+    first beat offset uniform 0-64, wander 0.1 sin(2 pi t / T_w + phi) with T_w uniform
+    700-1200, noise N(0, 0.05^2); not z-normalised."""
+    g = torch.Generator(device=dev)
+    g.manual_seed(seed)
+    out = torch.empty((N, m), dtype=torch.float32, device=dev)
+    t = torch.arange(m, dtype=torch.float32, device=dev)[None, :]
+    nb = m // 180 + 3
+    for a in range(0, N, chunk):
+        n = min(chunk, N - a)
+        per = torch.rand((n, nb), generator=g, device=dev) * 80.0 + 180.0
+        off = torch.rand((n, 1), generator=g, device=dev) * 64.0
+        cen = off + torch.cat([torch.zeros((n, 1), device=dev), torch.cumsum(per[:, :-1], 1)], 1)
+        x = torch.zeros((n, m), device=dev)
+        for b in range(nb):
+            c0, p = cen[:, b:b + 1], per[:, b:b + 1]
+            for rel, sig, amp in ((-0.2, 8.0, 0.15), (0.0, 3.0, 1.0), (0.3, 12.0, 0.3)):
+                x += amp * torch.exp(-0.5 * ((t - (c0 + rel * p)) / sig) ** 2)
+        tw = torch.rand((n, 1), generator=g, device=dev) * 500.0 + 700.0
+        phi = torch.rand((n, 1), generator=g, device=dev) * (2.0 * math.pi)
+        x += 0.1 * torch.sin(2.0 * math.pi * t / tw + phi)
+        x += 0.05 * torch.randn((n, m), generator=g, device=dev)
+        out[a:a + n] = x
+    return out
+
+
+SERVE_RATES = (1000, 5000, 20000, 50000)
+
+
+def serving_measurement(args, binding, torch, dev):
+    """Poisson query arrivals at several rates against a served ECG-like index while random
+    walks are inserted at 10k/s; open-loop latency from each query's scheduled arrival."""
+    import threading
+    small = args.small
+    N5, m, k = (20_000, 1024, 10) if small else (2_000_000, 1024, 10)
+    dur = 0.3 if small else 1.0
+    t0 = time.perf_counter()
+    db = ecg_like_gpu(torch, N5, m, 3, dev)
+    g = torch.Generator(device=dev)
+    g.manual_seed(5)
+    pool = 4096
+    src = torch.randint(0, N5, (pool,), generator=g, device=dev)
+    qd = db[src] + 0.1 * torch.randn((pool, m), generator=g, device=dev)
+    shifts = torch.randint(0, 9, (pool,), generator=g, device=dev).cpu().numpy()
+    q_host = np.stack([np.roll(r, int(sft)) for r, sft in zip(qd.cpu().numpy(), shifts)]).astype(np.float32)
+    ins_pool = synth.random_walk(2000, m, seed=77)
+    gen_s = time.perf_counter() - t0
+    ix = binding.SSHIndex(120, 5, 15, 4, 50, 0.10, 0)
+    ix.add_device(db, borrow=True)
+    torch.cuda.synchronize()
+    out = {"workload": "ECG-like index of %d x %d (W=120, delta=5, n=15, K=4, L=50, band 10%%), top-%d; "
+                       "Poisson arrivals, random walks inserted at 10k/s" % (N5, m, k),
+           "rates": []}
+    with binding.SSHServer([ix], k=k, max_batch=256, max_slots=4, reserve_bytes=2 << 30) as srv:
+        # warm-up: every slot's first batch runs directly and captures its graph
+        for _ in range(3):
+            tk = srv.submit(q_host[:256], np.full(256, m, np.int32))
+            srv.wait(tk[-1], 60.0)
+        srv.flush(60.0)
+        rng = np.random.default_rng(8)
+        for rate in SERVE_RATES:
+            n = max(1, int(rate * dur))
+            arr = np.cumsum(rng.exponential(1.0 / rate, n))
+            qidx = rng.integers(0, pool, n)
+            got = []
+            done_evt = threading.Event()
+
+            def collector():
+                while len(got) < n:
+                    tk, _, _, lat, stt = srv.collect(4096, 0.01)
+                    got.extend(zip(lat.tolist(), stt.tolist()))
+                done_evt.set()
+
+            while len(srv.collect(4096, 0.0)[0]):  # results of earlier phases
+                pass
+            st0 = srv.stats()
+            th = threading.Thread(target=collector, daemon=True)
+            th.start()
+            start = srv.now() + 0.02
+            arr_abs = start + arr
+            ins_t, ins_i, i = start, 0, 0
+            while i < n:
+                now = srv.now()
+                j = int(np.searchsorted(arr_abs, now, side="right"))
+                if j > i:
+                    sel = qidx[i:j]
+                    srv.submit(q_host[sel], np.full(j - i, m, np.int32), arr_abs[i:j])
+                    i = j
+                while ins_t <= now:  # 100 random walks every 10 ms
+                    a = (ins_i * 100) % (len(ins_pool) - 100)
+                    srv.insert(ins_pool[a:a + 100], np.full(100, m, np.int32))
+                    ins_t += 0.01
+                    ins_i += 1
+                time.sleep(0.0002)
+            done_evt.wait(120.0)
+            t_end = srv.now()
+            srv.flush(120.0)
+            st1 = srv.stats()
+            lat = np.array([l for l, sc in got])
+            ok = sum(1 for _, sc in got if sc == 0)
+            span = max(t_end - start, 1e-9)
+            out["rates"].append({
+                "offered_qps": rate, "queries": n, "completed_ok": ok,
+                "served_qps": ok / span,
+                "p50_ms": float(np.percentile(lat, 50)) if len(lat) else None,
+                "p99_ms": float(np.percentile(lat, 99)) if len(lat) else None,
+                "mean_batch": (st1["queries_done"] - st0["queries_done"]) / max(st1["batches"] - st0["batches"], 1),
+                "batches": st1["batches"] - st0["batches"],
+                "max_inflight": st1["max_inflight"],
+                "inserts_per_s": (st1["inserts_applied"] - st0["inserts_applied"]) / span,
+            })
+        st = srv.stats()
+        out["slots"] = st["slots"]
+        out["insert_mean_latency_ms"] = st["insert_latency_ms_sum"] / max(st["insert_batches"], 1)
+    # recall@10 of the served configuration against exact DTW over the whole index (a sample)
+    nrec = 4 if small else 12
+    d_qs = torch.from_numpy(q_host[:nrec]).to(dev)
+    ids = torch.empty((nrec, k), dtype=torch.int64, device=dev)
+    dd = torch.empty((nrec, k), dtype=torch.float32, device=dev)
+    ix.clear()
+    ix.add_device(db, borrow=True)  # without the inserted walks: exact top-k over the same rows
+    ix.query_device(d_qs, k, ids, dd)
+    rb = min(int(math.floor(np.float32(0.10) * np.float64(m))), m - 1)
+    ex = exact_topk_gpu(binding, torch, d_qs, db, np.arange(N5, dtype=np.int64), m, rb, k)
+    out["recall_at_10"] = recall(ids.cpu().numpy(), ex)
+    out["recall_queries"] = nrec
+    out["setup_s"] = gen_s
+    ix.close()
+    del db
+    return out
+
+
 def run_gpu(args, w):
     import torch
 
@@ -619,6 +754,8 @@ def run_gpu(args, w):
     }
     if rank == 0 and world == 1 and not args.no_batched:
         line["batched"] = batched_measurement(args, binding, torch, dev)
+    if rank == 0 and world == 1 and not args.no_served:
+        line["served"] = serving_measurement(args, binding, torch, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         n_s = 10000 if not args.small else 300
         r = oracle_sample(w, n_s, 10 if not args.small else 3)
@@ -642,6 +779,7 @@ def main():
     ap.add_argument("--no-recall", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the mixed-length batch-plan measurement")
+    ap.add_argument("--no-served", action="store_true", help="skip the serving-loop measurement")
     args = ap.parse_args()
     w = TINY if args.small else SCALE
     if args.impl == "reference":

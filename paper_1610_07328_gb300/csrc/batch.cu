@@ -36,7 +36,33 @@ struct ClassDev {
     const float* const* row_ptr;
     int64_t cap, nrows, words;
     int bin_bits, L;
+    // delta tables (rows added since the main tables were built)
+    const uint64_t* dkeys;
+    const uint32_t* drows;
+    const uint32_t* dbins;
+    int64_t dcap, dcount;
+    int dbin_bits;
 };
+
+ClassDev class_dev(const SubIndex& s, int L) {
+    ClassDev d;
+    d.skeys = s.skeys;
+    d.srows = s.srows;
+    d.bins = s.bins;
+    d.row_ptr = s.row_ptr;
+    d.cap = s.cap;
+    d.nrows = s.count;
+    d.words = (s.count + 31) / 32;
+    d.bin_bits = s.bin_bits;
+    d.L = L;
+    d.dkeys = s.dkeys;
+    d.drows = s.drows;
+    d.dbins = s.dbins;
+    d.dcap = s.dcap;
+    d.dcount = s.dcount;
+    d.dbin_bits = s.dbin_bits;
+    return d;
+}
 
 // Device counters the host reads after a batch.
 struct BatchStatus {
@@ -92,6 +118,17 @@ __global__ void batch_probe_kernel(const int64_t* nq, const int32_t* q_cls, cons
         if (sk[i] != key) continue;
         const uint32_t row = sr[i];
         atomicOr(&bm[row >> 5], 1u << (row & 31));
+    }
+    if (c.dcount > 0) {  // rows added since the main tables were built
+        const uint64_t* dk = c.dkeys + (int64_t)l * c.dcap;
+        const uint32_t* dr = c.drows + (int64_t)l * c.dcap;
+        const uint32_t* db = c.dbins + (int64_t)l * ((int64_t(1) << c.dbin_bits) + 1);
+        const uint32_t dbin = (uint32_t)(key >> (64 - c.dbin_bits));
+        for (int64_t i = db[dbin] + threadIdx.x; i < db[dbin + 1]; i += blockDim.x) {
+            if (dk[i] != key) continue;
+            const uint32_t row = dr[i];
+            atomicOr(&bm[row >> 5], 1u << (row & 31));
+        }
     }
 }
 
@@ -335,16 +372,7 @@ ssh_status build_plan(ssh_batch* b) {
             SSH_TRY(prepare_hash_args(idx, s.m, &hc.a));
             hc.plan = dtw_tuned_plan(s.m, s.rb, b->st);
             if (hc.plan.S == 0) return fail_status(SSH_ENOTSUP, "DTW radius %d (length %d) is not covered", s.rb, s.m);
-            ClassDev d;
-            d.skeys = s.skeys;
-            d.srows = s.srows;
-            d.bins = s.bins;
-            d.row_ptr = s.row_ptr;
-            d.cap = s.cap;
-            d.nrows = s.count;
-            d.words = (s.count + 31) / 32;
-            d.bin_bits = s.bin_bits;
-            d.L = idx->L;
+            const ClassDev d = class_dev(s, idx->L);
             b->class_of_length[kv.first] = (int)b->cls.size();
             b->cls.push_back(hc);
             dev.push_back(d);
@@ -522,16 +550,7 @@ ssh_status batch_refresh(ssh_batch* b) {
                 same = false;
                 break;
             }
-            ClassDev& d = dev[it->second];
-            d.skeys = s.skeys;
-            d.srows = s.srows;
-            d.bins = s.bins;
-            d.row_ptr = s.row_ptr;
-            d.cap = s.cap;
-            d.nrows = s.count;
-            d.words = (s.count + 31) / 32;
-            d.bin_bits = s.bin_bits;
-            d.L = b->handles[h]->L;
+            dev[it->second] = class_dev(s, b->handles[h]->L);
         }
     }
     if (!same || ncls != (int)b->cls.size()) return build_plan(b);

@@ -326,6 +326,9 @@ void free_sub(SubIndex& s) {
     cudaFree(s.skeys);
     cudaFree(s.srows);
     cudaFree(s.bins);
+    cudaFree(s.dkeys);
+    cudaFree(s.drows);
+    cudaFree(s.dbins);
     s = SubIndex();
 }
 
@@ -372,12 +375,45 @@ ssh_status reserve(ssh_index* idx, SubIndex& s, int64_t need, cudaStream_t st) {
     s.skeys = skeys;
     s.srows = srows;
     s.cap = cap;
+    s.main_count = 0;  // the main tables were not carried over: rebin every row
+    s.dcount = 0;
     return SSH_OK;
 }
 
-// Rebuild the bucket tables of a sub-index from its per-row keys.
+// Rebuild the bucket tables of a sub-index from its per-row keys: only the
+// delta tables (rows main_count .. count-1) while they stay within an eighth
+// of the main part, else every row into the main tables and no delta.
 ssh_status rebuild_tables(ssh_index* idx, SubIndex& s, cudaStream_t st) {
     const int L = idx->L;
+    const int64_t nd = s.count - s.main_count;
+    ScratchList sc(st);
+    if (s.main_count > 0 && nd >= 0 && nd <= s.main_count / 8) {
+        const int bits = table_bin_bits(nd);
+        if (nd > s.dcap) {
+            const int64_t dcap = std::max<int64_t>(nd, std::max<int64_t>(2 * s.dcap, 4096));
+            cudaFree(s.dkeys);
+            cudaFree(s.drows);
+            s.dkeys = nullptr;
+            s.drows = nullptr;
+            s.dcap = 0;
+            SSH_CUDA(cudaMalloc(&s.dkeys, (size_t)L * dcap * sizeof(uint64_t)));
+            SSH_CUDA(cudaMalloc(&s.drows, (size_t)L * dcap * sizeof(uint32_t)));
+            s.dcap = dcap;
+        }
+        if (bits > s.dbins_alloc_bits) {
+            cudaFree(s.dbins);
+            s.dbins = nullptr;
+            s.dbins_alloc_bits = 0;
+            SSH_CUDA(cudaMalloc(&s.dbins, (size_t)L * (((size_t)1 << bits) + 1) * sizeof(uint32_t)));
+            s.dbins_alloc_bits = bits;
+        }
+        s.dbin_bits = bits;
+        uint32_t* cursor;
+        SSH_TRY(sc.get(&cursor, (size_t)L * (((size_t)1 << bits) + 1)));
+        SSH_CUDA(build_tables(s.keys, s.main_count, nd, L, s.cap, s.dcap, bits, s.dbins, cursor, s.dkeys, s.drows, st));
+        s.dcount = nd;
+        return SSH_OK;
+    }
     const int64_t n = s.count;
     const int bits = table_bin_bits(n);
     if (bits > s.bins_alloc_bits) {
@@ -388,10 +424,11 @@ ssh_status rebuild_tables(ssh_index* idx, SubIndex& s, cudaStream_t st) {
         s.bins_alloc_bits = bits;
     }
     s.bin_bits = bits;
-    ScratchList sc(st);
     uint32_t* cursor;
     SSH_TRY(sc.get(&cursor, (size_t)L * (((size_t)1 << bits) + 1)));
-    SSH_CUDA(build_tables(s.keys, n, L, s.cap, bits, s.bins, cursor, s.skeys, s.srows, st));
+    SSH_CUDA(build_tables(s.keys, 0, n, L, s.cap, s.cap, bits, s.bins, cursor, s.skeys, s.srows, st));
+    s.main_count = n;
+    s.dcount = 0;
     return SSH_OK;
 }
 
@@ -552,7 +589,8 @@ ssh_status query_group(ssh_index* idx, SubIndex& s, const std::vector<const floa
     SSH_TRY(sc.get(&bitmap, (size_t)nq * words));
     SSH_TRY(sc.get(&counts, nq));
     SSH_CUDA(cudaMemsetAsync(bitmap, 0, (size_t)nq * words * sizeof(uint32_t), st));
-    ProbeArgs pa{qkeys, nq, L, s.skeys, s.srows, s.bins, s.bin_bits, s.cap, s.count, bitmap, words};
+    ProbeArgs pa{qkeys, nq, L, s.skeys, s.srows, s.bins, s.bin_bits, s.cap, s.count, bitmap, words,
+                 s.dkeys, s.drows, s.dbins, s.dbin_bits, s.dcap, s.dcount};
     {
         TimedRegion tr(idx, st, "query.probe_union", (double)nq * L);
         SSH_CUDA(launch_probe_union(pa, st));
@@ -1058,7 +1096,11 @@ ssh_status ssh_index_clear(ssh_index* idx) {
     if (!idx) return fail(SSH_EINVAL, "NULL index");
     SSH_TRY(check_device(idx));
     SSH_CUDA(cudaDeviceSynchronize());
-    for (auto& kv : idx->subs) kv.second.count = 0;  // keep the capacity for the next add
+    for (auto& kv : idx->subs) {  // keep the capacity for the next add
+        kv.second.count = 0;
+        kv.second.main_count = 0;
+        kv.second.dcount = 0;
+    }
     idx->version += 1;
     // the copies of the cleared series become staging buffers for later adds
     for (DevBuf& b : idx->owned) idx->spare.push_back(b);

@@ -36,6 +36,17 @@ __global__ void probe_union_kernel(ProbeArgs a) {
         const uint32_t row = sr[i];
         atomicOr(&bm[row >> 5], 1u << (row & 31));
     }
+    if (a.dcount > 0) {  // rows added since the main tables were built
+        const uint64_t* dk = a.dkeys + l * a.dcap;
+        const uint32_t* dr = a.drows + l * a.dcap;
+        const uint32_t* db = a.dbins + l * ((int64_t(1) << a.dbin_bits) + 1);
+        const uint32_t dbin = (uint32_t)(key >> (64 - a.dbin_bits));
+        for (int64_t i = db[dbin] + threadIdx.x; i < db[dbin + 1]; i += blockDim.x) {
+            if (dk[i] != key) continue;
+            const uint32_t row = dr[i];
+            atomicOr(&bm[row >> 5], 1u << (row & 31));
+        }
+    }
 }
 
 __global__ void bitmap_count_kernel(const uint32_t* bitmap, int64_t words, int64_t* counts) {

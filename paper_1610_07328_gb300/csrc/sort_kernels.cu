@@ -63,10 +63,10 @@ __global__ void __launch_bounds__(512) select_kth_kernel(const T* keys, const in
 
 // ---------------------------------------------------- table partition
 
-__global__ void bin_hist_kernel(const uint64_t* keys, int64_t n, int64_t cap, int shift, int nbins,
+__global__ void bin_hist_kernel(const uint64_t* keys, int64_t row0, int64_t n, int64_t cap, int shift, int nbins,
                                 uint32_t* counts) {
     const int l = blockIdx.y;
-    const uint64_t* k = keys + (int64_t)l * cap;
+    const uint64_t* k = keys + (int64_t)l * cap + row0;
     uint32_t* c = counts + (int64_t)l * (nbins + 1);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         atomicAdd(&c[(uint32_t)(k[i] >> shift)], 1u);
@@ -101,18 +101,18 @@ __global__ void __launch_bounds__(1024) bin_scan_kernel(uint32_t* counts, uint32
     }
 }
 
-__global__ void bin_scatter_kernel(const uint64_t* keys, int64_t n, int64_t cap, int shift, int nbins,
-                                   uint32_t* cursor, uint64_t* skeys, uint32_t* srows) {
+__global__ void bin_scatter_kernel(const uint64_t* keys, int64_t row0, int64_t n, int64_t cap, int64_t out_stride,
+                                   int shift, int nbins, uint32_t* cursor, uint64_t* skeys, uint32_t* srows) {
     const int l = blockIdx.y;
-    const uint64_t* k = keys + (int64_t)l * cap;
+    const uint64_t* k = keys + (int64_t)l * cap + row0;
     uint32_t* cur = cursor + (int64_t)l * (nbins + 1);
-    uint64_t* sk = skeys + (int64_t)l * cap;
-    uint32_t* sr = srows + (int64_t)l * cap;
+    uint64_t* sk = skeys + (int64_t)l * out_stride;
+    uint32_t* sr = srows + (int64_t)l * out_stride;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t key = k[i];
         const uint32_t pos = atomicAdd(&cur[(uint32_t)(key >> shift)], 1u);
         sk[pos] = key;
-        sr[pos] = (uint32_t)i;
+        sr[pos] = (uint32_t)(row0 + i);
     }
 }
 
@@ -126,8 +126,9 @@ int table_bin_bits(int64_t n) {
     return b;
 }
 
-cudaError_t build_tables(const uint64_t* keys, int64_t n, int L, int64_t cap, int bin_bits, uint32_t* bins,
-                         uint32_t* cursor, uint64_t* skeys, uint32_t* srows, cudaStream_t st) {
+cudaError_t build_tables(const uint64_t* keys, int64_t row0, int64_t n, int L, int64_t cap, int64_t out_stride,
+                         int bin_bits, uint32_t* bins, uint32_t* cursor, uint64_t* skeys, uint32_t* srows,
+                         cudaStream_t st) {
     const int nbins = 1 << bin_bits;
     const int shift = 64 - bin_bits;
     cudaError_t e = cudaMemsetAsync(bins, 0, (size_t)L * (nbins + 1) * sizeof(uint32_t), st);
@@ -135,11 +136,11 @@ cudaError_t build_tables(const uint64_t* keys, int64_t n, int L, int64_t cap, in
     int64_t g = (n + 255) / 256;
     if (g > 4096) g = 4096;
     dim3 grid((unsigned)g, (unsigned)L);
-    bin_hist_kernel<<<grid, 256, 0, st>>>(keys, n, cap, shift, nbins, bins);
+    bin_hist_kernel<<<grid, 256, 0, st>>>(keys, row0, n, cap, shift, nbins, bins);
     note_launch();
     bin_scan_kernel<<<(unsigned)L, 1024, 0, st>>>(bins, cursor, nbins);
     note_launch();
-    bin_scatter_kernel<<<grid, 256, 0, st>>>(keys, n, cap, shift, nbins, cursor, skeys, srows);
+    bin_scatter_kernel<<<grid, 256, 0, st>>>(keys, row0, n, cap, out_stride, shift, nbins, cursor, skeys, srows);
     note_launch();
     return cudaGetLastError();
 }

@@ -130,13 +130,16 @@ ssh_status prepare_hash_args(const ssh_index* idx, int m, HashArgs* a);
 int hash_warps_per_cta(int m, int nwords, int S, int KL);
 cudaError_t launch_hash(const HashArgs& a, cudaStream_t st);
 
-// ------------------------------------------------------------ radix sort
+// ------------------------------------------------------------ bucket tables
 
-// Bucket tables: per table, the (key, row) pairs partitioned into 2^bin_bits
-// bins by the top bin_bits key bits; bins[l][b] .. bins[l][b+1] is bin b.
+// Bucket tables: per table, the (key, row) pairs of rows row0 .. row0+n-1
+// (keys[l][row], row stride cap) partitioned into 2^bin_bits bins by the top
+// bin_bits key bits into skeys/srows[l][0 .. n) (table stride out_stride);
+// bins[l][b] .. bins[l][b+1] is bin b.
 int table_bin_bits(int64_t n);
-cudaError_t build_tables(const uint64_t* keys, int64_t n, int L, int64_t cap, int bin_bits, uint32_t* bins,
-                         uint32_t* cursor, uint64_t* skeys, uint32_t* srows, cudaStream_t st);
+cudaError_t build_tables(const uint64_t* keys, int64_t row0, int64_t n, int L, int64_t cap, int64_t out_stride,
+                         int bin_bits, uint32_t* bins, uint32_t* cursor, uint64_t* skeys, uint32_t* srows,
+                         cudaStream_t st);
 
 // -------------------------------------------------------------- queries
 
@@ -150,6 +153,12 @@ struct ProbeArgs {
     int64_t cap, nrows;
     uint32_t* bitmap;          // [nq][words] candidate bitmap
     int64_t words;
+    // the delta tables of the rows added since the main tables were built
+    const uint64_t* dkeys;     // [L][dcap]
+    const uint32_t* drows;     // [L][dcap]
+    const uint32_t* dbins;     // [L][2^dbin_bits + 1]
+    int dbin_bits;
+    int64_t dcap, dcount;      // dcount = 0: no delta
 };
 cudaError_t launch_probe_union(const ProbeArgs& a, cudaStream_t st);
 cudaError_t launch_bitmap_count(const uint32_t* bitmap, int64_t nq, int64_t words, int64_t* counts,
@@ -277,6 +286,14 @@ struct SubIndex {
     uint32_t* srows = nullptr;        // [L][cap] device: rows in the same order
     uint32_t* bins = nullptr;         // [L][2^bin_bits + 1] device: bin starts
     int bin_bits = 0, bins_alloc_bits = 0;
+    // Rows [0, main_count) are in the main tables above; rows added later are in
+    // the delta tables below (binned the same way, rows absolute) until the
+    // delta outgrows an eighth of the main part and everything is rebinned.
+    int64_t main_count = 0, dcount = 0, dcap = 0;
+    uint64_t* dkeys = nullptr;        // [L][dcap]
+    uint32_t* drows = nullptr;        // [L][dcap]
+    uint32_t* dbins = nullptr;        // [L][2^dbin_bits + 1]
+    int dbin_bits = 0, dbins_alloc_bits = 0;
 };
 
 struct KernelTimer {

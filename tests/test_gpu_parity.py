@@ -519,3 +519,27 @@ def test_batch_plan_grows_pair_buffers_and_follows_adds():
     finally:
         for ix in idxs:
             ix.close()
+
+
+def test_small_adds_go_to_delta_tables_then_merge():
+    """Adds of up to an eighth of the binned rows go to the delta tables; results and candidate
+    sets must equal the oracle's after each add, and after the merge that a large add triggers."""
+    cfg = CFG1
+    rng_db = synth.random_walk(800, 128, seed=41)
+    ref = oracle.OracleIndex(**cfg)
+    with _index(cfg) as idx:
+        chunks = [(0, 400), (400, 430), (430, 470), (470, 800)]  # full, delta, delta, merge
+        for a, b in chunks:
+            assert idx.add(rng_db[a:b]) == a
+            ref.add(rng_db[a:b])
+            qs, _ = synth.perturbed_queries(rng_db[:b], 6, seed=b)
+            qs[0] = rng_db[b - 1]  # an exact copy of the newest row: its own top-1
+            idx.reset_stats()
+            ids, d = idx.query(qs, 5)
+            st = idx.stats()
+            assert st["candidates"] == sum(len(ref.candidates(q)) for q in qs)
+            assert ids[0, 0] == b - 1 and d[0, 0] == 0.0
+            rb = oracle.band_radius(cfg["band"], 128)
+            for i, q in enumerate(qs):
+                oi, od = ref.query(q, 5)
+                assert_topk_match(q, ids[i], d[i], oi, od, lambda j: rng_db[j], rb)
