@@ -530,9 +530,33 @@ ssh_status add_series(ssh_index* idx, const float* dev, const int32_t* lengths, 
     return finish_add(idx, touched, count, st, first_id);
 }
 
-// A device buffer of at least `bytes` for a copy of series: a spare one left by
-// ssh_index_clear (the smallest that fits) or a new allocation.
+constexpr size_t kArenaChunk = (size_t)256 << 20;
+constexpr size_t kArenaMax = (size_t)16 << 20;
+
+// A device buffer of at least `bytes` for a copy of series: small copies are
+// carved from the arena (no allocation per streamed insert), larger ones take
+// a spare buffer left by ssh_index_clear (the smallest that fits) or a new one.
 ssh_status take_buffer(ssh_index* idx, size_t bytes, DevBuf* out) {
+    if (bytes <= kArenaMax) {
+        const size_t need = (bytes + 255) & ~(size_t)255;
+        if (idx->arena.empty() || idx->arena_off + need > kArenaChunk) {
+            if (!idx->arena.empty()) {
+                ++idx->arena_cur;
+                idx->arena_off = 0;
+            }
+            if (idx->arena_cur >= idx->arena.size()) {
+                void* p = nullptr;
+                SSH_CUDA(cudaMalloc(&p, kArenaChunk));
+                idx->arena.push_back(p);
+                idx->arena_cur = idx->arena.size() - 1;
+            }
+        }
+        out->p = static_cast<unsigned char*>(idx->arena[idx->arena_cur]) + idx->arena_off;
+        out->bytes = bytes;
+        out->arena = true;
+        idx->arena_off += need;
+        return SSH_OK;
+    }
     int best = -1;
     for (int q = 0; q < (int)idx->spare.size(); ++q)
         if (idx->spare[q].bytes >= bytes && (best < 0 || idx->spare[q].bytes < idx->spare[best].bytes)) best = q;
@@ -950,6 +974,7 @@ void ssh_destroy(ssh_index* idx) {
     for (auto& kv : idx->subs) free_sub(kv.second);
     for (DevBuf& b : idx->owned) cudaFree(b.p);
     for (DevBuf& b : idx->spare) cudaFree(b.p);
+    for (void* p : idx->arena) cudaFree(p);
     if (idx->cevent) cudaEventDestroy(idx->cevent);
     if (idx->h_pinned) cudaFreeHost(idx->h_pinned);
     if (idx->hstream) cudaStreamDestroy(idx->hstream);
@@ -1016,10 +1041,10 @@ static ssh_status index_add_impl(ssh_index* idx, const float* series, const int3
     if (status != SSH_OK) {
         cudaStreamSynchronize(cs);
         cudaStreamSynchronize(st);
-        idx->spare.push_back(buf);
+        if (!buf.arena) idx->spare.push_back(buf);
         return status;
     }
-    idx->owned.push_back(buf);  // referenced by the stored rows until ssh_index_clear
+    if (!buf.arena) idx->owned.push_back(buf);  // referenced by the stored rows until ssh_index_clear
     return SSH_OK;
 }
 
@@ -1075,20 +1100,20 @@ static ssh_status index_add_device_impl(ssh_index* idx, const float* d_series, c
         SSH_TRY(take_buffer(idx, (size_t)total * sizeof(float), &own));
         cudaError_t e = cudaMemcpyAsync(own.p, d_series, total * sizeof(float), cudaMemcpyDeviceToDevice, st);
         if (e != cudaSuccess) {
-            idx->spare.push_back(own);
+            if (!own.arena) idx->spare.push_back(own);
             return cuda_status(e, "cudaMemcpyAsync (series)");
         }
         src = static_cast<const float*>(own.p);
     }
     ssh_status s = add_series(idx, src, lengths, count, st, first_id);
     if (s != SSH_OK) {
-        if (own.p) {
+        if (own.p && !own.arena) {
             cudaStreamSynchronize(st);
             idx->spare.push_back(own);
         }
         return s;
     }
-    if (own.p) idx->owned.push_back(own);
+    if (own.p && !own.arena) idx->owned.push_back(own);
     return SSH_OK;
 }
 
@@ -1105,6 +1130,8 @@ ssh_status ssh_index_clear(ssh_index* idx) {
     // the copies of the cleared series become staging buffers for later adds
     for (DevBuf& b : idx->owned) idx->spare.push_back(b);
     idx->owned.clear();
+    idx->arena_cur = 0;
+    idx->arena_off = 0;
     idx->next_id = 0;
     return SSH_OK;
 }

@@ -306,6 +306,7 @@ struct KernelTimer {
 struct DevBuf {
     void* p = nullptr;
     size_t bytes = 0;
+    bool arena = false;  // carved from the index's arena (not freed on its own)
 };
 
 struct KernelTotals {
@@ -343,6 +344,10 @@ struct ssh_index {
     // `owned` are referenced by stored rows; ssh_index_clear moves them to
     // `spare`, from which later host adds take their staging buffer
     std::vector<DevBuf> owned, spare;
+    // small series copies (streamed inserts) are carved from arena chunks of
+    // kArenaChunk bytes in order; ssh_index_clear rewinds to the first chunk
+    std::vector<void*> arena;
+    size_t arena_cur = 0, arena_off = 0;
     // host-API calls run on these non-blocking streams: hstream hashes and
     // queries, cstream copies host series in chunks ahead of the hashing
     cudaStream_t hstream = nullptr, cstream = nullptr;
