@@ -602,10 +602,20 @@ def run_gpu(args, w):
     lengths = np.full(N, m, np.int32)
     qlengths = np.full(nq, m, np.int32)
 
+    def exchange():
+        """N > 1: the one exchange step of a sharded query (all-gather of every shard's
+        top-k with global ids, merged on every rank)."""
+        if not dist:
+            return None
+        from paper_1610_07328_gb300 import shard
+        g_ids = torch.where(d_ids >= 0, d_ids + rank * N, d_ids)
+        return shard.allgather_topk(g_ids, d_dists, k)
+
     def step():
         idx.clear()
         idx.add_device(d_db, lengths, borrow=True)
         idx.query_device(d_q, k, d_ids, d_dists, lengths=qlengths)
+        exchange()
 
     for _ in range(args.warmup):
         step()
@@ -628,6 +638,7 @@ def run_gpu(args, w):
         idx.add_device(d_db, lengths, borrow=True)
         ev[2 + 3 * s].record(stream)
         idx.query_device(d_q, k, d_ids, d_dists, lengths=qlengths)
+        exchange()
         ev[3 + 3 * s].record(stream)
     ev[-1].record(stream)
     torch.cuda.synchronize()
