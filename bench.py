@@ -346,6 +346,41 @@ def recall_operating_point(binding, torch, d_sub, d_q, exact, w, k):
     return {"subset": n_sub, "queries": nq, "points": points, "chosen": chosen}
 
 
+def _timed_query(torch, ix, d_q, k, reps=3):
+    ids = torch.empty((d_q.shape[0], k), dtype=torch.int64, device=d_q.device)
+    dd = torch.empty((d_q.shape[0], k), dtype=torch.float32, device=d_q.device)
+    ix.query_device(d_q, k, ids, dd)  # warm-up
+    torch.cuda.synchronize()
+    ix.reset_stats()
+    best = float("inf")
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ix.query_device(d_q, k, ids, dd)
+        e1.record()
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    st = ix.stats()
+    return ids, best, st
+
+
+def exact_scan_measurement(binding, torch, d_sub, d_db, d_q, exact_sub, w, k, n_full):
+    """The comparator without hashing (SSH_OPT_EXACT_SCAN): every stored series goes through the
+    same LB_Keogh filter and early-abandoning DTW; on the recall subset and on the whole database."""
+    out = {}
+    for name, db, nq in (("subset", d_sub, d_q.shape[0]), ("full_db", d_db, n_full)):
+        with binding.SSHIndex(w["W"], w["delta"], w["n"], w["K"], w["L"], w["band"], w["seed"]) as ix:
+            ix.add_device(db, borrow=True)
+            ix.set_exact_scan(True)
+            ids, ms, st = _timed_query(torch, ix, d_q[:nq].contiguous(), k, reps=3 if name == "subset" else 1)
+            entry = {"rows": int(db.shape[0]), "queries": int(nq), "queries_per_s": nq / (ms / 1000.0),
+                     "lb_pruned_fraction": 1.0 - st["dtw_computed"] / max(st["candidates"], 1)}
+            if name == "subset":
+                entry["recall_at_10"] = recall(ids.cpu().numpy(), exact_sub)
+            out[name] = entry
+    return out
+
+
 BATCH_LENGTHS = (128, 256, 512, 1024, 2048)
 
 
@@ -426,6 +461,21 @@ def batched_measurement(args, binding, torch, dev):
         rec.append(recall(res[sel], ex))
     out["recall_at_10"] = float(np.mean(rec)) if rec else None
     out["recall_queries"] = per_len * len(BATCH_LENGTHS)
+    # pruning and speed against length (the exact scan of each collection; a Table 4 analog)
+    per_length = []
+    for ix, m in zip(idxs, BATCH_LENGTHS):
+        sel = [i for i in range(nq4) if qlens[i] == m][:8]
+        d_sel = torch.stack([d_q[offs[i]:offs[i] + m] for i in sel]).contiguous()
+        _, ms_h, st_h = _timed_query(torch, ix, d_sel, k, reps=1)
+        ix.set_exact_scan(True)
+        _, ms_e, st_e = _timed_query(torch, ix, d_sel, k, reps=1)
+        ix.set_exact_scan(False)
+        per_length.append({"m": m, "ssh_queries_per_s": len(sel) / (ms_h / 1000.0),
+                           "ssh_candidate_fraction": st_h["candidates"] / max(st_h["queries"], 1) / N4,
+                           "ssh_filtered_by_hashing": 1.0 - st_h["candidates"] / max(st_h["queries"], 1) / N4,
+                           "exact_queries_per_s": len(sel) / (ms_e / 1000.0),
+                           "exact_lb_pruned_fraction": 1.0 - st_e["dtw_computed"] / max(st_e["candidates"], 1)})
+    out["per_length"] = per_length
     out["setup_s"] = gen_s
     for ix in idxs:
         ix.close()
@@ -677,6 +727,8 @@ def run_gpu(args, w):
         extra["recall_at_1"] = float(np.mean([s_ids[i, 0] == exact_sub[i, 0] for i in range(nq)]))
         extra["recall_operating_point"] = recall_operating_point(binding, torch, d_sub.contiguous(), d_q,
                                                                  exact_sub, w, k)
+        extra["exact_scan"] = exact_scan_measurement(binding, torch, d_sub.contiguous(), d_db, d_q, exact_sub, w, k,
+                                                     n_full=4 if args.small else 10)
         if not args.fast:
             n_full = min(nq, 20)
             exact_full = exact_topk_gpu(binding, torch, d_q[:n_full].contiguous(), d_db,

@@ -221,6 +221,11 @@ void ssh_server_destroy(ssh_server* s);
  * SSH_OPT_HASH_KERNEL (default 0): 0 hashes with the kernel specialised for the
  * index's (W, delta) and series length when one is compiled in, 1 always with
  * the generic kernel (same results; a diagnostic and test knob).
+ * SSH_OPT_EXACT_SCAN (default 0): 1 makes ssh_query / ssh_query_device rank every
+ * stored series of the query's length instead of the hashed candidates: exact
+ * banded-DTW top-k through the same reporting step (LB_Keogh filter and
+ * early-abandoning DTW, as in the UCR suite the paper compares against); the
+ * comparator without hashing. Batch plans and the server always hash.
  * SSH_OPT_CWS_FP64 (default 0): 1 decides every weighted minhash by the FP64
  * recomputation instead of the FP32 fast path (same results, much slower; a
  * test knob for the recomputation itself). */
@@ -228,7 +233,8 @@ typedef enum ssh_option {
     SSH_OPT_LB_PRUNE = 1,
     SSH_OPT_KERNEL_TIMING = 2,
     SSH_OPT_HASH_KERNEL = 3,
-    SSH_OPT_CWS_FP64 = 4
+    SSH_OPT_CWS_FP64 = 4,
+    SSH_OPT_EXACT_SCAN = 5
 } ssh_option;
 ssh_status ssh_set_option(ssh_index* idx, ssh_option opt, int64_t value);
 

@@ -21,6 +21,7 @@ SSH_OPT_LB_PRUNE = 1
 SSH_OPT_KERNEL_TIMING = 2
 SSH_OPT_HASH_KERNEL = 3
 SSH_OPT_CWS_FP64 = 4
+SSH_OPT_EXACT_SCAN = 5
 
 _lib = None
 _lock = threading.Lock()
@@ -475,6 +476,10 @@ class SSHIndex:
 
     def set_cws_fp64(self, on: bool):
         ssh_set_option(self.handle, SSH_OPT_CWS_FP64, 1 if on else 0)
+
+    def set_exact_scan(self, on: bool):
+        """Rank every stored series of the query's length (exact top-k, no hashing)."""
+        ssh_set_option(self.handle, SSH_OPT_EXACT_SCAN, 1 if on else 0)
 
     def set_kernel_timing(self, on: bool):
         ssh_set_option(self.handle, SSH_OPT_KERNEL_TIMING, 1 if on else 0)

@@ -247,6 +247,12 @@ __global__ void fill_rows_kernel(const float** row_ptr, int64_t* gid, int64_t n,
     }
 }
 
+// Every segment of n lists all rows: rows[p] = p mod n.
+__global__ void iota_rows_kernel(uint32_t* rows, int64_t total, int64_t n) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < total; p += (int64_t)gridDim.x * blockDim.x)
+        rows[p] = (uint32_t)(p % n);
+}
+
 __global__ void gather_ptrs_kernel(const uint32_t* rows, int64_t n, const float* const* row_ptr, const float** out) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         out[i] = row_ptr[rows[i]];
@@ -594,35 +600,40 @@ ssh_status query_group(ssh_index* idx, SubIndex& s, const std::vector<const floa
     SSH_CUDA(cudaMemcpyAsync(d_qptr, qptr.data(), nq * sizeof(float*), cudaMemcpyHostToDevice, st));
     SSH_CUDA(cudaMemcpyAsync(d_qpos, qpos.data(), nq * sizeof(int64_t), cudaMemcpyHostToDevice, st));
 
-    // Algorithm 2: hash the queries as the stored series were hashed
-    uint64_t* qkeys;
-    SSH_TRY(sc.get(&qkeys, (size_t)L * nq));
-    HashArgs a = base_hash_args(idx, m, g);
-    a.rows = d_qptr;
-    a.count = nq;
-    a.keys = qkeys;
-    a.key_stride = nq;
-    a.key_col0 = 0;
-    SSH_TRY(run_hash(idx, a, st, "query"));
-    idx->host_stats.series_hashed += nq;
-
-    // Algorithm 2: probe every table, union of the buckets
+    // exact scan (the comparator without hashing): every stored series of the
+    // query's length is a candidate of the reporting step below
+    const bool exact = idx->exact_scan;
     const int64_t words = (s.count + 31) / 32;
-    uint32_t* bitmap;
-    int64_t* counts;
-    SSH_TRY(sc.get(&bitmap, (size_t)nq * words));
-    SSH_TRY(sc.get(&counts, nq));
-    SSH_CUDA(cudaMemsetAsync(bitmap, 0, (size_t)nq * words * sizeof(uint32_t), st));
-    ProbeArgs pa{qkeys, nq, L, s.skeys, s.srows, s.bins, s.bin_bits, s.cap, s.count, bitmap, words,
-                 s.dkeys, s.drows, s.dbins, s.dbin_bits, s.dcap, s.dcount};
-    {
-        TimedRegion tr(idx, st, "query.probe_union", (double)nq * L);
-        SSH_CUDA(launch_probe_union(pa, st));
-        SSH_CUDA(launch_bitmap_count(bitmap, nq, words, counts, st));
+    uint32_t* bitmap = nullptr;
+    std::vector<int64_t> h_counts(nq, s.count), h_begin(nq + 1);
+    if (!exact) {
+        // Algorithm 2: hash the queries as the stored series were hashed
+        uint64_t* qkeys;
+        SSH_TRY(sc.get(&qkeys, (size_t)L * nq));
+        HashArgs a = base_hash_args(idx, m, g);
+        a.rows = d_qptr;
+        a.count = nq;
+        a.keys = qkeys;
+        a.key_stride = nq;
+        a.key_col0 = 0;
+        SSH_TRY(run_hash(idx, a, st, "query"));
+        idx->host_stats.series_hashed += nq;
+
+        // Algorithm 2: probe every table, union of the buckets
+        int64_t* counts;
+        SSH_TRY(sc.get(&bitmap, (size_t)nq * words));
+        SSH_TRY(sc.get(&counts, nq));
+        SSH_CUDA(cudaMemsetAsync(bitmap, 0, (size_t)nq * words * sizeof(uint32_t), st));
+        ProbeArgs pa{qkeys, nq, L, s.skeys, s.srows, s.bins, s.bin_bits, s.cap, s.count, bitmap, words,
+                     s.dkeys, s.drows, s.dbins, s.dbin_bits, s.dcap, s.dcount};
+        {
+            TimedRegion tr(idx, st, "query.probe_union", (double)nq * L);
+            SSH_CUDA(launch_probe_union(pa, st));
+            SSH_CUDA(launch_bitmap_count(bitmap, nq, words, counts, st));
+        }
+        SSH_CUDA(cudaMemcpyAsync(h_counts.data(), counts, nq * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        SSH_CUDA(cudaStreamSynchronize(st));
     }
-    std::vector<int64_t> h_counts(nq), h_begin(nq + 1);
-    SSH_CUDA(cudaMemcpyAsync(h_counts.data(), counts, nq * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-    SSH_CUDA(cudaStreamSynchronize(st));
     h_begin[0] = 0;
     int64_t max_c = 0;
     for (int64_t q = 0; q < nq; ++q) {
@@ -643,7 +654,15 @@ ssh_status query_group(ssh_index* idx, SubIndex& s, const std::vector<const floa
     SSH_TRY(sc.get(&lb, C));
     SSH_TRY(sc.get(&dist, C));
     SSH_CUDA(cudaMemcpyAsync(seg_begin, h_begin.data(), (nq + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
-    SSH_CUDA(launch_bitmap_compact(bitmap, nq, words, seg_begin, cand_rows, nullptr, st));
+    if (exact) {
+        if (C > 0) {
+            iota_rows_kernel<<<grid_for(C, 256, 8192), 256, 0, st>>>(cand_rows, C, s.count);
+            note_launch();
+            SSH_CUDA(cudaGetLastError());
+        }
+    } else {
+        SSH_CUDA(launch_bitmap_compact(bitmap, nq, words, seg_begin, cand_rows, nullptr, st));
+    }
     if (C > 0) {
         gather_ptrs_kernel<<<grid_for(C, 256, 8192), 256, 0, st>>>(cand_rows, C, s.row_ptr, pair_b);
         note_launch();
@@ -1245,6 +1264,9 @@ ssh_status ssh_set_option(ssh_index* idx, ssh_option opt, int64_t value) {
             return SSH_OK;
         case SSH_OPT_CWS_FP64:
             idx->cws_fp64 = value != 0;
+            return SSH_OK;
+        case SSH_OPT_EXACT_SCAN:
+            idx->exact_scan = value != 0;
             return SSH_OK;
         case SSH_OPT_HASH_KERNEL:
             if (value < 0 || value > 1) return fail(SSH_EINVAL, "SSH_OPT_HASH_KERNEL takes 0 or 1");

@@ -323,6 +323,7 @@ struct ssh_index {
     uint64_t seed = 0;
     int device = 0;
     bool lb_prune = true;
+    bool exact_scan = false;          // queries rank every stored series (no hashing)
     int hash_kernel = 0;              // 0: fastest available, 1: always the generic kernel
     int cws_fp64 = 0;                 // 1: every minhash through the FP64 recomputation
     float tau_norm = 0.f;

@@ -543,3 +543,28 @@ def test_small_adds_go_to_delta_tables_then_merge():
             for i, q in enumerate(qs):
                 oi, od = ref.query(q, 5)
                 assert_topk_match(q, ids[i], d[i], oi, od, lambda j: rng_db[j], rb)
+
+
+@pytest.mark.parametrize("prune", [True, False])
+def test_exact_scan_equals_brute_force_topk(prune):
+    """SSH_OPT_EXACT_SCAN: every stored series is a candidate; the top-k must be the oracle's
+    brute-force banded-DTW top-k (LB_Keogh pruning and early abandoning change nothing)."""
+    cfg = CFG1
+    db = synth.random_walk(700, 128, seed=13)
+    qs, _ = synth.perturbed_queries(db, 7, seed=14)
+    ref = oracle.OracleIndex(**cfg)
+    ref.add(db)
+    with _index(cfg) as idx:
+        idx.add(db)
+        idx.set_exact_scan(True)
+        idx.set_lb_prune(prune)
+        idx.reset_stats()
+        ids, d = idx.query(qs, 6)
+        st = idx.stats()
+    assert st["candidates"] == 7 * 700
+    if prune:
+        assert 0 < st["dtw_computed"] < st["candidates"]
+    rb = oracle.band_radius(cfg["band"], 128)
+    for i, q in enumerate(qs):
+        oi, od = ref.exact_topk(q, 6)
+        assert_topk_match(q, ids[i], d[i], oi, od, lambda j: db[j], rb)
