@@ -9,6 +9,9 @@
         each (rows of a random-walk table larger than L2) through
         ssh_dtw_device; prints the call time of the fastest repetition.
 
+    python -m paper_1610_07328_gb300.profile_cases tables 262144
+        an index of 262,144 random walks of length 512 with the scale
+        parameters, added twice (two table builds of 25 x 262,144 entries).
     python -m paper_1610_07328_gb300.profile_cases batch 50000 1024
         five per-length indexes (m = 128 .. 2048, W = m/8, delta=3, n=15, K=4,
         L=25) of 50,000 random walks each and three batches of 1,024 mixed-length
@@ -87,9 +90,23 @@ def _batch(n: int, nq: int) -> None:
         ix.close()
 
 
+def _tables(n: int) -> None:
+    import torch
+    from . import binding, synth
+    x = torch.from_numpy(synth.random_walk(n, 512, seed=0)).cuda()
+    with binding.SSHIndex(80, 3, 15, 4, 25, 0.05, 0) as idx:
+        for _ in range(2):
+            idx.clear()
+            idx.add_device(x, borrow=True)
+        torch.cuda.synchronize()
+        print("built twice;", len(idx), "rows")
+
+
 def main(argv: list[str]) -> None:
     if len(argv) >= 2 and argv[0] == "hash":
         _hash(int(argv[1]))
+    elif len(argv) >= 2 and argv[0] == "tables":
+        _tables(int(argv[1]))
     elif len(argv) >= 3 and argv[0] == "batch":
         _batch(int(argv[1]), int(argv[2]))
     elif len(argv) >= 2 and argv[0] == "dtw":

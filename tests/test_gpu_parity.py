@@ -568,3 +568,37 @@ def test_exact_scan_equals_brute_force_topk(prune):
     for i, q in enumerate(qs):
         oi, od = ref.exact_topk(q, 6)
         assert_topk_match(q, ids[i], d[i], oi, od, lambda j: db[j], rb)
+
+
+def test_large_tables_two_pass_partition_candidates():
+    """Tables of >= 65,536 rows are binned in two passes. The candidate set of every query must be
+    the union over tables of the rows whose bucket key equals the query's (computed here from the
+    keys ssh_hash_device returns), and a stored series must find itself at distance 0."""
+    b = _binding()
+    cfg = CFG1
+    N, m = 70_000, 128
+    db = synth.random_walk(N, m, seed=71)
+    with _index(cfg) as idx:
+        idx.add(db)
+        L = idx.L
+        d_db = torch.from_numpy(db).cuda()
+        keys = torch.zeros((L, N), dtype=torch.int64, device="cuda")
+        b.ssh_hash_device(idx.handle, d_db, m, N, d_keys=keys)
+        torch.cuda.synchronize()
+        keys = keys.cpu().numpy()
+        rng = np.random.default_rng(5)
+        src = rng.integers(0, N, 6)
+        qs = np.concatenate([db[src[:3]], synth.perturbed_queries(db, 3, seed=9)[0]])
+        qkeys = torch.zeros((L, len(qs)), dtype=torch.int64, device="cuda")
+        b.ssh_hash_device(idx.handle, torch.from_numpy(qs).cuda(), m, len(qs), d_keys=qkeys)
+        torch.cuda.synchronize()
+        qkeys = qkeys.cpu().numpy()
+        for i in range(len(qs)):
+            want = np.zeros(N, bool)
+            for l in range(L):
+                want |= keys[l] == qkeys[l, i]
+            idx.reset_stats()
+            ids, d = idx.query(qs[i:i + 1], 3)
+            assert idx.stats()["candidates"] == int(want.sum())
+            if i < 3:
+                assert ids[0, 0] == src[i] and d[0, 0] == 0.0
