@@ -128,7 +128,7 @@ __global__ void bin_scatter_kernel(const uint64_t* keys, int64_t row0, int64_t n
 // per block and places its entries into the bucket's 2^(B-b1) bins.
 
 constexpr int kPartThreads = 256;
-constexpr int kPartItems = 16;                            // rows per thread of pass 1
+constexpr int kPartItems = 8;                             // rows per thread of pass 1
 constexpr int kPartChunk = kPartThreads * kPartItems;     // rows per block of pass 1
 
 // Exclusive prefix sums of a[0 .. count) in shared memory (all threads of the block).
