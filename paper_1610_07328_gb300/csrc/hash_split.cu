@@ -1,9 +1,10 @@
 // hash_split.cu -- the hash path for the compiled-in shapes as two kernels and
 // a fix-up (Sec. 4.1-4.3 and the keys of Algorithm 1):
 //
-//  sketch_kernel<W, DELTA, R>: one warp per series at a time (persistent, with
-//    the next series staged into shared memory by cp.async while the current
-//    one is processed). Lane l owns the R consecutive windows [lR, lR + R); the
+//  sketch_kernel<W, DELTA, R, SPW>: one warp per SPW series at a time
+//    (persistent, with the next series staged into shared memory by cp.async
+//    while the current one is processed). Lane l of a series' 32 / SPW lanes
+//    owns the R consecutive windows [lR, lR + R); the
 //    filter r sits in registers and the loop over the lane's W + (R-1) DELTA
 //    samples is unrolled, so each sample read from shared memory feeds up to R
 //    FMAs and the strip's energy. A window whose |r.x| is not above
@@ -50,19 +51,20 @@ __device__ __forceinline__ const float* row_ptr(const HashArgs& a, int64_t row) 
 }
 
 // Start copying series `row` into dst (m floats); misaligned rows load synchronously.
-__device__ __forceinline__ void fetch_row(const HashArgs& a, int64_t row, float* dst, int lane) {
+// (copied by the lanes l, l + lanes, ... of the series' lanes)
+__device__ __forceinline__ void fetch_row(const HashArgs& a, int64_t row, float* dst, int lane, int lanes) {
     const float* src = row_ptr(a, row);
     const int m = a.m;
     if (((reinterpret_cast<uintptr_t>(src) & 15) == 0) && (m & 3) == 0) {
-        for (int c = lane; c < (m >> 2); c += 32) cp_async16(dst + 4 * c, src + 4 * c);
+        for (int c = lane; c < (m >> 2); c += lanes) cp_async16(dst + 4 * c, src + 4 * c);
     } else {
-        for (int i = lane; i < m; i += 32) dst[i] = __ldg(src + i);
+        for (int i = lane; i < m; i += lanes) dst[i] = __ldg(src + i);
     }
 }
 
-__host__ __device__ inline int sketch_xb(int m, int W, int DELTA, int R) {
+__host__ __device__ inline int sketch_xb(int m, int W, int DELTA, int R, int LPS) {
     int xb = m;
-    const int need = 32 * R * DELTA + W;  // samples read by the padded windows of the last lanes
+    const int need = LPS * R * DELTA + W;  // samples read by the padded windows of the last lanes
     if (need > xb) xb = need;
     return (xb + 3) & ~3;
 }
@@ -77,93 +79,109 @@ struct FilterParam {
 // Provisional bits go to `bits`; windows needing FP64 go to fix[0..cap) as
 // (row << 16 | window), counted in *nfix. If the list is full the window is
 // recomputed in place.
-template <int W, int DELTA, int R>
+// SPW series per warp (1 or 2): the LPS = 32 / SPW lanes of a series own
+// R consecutive windows each; with two series per warp a lane's R windows share
+// one strip of W + (R-1) DELTA samples, so R can be twice as large for the same
+// number of windows and each sample read from shared memory feeds twice as many
+// FMAs.
+template <int W, int DELTA, int R, int SPW>
 __global__ void __launch_bounds__(kSketchWarps * 32, 3)
     sketch_kernel(HashArgs a, const FilterParam<W> rp, uint32_t* bits, unsigned long long* fix,
                   unsigned long long fix_cap, unsigned long long* nfix) {
     constexpr int STRIP = W + (R - 1) * DELTA;
+    constexpr int LPS = 32 / SPW;
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int sl = lane / LPS, ll = lane - sl * LPS;  // series slot of the warp, lane within the series
     const int m = a.m, nb = a.nb, nwords = a.nwords;
-    const int xb = sketch_xb(m, W, DELTA, R);
+    const int xb = sketch_xb(m, W, DELTA, R, LPS);
     float* r_s = reinterpret_cast<float*>(smem);
-    unsigned char* wb = smem + a16(4 * W) + (size_t)warp * (2 * a16(4 * xb) + a16(32 * R));
+    const size_t per_slot = 2 * (size_t)a16(4 * xb) + a16(LPS * R);
+    unsigned char* wb = smem + a16(4 * W) + (size_t)(warp * SPW + sl) * per_slot;
     float* xbuf[2] = {reinterpret_cast<float*>(wb), reinterpret_cast<float*>(wb + a16(4 * xb))};
     unsigned char* bytes = wb + 2 * a16(4 * xb);
     for (int j = threadIdx.x; j < W; j += blockDim.x) r_s[j] = a.r[j];
-    for (int i = m + lane; i < xb; i += 32) {  // samples past the end feed only windows past N_B
+    for (int i = m + ll; i < xb; i += LPS) {  // samples past the end feed only windows past N_B
         xbuf[0][i] = 0.f;
         xbuf[1][i] = 0.f;
     }
     __syncthreads();
 
-    const int64_t nwarps = (int64_t)gridDim.x * kSketchWarps;
+    // the warp takes SPW consecutive rows at a time: group g holds rows g SPW .. g SPW + SPW - 1
+    const int64_t ngroups = (a.count + SPW - 1) / SPW;
+    const int64_t gstride = (int64_t)gridDim.x * kSketchWarps;
     const int64_t first = (int64_t)blockIdx.x * kSketchWarps + warp;
     unsigned long long n_inplace = 0;
-    if (first < a.count) fetch_row(a, first, xbuf[0], lane);
+    if (first < ngroups && first * SPW + sl < a.count) fetch_row(a, first * SPW + sl, xbuf[0], ll, LPS);
     cp_async_commit();
     int it = 0;
-    for (int64_t row = first; row < a.count; row += nwarps, ++it) {
+    for (int64_t g = first; g < ngroups; g += gstride, ++it) {
         const int cur = it & 1;
-        if (row + nwarps < a.count) fetch_row(a, row + nwarps, xbuf[cur ^ 1], lane);
+        const int64_t row = g * SPW + sl;
+        const int64_t nrow = (g + gstride) * SPW + sl;
+        if (g + gstride < ngroups && nrow < a.count) fetch_row(a, nrow, xbuf[cur ^ 1], ll, LPS);
         cp_async_commit();
         cp_async_wait1();
         __syncwarp();
-        const float* x = xbuf[cur];
-        // the R dot products and the energy of the lane's strip of STRIP samples,
-        // which holds every window of the lane: ||x_window||^2 <= strip energy
-        float acc[R];
+        if (row < a.count) {
+            const float* x = xbuf[cur];
+            // the R dot products and the energy of the lane's strip of STRIP samples,
+            // which holds every window of the lane: ||x_window||^2 <= strip energy
+            float acc[R];
 #pragma unroll
-        for (int k = 0; k < R; ++k) acc[k] = 0.f;
-        float e = 0.f;
-        const float* xs = x + lane * R * DELTA;
+            for (int k = 0; k < R; ++k) acc[k] = 0.f;
+            float e = 0.f;
+            const float* xs = x + ll * R * DELTA;
 #pragma unroll
-        for (int t = 0; t < STRIP; ++t) {
-            const float xv = xs[t];
-            e = fmaf(xv, xv, e);
+            for (int t = 0; t < STRIP; ++t) {
+                const float xv = xs[t];
+                e = fmaf(xv, xv, e);
 #pragma unroll
-            for (int k = 0; k < R; ++k) {
-                const int j = t - k * DELTA;
-                if (j >= 0 && j < W) acc[k] = fmaf(rp.v[j], xv, acc[k]);
-            }
-        }
-        // e carries at most STRIP roundings of relative 2^-24 each: inflate it past them
-        const float e_up = __fmul_ru(e, 1.0f + (float)(2 * STRIP + 64) * 5.9604645e-08f);
-        const float thr = __fmul_ru(a.tau_norm, __fsqrt_ru(__fmul_ru(e_up, 1.0f + a.gamma_ss)));
-#pragma unroll
-        for (int k = 0; k < R; ++k) {
-            const int i = lane * R + k;
-            uint8_t bit = 0;
-            if (i < nb) {
-                if (fabsf(acc[k]) > thr) {
-                    bit = acc[k] >= 0.f;
-                } else {
-                    const unsigned long long slot = atomicAdd(nfix, 1ull);
-                    if (slot < fix_cap) {
-                        fix[slot] = ((unsigned long long)row << 16) | (unsigned long long)i;
-                    } else {
-                        const float* xw = xs + k * DELTA;
-                        double d = 0.0;  // list full: the definition's FP64 order, in place
-#pragma unroll 1
-                        for (int j = 0; j < W; ++j) d = fma((double)r_s[j], (double)xw[j], d);
-                        bit = d >= 0.0;
-                        n_inplace += 1;
-                    }
+                for (int k = 0; k < R; ++k) {
+                    const int j = t - k * DELTA;
+                    if (j >= 0 && j < W) acc[k] = fmaf(rp.v[j], xv, acc[k]);
                 }
             }
-            bytes[lane * R + k] = bit;
+            // e carries at most STRIP roundings of relative 2^-24 each: inflate it past them
+            const float e_up = __fmul_ru(e, 1.0f + (float)(2 * STRIP + 64) * 5.9604645e-08f);
+            const float thr = __fmul_ru(a.tau_norm, __fsqrt_ru(__fmul_ru(e_up, 1.0f + a.gamma_ss)));
+#pragma unroll
+            for (int k = 0; k < R; ++k) {
+                const int i = ll * R + k;
+                uint8_t bit = 0;
+                if (i < nb) {
+                    if (fabsf(acc[k]) > thr) {
+                        bit = acc[k] >= 0.f;
+                    } else {
+                        const unsigned long long slot = atomicAdd(nfix, 1ull);
+                        if (slot < fix_cap) {
+                            fix[slot] = ((unsigned long long)row << 16) | (unsigned long long)i;
+                        } else {
+                            const float* xw = xs + k * DELTA;
+                            double d = 0.0;  // list full: the definition's FP64 order, in place
+#pragma unroll 1
+                            for (int j = 0; j < W; ++j) d = fma((double)r_s[j], (double)xw[j], d);
+                            bit = d >= 0.0;
+                            n_inplace += 1;
+                        }
+                    }
+                }
+                bytes[ll * R + k] = bit;
+            }
         }
         __syncwarp();
-        uint32_t* out = bits + row * nwords;
-        for (int w = lane; w < nwords; w += 32) {
-            uint32_t word = 0;
-            const uint32_t* b4 = reinterpret_cast<const uint32_t*>(bytes) + w * 8;
+        if (row < a.count) {
+            uint32_t* out = bits + row * nwords;
+            for (int w = ll; w < nwords; w += LPS) {
+                uint32_t word = 0;
+                const uint32_t* b4 = reinterpret_cast<const uint32_t*>(bytes) + w * 8;
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const uint32_t v = (w * 32 + q * 4 < 32 * R) ? b4[q] : 0u;
-                word |= (((v * 0x08040201u) >> 24) & 0xFu) << (28 - 4 * q);  // bytes 0..3 -> bits 3..0
+                for (int q = 0; q < 8; ++q) {
+                    const uint32_t v = (w * 32 + q * 4 < LPS * R) ? b4[q] : 0u;
+                    word |= (((v * 0x08040201u) >> 24) & 0xFu) << (28 - 4 * q);  // bytes 0..3 -> bits 3..0
+                }
+                out[w] = word;
             }
-            out[w] = word;
         }
         __syncwarp();
     }
@@ -509,23 +527,23 @@ int sms_of_device() {
     return sms > 0 ? sms : 1;
 }
 
-template <int W, int DELTA, int R>
+template <int W, int DELTA, int R, int SPW>
 cudaError_t launch_sketch_t(const HashArgs& a, uint32_t* bits, unsigned long long* fix, unsigned long long cap,
                             unsigned long long* nfix, cudaStream_t st) {
-    const int xb = sketch_xb(a.m, W, DELTA, R);
-    const size_t smem = (size_t)a16(4 * W) + (size_t)kSketchWarps * (2 * a16(4 * xb) + a16(32 * R));
+    const int xb = sketch_xb(a.m, W, DELTA, R, 32 / SPW);
+    const size_t smem = (size_t)a16(4 * W) + (size_t)kSketchWarps * SPW * (2 * a16(4 * xb) + a16((32 / SPW) * R));
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
-    cudaError_t e = ensure_dynamic_smem((const void*)sketch_kernel<W, DELTA, R>, smem);
+    cudaError_t e = ensure_dynamic_smem((const void*)sketch_kernel<W, DELTA, R, SPW>, smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sketch_kernel<W, DELTA, R>, kSketchWarps * 32, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sketch_kernel<W, DELTA, R, SPW>, kSketchWarps * 32, smem);
     int64_t grid = (int64_t)sms_of_device() * (per_sm > 0 ? per_sm : 1);
-    const int64_t need = (a.count + kSketchWarps - 1) / kSketchWarps;
+    const int64_t need = ((a.count + SPW - 1) / SPW + kSketchWarps - 1) / kSketchWarps;
     if (grid > need) grid = need;
     FilterParam<W> rp;
     if (!a.r_host) return cudaErrorInvalidValue;
     for (int j = 0; j < W; ++j) rp.v[j] = a.r_host[j];
-    sketch_kernel<W, DELTA, R><<<(unsigned)grid, kSketchWarps * 32, smem, st>>>(a, rp, bits, fix, cap, nfix);
+    sketch_kernel<W, DELTA, R, SPW><<<(unsigned)grid, kSketchWarps * 32, smem, st>>>(a, rp, bits, fix, cap, nfix);
     note_launch();
     return cudaGetLastError();
 }
@@ -576,15 +594,21 @@ cudaError_t launch_cws(const HashArgs& a, const uint32_t* sets, const int2* size
     return cudaGetLastError();
 }
 
+// Compiled (W, DELTA, R, series per warp) shapes; a shape serves the N_B in
+// (LPS (R-1), LPS R] with LPS = 32 / SPW. The first match wins, so the
+// two-series shapes come first.
 struct SketchShape {
-    int W, delta, R;
+    int W, delta, R, spw;
 };
 const SketchShape kSketchShapes[] = {
-    {80, 3, 5},  {32, 3, 2},  {120, 5, 6}, {16, 3, 2}, {32, 3, 3}, {64, 3, 5}, {128, 3, 10}, {256, 3, 19},
+    {80, 3, 10, 2},  {64, 3, 10, 2}, {32, 3, 3, 2},  {32, 3, 5, 2}, {16, 3, 3, 2}, {120, 5, 12, 2},
+    {128, 3, 19, 2}, {80, 3, 5, 1},  {32, 3, 2, 1},  {120, 5, 6, 1}, {16, 3, 2, 1}, {32, 3, 3, 1},
+    {64, 3, 5, 1},   {128, 3, 10, 1}, {256, 3, 19, 1},
 };
 
 bool sketch_shape_ok(const SketchShape& s, const HashArgs& a) {
-    return s.W == a.W && s.delta == a.delta && a.nb <= 32 * s.R && a.nb > 32 * (s.R - 1) && a.nb < 65536;
+    const int lps = 32 / s.spw;
+    return s.W == a.W && s.delta == a.delta && a.nb <= lps * s.R && a.nb > lps * (s.R - 1) && a.nb < 65536;
 }
 
 }  // namespace
@@ -637,16 +661,24 @@ cudaError_t hash_fast_sketch(const HashArgs& a, const FastHashBuffers& b, cudaSt
     if (e != cudaSuccess) return e;
     for (const SketchShape& s : kSketchShapes) {
         if (!sketch_shape_ok(s, a)) continue;
-#define SSH_SKETCH_CASE(W_, D_, R_) \
-    if (s.W == W_ && s.delta == D_ && s.R == R_) return launch_sketch_t<W_, D_, R_>(a, b.bits, b.fix, b.fix_cap, b.nfix, st);
-        SSH_SKETCH_CASE(80, 3, 5)
-        SSH_SKETCH_CASE(32, 3, 2)
-        SSH_SKETCH_CASE(120, 5, 6)
-        SSH_SKETCH_CASE(16, 3, 2)
-        SSH_SKETCH_CASE(32, 3, 3)
-        SSH_SKETCH_CASE(64, 3, 5)
-        SSH_SKETCH_CASE(128, 3, 10)
-        SSH_SKETCH_CASE(256, 3, 19)
+#define SSH_SKETCH_CASE(W_, D_, R_, P_)                                           \
+    if (s.W == W_ && s.delta == D_ && s.R == R_ && s.spw == P_)                     \
+        return launch_sketch_t<W_, D_, R_, P_>(a, b.bits, b.fix, b.fix_cap, b.nfix, st);
+        SSH_SKETCH_CASE(80, 3, 10, 2)
+        SSH_SKETCH_CASE(64, 3, 10, 2)
+        SSH_SKETCH_CASE(32, 3, 3, 2)
+        SSH_SKETCH_CASE(32, 3, 5, 2)
+        SSH_SKETCH_CASE(16, 3, 3, 2)
+        SSH_SKETCH_CASE(120, 5, 12, 2)
+        SSH_SKETCH_CASE(128, 3, 19, 2)
+        SSH_SKETCH_CASE(80, 3, 5, 1)
+        SSH_SKETCH_CASE(32, 3, 2, 1)
+        SSH_SKETCH_CASE(120, 5, 6, 1)
+        SSH_SKETCH_CASE(16, 3, 2, 1)
+        SSH_SKETCH_CASE(32, 3, 3, 1)
+        SSH_SKETCH_CASE(64, 3, 5, 1)
+        SSH_SKETCH_CASE(128, 3, 10, 1)
+        SSH_SKETCH_CASE(256, 3, 19, 1)
 #undef SSH_SKETCH_CASE
     }
     return cudaErrorInvalidValue;
