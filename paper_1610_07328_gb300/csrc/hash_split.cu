@@ -200,7 +200,19 @@ __global__ void sketch_fixup_kernel(HashArgs a, uint32_t* bits, const unsigned l
         const int i = (int)(v & 0xFFFFu);
         const float* xw = row_ptr(a, row) + i * a.delta;
         double d = 0.0;
-        for (int j = 0; j < a.W; ++j) d = fma((double)a.r[j], (double)xw[j], d);
+        int j = 0;
+        // groups of 8: the loads are issued together, the FMAs stay in the definition's order
+        for (; j + 8 <= a.W; j += 8) {
+            float xv[8], rv[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                xv[u] = __ldg(xw + j + u);
+                rv[u] = __ldg(a.r + j + u);
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) d = fma((double)rv[u], (double)xv[u], d);
+        }
+        for (; j < a.W; ++j) d = fma((double)__ldg(a.r + j), (double)__ldg(xw + j), d);
         if (d >= 0.0) atomicOr(&bits[row * a.nwords + (i >> 5)], 1u << (31 - (i & 31)));
     }
     if (blockIdx.x == 0 && threadIdx.x == 0 && a.stats && n) atomicAdd(&a.stats[kStatSketch64], n);
