@@ -97,7 +97,9 @@ ssh_status ssh_index_add(ssh_index* idx, const float* series, const int32_t* len
  * Without SSH_ADD_BORROW the series are copied into index-owned device memory.
  * With SSH_ADD_BORROW the index keeps d_series itself: the caller must keep that
  * buffer allocated and unchanged until ssh_index_clear or ssh_destroy.
- * Work is ordered on `stream`; the call returns after the tables are rebuilt. */
+ * Work is ordered on `stream` and the call returns once it is enqueued: later work
+ * on `stream`, and every query of this library on any stream, runs after the
+ * tables are rebuilt (queries wait for the index's latest add). */
 ssh_status ssh_index_add_device(ssh_index* idx, const float* d_series, const int32_t* lengths, int64_t count,
                                 uint32_t flags, void* stream, int64_t* first_id);
 

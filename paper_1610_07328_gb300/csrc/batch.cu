@@ -605,6 +605,7 @@ ssh_status batch_prepare(ssh_batch* b, const float* d_queries, const int32_t* le
 // Start the prepared batch on the plan's stream (the captured graph, or the
 // kernels themselves for a plan's first batch); returns without waiting.
 ssh_status batch_launch(ssh_batch* b) {
+    for (ssh_index* h : b->handles) SSH_CUDA(cudaStreamWaitEvent(b->st, h->ready, 0));  // latest adds' tables
     b->eager = b->exec == nullptr;
     if (b->eager) {
         SSH_TRY(enqueue_pipeline(b));

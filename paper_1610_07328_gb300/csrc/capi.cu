@@ -513,14 +513,16 @@ ssh_status hash_range(ssh_index* idx, const float* dev, const int32_t* lengths, 
     return SSH_OK;
 }
 
-// Rebuild the tables of the touched sub-indexes and wait for the call's work.
+// Rebuild the tables of the touched sub-indexes and mark the index ready after
+// them (the event queries wait for); `sync`: also wait for the call's work.
 ssh_status finish_add(ssh_index* idx, const std::vector<int>& touched, int64_t count, cudaStream_t st,
-                      int64_t* first_id) {
+                      int64_t* first_id, bool sync) {
     for (int m : touched) {
         TimedRegion tr(idx, st, "add.table_sort", (double)idx->subs[m].count * idx->L);
         SSH_TRY(rebuild_tables(idx, idx->subs[m], st));
     }
-    SSH_CUDA(cudaStreamSynchronize(st));
+    SSH_CUDA(cudaEventRecord(idx->ready, st));
+    if (sync) SSH_CUDA(cudaStreamSynchronize(st));
     if (first_id) *first_id = idx->next_id;
     idx->next_id += count;
     idx->version += 1;
@@ -533,7 +535,7 @@ ssh_status add_series(ssh_index* idx, const float* dev, const int32_t* lengths, 
     SSH_TRY(validate_lengths(idx, lengths, count));
     std::vector<int> touched;
     SSH_TRY(hash_range(idx, dev, lengths, 0, count, idx->next_id, st, touched));
-    return finish_add(idx, touched, count, st, first_id);
+    return finish_add(idx, touched, count, st, first_id, false);
 }
 
 constexpr size_t kArenaChunk = (size_t)256 << 20;
@@ -776,6 +778,7 @@ ssh_status query_group(ssh_index* idx, SubIndex& s, const std::vector<const floa
 ssh_status run_query(ssh_index* idx, const float* d_queries, const int32_t* lengths, int64_t nq, int k,
                      int64_t* d_ids, float* d_dists, cudaStream_t st) {
     if (k < 1 || k > kMaxTopK) return fail(SSH_EINVAL, "k = %d outside [1, %d]", k, kMaxTopK);
+    SSH_CUDA(cudaStreamWaitEvent(st, idx->ready, 0));  // the latest add's tables
     std::map<int, std::pair<std::vector<const float*>, std::vector<int64_t>>> groups;
     int64_t off = 0;
     for (int64_t i = 0; i < nq; ++i) {
@@ -899,6 +902,7 @@ ssh_status ssh_create(int W, int delta, int n, int K, int L, float band, uint64_
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&idx->cstream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&idx->cevent, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMallocHost(&idx->h_pinned, 8 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&idx->ready, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         ssh_status st = cuda_status(e, "ssh_create streams");
         ssh_destroy(idx);
@@ -996,6 +1000,7 @@ void ssh_destroy(ssh_index* idx) {
     for (void* p : idx->arena) cudaFree(p);
     if (idx->cevent) cudaEventDestroy(idx->cevent);
     if (idx->h_pinned) cudaFreeHost(idx->h_pinned);
+    if (idx->ready) cudaEventDestroy(idx->ready);
     if (idx->hstream) cudaStreamDestroy(idx->hstream);
     if (idx->cstream) cudaStreamDestroy(idx->cstream);
     for (auto& t : idx->pending) {
@@ -1056,7 +1061,7 @@ static ssh_status index_add_impl(ssh_index* idx, const float* series, const int3
         off += bytes / 4;
         i = j;
     }
-    if (status == SSH_OK) status = finish_add(idx, touched, count, st, first_id);
+    if (status == SSH_OK) status = finish_add(idx, touched, count, st, first_id, true);
     if (status != SSH_OK) {
         cudaStreamSynchronize(cs);
         cudaStreamSynchronize(st);
@@ -1232,6 +1237,7 @@ ssh_status ssh_group_query_device(ssh_index* const* handles, int nh, const float
     for (auto& kv : groups) {
         ssh_index* idx = handles[kv.first.first];
         SSH_TRY(check_device(idx));
+        SSH_CUDA(cudaStreamWaitEvent(st, idx->ready, 0));  // the latest add's tables
         LaunchCount lc(idx);
         SSH_TRY(query_group(idx, idx->subs[kv.first.second], kv.second.first, kv.second.second, k, d_ids, d_dists, st));
         if (d_which) {
@@ -1278,6 +1284,7 @@ ssh_status ssh_set_option(ssh_index* idx, ssh_option opt, int64_t value) {
 
 ssh_status ssh_get_stats(const ssh_index* idx, ssh_stats* out) {
     if (!idx || !out) return fail(SSH_EINVAL, "NULL argument");
+    SSH_CUDA(cudaEventSynchronize(idx->ready));
     unsigned long long dev[kNumStatSlots] = {0};
     SSH_CUDA(cudaMemcpy(dev, idx->d_stats, sizeof(dev), cudaMemcpyDeviceToHost));
     *out = idx->host_stats;

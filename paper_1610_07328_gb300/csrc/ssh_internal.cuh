@@ -354,5 +354,8 @@ struct ssh_index {
     cudaStream_t hstream = nullptr, cstream = nullptr;
     cudaEvent_t cevent = nullptr;
     unsigned long long* h_pinned = nullptr;  // small pinned host buffer for per-call device counters
+    // recorded after the work of the latest add: device adds return once their
+    // work is enqueued, and every query waits for this event on its own stream
+    cudaEvent_t ready = nullptr;
     uint64_t version = 0;                    // bumped by every add and clear (batch plans check it)
 };
