@@ -9,7 +9,8 @@
 // and the candidate offsets the pipeline computes itself -- so one captured
 // graph serves any batch of the plan. The host writes the query table into
 // pinned memory; the graph copies it in, hashes each class's queries (Sec.
-// 4.1-4.3), probes and unions the buckets (Algorithm 2), bounds the candidates
+// 4.1-4.3, with the specialised kernels where the class's shape has them),
+// probes and unions the buckets (Algorithm 2), bounds the candidates
 // by LB_Keogh (Sec. 3) and reranks them by banded DTW (Sec. 2.1) with the
 // tiling the autotuner chose for the class's (length, radius), and writes the
 // top-k. A batch whose candidates exceed the pair capacity sets a flag; the
@@ -250,6 +251,8 @@ struct ssh_batch {
     unsigned char* d_plan = nullptr;
     PlanView hv{}, dv{};
     ClassDev* d_cls = nullptr;
+    ClassDev* h_cls = nullptr;    // pinned staging of the class descriptors
+    void* hscratch = nullptr;     // scratch of the specialised hash kernels (largest class, qcap rows)
     BatchStatus* h_status = nullptr;
     BatchStatus* d_status = nullptr;
     // per-query buffers
@@ -318,6 +321,10 @@ void free_plan(ssh_batch* b) {
     cudaFreeHost(b->h_plan);
     cudaFree(b->d_plan);
     cudaFree(b->d_cls);
+    cudaFreeHost(b->h_cls);
+    b->h_cls = nullptr;
+    cudaFree(b->hscratch);
+    b->hscratch = nullptr;
     cudaFree(b->qkeys);
     cudaFree(b->bitmap);
     cudaFree(b->counts);
@@ -388,6 +395,14 @@ ssh_status build_plan(ssh_batch* b) {
     cudaError_t e = cudaMallocHost(&b->h_plan, plan_bytes);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_plan, plan_bytes);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_cls, C * sizeof(ClassDev));
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_cls, C * sizeof(ClassDev));
+    size_t hbytes = 256;
+    for (const ssh_batch::HostClass& hc : b->cls) {
+        HashArgs a = hc.a;
+        a.count = Q;
+        if (!a.force_generic && hash_fast_supported(a)) hbytes = std::max(hbytes, hash_fast_scratch_bytes(a));
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&b->hscratch, hbytes);
     if (e == cudaSuccess) e = cudaMalloc(&b->qkeys, (size_t)b->Lmax * Q * 8);
     if (e == cudaSuccess) e = cudaMalloc(&b->bitmap, (size_t)Q * b->max_words * 4);
     if (e == cudaSuccess) e = cudaMalloc(&b->counts, (size_t)Q * 8);
@@ -439,8 +454,16 @@ ssh_status enqueue_pipeline(ssh_batch* b) {
         a.keys = b->qkeys;
         a.key_stride = Q;
         a.key_col0 = 0;
-        a.force_generic = 1;
-        SSH_CUDA(launch_hash_generic(a, st));
+        if (!a.force_generic && hash_fast_supported(a)) {
+            // the specialised kernels, on the plan's scratch (rows are absolute in the sorted table)
+            const FastHashBuffers hb = hash_fast_buffers(a, b->hscratch);
+            SSH_CUDA(hash_fast_sketch(a, hb, st));
+            SSH_CUDA(hash_fast_fixup(a, hb, st));
+            SSH_CUDA(hash_fast_shingle(a, hb, st));
+            SSH_CUDA(hash_fast_cws(a, hb, st));
+        } else {
+            SSH_CUDA(launch_hash_generic(a, st));
+        }
     }
     // Algorithm 2: probe, union, candidates
     batch_probe_kernel<<<dim3((unsigned)Q, (unsigned)b->Lmax), 256, 0, st>>>(d.nq, d.q_cls, b->d_cls, b->qkeys, Q,
@@ -460,7 +483,8 @@ ssh_status enqueue_pipeline(ssh_batch* b) {
     for (int c = 0; c < C; ++c) {
         const ssh_batch::HostClass& hc = b->cls[c];
         SSH_CUDA(launch_envelope(d.q_ptr, Q, hc.m, hc.rb, b->upper, b->lower, st, d.cls_begin + c, b->max_m));
-        PairSet ps{b->seg_begin, Q, d.q_ptr, b->pair_b, nullptr, kLbGridPairs, d.cls_begin + c, b->max_m, kGridSegs};
+        PairSet ps{b->seg_begin, Q, d.q_ptr, b->pair_b, nullptr, kLbGridPairs, d.cls_begin + c, b->max_m,
+                   std::min<int64_t>(kGridSegs, Q)};
         SSH_CUDA(launch_lb_keogh(ps, b->upper, b->lower, hc.m, b->lb, st));
     }
     // Sec. 2.1 rerank: DTW of the k smallest-LB candidates bounds the k-th
@@ -475,7 +499,8 @@ ssh_status enqueue_pipeline(ssh_batch* b) {
         SSH_CUDA(launch_filter(f, st));
         for (int c = 0; c < C; ++c) {
             const ssh_batch::HostClass& hc = b->cls[c];
-            PairSet ps{b->fbegin, Q, d.q_ptr, b->fb, b->fslot, kDtwGridPairs, d.cls_begin + c, 0, kGridSegs};
+            PairSet ps{b->fbegin, Q, d.q_ptr, b->fb, b->fslot, kDtwGridPairs, d.cls_begin + c, 0,
+                       std::min<int64_t>(kGridSegs, Q)};
             if (mode == 1) {  // survivors: stop at the bound U of the seeds' k-th distance
                 ps.abandon = b->U;
                 ps.abandon_shrink = shrink;
@@ -554,8 +579,11 @@ ssh_status batch_refresh(ssh_batch* b) {
         }
     }
     if (!same || ncls != (int)b->cls.size()) return build_plan(b);
-    SSH_CUDA(cudaStreamSynchronize(b->st));
-    SSH_CUDA(cudaMemcpy(b->d_cls, dev.data(), dev.size() * sizeof(ClassDev), cudaMemcpyHostToDevice));
+    // stream-ordered on the plan's stream: after the batches that read the old
+    // descriptors, before the next one (the pinned copy is not rewritten before
+    // that batch has finished: every batch is finished before the next prepare)
+    memcpy(b->h_cls, dev.data(), dev.size() * sizeof(ClassDev));
+    SSH_CUDA(cudaMemcpyAsync(b->d_cls, b->h_cls, dev.size() * sizeof(ClassDev), cudaMemcpyHostToDevice, b->st));
     for (size_t h = 0; h < b->handles.size(); ++h) b->versions[h] = b->handles[h]->version;
     return SSH_OK;
 }
@@ -645,6 +673,25 @@ ssh_status batch_finish(ssh_batch* b) {
     return SSH_OK;
 }
 
+// Queries through a plan into the caller's rows, ordered on stream `us`.
+ssh_status batch_query_into(ssh_batch* b, const float* d_queries, const int32_t* lengths, int64_t nq,
+                            int64_t* d_ids, float* d_dists, int32_t* d_which, cudaStream_t us) {
+    SSH_TRY(batch_prepare(b, d_queries, lengths, nq));
+    SSH_CUDA(cudaEventRecord(b->ev_in, us));
+    SSH_CUDA(cudaStreamWaitEvent(b->st, b->ev_in, 0));
+    SSH_TRY(batch_launch(b));
+    SSH_TRY(batch_finish(b));
+    SSH_CUDA(cudaMemcpyAsync(d_ids, b->out_ids, (size_t)nq * b->k * 8, cudaMemcpyDeviceToDevice, b->st));
+    SSH_CUDA(cudaMemcpyAsync(d_dists, b->out_dists, (size_t)nq * b->k * 4, cudaMemcpyDeviceToDevice, b->st));
+    if (d_which) SSH_CUDA(cudaMemcpyAsync(d_which, b->out_which, (size_t)nq * 4, cudaMemcpyDeviceToDevice, b->st));
+    SSH_CUDA(cudaEventRecord(b->ev_out, b->st));
+    SSH_CUDA(cudaStreamWaitEvent(us, b->ev_out, 0));
+    return SSH_OK;
+}
+
+int64_t batch_capacity(const ssh_batch* b) { return b->qcap; }
+int batch_k(const ssh_batch* b) { return b->k; }
+
 void batch_outputs(const ssh_batch* b, const int64_t** ids, const float** dists, const int32_t** which) {
     *ids = b->out_ids;
     *dists = b->out_dists;
@@ -715,18 +762,7 @@ ssh_status ssh_batch_query(ssh_batch* b, const float* d_queries, const int32_t* 
     if (!b || nq < 0 || (nq > 0 && (!d_queries || !lengths || !d_ids || !d_dists)))
         return fail_status(SSH_EINVAL, "bad arguments");
     if (nq == 0) return SSH_OK;
-    SSH_TRY(batch_prepare(b, d_queries, lengths, nq));
-    cudaStream_t us = (cudaStream_t)stream;
-    SSH_CUDA(cudaEventRecord(b->ev_in, us));
-    SSH_CUDA(cudaStreamWaitEvent(b->st, b->ev_in, 0));
-    SSH_TRY(batch_launch(b));
-    SSH_TRY(batch_finish(b));
-    SSH_CUDA(cudaMemcpyAsync(d_ids, b->out_ids, (size_t)nq * b->k * 8, cudaMemcpyDeviceToDevice, b->st));
-    SSH_CUDA(cudaMemcpyAsync(d_dists, b->out_dists, (size_t)nq * b->k * 4, cudaMemcpyDeviceToDevice, b->st));
-    if (d_which) SSH_CUDA(cudaMemcpyAsync(d_which, b->out_which, (size_t)nq * 4, cudaMemcpyDeviceToDevice, b->st));
-    SSH_CUDA(cudaEventRecord(b->ev_out, b->st));
-    SSH_CUDA(cudaStreamWaitEvent(us, b->ev_out, 0));
-    return SSH_OK;
+    return batch_query_into(b, d_queries, lengths, nq, d_ids, d_dists, d_which, (cudaStream_t)stream);
 }
 
 ssh_status ssh_batch_stats(const ssh_batch* b, int64_t* pairs, int64_t* dtw, int64_t* pair_capacity,

@@ -46,6 +46,18 @@ __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
+// Rows [r0, r1) a launch hashes: 0 .. count-1, or the device range of a batch
+// plan (rows are then absolute in the plan's sorted query table and scratch).
+__device__ __forceinline__ void row_range(const HashArgs& a, int64_t* r0, int64_t* r1) {
+    if (a.dev_range) {
+        *r0 = a.dev_range[0];
+        *r1 = min(a.dev_range[1], *r0 + a.count);
+    } else {
+        *r0 = 0;
+        *r1 = a.count;
+    }
+}
+
 __device__ __forceinline__ const float* row_ptr(const HashArgs& a, int64_t row) {
     return a.rows ? a.rows[row] : a.series + row * a.stride;
 }
@@ -108,22 +120,24 @@ __global__ void __launch_bounds__(kSketchWarps * 32, 3)
     __syncthreads();
 
     // the warp takes SPW consecutive rows at a time: group g holds rows g SPW .. g SPW + SPW - 1
-    const int64_t ngroups = (a.count + SPW - 1) / SPW;
+    int64_t r0, r1;
+    row_range(a, &r0, &r1);
+    const int64_t ngroups = (r1 - r0 + SPW - 1) / SPW;
     const int64_t gstride = (int64_t)gridDim.x * kSketchWarps;
     const int64_t first = (int64_t)blockIdx.x * kSketchWarps + warp;
     unsigned long long n_inplace = 0;
-    if (first < ngroups && first * SPW + sl < a.count) fetch_row(a, first * SPW + sl, xbuf[0], ll, LPS);
+    if (first < ngroups && r0 + first * SPW + sl < r1) fetch_row(a, r0 + first * SPW + sl, xbuf[0], ll, LPS);
     cp_async_commit();
     int it = 0;
     for (int64_t g = first; g < ngroups; g += gstride, ++it) {
         const int cur = it & 1;
-        const int64_t row = g * SPW + sl;
-        const int64_t nrow = (g + gstride) * SPW + sl;
-        if (g + gstride < ngroups && nrow < a.count) fetch_row(a, nrow, xbuf[cur ^ 1], ll, LPS);
+        const int64_t row = r0 + g * SPW + sl;
+        const int64_t nrow = r0 + (g + gstride) * SPW + sl;
+        if (g + gstride < ngroups && nrow < r1) fetch_row(a, nrow, xbuf[cur ^ 1], ll, LPS);
         cp_async_commit();
         cp_async_wait1();
         __syncwarp();
-        if (row < a.count) {
+        if (row < r1) {
             const float* x = xbuf[cur];
             // the R dot products and the energy of the lane's strip of STRIP samples,
             // which holds every window of the lane: ||x_window||^2 <= strip energy
@@ -170,7 +184,7 @@ __global__ void __launch_bounds__(kSketchWarps * 32, 3)
             }
         }
         __syncwarp();
-        if (row < a.count) {
+        if (row < r1) {
             uint32_t* out = bits + row * nwords;
             for (int w = ll; w < nwords; w += LPS) {
                 uint32_t word = 0;
@@ -273,7 +287,9 @@ __global__ void __launch_bounds__(256) shingle_kernel(HashArgs a, const uint32_t
     const unsigned lt = (1u << lane) - 1u;
     const int rounds = (S + 31) >> 5;
     const int64_t nwarps = (int64_t)gridDim.x * wpb;
-    for (int64_t row = (int64_t)blockIdx.x * wpb + warp; row < a.count; row += nwarps) {
+    int64_t r0, r1;
+    row_range(a, &r0, &r1);
+    for (int64_t row = r0 + (int64_t)blockIdx.x * wpb + warp; row < r1; row += nwarps) {
         const uint32_t* brow = gbits + row * nwords;
         uint32_t hi = __ldg(brow);
         for (int t = 0; t < rounds; ++t) {
@@ -421,7 +437,9 @@ __global__ void __launch_bounds__(256, 4) cws_kernel(HashArgs a, const uint32_t*
     const int kstride = a.rank_stride;
     unsigned long long n64c = 0;
     const int64_t nwarps = (int64_t)gridDim.x * wpb;
-    for (int64_t row = (int64_t)blockIdx.x * wpb + warp; row < a.count; row += nwarps) {
+    int64_t r0, r1;
+    row_range(a, &r0, &r1);
+    for (int64_t row = r0 + (int64_t)blockIdx.x * wpb + warp; row < r1; row += nwarps) {
         const int2 sz = __ldg(sizes + row);
         const int n1 = sz.x, nm = sz.y;
         for (int e = lane; e < n1 + nm; e += 32) set[e] = __ldg(sets + row * S + e);

@@ -263,6 +263,10 @@ ssh_status batch_refresh(ssh_batch* b);
 void batch_outputs(const ssh_batch* b, const int64_t** ids, const float** dists, const int32_t** which);
 cudaStream_t batch_stream(const ssh_batch* b);
 size_t batch_device_bytes(const ssh_batch* b);
+ssh_status batch_query_into(ssh_batch* b, const float* d_queries, const int32_t* lengths, int64_t nq,
+                            int64_t* d_ids, float* d_dists, int32_t* d_which, cudaStream_t us);
+int64_t batch_capacity(const ssh_batch* b);
+int batch_k(const ssh_batch* b);
 
 // k-th smallest key of each segment (keys read through `keys`, segment s is
 // [seg_begin[s], seg_begin[s+1])); kth_out[s] = that key, or all-ones if the
@@ -357,5 +361,6 @@ struct ssh_index {
     // recorded after the work of the latest add: device adds return once their
     // work is enqueued, and every query waits for this event on its own stream
     cudaEvent_t ready = nullptr;
+
     uint64_t version = 0;                    // bumped by every add and clear (batch plans check it)
 };
