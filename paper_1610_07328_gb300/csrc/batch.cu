@@ -489,7 +489,8 @@ ssh_status enqueue_pipeline(ssh_batch* b) {
     }
     // Sec. 2.1 rerank: DTW of the k smallest-LB candidates bounds the k-th
     // distance; DTW of the others only where LB (1 - eta) stays below it
-    SSH_CUDA(launch_select_kth_u32(reinterpret_cast<const uint32_t*>(b->lb), b->seg_begin, Q, b->k, b->T, st));
+    SSH_CUDA(launch_select_kth_u32(reinterpret_cast<const uint32_t*>(b->lb), b->seg_begin, Q, kSeedFactor * b->k, b->T,
+                                       st));
     const float shrink = (float)(1.0 - 4.0 * (b->max_m + 3) * std::ldexp(1.0, -24));
     for (int mode = 0; mode < 2; ++mode) {
         if (mode == 1)

@@ -698,7 +698,7 @@ ssh_status query_group(ssh_index* idx, SubIndex& s, const std::vector<const floa
         uint32_t *T, *U;
         SSH_TRY(sc.get(&T, nq));
         SSH_TRY(sc.get(&U, nq));
-        SSH_CUDA(launch_select_kth_u32(reinterpret_cast<const uint32_t*>(lb), seg_begin, nq, k, T, st));
+        SSH_CUDA(launch_select_kth_u32(reinterpret_cast<const uint32_t*>(lb), seg_begin, nq, kSeedFactor * k, T, st));
         // eta bounds the FP32 rounding of LB (m + 3 terms) and of DTW (2m terms): 4 (m + 3) 2^-24
         const float shrink = (float)(1.0 - 4.0 * (m + 3) * std::ldexp(1.0, -24));
         int64_t *fcount, *fbegin;

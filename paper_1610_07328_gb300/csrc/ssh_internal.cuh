@@ -55,6 +55,10 @@ constexpr int kMaxCount = 65535;        // shingles per series (u16 counts)
 // a lane's 4 consecutive hashes are one aligned 8-byte (ranks) or 16-byte load.
 inline int rank_stride_of(int KL) { return (KL + 3) & ~3; }
 constexpr int kMaxTopK = 1024;
+// The rerank's seeds are the kSeedFactor k candidates of smallest LB_Keogh; the
+// k-th smallest DTW among them bounds the k-th best distance (pruning and early
+// abandoning against it never change the result; more seeds give a tighter bound).
+constexpr int kSeedFactor = 16;
 constexpr int kTabCounts = 8;           // counts whose ln a is tabulated exactly rounded
 constexpr int kMaxW = 8192;
 constexpr int kMaxKL = 4096;
