@@ -62,6 +62,23 @@ def peaks():
     return dict(hbm_gbs=6800.0, source="fallback")
 
 
+def l2_read_gbs(torch, dev):
+    """L2 read bandwidth measured here: repeated reductions of a 32 MB tensor that stays in
+    L2 (129 MB), so the bytes come from L2, not HBM (a torch reduction kernel; plumbing)."""
+    x = torch.ones(8 << 20, dtype=torch.float32, device=dev)
+    for _ in range(5):
+        x.sum()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 200
+    e0.record()
+    for _ in range(reps):
+        x.sum()
+    e1.record()
+    e1.synchronize()
+    return x.numel() * 4 * reps / (e0.elapsed_time(e1) / 1000.0) / 1e9
+
+
 def fp32_peak_tflops():
     # 152 SMs x 128 FP32 lanes x 2 FLOP (FMA) x 2.07 GHz maximum SM clock
     return NUM_SMS * FP32_LANES_PER_SM * 2 * MAX_SM_MHZ * 1e6 / 1e12
@@ -201,8 +218,9 @@ KERNEL_SOURCES = {
 }
 
 
-def traffic_for(group):
-    """DRAM bytes per launch from a committed ncu summary, if taken on the current source."""
+def traffic_for(group, field="bytes_per_launch"):
+    """DRAM bytes (or another field) per launch from a committed ncu summary, if taken on the
+    current source."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     stage = group.split(".", 1)[-1]
     if not os.path.exists(path) or stage not in KERNEL_SOURCES:
@@ -212,7 +230,7 @@ def traffic_for(group):
     e = t.get(group)
     if not e or e.get("source_digest") != source_digest(KERNEL_SOURCES[stage]):
         return None
-    return e.get("bytes_per_launch")
+    return e.get(field)
 
 
 def algorithmic(w, stage):
@@ -791,6 +809,15 @@ def run_gpu(args, w):
     roofline = {"kernel": dominant, "bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"],
                 "unit": d["unit"], "frac": d["frac"], "traffic": traffic_for(dominant),
                 "peak_source": pk["source"] if d["unit"] == "GB/s" else "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
+    l2b = traffic_for(dominant, "l2_read_bytes_per_launch")
+    if l2b:
+        # the minhash kernel's binding resource: its L2 reads (rank-row gathers) per launch from the
+        # ncu capture, over its CUDA-event time, against the L2 read bandwidth measured in this run
+        l2_peak = l2_read_gbs(torch, dev)
+        ach = l2b / (d["avg_ms"] / 1000.0) / 1e9
+        roofline["binding"] = {"resource": "L2 reads (gathers)", "bytes_per_launch": l2b, "achieved": ach,
+                               "peak": l2_peak, "unit": "GB/s", "frac": ach / l2_peak,
+                               "peak_source": "measured here: reductions over a 32 MB L2-resident tensor"}
 
     line = {
         "metric": METRIC, "value": value, "unit": "series/s", "n_gpus": world, "steps": args.steps,
