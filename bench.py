@@ -247,8 +247,8 @@ def algorithmic(w, stage):
         return "hbm", 4 * S + 8 * L
     if stage == "hash_generic":
         return "hbm", 4 * m + 8 * L
-    if stage == "table_sort":   # per table entry: one read and one write of (key, row)
-        return "hbm", 24
+    if stage == "table_sort":   # per table entry: the key read once, (key, row) written once
+        return "hbm", 20
     if stage == "lb_keogh":     # per candidate sample read
         return "hbm", 4
     if stage == "dtw":          # per DTW cell: difference and fused square-add (3 FLOP)
