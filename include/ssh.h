@@ -334,6 +334,15 @@ ssh_status ssh_dtw_device(const float* d_a, const int64_t* d_a_idx, const float*
 ssh_status ssh_lb_keogh_device(const float* d_a, const int64_t* d_a_idx, const float* d_b, const int64_t* d_b_idx,
                                int64_t npairs, int32_t m, int32_t rb, float* d_out, void* stream);
 
+/* Measurement helper, not part of the method: reads the `bytes` bytes at d_buf
+ * (16-byte aligned, bytes a multiple of 16) `passes` times in one kernel launch
+ * on `stream`, with loads that bypass L1, and returns once the launch is enqueued.
+ * A buffer that fits in L2 gives the L2 read bandwidth when the caller times the
+ * launch with events on that stream: bytes * passes / time. The buffer is only
+ * read. SSH_EINVAL for a null or unaligned buffer, a size that is zero or not a
+ * multiple of 16, or passes < 1; SSH_ECUDA if the launch fails. */
+ssh_status ssh_read_device(const void* d_buf, uint64_t bytes, int32_t passes, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

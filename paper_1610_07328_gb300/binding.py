@@ -98,6 +98,7 @@ _SIGS = {
     "ssh_hash_device_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int64, _P] + [_P] * 7),
     "ssh_dtw_device": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _P, _P]),
     "ssh_lb_keogh_device": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _P, _P]),
+    "ssh_read_device": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_int32, _P]),
 }
 EXPORTED = tuple(_SIGS)
 
@@ -407,6 +408,12 @@ def ssh_dtw_device(d_a, d_a_idx, d_b, d_b_idx, m: int, rb: int, d_out, stream=No
 def ssh_lb_keogh_device(d_a, d_a_idx, d_b, d_b_idx, m: int, rb: int, d_out, stream=None) -> None:
     _check(load().ssh_lb_keogh_device(_dev_ptr(d_a), _dev_ptr(d_a_idx), _dev_ptr(d_b), _dev_ptr(d_b_idx),
                                       d_a_idx.numel(), m, rb, _dev_ptr(d_out), _stream(stream)))
+
+
+def ssh_read_device(d_buf, passes: int, stream=None) -> None:
+    """Enqueue `passes` L1-bypassing reads of the whole of d_buf (a measurement helper)."""
+    _check(load().ssh_read_device(_dev_ptr(d_buf), d_buf.numel() * d_buf.element_size(), passes,
+                                  _stream(stream)))
 
 
 # ------------------------------------------------------------ convenience

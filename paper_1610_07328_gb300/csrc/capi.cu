@@ -311,6 +311,7 @@ HashArgs base_hash_args(const ssh_index* idx, int m, const Geometry& g) {
     a.gamma_ss = (float)(2.0 * gw);
     a.rank = idx->d_rank;
     a.rank_stride = rank_stride_of(idx->KL);
+    a.tab_stride = tab_stride_of(idx->KL);
     a.force_generic = idx->hash_kernel == 1;
     a.force_fp64 = idx->cws_fp64;
     a.kla = idx->d_kla;
@@ -920,8 +921,8 @@ ssh_status ssh_create(int W, int delta, int n, int K, int L, float band, uint64_
     // Sec. 4.3 draw tables for every (hash j, shingle k)
     const int KL = idx->KL;
     const int64_t nk = (int64_t)1 << n;
-    const int KLp = rank_stride_of(KL);
-    std::vector<uint16_t> rank((size_t)nk * KLp, (uint16_t)0xFFFF);
+    const int KLr = rank_stride_of(KL), KLp = tab_stride_of(KL);
+    std::vector<uint16_t> rank((size_t)nk * KLr, (uint16_t)0xFFFF);
     std::vector<uint2> kla((size_t)KL * nk);  // per rank: (shingle id, fl32 ln a at count 1)
     std::vector<float4> p32((size_t)nk * KL);
     std::vector<double> p64((size_t)KL * nk * 3);
@@ -950,7 +951,7 @@ ssh_status ssh_create(int W, int delta, int n, int K, int L, float band, uint64_
         }
         std::sort(la1.begin(), la1.end());  // (value, id): equal values keep the smaller id first
         for (int64_t rnk = 0; rnk < nk; ++rnk) {
-            rank[(size_t)la1[rnk].second * KLp + j] = (uint16_t)rnk;
+            rank[(size_t)la1[rnk].second * KLr + j] = (uint16_t)rnk;
             const uint32_t k = la1[rnk].second;
             float v = lav[(size_t)k * kTabCounts * KLp + j];
             uint32_t bitsv;
@@ -1415,7 +1416,7 @@ static ssh_status pairwise(const float* d_a, const int64_t* d_a_idx, const float
         SSH_CUDA(launch_envelope(dsa, nseg, m, rb, up, lo, st));
         SSH_CUDA(launch_lb_keogh(ps, up, lo, m, d_out, st));
     } else {
-        cudaError_t e = launch_dtw(ps, m, rb, d_out, st);
+        cudaError_t e = launch_dtw_plan(ps, m, rb, dtw_tuned_plan(m, rb, st), d_out, st);
         if (e == cudaErrorNotSupported) return fail(SSH_ENOTSUP, "DTW radius %d is wider than this build covers", rb);
         SSH_CUDA(e);
     }

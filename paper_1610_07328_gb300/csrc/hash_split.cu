@@ -434,7 +434,7 @@ __global__ void __launch_bounds__(256, 4) cws_kernel(HashArgs a, const uint32_t*
     uint32_t* kst = reinterpret_cast<uint32_t*>(wb + lay.kst);
     uint32_t* tst = reinterpret_cast<uint32_t*>(wb + lay.tst);
     const size_t nk = (size_t)1 << a.n;
-    const int kstride = a.rank_stride;
+    const int kstride = a.rank_stride, tstride = a.tab_stride;
     unsigned long long n64c = 0;
     const int64_t nwarps = (int64_t)gridDim.x * wpb;
     int64_t r0, r1;
@@ -462,10 +462,16 @@ __global__ void __launch_bounds__(256, 4) cws_kernel(HashArgs a, const uint32_t*
                     }
                 }
 #pragma unroll 1
-                for (; e < n1; ++e) {
-                    const uint2 r2 = __ldg(reinterpret_cast<const uint2*>(rk + set[e] * (uint32_t)kstride));
-                    m01 = __vminu2(m01, r2.x);
-                    m23 = __vminu2(m23, r2.y);
+                for (; e < n1; e += 4) {
+                    uint2 rv[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        rv[u] = __ldg(reinterpret_cast<const uint2*>(rk + set[min(e + u, n1 - 1)] * (uint32_t)kstride));
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        m01 = __vminu2(m01, rv[u].x);
+                        m23 = __vminu2(m23, rv[u].y);
+                    }
                 }
                 const uint32_t rmin[4] = {m01 & 0xFFFFu, m01 >> 16, m23 & 0xFFFFu, m23 >> 16};
                 // exact group: the count-1 winner and every shingle seen 2..kTabCounts times
@@ -485,9 +491,9 @@ __global__ void __launch_bounds__(256, 4) cws_kernel(HashArgs a, const uint32_t*
                     const uint32_t k = set_id(v), c = set_count(v);
                     if (c <= (uint32_t)kTabCounts) {
                         const float4 L = __ldg(reinterpret_cast<const float4*>(
-                            a.lav + ((size_t)k * kTabCounts + (c - 1)) * kstride + j0));
+                            a.lav + ((size_t)k * kTabCounts + (c - 1)) * tstride + j0));
                         const uchar4 T = __ldg(reinterpret_cast<const uchar4*>(
-                            a.tsm + ((size_t)k * (kTabCounts - 1) + (c - 2)) * kstride + j0));
+                            a.tsm + ((size_t)k * (kTabCounts - 1) + (c - 2)) * tstride + j0));
                         ex[0].add(L.x, k, T.x);
                         ex[1].add(L.y, k, T.y);
                         ex[2].add(L.z, k, T.z);

@@ -647,10 +647,6 @@ cudaError_t launch_lb_keogh(const PairSet& ps, const float* upper, const float* 
     return cudaGetLastError();
 }
 
-cudaError_t launch_dtw(const PairSet& ps, int m, int rb, float* out, cudaStream_t st) {
-    return launch_dtw_plan(ps, m, rb, dtw_plan(m, rb), out, st);
-}
-
 cudaError_t launch_dtw_plan(const PairSet& ps, int m, int rb, const DtwPlan& pl, float* out, cudaStream_t st) {
     if (ps.nseg <= 0 || ps.max_seg_pairs <= 0) return cudaSuccess;
     if (pl.S == 8) return launch_wave<8>(ps, m, rb, pl.G, pl.pmask, out, st);

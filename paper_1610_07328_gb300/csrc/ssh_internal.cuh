@@ -51,9 +51,13 @@ constexpr float kPad = 1.0e18f;
 
 constexpr int kMaxShingleBits = 16;     // n limit of the tabulated minhash draws
 constexpr int kMaxCount = 65535;        // shingles per series (u16 counts)
-// Row stride (in hashes) of the per-shingle draw tables: K L rounded up to 4, so
-// a lane's 4 consecutive hashes are one aligned 8-byte (ranks) or 16-byte load.
-inline int rank_stride_of(int KL) { return (KL + 3) & ~3; }
+// Row stride (in hashes) of the per-shingle ln a / t tables: K L rounded up to
+// 4, so a lane's 4 consecutive hashes are one aligned 16-byte (or 4-byte) load.
+inline int tab_stride_of(int KL) { return (KL + 3) & ~3; }
+// Row stride (in hashes) of the u16 rank table: K L rounded up to 64, so every
+// row starts on a 128-byte line and a row's read touches the fewest lines and
+// sectors; a lane's 4 consecutive ranks are one aligned 8-byte load.
+inline int rank_stride_of(int KL) { return (KL + 63) & ~63; }
 constexpr int kMaxTopK = 1024;
 // The rerank's seeds are the kSeedFactor k candidates of smallest LB_Keogh; the
 // k-th smallest DTW among them bounds the k-th best distance (pruning and early
@@ -79,14 +83,15 @@ struct HashArgs {
     float tau_norm;          // threshold factor tau * ||r|| (rounded up)
     float gamma_ss;          // relative inflation of the FP32 sum of squares
     const uint16_t* rank;    // [2^n][rank_stride] rank of the count-1 value of (j, k) among all k
-    int rank_stride;         // KL rounded up to a multiple of 4 (row padding holds 0xFFFF)
+    int rank_stride;         // KL rounded up to a multiple of 64 (row padding holds 0xFFFF)
     int force_generic;       // 1: use the generic kernel even when a specialised one exists
     int force_fp64;          // 1: decide every minhash by the FP64 recomputation (a test knob)
     const uint2* kla;        // [KL][2^n] per rank: (shingle id, ln a at count 1 rounded once to FP32, as bits)
     const float4* p32;       // [2^n][KL] (r, 1/r, beta, ln c) rounded to FP32
     const double* p64;       // [KL][2^n][3] (r, beta, ln c) in FP64
-    const float* lav;        // [2^n][kTabCounts][rank_stride] ln a of counts 1..kTabCounts, rounded once to FP32
-    const uint8_t* tsm;      // [2^n][kTabCounts-1][rank_stride] t of counts 2..kTabCounts (255: not tabulated)
+    const float* lav;        // [2^n][kTabCounts][tab_stride] ln a of counts 1..kTabCounts, rounded once to FP32
+    const uint8_t* tsm;      // [2^n][kTabCounts-1][tab_stride] t of counts 2..kTabCounts (255: not tabulated)
+    int tab_stride;          // KL rounded up to a multiple of 4
     const float* lns32;      // [kMaxCount+1] ln s rounded to FP32
     const double* lns64;     // [kMaxCount+1] ln s in FP64
     uint64_t seed;

@@ -602,3 +602,17 @@ def test_large_tables_two_pass_partition_candidates():
             assert idx.stats()["candidates"] == int(want.sum())
             if i < 3:
                 assert ids[0, 0] == src[i] and d[0, 0] == 0.0
+
+
+def test_read_probe_runs_and_rejects_bad_sizes():
+    """The measurement helper reads a buffer and refuses sizes it cannot read in 16-byte words."""
+    from paper_1610_07328_gb300 import binding
+    x = torch.ones(1 << 20, dtype=torch.float32, device="cuda")
+    binding.ssh_read_device(x, 4)
+    torch.cuda.synchronize()
+    assert float(x.sum()) == float(1 << 20)  # only read
+    with pytest.raises(binding.SSHError) as e:
+        binding.ssh_read_device(x[:3], 1)
+    assert e.value.status == binding.SSH_EINVAL
+    with pytest.raises(binding.SSHError):
+        binding.ssh_read_device(x, 0)
