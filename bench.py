@@ -172,6 +172,68 @@ def oracle_sample(w, n_sample: int, n_queries: int, row0: int = 0):
                         f"extrapolated as N*t_hash + nq*t_query*N/{n_sample}"))
 
 
+_ORACLE_WORKER = {}
+
+
+def _oracle_worker_init(w, n_sample, n_queries):
+    db = synth.random_walk(n_sample, w["m"], seed=w["seed"])
+    qs, _ = synth.perturbed_queries(db, n_queries, seed=1)
+    _ORACLE_WORKER.update(w=w, db=db, qs=qs, idx=None)
+
+
+def _oracle_index(rows):
+    import oracle
+    w = _ORACLE_WORKER["w"]
+    ix = oracle.OracleIndex(w["W"], w["delta"], w["n"], w["K"], w["L"], w["band"], w["seed"])
+    ix.add(rows)
+    return ix
+
+
+def _oracle_hash_slice(bounds):
+    a, b = bounds
+    _oracle_index(_ORACLE_WORKER["db"][a:b])
+    return b - a
+
+
+def _oracle_build(_):
+    if _ORACLE_WORKER["idx"] is None:
+        _ORACLE_WORKER["idx"] = _oracle_index(_ORACLE_WORKER["db"])
+    return os.getpid()
+
+
+def _oracle_query(i):
+    if _ORACLE_WORKER["idx"] is None:  # a worker that got no build task builds here (slower, never faster)
+        _oracle_build(0)
+    return _ORACLE_WORKER["idx"].query(_ORACLE_WORKER["qs"][i], _ORACLE_WORKER["w"]["k"])[0].tolist()
+
+
+def oracle_sample_all_cores(w, n_sample: int, n_queries: int, timeout: float = 300.0):
+    """oracle_sample with one spawned process per host core: the sample's series hashed in
+    slices across the processes (wall time), then the queries spread over processes that each
+    hold the sample's index (built before the timed query phase); same extrapolation."""
+    import multiprocessing as mp
+    P = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(P, initializer=_oracle_worker_init, initargs=(w, n_sample, n_queries)) as pool:
+        pool.map_async(_oracle_hash_slice, [(0, 2)] * P, chunksize=1).get(timeout)  # warm-up
+        step = (n_sample + P - 1) // P
+        slices = [(a, min(n_sample, a + step)) for a in range(0, n_sample, step)]
+        t0 = time.perf_counter()
+        pool.map_async(_oracle_hash_slice, slices, chunksize=1).get(timeout)
+        t1 = time.perf_counter()
+        pool.map_async(_oracle_build, range(2 * P), chunksize=1).get(timeout)
+        t2 = time.perf_counter()
+        pool.map_async(_oracle_query, range(n_queries), chunksize=1).get(timeout)
+        t3 = time.perf_counter()
+    t_hash = (t1 - t0) / n_sample
+    t_query = (t3 - t2) / n_queries
+    step_s = w["N"] * t_hash + w["nq"] * t_query * (w["N"] / n_sample)
+    return dict(value=w["N"] / step_s, cores=P, seconds=(t1 - t0) + (t3 - t2),
+                sample=(f"{P} processes: the oracle hashed {n_sample} series in slices (wall time) and answered "
+                        f"{n_queries} queries on their index spread over the processes; step time extrapolated "
+                        f"as N*t_hash + nq*t_query*N/{n_sample}"))
+
+
 def run_reference(args, w):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -327,12 +389,13 @@ OPERATING_POINTS = [
 ]
 
 
-def recall_operating_point(binding, torch, d_sub, d_q, exact, w, k):
-    """recall@10, candidate fraction and queries/s of each parameter set on the recall subset."""
-    n_sub, m, nq = d_sub.shape[0], w["m"], d_q.shape[0]
-    points = []
-    for (W, delta, n, K, L) in OPERATING_POINTS:
-        with binding.SSHIndex(W, delta, n, K, L, w["band"], w["seed"]) as ix:
+def sweep_points(binding, torch, d_sub, d_q, exact, points, band, seed, k, n_plain=20):
+    """recall@10, candidate fraction and queries/s of each parameter set (W, delta, n, K, L) on a
+    subset; the chosen point is the fastest with recall@10 >= 0.9 (else the one of highest recall)."""
+    n_sub, nq = d_sub.shape[0], d_q.shape[0]
+    out = []
+    for (W, delta, n, K, L) in points:
+        with binding.SSHIndex(W, delta, n, K, L, band, seed) as ix:
             ix.add_device(d_sub)
             ids = torch.empty((nq, k), dtype=torch.int64, device=d_q.device)
             dd = torch.empty((nq, k), dtype=torch.float32, device=d_q.device)
@@ -352,20 +415,26 @@ def recall_operating_point(binding, torch, d_sub, d_q, exact, w, k):
             one_i = torch.empty((1, k), dtype=torch.int64, device=d_q.device)
             one_d = torch.empty((1, k), dtype=torch.float32, device=d_q.device)
             lat = []
-            for i in range(min(nq, 20)):
+            for i in range(min(nq, n_plain)):
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record()
                 ix.query_device(d_q[i:i + 1], k, one_i, one_d)
                 e1.record()
                 e1.synchronize()
                 lat.append(e0.elapsed_time(e1))
-        points.append({"W": W, "delta": delta, "n": n, "K": K, "L": L, "recall_at_10": r10,
-                       "candidate_fraction": st["candidates"] / (3 * nq) / n_sub,
-                       "queries_per_s": nq / (best / 1000.0),
-                       "plain_gpu_path_queries_per_s": 1000.0 / statistics.mean(lat)})
-    ok = [p for p in points if p["recall_at_10"] >= 0.9]
-    chosen = max(ok, key=lambda p: p["queries_per_s"]) if ok else None
-    return {"subset": n_sub, "queries": nq, "points": points, "chosen": chosen}
+        out.append({"W": W, "delta": delta, "n": n, "K": K, "L": L, "recall_at_10": r10,
+                    "candidate_fraction": st["candidates"] / (3 * nq) / n_sub,
+                    "queries_per_s": nq / (best / 1000.0),
+                    "plain_gpu_path_queries_per_s": 1000.0 / statistics.mean(lat) if lat else None})
+    ok = [p for p in out if p["recall_at_10"] >= 0.9]
+    chosen = max(ok, key=lambda p: p["queries_per_s"]) if ok else max(out, key=lambda p: p["recall_at_10"])
+    return {"subset": n_sub, "queries": nq, "points": out, "chosen": chosen,
+            "meets_recall_0_9": chosen["recall_at_10"] >= 0.9}
+
+
+def recall_operating_point(binding, torch, d_sub, d_q, exact, w, k):
+    """The OPERATING_POINTS sweep on the recall subset of the scale workload."""
+    return sweep_points(binding, torch, d_sub, d_q, exact, OPERATING_POINTS, w["band"], w["seed"], k)
 
 
 def _timed_query(torch, ix, d_q, k, reps=3):
@@ -501,7 +570,89 @@ def batched_measurement(args, binding, torch, dev):
     out["setup_s"] = gen_s
     for ix in idxs:
         ix.close()
+    out["at_recall"] = batched_at_recall(args, binding, torch, dev, data, qlens, d_q, offs, k)
     return out
+
+
+def recall_points_for(m):
+    """Parameter sets tried per length for recall@10 >= 0.9 (the scale workload's sweep, W scaled
+    with m): narrower windows and shorter shingles, then one hash per table."""
+    w1, w2 = max(8, m * 5 // 64), m // 8
+    return [(w1, 3, 10, 4, 25), (w1, 3, 8, 4, 25), (w2, 3, 10, 1, 25), (w2, 3, 8, 1, 25)]
+
+
+def batched_at_recall(args, binding, torch, dev, data, qlens, d_q, offs, k):
+    """The batched workload at parameters that reach recall@10 >= 0.9: per length, the fastest
+    point of recall_points_for(m) with recall >= 0.9 on the first 10,000 rows (20 queries), then
+    the five indexes at those parameters through one batch plan on 1,024 of the mixed-length
+    queries, against one query per call, and recall@10 over the whole per-length collections."""
+    small = args.small
+    n_sub, n_sweep, nq_r, n_plain, per_len = (1000, 8, 128, 16, 2) if small else (10_000, 20, 1024, 64, 4)
+    N4 = int(next(iter(data.values())).shape[0])
+    chosen, sweeps = {}, []
+    for m in BATCH_LENGTHS:
+        sel = [i for i in range(len(qlens)) if qlens[i] == m][:n_sweep]
+        d_sel = torch.stack([d_q[offs[i]:offs[i] + m] for i in sel]).contiguous()
+        d_sub = data[m][:n_sub].contiguous()
+        rb = min(int(math.floor(np.float32(0.05) * np.float64(m))), m - 1)
+        ex = exact_topk_gpu(binding, torch, d_sel, d_sub, np.arange(n_sub, dtype=np.int64), m, rb, k)
+        sw = sweep_points(binding, torch, d_sub, d_sel, ex, recall_points_for(m), 0.05, 0, k, n_plain=0)
+        chosen[m] = sw["chosen"]
+        sweeps.append({"m": m, **{key: sw["chosen"][key] for key in ("W", "delta", "n", "K", "L", "recall_at_10",
+                                                                   "candidate_fraction")}})
+    idxs = [binding.SSHIndex(chosen[m]["W"], chosen[m]["delta"], chosen[m]["n"], chosen[m]["K"], chosen[m]["L"],
+                             0.05, 0) for m in BATCH_LENGTHS]
+    for ix, m in zip(idxs, BATCH_LENGTHS):
+        ix.add_device(data[m], borrow=True)
+    ql = np.asarray(qlens[:nq_r])
+    nfloat = int(offs[nq_r])
+    d_qr = d_q[:nfloat].contiguous()
+    ids = torch.empty((nq_r, k), dtype=torch.int64, device=dev)
+    dd = torch.empty((nq_r, k), dtype=torch.float32, device=dev)
+    which = torch.empty((nq_r,), dtype=torch.int32, device=dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with binding.SSHBatch(idxs, max_queries=nq_r, k=k) as bt:
+        for _ in range(2):  # the first batch runs directly (growing the pair buffers) and captures the graph
+            bt.query(d_qr, ql, ids, dd, which)
+        torch.cuda.synchronize()
+        steps = 3
+        e0.record()
+        for _ in range(steps):
+            bt.query(d_qr, ql, ids, dd, which)
+        e1.record()
+        e1.synchronize()
+        batch_ms = e0.elapsed_time(e1) / steps
+        st = bt.stats()
+    one_i = torch.empty((1, k), dtype=torch.int64, device=dev)
+    one_d = torch.empty((1, k), dtype=torch.float32, device=dev)
+    for i in range(4):  # warm-up
+        m = int(ql[i])
+        idxs[BATCH_LENGTHS.index(m)].query_device(d_qr[offs[i]:offs[i] + m].view(1, m), k, one_i, one_d)
+    torch.cuda.synchronize()
+    e0.record()
+    for i in range(n_plain):
+        m = int(ql[i])
+        idxs[BATCH_LENGTHS.index(m)].query_device(d_qr[offs[i]:offs[i] + m].view(1, m), k, one_i, one_d)
+    e1.record()
+    e1.synchronize()
+    plain_qps = n_plain / (e0.elapsed_time(e1) / 1000.0)
+    res = ids.cpu().numpy()
+    rec = []
+    for m in BATCH_LENGTHS:
+        sel = [i for i in range(nq_r) if ql[i] == m][:per_len]
+        if not sel:
+            continue
+        d_sel = torch.stack([d_qr[offs[i]:offs[i] + m] for i in sel]).contiguous()
+        rb = min(int(math.floor(np.float32(0.05) * np.float64(m))), m - 1)
+        ex = exact_topk_gpu(binding, torch, d_sel, data[m], np.arange(N4, dtype=np.int64), m, rb, k)
+        rec.append(recall(res[sel], ex))
+    for ix in idxs:
+        ix.close()
+    return {"params_per_length": sweeps, "sweep_subset": n_sub, "sweep_queries_per_length": n_sweep,
+            "queries": nq_r, "batched_queries_per_s": nq_r / (batch_ms / 1000.0), "ms_per_batch": batch_ms,
+            "candidates_per_query": st["pairs"] / nq_r, "dtw_per_query": st["dtw"] / nq_r,
+            "plain_gpu_path_queries_per_s": plain_qps, "plain_sample": n_plain,
+            "recall_at_10": float(np.mean(rec)) if rec else None, "recall_queries": per_len * len(BATCH_LENGTHS)}
 
 
 def ecg_like_gpu(torch, N, m, seed, dev, chunk=65536):
@@ -536,10 +687,75 @@ def ecg_like_gpu(torch, N, m, seed, dev, chunk=65536):
 SERVE_RATES = (1000, 5000, 20000, 50000)
 
 
+def serve_rates(srv, rates, dur, q_host, ins_pool, m, rng):
+    """Open-loop serving phases: per offered rate, Poisson arrivals for `dur` seconds (queries
+    drawn from q_host) while 100 random walks are inserted every 10 ms; served queries/s, p50/p99
+    latency from each query's scheduled arrival to its rows on the host, batch sizes, inserts/s."""
+    import threading
+    pool = len(q_host)
+    # warm-up: every slot's first batch runs directly and captures its graph
+    for _ in range(3):
+        tk = srv.submit(q_host[:256], np.full(min(256, pool), m, np.int32))
+        srv.wait(tk[-1], 120.0)
+    srv.flush(120.0)
+    res = []
+    for rate in rates:
+        n = max(1, int(rate * dur))
+        arr = np.cumsum(rng.exponential(1.0 / rate, n))
+        qidx = rng.integers(0, pool, n)
+        got = []
+        done_evt = threading.Event()
+
+        def collector():
+            while len(got) < n:
+                tk, _, _, lat, stt = srv.collect(4096, 0.01)
+                got.extend(zip(lat.tolist(), stt.tolist()))
+            done_evt.set()
+
+        while len(srv.collect(4096, 0.0)[0]):  # results of earlier phases
+            pass
+        st0 = srv.stats()
+        th = threading.Thread(target=collector, daemon=True)
+        th.start()
+        start = srv.now() + 0.02
+        arr_abs = start + arr
+        ins_t, ins_i, i = start, 0, 0
+        while i < n:
+            now = srv.now()
+            j = int(np.searchsorted(arr_abs, now, side="right"))
+            if j > i:
+                sel = qidx[i:j]
+                srv.submit(q_host[sel], np.full(j - i, m, np.int32), arr_abs[i:j])
+                i = j
+            while ins_t <= now:  # 100 random walks every 10 ms
+                a = (ins_i * 100) % (len(ins_pool) - 100)
+                srv.insert(ins_pool[a:a + 100], np.full(100, m, np.int32))
+                ins_t += 0.01
+                ins_i += 1
+            time.sleep(0.0002)
+        done_evt.wait(300.0)
+        t_end = srv.now()
+        srv.flush(300.0)
+        st1 = srv.stats()
+        lat = np.array([l for l, sc in got])
+        ok = sum(1 for _, sc in got if sc == 0)
+        span = max(t_end - start, 1e-9)
+        res.append({
+            "offered_qps": rate, "queries": n, "completed_ok": ok,
+            "served_qps": ok / span,
+            "p50_ms": float(np.percentile(lat, 50)) if len(lat) else None,
+            "p99_ms": float(np.percentile(lat, 99)) if len(lat) else None,
+            "mean_batch": (st1["queries_done"] - st0["queries_done"]) / max(st1["batches"] - st0["batches"], 1),
+            "batches": st1["batches"] - st0["batches"],
+            "max_inflight": st1["max_inflight"],
+            "inserts_per_s": (st1["inserts_applied"] - st0["inserts_applied"]) / span,
+        })
+    return res
+
+
 def serving_measurement(args, binding, torch, dev):
     """Poisson query arrivals at several rates against a served ECG-like index while random
     walks are inserted at 10k/s; open-loop latency from each query's scheduled arrival."""
-    import threading
     small = args.small
     N5, m, k = (20_000, 1024, 10) if small else (2_000_000, 1024, 10)
     dur = 0.3 if small else 1.0
@@ -561,63 +777,7 @@ def serving_measurement(args, binding, torch, dev):
                        "Poisson arrivals, random walks inserted at 10k/s" % (N5, m, k),
            "rates": []}
     with binding.SSHServer([ix], k=k, max_batch=256, max_slots=4, reserve_bytes=2 << 30) as srv:
-        # warm-up: every slot's first batch runs directly and captures its graph
-        for _ in range(3):
-            tk = srv.submit(q_host[:256], np.full(256, m, np.int32))
-            srv.wait(tk[-1], 60.0)
-        srv.flush(60.0)
-        rng = np.random.default_rng(8)
-        for rate in SERVE_RATES:
-            n = max(1, int(rate * dur))
-            arr = np.cumsum(rng.exponential(1.0 / rate, n))
-            qidx = rng.integers(0, pool, n)
-            got = []
-            done_evt = threading.Event()
-
-            def collector():
-                while len(got) < n:
-                    tk, _, _, lat, stt = srv.collect(4096, 0.01)
-                    got.extend(zip(lat.tolist(), stt.tolist()))
-                done_evt.set()
-
-            while len(srv.collect(4096, 0.0)[0]):  # results of earlier phases
-                pass
-            st0 = srv.stats()
-            th = threading.Thread(target=collector, daemon=True)
-            th.start()
-            start = srv.now() + 0.02
-            arr_abs = start + arr
-            ins_t, ins_i, i = start, 0, 0
-            while i < n:
-                now = srv.now()
-                j = int(np.searchsorted(arr_abs, now, side="right"))
-                if j > i:
-                    sel = qidx[i:j]
-                    srv.submit(q_host[sel], np.full(j - i, m, np.int32), arr_abs[i:j])
-                    i = j
-                while ins_t <= now:  # 100 random walks every 10 ms
-                    a = (ins_i * 100) % (len(ins_pool) - 100)
-                    srv.insert(ins_pool[a:a + 100], np.full(100, m, np.int32))
-                    ins_t += 0.01
-                    ins_i += 1
-                time.sleep(0.0002)
-            done_evt.wait(120.0)
-            t_end = srv.now()
-            srv.flush(120.0)
-            st1 = srv.stats()
-            lat = np.array([l for l, sc in got])
-            ok = sum(1 for _, sc in got if sc == 0)
-            span = max(t_end - start, 1e-9)
-            out["rates"].append({
-                "offered_qps": rate, "queries": n, "completed_ok": ok,
-                "served_qps": ok / span,
-                "p50_ms": float(np.percentile(lat, 50)) if len(lat) else None,
-                "p99_ms": float(np.percentile(lat, 99)) if len(lat) else None,
-                "mean_batch": (st1["queries_done"] - st0["queries_done"]) / max(st1["batches"] - st0["batches"], 1),
-                "batches": st1["batches"] - st0["batches"],
-                "max_inflight": st1["max_inflight"],
-                "inserts_per_s": (st1["inserts_applied"] - st0["inserts_applied"]) / span,
-            })
+        out["rates"] = serve_rates(srv, SERVE_RATES, dur, q_host, ins_pool, m, np.random.default_rng(8))
         st = srv.stats()
         out["slots"] = st["slots"]
         out["insert_mean_latency_ms"] = st["insert_latency_ms_sum"] / max(st["insert_batches"], 1)
@@ -635,7 +795,60 @@ def serving_measurement(args, binding, torch, dev):
     out["recall_queries"] = nrec
     out["setup_s"] = gen_s
     ix.close()
+    out["at_recall"] = served_at_recall(args, binding, torch, dev, db, q_host, ins_pool, m, k)
     del db
+    return out
+
+
+# Parameter sets tried on the ECG-like index for recall@10 >= 0.9 (m = 1024, band 10%).
+ECG_RECALL_POINTS = [(60, 5, 10, 4, 50), (60, 5, 8, 4, 50), (120, 5, 10, 1, 50), (120, 5, 8, 1, 50)]
+
+
+def served_at_recall(args, binding, torch, dev, db, q_host, ins_pool, m, k):
+    """The served workload at parameters that reach recall@10 >= 0.9: the fastest point of
+    ECG_RECALL_POINTS with recall >= 0.9 on the first 10,000 rows (20 queries); its batched
+    capacity (one call of 256 queries) and recall@10 over the whole index; then the serving loop
+    at 25%, 50% and 90% of that capacity for 3 s each, inserts at 10k/s as before."""
+    small = args.small
+    n_sub, n_sweep, nrec = (2000, 8, 4) if small else (10_000, 20, 8)
+    N5 = int(db.shape[0])
+    rb = min(int(math.floor(np.float32(0.10) * np.float64(m))), m - 1)
+    d_sub = db[:n_sub].contiguous()
+    d_sw = torch.from_numpy(q_host[:n_sweep]).to(dev)
+    ex = exact_topk_gpu(binding, torch, d_sw, d_sub, np.arange(n_sub, dtype=np.int64), m, rb, k)
+    sw = sweep_points(binding, torch, d_sub, d_sw, ex, ECG_RECALL_POINTS, 0.10, 0, k, n_plain=0)
+    c = sw["chosen"]
+    out = {"params": {key: c[key] for key in ("W", "delta", "n", "K", "L")},
+           "sweep": [{key: p[key] for key in ("W", "delta", "n", "K", "L", "recall_at_10", "candidate_fraction",
+                                              "queries_per_s")} for p in sw["points"]],
+           "sweep_subset": n_sub, "sweep_queries": n_sweep}
+    ix = binding.SSHIndex(c["W"], c["delta"], c["n"], c["K"], c["L"], 0.10, 0)
+    ix.add_device(db, borrow=True)
+    ncap = min(256, len(q_host))
+    d_cap = torch.from_numpy(q_host[:ncap]).to(dev)
+    ids, ms, _ = _timed_query(torch, ix, d_cap, k, reps=1)
+    cap_qps = ncap / (ms / 1000.0)
+    ex = exact_topk_gpu(binding, torch, d_cap[:nrec].contiguous(), db, np.arange(N5, dtype=np.int64), m, rb, k)
+    out.update({"capacity_queries_per_s": cap_qps, "recall_at_10": recall(ids.cpu().numpy()[:nrec], ex),
+                "recall_queries": nrec})
+    one_i = torch.empty((1, k), dtype=torch.int64, device=dev)
+    one_d = torch.empty((1, k), dtype=torch.float32, device=dev)
+    lat = []
+    for i in range(8):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ix.query_device(d_cap[i:i + 1], k, one_i, one_d)
+        e1.record()
+        e1.synchronize()
+        lat.append(e0.elapsed_time(e1))
+    out["plain_gpu_path_queries_per_s"] = 1000.0 / statistics.mean(lat[1:])
+    rates = [max(1.0, round(f * cap_qps, 1)) for f in (0.25, 0.5, 0.9)]
+    with binding.SSHServer([ix], k=k, max_batch=64, max_slots=4, reserve_bytes=4 << 30) as srv:
+        out["rates"] = serve_rates(srv, rates, 1.0 if small else 3.0, q_host, ins_pool, m,
+                                   np.random.default_rng(9))
+        st = srv.stats()
+        out["slots"] = st["slots"]
+    ix.close()
     return out
 
 
@@ -861,6 +1074,12 @@ def run_gpu(args, w):
         r = oracle_sample(w, n_s, 10 if not args.small else 3)
         line["cpu_baseline"] = {"value": r["value"], "unit": "series/s", "cores": 1, "kind": "oracle",
                                 "sample": r["sample"], "seconds": r["seconds"]}
+        try:
+            ra = oracle_sample_all_cores(w, n_s, 32 if not args.small else 8)
+            line["cpu_baseline"]["all_cores"] = {"value": ra["value"], "unit": "series/s", "cores": ra["cores"],
+                                                 "sample": ra["sample"], "seconds": ra["seconds"]}
+        except Exception as e:  # reported, never fatal to the line
+            line["cpu_baseline"]["all_cores"] = {"error": repr(e)[:200]}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
