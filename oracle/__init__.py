@@ -18,7 +18,9 @@ Massive-Scale Time Series", arXiv:1610.07328.
   -> ``OracleIndex.add``
 * Algorithm 2 (probe every table, union the buckets, top-k by DTW)
   -> ``OracleIndex.query``
-* Sec. 2.1 (DTW by dynamic programming) -> ``dtw``; Sec. 3 (LB_Keogh) -> ``lb_keogh``
+* Sec. 2.1 (DTW by dynamic programming) -> ``dtw``; Sec. 3 (LB_Keogh) -> ``lb_keogh``,
+  with the UCR suite's cascade the paper prunes with: ``lb_kim_fl``, ``lb_keogh_kim``,
+  ``lb_keogh_rev``
 * Sec. 5.3 (precision of the top-k against the exact DTW top-k) -> ``recall_at_k``
 """
 from __future__ import annotations
@@ -82,6 +84,8 @@ def _load():
             "ssh_oracle_band_radius": (ctypes.c_int, [ctypes.c_float, ctypes.c_int]),
             "ssh_oracle_dtw": (ctypes.c_double, [f32p, f32p, ctypes.c_int, ctypes.c_int]),
             "ssh_oracle_lb_keogh": (ctypes.c_double, [f32p, f32p, ctypes.c_int, ctypes.c_int]),
+            "ssh_oracle_lb_kim_fl": (ctypes.c_double, [f32p, f32p, ctypes.c_int]),
+            "ssh_oracle_lb_keogh_kim": (ctypes.c_double, [f32p, f32p, ctypes.c_int, ctypes.c_int]),
             "ssh_oracle_topk_dtw": (None, [f32p, f32p, i64p, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
                                            ctypes.c_int, i64p, f64p]),
         }
@@ -198,9 +202,32 @@ def dtw(a, b, rb: int) -> float:
 
 
 def lb_keogh(q, c, rb: int) -> float:
+    """Sec. 3: LB_Keogh, the envelope (radius rb) of q against the samples of c."""
     q = _f32(q)
     c = _f32(c)
     return _load().ssh_oracle_lb_keogh(_ptr(q, ctypes.c_float), _ptr(c, ctypes.c_float), len(q), int(rb))
+
+
+def lb_kim_fl(q, c) -> float:
+    """LB_Kim's endpoint bound (the UCR suite's first stage, which Sec. 3 relies on):
+    the costs of the first and last cells, which every warping path contains."""
+    q = _f32(q)
+    c = _f32(c)
+    return _load().ssh_oracle_lb_kim_fl(_ptr(q, ctypes.c_float), _ptr(c, ctypes.c_float), len(q))
+
+
+def lb_keogh_kim(q, c, rb: int) -> float:
+    """LB_Keogh with the terms of c's first and last samples replaced by the exact
+    first and last cell costs (LB_Kim folded into LB_Keogh)."""
+    q = _f32(q)
+    c = _f32(c)
+    return _load().ssh_oracle_lb_keogh_kim(_ptr(q, ctypes.c_float), _ptr(c, ctypes.c_float), len(q), int(rb))
+
+
+def lb_keogh_rev(q, c, rb: int) -> float:
+    """LB_Keogh with the roles reversed: the envelope of the candidate c against the
+    samples of q (the UCR suite's second LB_Keogh stage)."""
+    return lb_keogh(c, q, rb)
 
 
 def topk_dtw(q, rows, ids, rb: int, k: int):

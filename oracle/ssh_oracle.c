@@ -276,6 +276,41 @@ double ssh_oracle_lb_keogh(const float* q, const float* c, int m, int rb) {
     return lb;
 }
 
+double ssh_oracle_lb_kim_fl(const float* q, const float* c, int m) {
+    double d0 = (double)q[0] - (double)c[0];
+    double lb = d0 * d0;
+    if (m > 1) {
+        double d1 = (double)q[m - 1] - (double)c[m - 1];
+        lb = lb + d1 * d1;
+    }
+    return lb;
+}
+
+double ssh_oracle_lb_keogh_kim(const float* q, const float* c, int m, int rb) {
+    double lb = 0.0;
+    for (int i = 0; i < m; ++i) {
+        double term;
+        if (i == 0 || i == m - 1) {
+            double d = (double)q[i] - (double)c[i];
+            term = d * d;
+        } else {
+            int lo = i - rb < 0 ? 0 : i - rb;
+            int hi = i + rb > m - 1 ? m - 1 : i + rb;
+            double up = (double)q[lo], low = (double)q[lo];
+            for (int t = lo; t <= hi; ++t) {
+                if ((double)q[t] > up) up = (double)q[t];
+                if ((double)q[t] < low) low = (double)q[t];
+            }
+            double ci = (double)c[i];
+            term = 0.0;
+            if (ci > up) term = (ci - up) * (ci - up);
+            else if (ci < low) term = (ci - low) * (ci - low);
+        }
+        lb = lb + term;
+    }
+    return lb;
+}
+
 /* (d1, id1) < (d2, id2) in lexicographic order; an empty slot (id -1) is last. */
 static int pair_less(double d1, int64_t id1, double d2, int64_t id2) {
     if (id2 < 0) return 1;

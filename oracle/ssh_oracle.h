@@ -89,6 +89,12 @@ double ssh_oracle_dtw(const float* a, const float* b, int m, int rb);
  * U_i = max q[i-rb .. i+rb], L_i = min q[i-rb .. i+rb] (clipped to the series),
  * LB = sum over i of (c_i - U_i)^2 if c_i > U_i, (c_i - L_i)^2 if c_i < L_i, else 0. */
 double ssh_oracle_lb_keogh(const float* q, const float* c, int m, int rb);
+/* LB_Kim's endpoint bound: every warping path contains the cells (0, 0) and
+ * (m-1, m-1), so DTW >= (q_0 - c_0)^2 + (q_{m-1} - c_{m-1})^2 (one cell if m = 1). */
+double ssh_oracle_lb_kim_fl(const float* q, const float* c, int m);
+/* LB_Keogh whose terms for candidate samples 0 and m-1 are replaced by those two
+ * cell costs (each is at least the envelope term it replaces). */
+double ssh_oracle_lb_keogh_kim(const float* q, const float* c, int m, int rb);
 
 /* Exact top-k by DTW over rows[0..n) of a row-major [n, m] array (ids[i] names
  * row i): the k smallest (distance, id) pairs in lexicographic order. Unfilled

@@ -395,6 +395,55 @@ def test_lb_keogh_band0_and_self():
     assert oracle.lb_keogh(q, np.clip(c, q.min(), q.max()) * 0 + np.median(q), 49) == 0.0
 
 
+def test_lb_cascade_hand_computed():
+    """The UCR cascade's bounds on one 3-sample pair, worked by hand (band radius 1).
+    q = [0, 3, 0], c = [2, 1, 2]; cell costs (q_i - c_j)^2: row0 [4, 1, 4], row1 [1, 4, 1],
+    row2 [4, 1, 4]; the cheapest paths (0,0)(0,1)(1,2)(2,2) and (0,0)(1,0)(2,1)(2,2) cost 10.
+    Envelope of q: U = 3, L = 0 at every i, so every c_i is inside: LB_Keogh = 0.
+    Endpoint cells: (0 - 2)^2 + (0 - 2)^2 = 8 (LB_Kim), and LB_Keogh with those two terms = 8.
+    Envelope of c: U = 2, L = 1 everywhere; q = 0, 3, 0 lie 1 outside each: reversed LB = 3."""
+    q = np.array([0, 3, 0], np.float32)
+    c = np.array([2, 1, 2], np.float32)
+    assert oracle.dtw(q, c, 1) == 10.0
+    assert oracle.lb_keogh(q, c, 1) == 0.0
+    assert oracle.lb_kim_fl(q, c) == 8.0
+    assert oracle.lb_keogh_kim(q, c, 1) == 8.0
+    assert oracle.lb_keogh_rev(q, c, 1) == 3.0
+    assert oracle.lb_kim_fl(q[:1], c[:1]) == 4.0  # one sample: one cell
+
+
+def test_lb_cascade_bounds_lower_bound_dtw():
+    rng = np.random.default_rng(14)
+    for _ in range(200):
+        m = int(rng.integers(1, 70))
+        rb = int(rng.integers(0, m))
+        q = np.cumsum(rng.standard_normal(m)).astype(np.float32)
+        c = np.cumsum(rng.standard_normal(m)).astype(np.float32)
+        d = oracle.dtw(q, c, rb) * (1 + 1e-12) + 1e-12
+        kim, kk, rev = oracle.lb_kim_fl(q, c), oracle.lb_keogh_kim(q, c, rb), oracle.lb_keogh_rev(q, c, rb)
+        assert kim <= d and kk <= d and rev <= d
+        # the fused bound is at least each of the two it combines
+        assert kk >= oracle.lb_keogh(q, c, rb) * (1 - 1e-12) - 1e-12
+        assert kk >= kim * (1 - 1e-12) - 1e-12
+        assert rev == oracle.lb_keogh(c, q, rb)
+    for _ in range(40):  # brute force over all warping paths on tiny pairs
+        m = int(rng.integers(1, 7))
+        rb = int(rng.integers(0, m))
+        q = rng.standard_normal(m).astype(np.float32)
+        c = rng.standard_normal(m).astype(np.float32)
+        best = _dtw_all_paths(q, c, rb) * (1 + 1e-12) + 1e-12
+        assert oracle.lb_keogh_kim(q, c, rb) <= best and oracle.lb_keogh_rev(q, c, rb) <= best
+
+
+def test_lb_cascade_band0_is_euclidean():
+    rng = np.random.default_rng(15)
+    q = rng.standard_normal(40).astype(np.float32)
+    c = rng.standard_normal(40).astype(np.float32)
+    euclid = float(np.sum((q.astype(np.float64) - c.astype(np.float64)) ** 2))
+    assert oracle.lb_keogh_kim(q, c, 0) == pytest.approx(euclid, rel=1e-12)
+    assert oracle.lb_keogh_rev(q, c, 0) == pytest.approx(euclid, rel=1e-12)
+
+
 # --------------------------------------------------------- Algorithms 1 and 2
 
 def test_topk_matches_sort():
