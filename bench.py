@@ -455,6 +455,20 @@ def _timed_query(torch, ix, d_q, k, reps=3):
     return ids, best, st
 
 
+def cascade_modes(torch, ix, d_q, k, reps=1):
+    """Queries/s and pruned fractions of each SSH_OPT_LB_CASCADE mode (0 LB_Keogh, 1 with the LB_Kim
+    endpoints, 2 with the reversed LB_Keogh too); the index is left in mode 1 (the default)."""
+    out = {}
+    for mode in (0, 1, 2):
+        ix.set_lb_cascade(mode)
+        _, ms, st = _timed_query(torch, ix, d_q, k, reps=reps)
+        out[str(mode)] = {"queries_per_s": d_q.shape[0] / (ms / 1000.0),
+                          "lb_pruned_fraction": 1.0 - st["dtw_computed"] / max(st["candidates"], 1),
+                          "reversed_lb_pruned_fraction": st["lb2_pruned"] / max(st["candidates"], 1)}
+    ix.set_lb_cascade(1)
+    return out
+
+
 def exact_scan_measurement(binding, torch, d_sub, d_db, d_q, exact_sub, w, k, n_full):
     """The comparator without hashing (SSH_OPT_EXACT_SCAN): every stored series goes through the
     same LB_Keogh filter and early-abandoning DTW; on the recall subset and on the whole database."""
@@ -465,7 +479,10 @@ def exact_scan_measurement(binding, torch, d_sub, d_db, d_q, exact_sub, w, k, n_
             ix.set_exact_scan(True)
             ids, ms, st = _timed_query(torch, ix, d_q[:nq].contiguous(), k, reps=3 if name == "subset" else 1)
             entry = {"rows": int(db.shape[0]), "queries": int(nq), "queries_per_s": nq / (ms / 1000.0),
-                     "lb_pruned_fraction": 1.0 - st["dtw_computed"] / max(st["candidates"], 1)}
+                     "lb_pruned_fraction": 1.0 - st["dtw_computed"] / max(st["candidates"], 1),
+                     "reversed_lb_pruned_fraction": st["lb2_pruned"] / max(st["candidates"], 1),
+                     "by_cascade_mode": cascade_modes(torch, ix, d_q[:nq].contiguous(), k,
+                                                      reps=3 if name == "subset" else 1)}
             if name == "subset":
                 entry["recall_at_10"] = recall(ids.cpu().numpy(), exact_sub)
             out[name] = entry
@@ -560,12 +577,15 @@ def batched_measurement(args, binding, torch, dev):
         _, ms_h, st_h = _timed_query(torch, ix, d_sel, k, reps=1)
         ix.set_exact_scan(True)
         _, ms_e, st_e = _timed_query(torch, ix, d_sel, k, reps=1)
+        by_mode = cascade_modes(torch, ix, d_sel, k)
         ix.set_exact_scan(False)
         per_length.append({"m": m, "ssh_queries_per_s": len(sel) / (ms_h / 1000.0),
                            "ssh_candidate_fraction": st_h["candidates"] / max(st_h["queries"], 1) / N4,
                            "ssh_filtered_by_hashing": 1.0 - st_h["candidates"] / max(st_h["queries"], 1) / N4,
                            "exact_queries_per_s": len(sel) / (ms_e / 1000.0),
-                           "exact_lb_pruned_fraction": 1.0 - st_e["dtw_computed"] / max(st_e["candidates"], 1)})
+                           "exact_lb_pruned_fraction": 1.0 - st_e["dtw_computed"] / max(st_e["candidates"], 1),
+                           "exact_reversed_lb_pruned_fraction": st_e["lb2_pruned"] / max(st_e["candidates"], 1),
+                           "exact_by_cascade_mode": by_mode})
     out["per_length"] = per_length
     out["setup_s"] = gen_s
     for ix in idxs:

@@ -230,13 +230,22 @@ void ssh_server_destroy(ssh_server* s);
  * comparator without hashing. Batch plans and the server always hash.
  * SSH_OPT_CWS_FP64 (default 0): 1 decides every weighted minhash by the FP64
  * recomputation instead of the FP32 fast path (same results, much slower; a
- * test knob for the recomputation itself). */
+ * test knob for the recomputation itself).
+ * SSH_OPT_LB_CASCADE (default 1): with LB pruning on, the UCR-style cascade of
+ * the plain query path (ssh_query, ssh_query_device, the group query and the
+ * exact scan): 0 the query-envelope LB_Keogh alone; 1 with the LB_Kim endpoint
+ * costs folded into it; 2 as 1, then the reversed LB_Keogh (the candidate's
+ * envelope against the query) on the candidates that pass, before their DTW
+ * (it prunes more but builds each candidate's envelope, which costs more than
+ * the DTW it saves at the band radii measured, up to 102). Batch plans use 1.
+ * Same results in every mode: all are lower bounds of the banded DTW. */
 typedef enum ssh_option {
     SSH_OPT_LB_PRUNE = 1,
     SSH_OPT_KERNEL_TIMING = 2,
     SSH_OPT_HASH_KERNEL = 3,
     SSH_OPT_CWS_FP64 = 4,
-    SSH_OPT_EXACT_SCAN = 5
+    SSH_OPT_EXACT_SCAN = 5,
+    SSH_OPT_LB_CASCADE = 6
 } ssh_option;
 ssh_status ssh_set_option(ssh_index* idx, ssh_option opt, int64_t value);
 
@@ -250,6 +259,8 @@ typedef struct ssh_stats {
     int64_t dtw_computed;      /* candidates whose DTW was computed */
     int64_t lb_pruned;         /* candidates pruned by LB_Keogh */
     int64_t kernel_launches;   /* kernels launched by calls on this index */
+    int64_t lb2_pruned;        /* of lb_pruned: candidates that passed LB_Keogh and were pruned by the
+                                  reversed LB_Keogh (SSH_OPT_LB_CASCADE) */
 } ssh_stats;
 ssh_status ssh_get_stats(const ssh_index* idx, ssh_stats* out);
 ssh_status ssh_reset_stats(ssh_index* idx);
@@ -333,6 +344,19 @@ ssh_status ssh_dtw_device(const float* d_a, const int64_t* d_a_idx, const float*
  * against the envelope (radius rb) of row d_a_idx[p] of d_a. */
 ssh_status ssh_lb_keogh_device(const float* d_a, const int64_t* d_a_idx, const float* d_b, const int64_t* d_b_idx,
                                int64_t npairs, int32_t m, int32_t rb, float* d_out, void* stream);
+
+/* Lower bounds of the banded DTW for `npairs` pairs (a = query rows, b =
+ * candidate rows, as in ssh_dtw_device), chosen by `kind`:
+ *   0: LB_Keogh (Sec. 3): the envelope (radius rb) of the a-row against the
+ *      b-row's samples, sum of squared excursions (= ssh_lb_keogh_device);
+ *   1: kind 0 with the terms of samples 0 and m-1 replaced by the exact costs
+ *      of the first and last cells, (a_0 - b_0)^2 and (a_{m-1} - b_{m-1})^2
+ *      (the LB_Kim endpoint bound of the UCR suite folded into LB_Keogh);
+ *   2: reversed LB_Keogh: the envelope of the b-row against the a-row's samples.
+ * d_out[p] receives the bound of pair p. SSH_EINVAL for another kind or bad
+ * sizes. */
+ssh_status ssh_lb_bound_device(const float* d_a, const int64_t* d_a_idx, const float* d_b, const int64_t* d_b_idx,
+                               int64_t npairs, int32_t m, int32_t rb, int32_t kind, float* d_out, void* stream);
 
 /* Measurement helper, not part of the method: reads the `bytes` bytes at d_buf
  * (16-byte aligned, bytes a multiple of 16) `passes` times in one kernel launch

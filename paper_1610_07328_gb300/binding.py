@@ -22,6 +22,7 @@ SSH_OPT_KERNEL_TIMING = 2
 SSH_OPT_HASH_KERNEL = 3
 SSH_OPT_CWS_FP64 = 4
 SSH_OPT_EXACT_SCAN = 5
+SSH_OPT_LB_CASCADE = 6
 
 _lib = None
 _lock = threading.Lock()
@@ -36,7 +37,7 @@ class SSHError(RuntimeError):
 class ssh_stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in (
         "series_hashed", "sketch_fp64", "cws_fp64", "queries", "candidates", "dtw_computed", "lb_pruned",
-        "kernel_launches")]
+        "kernel_launches", "lb2_pruned")]
 
     def as_dict(self):
         return {n: int(getattr(self, n)) for n, _ in self._fields_}
@@ -98,6 +99,8 @@ _SIGS = {
     "ssh_hash_device_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int64, _P] + [_P] * 7),
     "ssh_dtw_device": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _P, _P]),
     "ssh_lb_keogh_device": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _P, _P]),
+    "ssh_lb_bound_device": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                           ctypes.c_int32, _P, _P]),
     "ssh_read_device": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_int32, _P]),
 }
 EXPORTED = tuple(_SIGS)
@@ -410,6 +413,12 @@ def ssh_lb_keogh_device(d_a, d_a_idx, d_b, d_b_idx, m: int, rb: int, d_out, stre
                                       d_a_idx.numel(), m, rb, _dev_ptr(d_out), _stream(stream)))
 
 
+def ssh_lb_bound_device(d_a, d_a_idx, d_b, d_b_idx, m: int, rb: int, kind: int, d_out, stream=None) -> None:
+    """Lower bounds of the banded DTW: kind 0 LB_Keogh, 1 with the LB_Kim endpoints, 2 reversed."""
+    _check(load().ssh_lb_bound_device(_dev_ptr(d_a), _dev_ptr(d_a_idx), _dev_ptr(d_b), _dev_ptr(d_b_idx),
+                                      d_a_idx.numel(), m, rb, kind, _dev_ptr(d_out), _stream(stream)))
+
+
 def ssh_read_device(d_buf, passes: int, stream=None) -> None:
     """Enqueue `passes` L1-bypassing reads of the whole of d_buf (a measurement helper)."""
     _check(load().ssh_read_device(_dev_ptr(d_buf), d_buf.numel() * d_buf.element_size(), passes,
@@ -487,6 +496,12 @@ class SSHIndex:
     def set_exact_scan(self, on: bool):
         """Rank every stored series of the query's length (exact top-k, no hashing)."""
         ssh_set_option(self.handle, SSH_OPT_EXACT_SCAN, 1 if on else 0)
+
+    def set_lb_cascade(self, mode):
+        """0 LB_Keogh alone, 1 with the LB_Kim endpoints (default), 2 + reversed LB_Keogh;
+        True / False select 2 / 0."""
+        mode = {True: 2, False: 0}.get(mode, mode) if isinstance(mode, bool) else int(mode)
+        ssh_set_option(self.handle, SSH_OPT_LB_CASCADE, mode)
 
     def set_kernel_timing(self, on: bool):
         ssh_set_option(self.handle, SSH_OPT_KERNEL_TIMING, 1 if on else 0)

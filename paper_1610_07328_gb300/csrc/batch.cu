@@ -485,7 +485,7 @@ ssh_status enqueue_pipeline(ssh_batch* b) {
         SSH_CUDA(launch_envelope(d.q_ptr, Q, hc.m, hc.rb, b->upper, b->lower, st, d.cls_begin + c, b->max_m));
         PairSet ps{b->seg_begin, Q, d.q_ptr, b->pair_b, nullptr, kLbGridPairs, d.cls_begin + c, b->max_m,
                    std::min<int64_t>(kGridSegs, Q)};
-        SSH_CUDA(launch_lb_keogh(ps, b->upper, b->lower, hc.m, b->lb, st));
+        SSH_CUDA(launch_lb_keogh(ps, b->upper, b->lower, hc.m, b->lb, st, true));  // with the LB_Kim endpoints
     }
     // Sec. 2.1 rerank: DTW of the k smallest-LB candidates bounds the k-th
     // distance; DTW of the others only where LB (1 - eta) stays below it

@@ -694,7 +694,7 @@ ssh_status query_group(ssh_index* idx, SubIndex& s, const std::vector<const floa
         {
             TimedRegion tr(idx, st, "query.lb_keogh", (double)C * m);
             SSH_CUDA(launch_envelope(d_qptr, nq, m, rb, upper, lower, st));
-            SSH_CUDA(launch_lb_keogh(all, upper, lower, m, lb, st));
+            SSH_CUDA(launch_lb_keogh(all, upper, lower, m, lb, st, idx->lb_cascade >= 1));
         }
         uint32_t *T, *U;
         SSH_TRY(sc.get(&T, nq));
@@ -709,11 +709,13 @@ ssh_status query_group(ssh_index* idx, SubIndex& s, const std::vector<const floa
         SSH_TRY(sc.get(&fcount, nq));
         SSH_TRY(sc.get(&fbegin, nq + 1));
         SSH_TRY(sc.get(&cursor, nq));
-        SSH_TRY(sc.get(&ftotal, 2));
+        SSH_TRY(sc.get(&ftotal, 3));
         SSH_TRY(sc.get(&fb, C));
         SSH_TRY(sc.get(&fslot, C));
         unsigned long long* h_tot = idx->h_pinned;
-        h_tot[0] = h_tot[1] = 0;
+        h_tot[0] = h_tot[1] = h_tot[2] = 0;
+        const bool rev = idx->lb_cascade == 2;
+        SSH_CUDA(cudaMemsetAsync(ftotal + 2, 0, sizeof(unsigned long long), st));
         ssh_status fst = SSH_OK;
         size_t tslot[2] = {SIZE_MAX, SIZE_MAX};  // the two DTW timings: cells are known after the sync
         for (int mode = 0; mode < 2 && fst == SSH_OK; ++mode) {
@@ -728,6 +730,11 @@ ssh_status query_group(ssh_index* idx, SubIndex& s, const std::vector<const floa
             if (mode == 1) {  // survivors: stop at the bound U of the seeds' k-th distance
                 sub.abandon = U;
                 sub.abandon_shrink = shrink;
+                // UCR cascade: the reversed LB_Keogh clears the survivors it proves too far
+                if (e == cudaSuccess && rev) {
+                    TimedRegion tr(idx, st, "query.lb_rev", 0.0);
+                    e = launch_lb_rev(sub, m, rb, nullptr, U, shrink, fb, ftotal + 2, st);
+                }
             }
             if (e == cudaSuccess) {
                 {
@@ -740,7 +747,7 @@ ssh_status query_group(ssh_index* idx, SubIndex& s, const std::vector<const floa
         }
         if (fst == SSH_OK) {
             // read at the end of the query with the results
-            cudaError_t e = cudaMemcpyAsync(h_tot, ftotal, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
+            cudaError_t e = cudaMemcpyAsync(h_tot, ftotal, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
             if (e != cudaSuccess) fst = cuda_status(e, "rerank counts");
         }
         if (fst != SSH_OK) {
@@ -766,10 +773,13 @@ ssh_status query_group(ssh_index* idx, SubIndex& s, const std::vector<const floa
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e == cudaSuccess && pruned_counts) {
-        idx->host_stats.dtw_computed += (int64_t)(pruned_counts[0] + pruned_counts[1]);
+        const unsigned long long rev = pruned_counts[2];
+        idx->host_stats.dtw_computed += (int64_t)(pruned_counts[0] + pruned_counts[1] - rev);
+        idx->host_stats.lb2_pruned += (int64_t)rev;
         for (int mode = 0; mode < 2; ++mode)
             if (pruned_slots[mode] != SIZE_MAX)
-                idx->pending[pruned_slots[mode]].units = (double)pruned_counts[mode] * dtw_cells(m, rb);
+                idx->pending[pruned_slots[mode]].units =
+                    (double)(pruned_counts[mode] - (mode == 1 ? rev : 0ull)) * dtw_cells(m, rb);
     }
     idx->host_stats.lb_pruned = idx->host_stats.candidates - idx->host_stats.dtw_computed;
     SSH_CUDA(e);
@@ -1272,6 +1282,10 @@ ssh_status ssh_set_option(ssh_index* idx, ssh_option opt, int64_t value) {
         case SSH_OPT_CWS_FP64:
             idx->cws_fp64 = value != 0;
             return SSH_OK;
+        case SSH_OPT_LB_CASCADE:
+            if (value < 0 || value > 2) return fail(SSH_EINVAL, "SSH_OPT_LB_CASCADE takes 0, 1 or 2");
+            idx->lb_cascade = (int)value;
+            return SSH_OK;
         case SSH_OPT_EXACT_SCAN:
             idx->exact_scan = value != 0;
             return SSH_OK;
@@ -1367,8 +1381,9 @@ ssh_status ssh_hash_device(const ssh_index* idx, const float* d_series, int32_t 
     return SSH_OK;
 }
 
+// lb: -1 DTW, 0 LB_Keogh, 1 LB_Keogh with the LB_Kim endpoints, 2 reversed LB_Keogh
 static ssh_status pairwise(const float* d_a, const int64_t* d_a_idx, const float* d_b, const int64_t* d_b_idx,
-                           int64_t npairs, int32_t m, int32_t rb, float* d_out, cudaStream_t st, bool lb) {
+                           int64_t npairs, int32_t m, int32_t rb, float* d_out, cudaStream_t st, int lb) {
     if (npairs < 0 || m < 1 || rb < 0 || rb >= m || (npairs > 0 && (!d_a || !d_a_idx || !d_b || !d_b_idx || !d_out)))
         return fail(SSH_EINVAL, "bad arguments");
     if (npairs == 0) return SSH_OK;
@@ -1409,12 +1424,14 @@ static ssh_status pairwise(const float* d_a, const int64_t* d_a_idx, const float
     SSH_CUDA(cudaMemcpyAsync(dsa, sa.data(), nseg * sizeof(float*), cudaMemcpyHostToDevice, st));
     SSH_CUDA(cudaMemcpyAsync(dpb, pb.data(), npairs * sizeof(float*), cudaMemcpyHostToDevice, st));
     PairSet ps{dbeg, nseg, dsa, dpb, dslot, mx};
-    if (lb) {
+    if (lb == 0 || lb == 1) {
         float *up, *lo;
         SSH_TRY(sc.get(&up, (size_t)nseg * m));
         SSH_TRY(sc.get(&lo, (size_t)nseg * m));
         SSH_CUDA(launch_envelope(dsa, nseg, m, rb, up, lo, st));
-        SSH_CUDA(launch_lb_keogh(ps, up, lo, m, d_out, st));
+        SSH_CUDA(launch_lb_keogh(ps, up, lo, m, d_out, st, lb == 1));
+    } else if (lb == 2) {
+        SSH_CUDA(launch_lb_rev(ps, m, rb, d_out, nullptr, 1.f, nullptr, nullptr, st));
     } else {
         cudaError_t e = launch_dtw_plan(ps, m, rb, dtw_tuned_plan(m, rb, st), d_out, st);
         if (e == cudaErrorNotSupported) return fail(SSH_ENOTSUP, "DTW radius %d is wider than this build covers", rb);
@@ -1426,12 +1443,18 @@ static ssh_status pairwise(const float* d_a, const int64_t* d_a_idx, const float
 
 ssh_status ssh_dtw_device(const float* d_a, const int64_t* d_a_idx, const float* d_b, const int64_t* d_b_idx,
                           int64_t npairs, int32_t m, int32_t rb, float* d_out, void* stream) {
-    return pairwise(d_a, d_a_idx, d_b, d_b_idx, npairs, m, rb, d_out, (cudaStream_t)stream, false);
+    return pairwise(d_a, d_a_idx, d_b, d_b_idx, npairs, m, rb, d_out, (cudaStream_t)stream, -1);
 }
 
 ssh_status ssh_lb_keogh_device(const float* d_a, const int64_t* d_a_idx, const float* d_b, const int64_t* d_b_idx,
                                int64_t npairs, int32_t m, int32_t rb, float* d_out, void* stream) {
-    return pairwise(d_a, d_a_idx, d_b, d_b_idx, npairs, m, rb, d_out, (cudaStream_t)stream, true);
+    return pairwise(d_a, d_a_idx, d_b, d_b_idx, npairs, m, rb, d_out, (cudaStream_t)stream, 0);
+}
+
+ssh_status ssh_lb_bound_device(const float* d_a, const int64_t* d_a_idx, const float* d_b, const int64_t* d_b_idx,
+                               int64_t npairs, int32_t m, int32_t rb, int32_t kind, float* d_out, void* stream) {
+    if (kind < 0 || kind > 2) return fail(SSH_EINVAL, "LB kind %d is not 0, 1 or 2", (int)kind);
+    return pairwise(d_a, d_a_idx, d_b, d_b_idx, npairs, m, rb, d_out, (cudaStream_t)stream, kind);
 }
 
 }  // extern "C"

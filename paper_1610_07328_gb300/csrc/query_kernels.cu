@@ -130,6 +130,12 @@ __global__ void envelope_kernel(const float* const* seg_a, int64_t nseg, int m, 
 
 constexpr int kLbWarps = 8;
 
+// KIM: the terms of candidate samples 0 and m-1 are the exact costs of the
+// path's first and last cells, (q_0 - c_0)^2 and (q_{m-1} - c_{m-1})^2 (every
+// warping path starts at (0, 0) and ends at (m-1, m-1)), the LB_Kim endpoint
+// bound folded into LB_Keogh; each is at least the envelope term it replaces.
+// It costs nothing in the loop: the staged envelope is the single point q_i there.
+template <bool KIM>
 __global__ void __launch_bounds__(kLbWarps * 32) lb_keogh_kernel(PairSet ps, const float* upper, const float* lower,
                                                                  int m, float* out) {
     extern __shared__ float env[];  // [2m]: upper then lower
@@ -141,9 +147,12 @@ __global__ void __launch_bounds__(kLbWarps * 32) lb_keogh_kernel(PairSet ps, con
         const int64_t b = ps.seg_begin[s], e = ps.seg_begin[s + 1];
         if (b + (int64_t)blockIdx.x * per_cta >= e) continue;  // uniform over the block
         __syncthreads();  // the previous segment's envelope is no longer read
+        const float* qa = ps.seg_a[s];
         for (int i = threadIdx.x; i < m; i += blockDim.x) {
-            env[i] = upper[s * es + i];
-            env[m + i] = lower[s * es + i];
+            // KIM: a one-point envelope {q_i} at i = 0 and m-1 makes those terms the exact cell costs
+            const bool endpoint = KIM && (i == 0 || i == m - 1);
+            env[i] = endpoint ? qa[i] : upper[s * es + i];
+            env[m + i] = endpoint ? qa[i] : lower[s * es + i];
         }
         __syncthreads();
         for (int64_t p = b + (int64_t)blockIdx.x * per_cta + warp; p < e; p += (int64_t)gridDim.x * per_cta) {
@@ -160,6 +169,96 @@ __global__ void __launch_bounds__(kLbWarps * 32) lb_keogh_kernel(PairSet ps, con
             if (lane == 0) out[ps.pair_slot ? ps.pair_slot[p] : p] = acc;
         }
     }
+}
+
+// LB_Keogh with the roles reversed (Sec. 3 applied to the candidate): the
+// envelope of the candidate c with radius rb against the query's samples,
+// LB(i) = (q_i - U_c(i))^2 if q_i > U_c(i), (q_i - L_c(i))^2 if q_i < L_c(i),
+// U_c / L_c the max / min of c over [i - rb, i + rb] clipped to [0, m). Still a
+// lower bound of DTW(q, c): every query sample is matched to some candidate
+// sample inside its band.
+//
+// One warp per pair builds the envelope in shared memory: the candidate padded
+// with rb samples of -inf / +inf on each side (so every window has exactly
+// w = 2 rb + 1 entries), then log2(P) doubling passes give T[t] = max/min of the
+// P entries from t (P the largest power of two <= w), and a window is the
+// union of the two length-P runs starting at i and at i + w - P. The query is
+// in shared memory once per block (a block's pairs share one segment).
+// MARK: the pairs of a rerank's survivor pass, with the segment's bound U: a
+// pair whose LB * shrink > U cannot reach the top-k; its candidate pointer is
+// cleared (the DTW pass skips it) and `pruned` counts it. Otherwise: out[slot].
+template <bool MARK>
+__global__ void __launch_bounds__(256) lb_rev_kernel(PairSet ps, int m, int rb, float* out, const uint32_t* U,
+                                                     float shrink, const float** pair_mut,
+                                                     unsigned long long* pruned) {
+    extern __shared__ float lsm[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int mp = m + 2 * rb;         // padded length
+    const int mpa = (mp + 3) & ~3;
+    float* qs = lsm;                   // [m]
+    float* wb = lsm + ((m + 3) & ~3) + (size_t)warp * 4 * mpa;
+    const int w = 2 * rb + 1;
+    int P = 1;
+    while (2 * P <= w) P *= 2;
+    const float NINF = __int_as_float(0xFF800000), PINF = __int_as_float(0x7F800000);
+    unsigned long long npr = 0;
+    const int64_t s_lo = ps.seg_range ? ps.seg_range[0] : 0, s_hi = ps.seg_range ? ps.seg_range[1] : ps.nseg;
+    for (int64_t s = s_lo + blockIdx.y; s < s_hi; s += gridDim.y) {
+        const int64_t b = ps.seg_begin[s], e = ps.seg_begin[s + 1];
+        if (b + (int64_t)blockIdx.x * nw >= e) continue;  // uniform over the block
+        __syncthreads();
+        const float* qg = ps.seg_a[s];
+        for (int i = threadIdx.x; i < m; i += blockDim.x) qs[i] = qg[i];
+        __syncthreads();
+        float u = PINF;
+        if (MARK) {
+            const uint32_t ub = U[s];
+            if (ub != 0xFFFFFFFFu) u = __uint_as_float(ub);
+        }
+        for (int64_t p = b + (int64_t)blockIdx.x * nw + warp; p < e; p += (int64_t)gridDim.x * nw) {
+            const float* c = ps.pair_b[p];
+            float *mx = wb, *mn = wb + mpa, *mx2 = wb + 2 * mpa, *mn2 = wb + 3 * mpa;
+            for (int t = lane; t < mp; t += 32) {
+                const int i = t - rb;
+                const bool in = i >= 0 && i < m;
+                const float v = in ? __ldg(c + i) : 0.f;
+                mx[t] = in ? v : NINF;
+                mn[t] = in ? v : PINF;
+            }
+            __syncwarp();
+            for (int len = 1; len < P; len *= 2) {
+                for (int t = lane; t < mp; t += 32) {
+                    const int t2 = min(t + len, mp - 1);  // past the end: the last entry, a pad
+                    mx2[t] = fmaxf(mx[t], mx[t2]);
+                    mn2[t] = fminf(mn[t], mn[t2]);
+                }
+                __syncwarp();
+                float* x = mx; mx = mx2; mx2 = x;
+                x = mn; mn = mn2; mn2 = x;
+            }
+            float acc = 0.f;
+            for (int i = lane; i < m; i += 32) {
+                const int t2 = i + w - P;  // window [i, i + w) of the padded array
+                const float up = fmaxf(mx[i], mx[t2]), lo = fminf(mn[i], mn[t2]);
+                const float v = qs[i];
+                const float d = v > up ? v - up : (v < lo ? v - lo : 0.f);
+                acc = fmaf(d, d, acc);
+            }
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+            if (lane == 0) {
+                if (MARK) {
+                    if (acc * shrink > u) {
+                        pair_mut[p] = nullptr;
+                        ++npr;
+                    }
+                } else {
+                    out[ps.pair_slot ? ps.pair_slot[p] : p] = acc;
+                }
+            }
+            __syncwarp();  // the envelope buffers are rebuilt for the next pair
+        }
+    }
+    if (MARK && npr) atomicAdd(pruned, npr);
 }
 
 // --------------------------------------------------- DTW wavefront kernel
@@ -247,7 +346,11 @@ __global__ void __launch_bounds__(256) dtw_wave_kernel(PairSet ps, int m, int rb
         while (true) {
             // groups without a pair claim the next one (leader's atomic, shuffled to the group)
             unsigned long long v = ~0ull;
-            if (need && g == 0) v = atomicAdd(&s_next, 1ull);
+            if (need && g == 0) {
+                v = atomicAdd(&s_next, 1ull);
+                // pairs a reversed LB_Keogh pass cleared are skipped (their distance stays +inf)
+                while (v < (unsigned long long)b1 && ps.pair_b[v] == nullptr) v = atomicAdd(&s_next, 1ull);
+            }
             v = __shfl_sync(kFull, v, lane_in_group ? grp * G : lane);
             if (need) {
                 p = (v < (unsigned long long)b1) ? (int64_t)v : -1;
@@ -634,15 +737,46 @@ cudaError_t launch_envelope(const float* const* seg_a, int64_t nseg, int m, int 
 }
 
 cudaError_t launch_lb_keogh(const PairSet& ps, const float* upper, const float* lower, int m, float* out,
-                            cudaStream_t st) {
+                            cudaStream_t st, bool kim) {
     if (ps.nseg <= 0 || ps.max_seg_pairs <= 0) return cudaSuccess;
     int64_t gx = (ps.max_seg_pairs + kLbWarps - 1) / kLbWarps;
     if (gx > 65535) gx = 65535;
     const size_t smem = 2 * (size_t)m * sizeof(float);
-    cudaError_t e = ensure_dynamic_smem((const void*)lb_keogh_kernel, smem);
+    const void* fn = kim ? (const void*)lb_keogh_kernel<true> : (const void*)lb_keogh_kernel<false>;
+    cudaError_t e = ensure_dynamic_smem(fn, smem);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)gx, (unsigned)(ps.grid_y ? ps.grid_y : std::min<int64_t>(ps.nseg, 65535)));
-    lb_keogh_kernel<<<grid, kLbWarps * 32, smem, st>>>(ps, upper, lower, m, out);
+    if (kim)
+        lb_keogh_kernel<true><<<grid, kLbWarps * 32, smem, st>>>(ps, upper, lower, m, out);
+    else
+        lb_keogh_kernel<false><<<grid, kLbWarps * 32, smem, st>>>(ps, upper, lower, m, out);
+    note_launch();
+    return cudaGetLastError();
+}
+
+size_t lb_rev_smem(int m, int rb, int warps) {
+    const size_t mpa = (size_t)((m + 2 * rb + 3) & ~3);
+    return ((size_t)((m + 3) & ~3) + (size_t)warps * 4 * mpa) * sizeof(float);
+}
+
+cudaError_t launch_lb_rev(const PairSet& ps, int m, int rb, float* out, const uint32_t* U, float shrink,
+                          const float** pair_mut, unsigned long long* pruned, cudaStream_t st) {
+    if (ps.nseg <= 0 || ps.max_seg_pairs <= 0) return cudaSuccess;
+    int warps = 8;
+    while (warps > 1 && lb_rev_smem(m, rb, warps) > 200 * 1024) --warps;
+    const size_t smem = lb_rev_smem(m, rb, warps);
+    if (smem > 227 * 1024) return cudaErrorInvalidValue;
+    const bool mark = U != nullptr;
+    const void* fn = mark ? (const void*)lb_rev_kernel<true> : (const void*)lb_rev_kernel<false>;
+    cudaError_t e = ensure_dynamic_smem(fn, smem);
+    if (e != cudaSuccess) return e;
+    int64_t gx = (ps.max_seg_pairs + warps - 1) / warps;
+    if (gx > 65535) gx = 65535;
+    dim3 grid((unsigned)gx, (unsigned)(ps.grid_y ? ps.grid_y : std::min<int64_t>(ps.nseg, 65535)));
+    if (mark)
+        lb_rev_kernel<true><<<grid, warps * 32, smem, st>>>(ps, m, rb, out, U, shrink, pair_mut, pruned);
+    else
+        lb_rev_kernel<false><<<grid, warps * 32, smem, st>>>(ps, m, rb, out, U, shrink, pair_mut, pruned);
     note_launch();
     return cudaGetLastError();
 }

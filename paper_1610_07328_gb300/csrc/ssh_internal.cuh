@@ -198,8 +198,14 @@ struct PairSet {
 
 cudaError_t launch_envelope(const float* const* seg_a, int64_t nseg, int m, int rb, float* upper, float* lower,
                             cudaStream_t st, const int64_t* seg_range = nullptr, int64_t env_stride = 0);
+// kim: the endpoint samples take the exact first / last cell costs (LB_Kim folded in)
 cudaError_t launch_lb_keogh(const PairSet& ps, const float* upper, const float* lower, int m, float* out,
-                            cudaStream_t st);
+                            cudaStream_t st, bool kim = false);
+// Reversed LB_Keogh (the candidate's envelope, the query's samples). With U (per
+// segment bound bits): clears pair_mut[p] of pairs whose LB * shrink > U and
+// counts them in *pruned; without: writes out[slot].
+cudaError_t launch_lb_rev(const PairSet& ps, int m, int rb, float* out, const uint32_t* U, float shrink,
+                          const float** pair_mut, unsigned long long* pruned, cudaStream_t st);
 
 struct DtwPlan {
     int S, G, pmask;
@@ -337,6 +343,7 @@ struct ssh_index {
     int device = 0;
     bool lb_prune = true;
     bool exact_scan = false;          // queries rank every stored series (no hashing)
+    int lb_cascade = 1;               // SSH_OPT_LB_CASCADE: 0 none, 1 LB_Kim endpoints, 2 + reversed LB_Keogh
     int hash_kernel = 0;              // 0: fastest available, 1: always the generic kernel
     int cws_fp64 = 0;                 // 1: every minhash through the FP64 recomputation
     float tau_norm = 0.f;

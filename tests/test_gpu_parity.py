@@ -226,6 +226,55 @@ def test_lb_keogh_parity(m, rb):
     np.testing.assert_allclose(got, want, rtol=RTOL, atol=1e-6)
 
 
+@pytest.mark.parametrize("m,rb", [(128, 6), (512, 25), (1024, 102), (37, 5), (64, 0), (50, 49)])
+def test_lb_bound_kinds_parity(m, rb):
+    """The cascade's bounds through ssh_lb_bound_device against the oracle: kind 0 LB_Keogh,
+    1 LB_Keogh with the LB_Kim endpoint costs, 2 the reversed LB_Keogh (candidate envelope)."""
+    b = _binding()
+    A = synth.random_walk(10, m, seed=m + 15)
+    B = synth.random_walk(30, m, seed=m + 16)
+    ai, bi = _pairs(len(A), len(B), 50, seed=m + 2)
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    dai, dbi = torch.from_numpy(ai).cuda(), torch.from_numpy(bi).cuda()
+    refs = (oracle.lb_keogh, oracle.lb_keogh_kim, oracle.lb_keogh_rev)
+    for kind, ref in enumerate(refs):
+        out = torch.full((len(ai),), -1.0, dtype=torch.float32, device="cuda")
+        b.ssh_lb_bound_device(dA, dai, dB, dbi, m, rb, kind, out)
+        got = out.cpu().numpy()
+        want = np.array([ref(A[i], B[j], rb) for i, j in zip(ai, bi)])
+        np.testing.assert_allclose(got, want, rtol=RTOL, atol=1e-6, err_msg=f"kind {kind}")
+    with pytest.raises(b.SSHError) as e:
+        b.ssh_lb_bound_device(dA, dai, dB, dbi, m, rb, 3, out)
+    assert e.value.status == b.SSH_EINVAL
+
+
+@pytest.mark.parametrize("exact", [False, True])
+def test_lb_cascade_changes_no_result(exact):
+    """The cascade (LB_Kim endpoints, reversed LB_Keogh) only skips DTWs that cannot reach the
+    top-k: ids and distances are identical with it on and off, and with pruning off."""
+    cfg = CFG2
+    db = synth.random_walk(3000, 512, seed=21)
+    qs, _ = synth.perturbed_queries(db, 12, seed=22)
+    res = {}
+    with _index(cfg) as idx:
+        idx.add(db)
+        idx.set_exact_scan(exact)
+        for name, prune, cascade in (("off", False, 0), ("lb", True, 0), ("kim", True, 1), ("cascade", True, 2)):
+            idx.set_lb_prune(prune)
+            idx.set_lb_cascade(cascade)
+            idx.reset_stats()
+            ids, d = idx.query(qs, 10)
+            res[name] = (ids, d, idx.stats())
+    for name in ("lb", "kim", "cascade"):
+        assert np.array_equal(res[name][0], res["off"][0]) and np.array_equal(res[name][1], res["off"][1]), name
+    st_lb, st_c = res["lb"][2], res["cascade"][2]
+    assert st_lb["lb2_pruned"] == 0 and res["kim"][2]["lb2_pruned"] == 0
+    assert st_c["dtw_computed"] <= res["kim"][2]["dtw_computed"]  # the reversed bound only removes survivors
+    if exact:
+        assert st_c["lb2_pruned"] > 0 and st_c["dtw_computed"] < res["kim"][2]["dtw_computed"]
+    assert st_c["lb_pruned"] == st_c["candidates"] - st_c["dtw_computed"]
+
+
 # ------------------------------------------------------------- end to end
 
 def assert_topk_match(q, ids_g, d_g, ids_o, d_o, db_by_id, rb):
