@@ -707,6 +707,55 @@ def ecg_like_gpu(torch, N, m, seed, dev, chunk=65536):
 SERVE_RATES = (1000, 5000, 20000, 50000)
 
 
+def subsequence_measurement(args, binding, torch, dev):
+    """Sec. 5.1's workload: every length-128 window (step 1) of one long random-walk stream,
+    indexed with the paper's Random Walk parameters (W=30, delta=5, n=15, one hash per table,
+    20 tables) through ssh_index_add_windows_device (windows borrowed, sketch positions shared);
+    the same windows hashed as rows for comparison; queries/s and recall@10 against the exact scan
+    of the same windows."""
+    small = args.small
+    n_s, t, nq, k = ((1 << 18) if small else (1 << 24)), 128, 100, 10
+    W, delta, n, K, L, band = 30, 5, 15, 1, 20, 0.05
+    t0 = time.perf_counter()
+    stream = synth.random_walk(1, n_s, seed=90)[0]
+    d_s = torch.from_numpy(stream).to(dev)
+    starts = np.random.default_rng(91).integers(0, n_s - t, nq)
+    qs, _ = synth.perturbed_queries(np.stack([stream[p:p + t] for p in starts]), nq, seed=92)
+    d_q = torch.from_numpy(qs).to(dev)
+    gen_s = time.perf_counter() - t0
+    nwin = n_s - t + 1
+    out = {"workload": "windows of length %d at every offset of a %d-sample random-walk stream (%d windows), "
+                       "W=%d, delta=%d, n=%d, K=%d, L=%d, band 5%%, %d queries (perturbed windows), top-%d"
+                       % (t, n_s, nwin, W, delta, n, K, L, nq, k), "setup_s": gen_s}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with binding.SSHIndex(W, delta, n, K, L, band, 0) as ix:
+        for generic in (True, False):  # rows first (the stream path's index stays for the queries)
+            ix.set_hash_kernel(generic)
+            best = float("inf")
+            for _ in range(3):
+                ix.clear()
+                torch.cuda.synchronize()
+                e0.record()
+                ix.add_windows_device(d_s, t, 1)
+                e1.record()
+                e1.synchronize()
+                best = min(best, e0.elapsed_time(e1))
+            out["rows_path" if generic else "stream_path"] = {"index_ms": best,
+                                                              "windows_per_s": nwin / (best / 1000.0)}
+        ix.set_hash_kernel(False)
+        ids, ms, st = _timed_query(torch, ix, d_q, k)
+        out.update({"queries_per_s": nq / (ms / 1000.0),
+                    "candidate_fraction": st["candidates"] / max(st["queries"], 1) / nwin})
+        nrec = 4 if small else 10
+        ix.set_exact_scan(True)
+        ex_ids, ms_e, _ = _timed_query(torch, ix, d_q[:nrec].contiguous(), k, reps=1)
+        ix.set_exact_scan(False)
+        out["recall_at_10"] = recall(ids.cpu().numpy()[:nrec], ex_ids.cpu().numpy())
+        out["recall_queries"] = nrec
+        out["exact_scan_queries_per_s"] = nrec / (ms_e / 1000.0)
+    return out
+
+
 def serve_rates(srv, rates, dur, q_host, ins_pool, m, rng):
     """Open-loop serving phases: per offered rate, Poisson arrivals for `dur` seconds (queries
     drawn from q_host) while 100 random walks are inserted every 10 ms; served queries/s, p50/p99
@@ -1089,6 +1138,8 @@ def run_gpu(args, w):
         line["batched"] = batched_measurement(args, binding, torch, dev)
     if rank == 0 and world == 1 and not args.no_served:
         line["served"] = serving_measurement(args, binding, torch, dev)
+    if rank == 0 and world == 1 and not args.no_subsequence:
+        line["subsequence"] = subsequence_measurement(args, binding, torch, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         n_s = 10000 if not args.small else 300
         r = oracle_sample(w, n_s, 10 if not args.small else 3)
@@ -1119,6 +1170,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the mixed-length batch-plan measurement")
     ap.add_argument("--no-served", action="store_true", help="skip the serving-loop measurement")
+    ap.add_argument("--no-subsequence", action="store_true", help="skip the sliding-window index measurement")
     args = ap.parse_args()
     w = TINY if args.small else SCALE
     if args.impl == "reference":

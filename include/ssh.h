@@ -103,6 +103,19 @@ ssh_status ssh_index_add(ssh_index* idx, const float* series, const int32_t* len
 ssh_status ssh_index_add_device(ssh_index* idx, const float* d_series, const int32_t* lengths, int64_t count,
                                 uint32_t flags, void* stream, int64_t* first_id);
 
+/* Sec. 5.1's workload: every length-t window of one long series. Adds the
+ * windows d_stream[p, p + t) for p = 0, step, 2 step, ... with p + t <= stream_len
+ * ((stream_len - t) / step + 1 windows) as series of length t with consecutive
+ * ids (the first in *first_id, may be NULL), into the sub-index of length t.
+ * The windows are borrowed: the index keeps pointers into d_stream (device, the
+ * index's device), which must stay allocated and unchanged until
+ * ssh_index_clear or ssh_destroy. Each window is hashed exactly as the same
+ * samples added as a series would be. Stream-ordered like ssh_index_add_device.
+ * SSH_EINVAL for step < 1 or stream_len < t; SSH_ELENGTH for a t that
+ * ssh_index_add would refuse. */
+ssh_status ssh_index_add_windows_device(ssh_index* idx, const float* d_stream, int64_t stream_len, int32_t t,
+                                        int64_t step, void* stream, int64_t* first_id);
+
 /* Drop every stored series and table; parameters, filter and draw tables stay.
  * Ids restart at 0. */
 ssh_status ssh_index_clear(ssh_index* idx);

@@ -70,6 +70,8 @@ _SIGS = {
     "ssh_get_filter": (ctypes.c_int, [_P, _P]),
     "ssh_index_add": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, _I64P]),
     "ssh_index_add_device": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, ctypes.c_uint32, _P, _I64P]),
+    "ssh_index_add_windows_device": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64, _P,
+                                                    _I64P]),
     "ssh_index_clear": (ctypes.c_int, [_P]),
     "ssh_index_size": (ctypes.c_int, [_P, _I64P]),
     "ssh_query": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, ctypes.c_int, _P, _P]),
@@ -466,6 +468,14 @@ class SSHIndex:
         if lengths is None:
             lengths = np.full(d_series.shape[0], d_series.shape[1], np.int32)
         return ssh_index_add_device(self.handle, d_series, lengths, SSH_ADD_BORROW if borrow else 0, stream)
+
+    def add_windows_device(self, d_stream, t: int, step: int = 1, stream=None) -> int:
+        """Every length-t window of the 1-D device tensor d_stream at offsets 0, step, 2 step, ...
+        (borrowed: keep d_stream alive and unchanged); returns the first window's id."""
+        first = ctypes.c_int64(0)
+        _check(load().ssh_index_add_windows_device(self.handle, _dev_ptr(d_stream), d_stream.numel(), t, step,
+                                                   _stream(stream), ctypes.byref(first)))
+        return first.value
 
     def clear(self):
         ssh_index_clear(self.handle)

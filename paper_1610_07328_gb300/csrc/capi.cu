@@ -472,6 +472,19 @@ ssh_status validate_lengths(ssh_index* idx, const int32_t* lengths, int64_t coun
     return SSH_OK;
 }
 
+// The sub-index of length m (created empty on first use).
+SubIndex& sub_for(ssh_index* idx, int m, const Geometry& g) {
+    SubIndex& s = idx->subs[m];
+    if (s.m == 0) {
+        s.m = m;
+        s.nb = g.nb;
+        s.nwords = g.nwords;
+        s.S = g.S;
+        s.rb = band_radius(idx->band, m);
+    }
+    return s;
+}
+
 // Algorithm 1 (sketch, shingle, minhash and row keys) for series [i0, i1) of a
 // call whose first id is id0; `dev` points at series i0, the series back to
 // back in device memory that stays valid while the index uses it. The
@@ -485,14 +498,7 @@ ssh_status hash_range(ssh_index* idx, const float* dev, const int32_t* lengths, 
         const int64_t nrun = j - i;
         Geometry g;
         SSH_TRY(geometry(idx, m, &g));
-        SubIndex& s = idx->subs[m];
-        if (s.m == 0) {
-            s.m = m;
-            s.nb = g.nb;
-            s.nwords = g.nwords;
-            s.S = g.S;
-            s.rb = band_radius(idx->band, m);
-        }
+        SubIndex& s = sub_for(idx, m, g);
         if (std::find(touched.begin(), touched.end(), m) == touched.end()) touched.push_back(m);
         SSH_TRY(reserve(idx, s, s.count + nrun, st));
         fill_rows_kernel<<<grid_for(nrun, 256, 8192), 256, 0, st>>>(s.row_ptr + s.count, s.gid + s.count, nrun,
@@ -1109,6 +1115,52 @@ ssh_status ssh_index_add_device(ssh_index* idx, const float* d_series, const int
                                 uint32_t flags, void* stream, int64_t* first_id) {
     LaunchCount lc(idx);
     return index_add_device_impl(idx, d_series, lengths, count, flags, stream, first_id);
+}
+
+ssh_status ssh_index_add_windows_device(ssh_index* idx, const float* d_stream, int64_t stream_len, int32_t t,
+                                        int64_t step, void* stream, int64_t* first_id) {
+    LaunchCount lc(idx);
+    if (!idx || !d_stream || step < 1 || t < 1 || stream_len < t)
+        return fail(SSH_EINVAL, "windows: need a stream, step >= 1 and 1 <= t <= stream_len");
+    SSH_TRY(check_device(idx));
+    SSH_TRY(validate_lengths(idx, &t, 1));
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t count = (stream_len - t) / step + 1;
+    Geometry g;
+    SSH_TRY(geometry(idx, t, &g));
+    SubIndex& s = sub_for(idx, t, g);
+    SSH_TRY(reserve(idx, s, s.count + count, st));
+    // row p of the call is the window that starts at sample p * step
+    fill_rows_kernel<<<grid_for(count, 256, 8192), 256, 0, st>>>(s.row_ptr + s.count, s.gid + s.count, count,
+                                                                 d_stream, step, idx->next_id);
+    note_launch();
+    SSH_CUDA(cudaGetLastError());
+    HashArgs a = base_hash_args(idx, t, g);
+    a.rows = s.row_ptr + s.count;
+    a.count = count;
+    a.keys = s.keys;
+    a.key_stride = s.cap;
+    a.key_col0 = s.count;
+    if (!a.force_generic && step < g.nb && hash_windows_supported(a)) {
+        // overlapping windows share their sketch positions: the stream's bits and
+        // shingle ids are computed once (N_B / step times fewer dot products)
+        static const char* names[4] = {"add.sketch", "add.sketch_fixup", "add.shingle", "add.cws"};
+        void* scratch = nullptr;
+        SSH_CUDA(cudaMallocAsync(&scratch, hash_windows_scratch_bytes(a, step), st));
+        cudaError_t e = cudaSuccess;
+        for (int stage = 0; stage < 4 && e == cudaSuccess; ++stage) {
+            TimedRegion tr(idx, st, names[stage], (double)count);
+            e = hash_windows_stage(a, d_stream, step, scratch, stage, st);
+        }
+        cudaError_t f = cudaFreeAsync(scratch, st);
+        SSH_CUDA(e);
+        SSH_CUDA(f);
+    } else {
+        SSH_TRY(run_hash(idx, a, st, "add"));
+    }
+    s.count += count;
+    idx->host_stats.series_hashed += count;
+    return finish_add(idx, std::vector<int>{t}, count, st, first_id, false);
 }
 
 ssh_status ssh_query(ssh_index* idx, const float* queries, const int32_t* lengths, int64_t nq, int k, int64_t* ids,

@@ -268,8 +268,12 @@ __host__ __device__ inline ShingleLayout shingle_layout(int S, bool sorted_out) 
 // fills an empty slot owns the id, a lane that meets its id adds 1 to the
 // count, any other id in the slot moves it on to the next slot. The owners
 // then write the set, count-1 ids first, and clear their slots.
+// WIN: the rows are the windows of one stream (window k starts at sample
+// k * step) and shingle i of window k is the id precomputed at stream position
+// k * step + i * delta (stream_ids_kernel); otherwise ids come from the row's bits.
+template <bool WIN>
 __global__ void __launch_bounds__(256) shingle_kernel(HashArgs a, const uint32_t* gbits, uint32_t* sets,
-                                                      int2* sizes) {
+                                                      int2* sizes, const uint16_t* sh, int64_t step) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
     const int nwords = a.nwords, S = a.S, n = a.n;
@@ -290,14 +294,19 @@ __global__ void __launch_bounds__(256) shingle_kernel(HashArgs a, const uint32_t
     int64_t r0, r1;
     row_range(a, &r0, &r1);
     for (int64_t row = r0 + (int64_t)blockIdx.x * wpb + warp; row < r1; row += nwarps) {
-        const uint32_t* brow = gbits + row * nwords;
-        uint32_t hi = __ldg(brow);
+        const uint32_t* brow = WIN ? nullptr : gbits + row * nwords;
+        uint32_t hi = WIN ? 0u : __ldg(brow);
         for (int t = 0; t < rounds; ++t) {
-            const uint32_t lo = (t + 1 < nwords) ? __ldg(brow + t + 1) : 0u;
+            const uint32_t lo = (!WIN && t + 1 < nwords) ? __ldg(brow + t + 1) : 0u;
             const int i = lane + 32 * t;
             if (i < S) {
-                const uint64_t bb = ((uint64_t)hi << 32) | (uint64_t)lo;
-                const uint32_t id = (uint32_t)((bb << lane) >> (64 - n));
+                uint32_t id;
+                if constexpr (WIN) {
+                    id = __ldg(sh + row * step + (int64_t)i * a.delta);
+                } else {
+                    const uint64_t bb = ((uint64_t)hi << 32) | (uint64_t)lo;
+                    id = (uint32_t)((bb << lane) >> (64 - n));
+                }
                 uint32_t h = (id * 0x9E3779B1u) >> tshift;
                 uint32_t own = 0u;
                 // at most S distinct ids in 2S slots: an empty slot or the id itself
@@ -592,21 +601,27 @@ int warps_for(size_t per_warp) {
     return w;
 }
 
-cudaError_t launch_shingle(const HashArgs& a, const uint32_t* bits, uint32_t* sets, int2* sizes, cudaStream_t st) {
+template <bool WIN>
+cudaError_t launch_shingle_t(const HashArgs& a, const uint32_t* bits, uint32_t* sets, int2* sizes, const uint16_t* sh,
+                             int64_t step, cudaStream_t st) {
     const ShingleLayout lay = shingle_layout(a.S, a.sh_ids_out != nullptr);
     const int wpb = warps_for((size_t)lay.total);
     if (wpb < 1) return cudaErrorInvalidValue;
     const size_t smem = (size_t)wpb * lay.total;
-    cudaError_t e = ensure_dynamic_smem((const void*)shingle_kernel, smem);
+    cudaError_t e = ensure_dynamic_smem((const void*)shingle_kernel<WIN>, smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, shingle_kernel, wpb * 32, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, shingle_kernel<WIN>, wpb * 32, smem);
     int64_t grid = (int64_t)sms_of_device() * (per_sm > 0 ? per_sm : 1);
     const int64_t need = (a.count + wpb - 1) / wpb;
     if (grid > need) grid = need;
-    shingle_kernel<<<(unsigned)grid, wpb * 32, smem, st>>>(a, bits, sets, sizes);
+    shingle_kernel<WIN><<<(unsigned)grid, wpb * 32, smem, st>>>(a, bits, sets, sizes, sh, step);
     note_launch();
     return cudaGetLastError();
+}
+
+cudaError_t launch_shingle(const HashArgs& a, const uint32_t* bits, uint32_t* sets, int2* sizes, cudaStream_t st) {
+    return launch_shingle_t<false>(a, bits, sets, sizes, nullptr, 0, st);
 }
 
 cudaError_t launch_cws(const HashArgs& a, const uint32_t* sets, const int2* sizes, cudaStream_t st) {
@@ -642,6 +657,92 @@ const SketchShape kSketchShapes[] = {
     {64, 3, 5, 1},   {128, 3, 10, 1}, {256, 3, 19, 1},
 };
 
+// ---------------------------------------------- windows of one stream (Sec. 5.1)
+//
+// Window k of a stream starts at sample k * step; its sketch bit i is the sign
+// of r . s[k step + i delta, + W), which depends only on the stream position
+// j = k step + i delta. So the bits of every position are computed once
+// (stream_sketch_kernel, with the same FP64 fix-up rule as sketch_kernel), then
+// the n-bit shingle id of every position (stream_ids_kernel: bits j, j + delta,
+// ..., j + (n-1) delta, first bit most significant), and a window's shingles
+// are the ids at positions k step + i delta, i < S (shingle_kernel<true>).
+
+// Bits of positions [0, J): word j / 32, bit 31 - j % 32. A thread per position;
+// a block stages its 256 positions' samples (256 + W - 1) and r in shared memory.
+__global__ void __launch_bounds__(256) stream_sketch_kernel(HashArgs a, const float* s, int64_t J, uint32_t* bits,
+                                                            unsigned long long* fix, unsigned long long cap,
+                                                            unsigned long long* nfix) {
+    extern __shared__ float ssm[];
+    const int W = a.W;
+    float* r_s = ssm;
+    float* xs = ssm + ((W + 3) & ~3);
+    for (int i = threadIdx.x; i < W; i += blockDim.x) r_s[i] = a.r[i];
+    unsigned long long n_inplace = 0;
+    const int64_t send = J + W - 1;  // samples the positions read
+    for (int64_t j0 = (int64_t)blockIdx.x * 256; j0 < J; j0 += (int64_t)gridDim.x * 256) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < 256 + W - 1; i += blockDim.x) xs[i] = (j0 + i < send) ? __ldg(s + j0 + i) : 0.f;
+        __syncthreads();
+        const int64_t j = j0 + threadIdx.x;
+        bool bit = false;
+        if (j < J) {
+            float acc = 0.f, e = 0.f;
+            for (int t = 0; t < W; ++t) {
+                const float xv = xs[threadIdx.x + t];
+                acc = fmaf(r_s[t], xv, acc);
+                e = fmaf(xv, xv, e);
+            }
+            // e carries at most W roundings of relative 2^-24 each: inflate it past them
+            const float e_up = __fmul_ru(e, 1.0f + (float)(2 * W + 64) * 5.9604645e-08f);
+            const float thr = __fmul_ru(a.tau_norm, __fsqrt_ru(__fmul_ru(e_up, 1.0f + a.gamma_ss)));
+            if (fabsf(acc) > thr) {
+                bit = acc >= 0.f;
+            } else {
+                const unsigned long long slot = atomicAdd(nfix, 1ull);
+                if (slot < cap) {
+                    fix[slot] = (unsigned long long)j;
+                } else {
+                    double d = 0.0;  // list full: the definition's FP64 order, in place
+                    for (int t = 0; t < W; ++t) d = fma((double)r_s[t], (double)xs[threadIdx.x + t], d);
+                    bit = d >= 0.0;
+                    n_inplace += 1;
+                }
+            }
+        }
+        const unsigned bal = __ballot_sync(kFull, bit);
+        const int64_t jw = j0 + (threadIdx.x & ~31);
+        if ((threadIdx.x & 31) == 0 && jw < J) bits[jw >> 5] = __brev(bal);
+    }
+    if (n_inplace && a.stats) atomicAdd(&a.stats[kStatSketch64], n_inplace);
+}
+
+// One thread per listed position: FP64 in the definition's order, as sketch_fixup_kernel.
+__global__ void stream_fixup_kernel(HashArgs a, const float* s, uint32_t* bits, const unsigned long long* fix,
+                                    const unsigned long long* nfix, unsigned long long cap) {
+    const unsigned long long n = min(*nfix, cap);
+    for (unsigned long long t = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; t < n;
+         t += (unsigned long long)gridDim.x * blockDim.x) {
+        const int64_t j = (int64_t)fix[t];
+        const float* xw = s + j;
+        double d = 0.0;
+        for (int q = 0; q < a.W; ++q) d = fma((double)__ldg(a.r + q), (double)__ldg(xw + q), d);
+        if (d >= 0.0) atomicOr(&bits[j >> 5], 1u << (31 - (j & 31)));
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && a.stats && n) atomicAdd(&a.stats[kStatSketch64], n);
+}
+
+// The n-bit shingle id of every position j in [0, Jsh): bits j + b delta, b < n, first bit most significant.
+__global__ void stream_ids_kernel(const uint32_t* bits, int64_t Jsh, int n, int delta, uint16_t* sh) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < Jsh; j += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t id = 0;
+        for (int b = 0; b < n; ++b) {
+            const int64_t q = j + (int64_t)b * delta;
+            id = (id << 1) | ((__ldg(bits + (q >> 5)) >> (31 - (q & 31))) & 1u);
+        }
+        sh[j] = (uint16_t)id;
+    }
+}
+
 bool sketch_shape_ok(const SketchShape& s, const HashArgs& a) {
     const int lps = 32 / s.spw;
     return s.W == a.W && s.delta == a.delta && a.nb <= lps * s.R && a.nb > lps * (s.R - 1) && a.nb < 65536;
@@ -654,6 +755,78 @@ bool hash_fast_supported(const HashArgs& a) {
     for (const SketchShape& s : kSketchShapes) ok |= sketch_shape_ok(s, a);
     return ok && a.n <= 16 && a.S >= 1 && warps_for((size_t)shingle_layout(a.S, true).total) >= 1 &&
            warps_for((size_t)cws_layout(a.S, a.KL).total) >= 1;
+}
+
+bool hash_windows_supported(const HashArgs& a) {
+    return a.n <= 16 && a.S >= 1 && warps_for((size_t)shingle_layout(a.S, a.sh_ids_out != nullptr).total) >= 1 &&
+           warps_for((size_t)cws_layout(a.S, a.KL).total) >= 1;
+}
+
+// Scratch of the window path: position bits, the fix-up counter and list, the
+// position ids, the windows' weighted sets [count][S] and sizes [count].
+struct WinScratch {
+    size_t bits, nfix, fix, sh, sets, sizes, total;
+    int64_t J, Jsh;
+    unsigned long long fix_cap;
+};
+
+WinScratch win_scratch(const HashArgs& a, int64_t step) {
+    WinScratch f;
+    auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    f.J = (a.count - 1) * step + (int64_t)(a.nb - 1) * a.delta + 1;
+    f.Jsh = (a.count - 1) * step + (int64_t)(a.S - 1) * a.delta + 1;
+    f.fix_cap = (unsigned long long)f.J / 8ull + 65536ull;
+    size_t off = 0;
+    f.bits = off; off += up((size_t)((f.J + 31) / 32) * sizeof(uint32_t));
+    f.nfix = off; off += 256;
+    f.fix = off; off += up((size_t)f.fix_cap * sizeof(unsigned long long));
+    f.sh = off; off += up((size_t)f.Jsh * sizeof(uint16_t));
+    f.sets = off; off += up((size_t)a.count * a.S * sizeof(uint32_t));
+    f.sizes = off; off += up((size_t)a.count * sizeof(int2));
+    f.total = off;
+    return f;
+}
+
+size_t hash_windows_scratch_bytes(const HashArgs& a, int64_t step) { return win_scratch(a, step).total; }
+
+cudaError_t hash_windows_stage(const HashArgs& a, const float* s, int64_t step, void* scratch, int stage,
+                               cudaStream_t st) {
+    const WinScratch f = win_scratch(a, step);
+    unsigned char* p = static_cast<unsigned char*>(scratch);
+    uint32_t* bits = reinterpret_cast<uint32_t*>(p + f.bits);
+    unsigned long long* nfix = reinterpret_cast<unsigned long long*>(p + f.nfix);
+    unsigned long long* fix = reinterpret_cast<unsigned long long*>(p + f.fix);
+    uint16_t* sh = reinterpret_cast<uint16_t*>(p + f.sh);
+    uint32_t* sets = reinterpret_cast<uint32_t*>(p + f.sets);
+    int2* sizes = reinterpret_cast<int2*>(p + f.sizes);
+    cudaError_t e = cudaSuccess;
+    if (stage == 0) {  // sketch of every position
+        e = cudaMemsetAsync(nfix, 0, sizeof(unsigned long long), st);
+        if (e != cudaSuccess) return e;
+        const size_t smem = (size_t)(((a.W + 3) & ~3) + 256 + a.W) * sizeof(float);
+        e = ensure_dynamic_smem((const void*)stream_sketch_kernel, smem);
+        if (e != cudaSuccess) return e;
+        const int64_t g = std::min<int64_t>((f.J + 255) / 256, (int64_t)sms_of_device() * 8);
+        stream_sketch_kernel<<<(unsigned)std::max<int64_t>(g, 1), 256, smem, st>>>(a, s, f.J, bits, fix, f.fix_cap,
+                                                                                   nfix);
+        note_launch();
+        return cudaGetLastError();
+    }
+    if (stage == 1) {  // FP64 fix-up of the listed positions
+        const int64_t g = std::max<int64_t>(1, std::min<int64_t>((f.J / 64 + 255) / 256, 8192));
+        stream_fixup_kernel<<<(unsigned)g, 256, 0, st>>>(a, s, bits, fix, nfix, f.fix_cap);
+        note_launch();
+        return cudaGetLastError();
+    }
+    if (stage == 2) {  // position ids, then the windows' weighted sets
+        const int64_t g = std::max<int64_t>(1, std::min<int64_t>((f.Jsh + 255) / 256, 8192));
+        stream_ids_kernel<<<(unsigned)g, 256, 0, st>>>(bits, f.Jsh, a.n, a.delta, sh);
+        note_launch();
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        return launch_shingle_t<true>(a, nullptr, sets, sizes, sh, step, st);
+    }
+    return launch_cws(a, sets, sizes, st);  // stage 3: weighted minhash and bucket keys
 }
 
 // Scratch of the split hash path: bits [count][nwords], the fix-up counter and

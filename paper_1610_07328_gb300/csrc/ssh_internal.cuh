@@ -114,6 +114,16 @@ struct HashArgs {
 bool hash_fast_supported(const HashArgs& a);
 cudaError_t launch_hash_fast(const HashArgs& a, cudaStream_t st);
 
+// Windows of one stream (row k = samples [k step, k step + m)): the sketch bits
+// and shingle ids of every stream position computed once, then the windows'
+// sets and the minhash. Stages 0 sketch, 1 FP64 fix-up, 2 ids and sets, 3 CWS
+// and keys, over one scratch block of hash_windows_scratch_bytes(a, step) bytes;
+// a.count = windows, a.keys / key_stride / key_col0 as for rows.
+bool hash_windows_supported(const HashArgs& a);
+size_t hash_windows_scratch_bytes(const HashArgs& a, int64_t step);
+cudaError_t hash_windows_stage(const HashArgs& a, const float* stream, int64_t step, void* scratch, int stage,
+                               cudaStream_t st);
+
 // The specialised hash path in stages (sketch -> FP64 fix-up -> shingle -> CWS)
 // over one scratch block of hash_fast_scratch_bytes(a) bytes.
 struct FastHashBuffers {

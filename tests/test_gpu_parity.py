@@ -665,3 +665,53 @@ def test_read_probe_runs_and_rejects_bad_sizes():
     assert e.value.status == binding.SSH_EINVAL
     with pytest.raises(binding.SSHError):
         binding.ssh_read_device(x, 0)
+
+
+# the paper's Random Walk parameters (Sec. 5.1: W = 30, delta = 5, n = 15, one hash per table, 20 tables)
+CFG_RW = dict(W=30, delta=5, n=15, K=1, L=20, band=0.05, seed=0)
+
+
+@pytest.mark.parametrize("cfg,step,generic", [(CFG1, 1, False), (CFG1, 7, False), (CFG1, 1, True),
+                                              (CFG1, 40, False), (CFG_RW, 1, False), (CFG_RW, 3, True)],
+                         ids=["cfg1-step1", "cfg1-step7", "cfg1-step1-rows", "cfg1-step40-rows", "rw-step1",
+                              "rw-step3-rows"])
+def test_windows_of_one_stream_equal_the_oracle_over_the_same_windows(cfg, step, generic):
+    """Sec. 5.1's workload: every length-t window of one long series (offsets 0, step, ...),
+    added without copies; queries must return the oracle's top-k over the same windows added
+    one by one as series, and a window used as the query finds itself at distance 0. Steps
+    below N_B take the shared-stream sketch; larger steps and the generic-kernel knob hash the
+    windows as rows."""
+    b = _binding()
+    stream = synth.random_walk(1, 2400, seed=31)[0]
+    t = 128
+    starts = list(range(0, len(stream) - t + 1, step))
+    windows = np.stack([stream[p:p + t] for p in starts])
+    d_stream = torch.from_numpy(stream).cuda()
+    extra = synth.random_walk(3, t, seed=33)  # ids of the windows follow these
+    ref = oracle.OracleIndex(**cfg)
+    ref.add(extra)
+    ref.add(windows)
+    rows = np.concatenate([extra, windows])
+    qs, _ = synth.perturbed_queries(windows, 5, seed=32)
+    qs = np.concatenate([qs, windows[len(windows) // 3][None]])
+    with _index(cfg) as idx:
+        idx.set_hash_kernel(generic)
+        idx.add(extra)
+        first = idx.add_windows_device(d_stream, t, step)
+        assert first == 3 and len(idx) == 3 + len(starts)
+        ids, d = idx.query(qs, 5)
+        with pytest.raises(b.SSHError) as e:
+            idx.add_windows_device(d_stream, t, 0)
+        assert e.value.status == b.SSH_EINVAL
+        with pytest.raises(b.SSHError) as e:
+            idx.add_windows_device(d_stream[:100], t, 1)
+        assert e.value.status == b.SSH_EINVAL
+        with pytest.raises(b.SSHError) as e:
+            idx.add_windows_device(d_stream, 40, 1)  # shorter than W + (n-1) delta (53 or 100)
+        assert e.value.status == b.SSH_ELENGTH
+        assert len(idx) == 3 + len(starts)
+    rb = oracle.band_radius(cfg["band"], t)
+    for i, q in enumerate(qs):
+        oi, od = ref.query(q, 5)
+        assert_topk_match(q, ids[i], d[i], oi, od, lambda j: rows[j], rb)
+    assert ids[-1][0] == 3 + len(windows) // 3 and d[-1][0] == 0.0
