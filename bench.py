@@ -381,6 +381,20 @@ def recall(ids, exact):
     return float(np.mean(r))
 
 
+def ndcg(ids, exact):
+    """Mean NDCG@k (Sec. 5.3, standard DCG): a returned id's relevance is k - g + 1 for gold
+    rank g (1..k) in the exact top-k, 0 outside it; position i (1..k) is discounted by
+    log2(i + 1); normalised by the DCG of the exact list."""
+    out = []
+    for a, b in zip(ids, exact):
+        k = len(b)
+        rel = {int(g): k - r for r, g in enumerate(b)}
+        dcg = sum(rel.get(int(x), 0) / math.log2(p + 2) for p, x in enumerate(list(a)[:k]))
+        idcg = sum((k - r) / math.log2(r + 2) for r in range(k))
+        out.append(dcg / idcg if idcg > 0 else 1.0)
+    return float(np.mean(out))
+
+
 # Parameter sets tried for the recall operating point, from the most to the
 # least selective; the operating point is the fastest one with recall@10 >= 0.9.
 OPERATING_POINTS = [
@@ -396,7 +410,17 @@ def sweep_points(binding, torch, d_sub, d_q, exact, points, band, seed, k, n_pla
     out = []
     for (W, delta, n, K, L) in points:
         with binding.SSHIndex(W, delta, n, K, L, band, seed) as ix:
-            ix.add_device(d_sub)
+            ix.add_device(d_sub)  # warm-up build (first use of the shapes)
+            build = float("inf")
+            for _ in range(2):
+                ix.clear()
+                b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                b0.record()
+                ix.add_device(d_sub)
+                b1.record()
+                b1.synchronize()
+                build = min(build, b0.elapsed_time(b1))
             ids = torch.empty((nq, k), dtype=torch.int64, device=d_q.device)
             dd = torch.empty((nq, k), dtype=torch.float32, device=d_q.device)
             ix.query_device(d_q, k, ids, dd)  # warm-up (and the DTW tiling's timing)
@@ -423,6 +447,7 @@ def sweep_points(binding, torch, d_sub, d_q, exact, points, band, seed, k, n_pla
                 e1.synchronize()
                 lat.append(e0.elapsed_time(e1))
         out.append({"W": W, "delta": delta, "n": n, "K": K, "L": L, "recall_at_10": r10,
+                    "ndcg_at_10": ndcg(ids.cpu().numpy(), exact), "index_ms": build,
                     "candidate_fraction": st["candidates"] / (3 * nq) / n_sub,
                     "queries_per_s": nq / (best / 1000.0),
                     "plain_gpu_path_queries_per_s": 1000.0 / statistics.mean(lat) if lat else None})
@@ -435,6 +460,27 @@ def sweep_points(binding, torch, d_sub, d_q, exact, points, band, seed, k, n_pla
 def recall_operating_point(binding, torch, d_sub, d_q, exact, w, k):
     """The OPERATING_POINTS sweep on the recall subset of the scale workload."""
     return sweep_points(binding, torch, d_sub, d_q, exact, OPERATING_POINTS, w["band"], w["seed"], k)
+
+
+# Sec. 5.5's parameter study on the scale workload's recall subset: the window W,
+# the step delta and the shingle length n, one at a time around (80, 3, 15), K=4, L=25.
+STUDY_POINTS = {
+    "W": [(W, 3, 15, 4, 25) for W in (40, 80, 120, 160)],
+    "delta": [(80, d, 15, 4, 25) for d in (1, 2, 3, 5, 8)],
+    "n": [(80, 3, n, 4, 25) for n in (8, 10, 12, 15)],
+}
+
+
+def parameter_study(binding, torch, d_sub, d_q, exact, w, k):
+    """recall@10, NDCG@10, candidate fraction, index build time and queries/s as W, delta and n vary."""
+    out = {}
+    for name, pts in STUDY_POINTS.items():
+        sw = sweep_points(binding, torch, d_sub, d_q, exact, pts, w["band"], w["seed"], k, n_plain=0)
+        out[name] = [{key: p[key] for key in ("W", "delta", "n", "recall_at_10", "ndcg_at_10", "candidate_fraction",
+                                              "index_ms", "queries_per_s")} for p in sw["points"]]
+    out["subset"] = int(d_sub.shape[0])
+    out["queries"] = int(d_q.shape[0])
+    return out
 
 
 def _timed_query(torch, ix, d_q, k, reps=3):
@@ -1034,9 +1080,11 @@ def run_gpu(args, w):
             s_ids = s_ids.cpu().numpy()
         exact_sub = exact_topk_gpu(binding, torch, d_q, d_sub.contiguous(), subset_rows, m, rb, k)
         extra["recall_at_10"] = recall(s_ids, exact_sub)
+        extra["ndcg_at_10"] = ndcg(s_ids, exact_sub)
         extra["recall_at_1"] = float(np.mean([s_ids[i, 0] == exact_sub[i, 0] for i in range(nq)]))
         extra["recall_operating_point"] = recall_operating_point(binding, torch, d_sub.contiguous(), d_q,
                                                                  exact_sub, w, k)
+        extra["parameter_study"] = parameter_study(binding, torch, d_sub.contiguous(), d_q, exact_sub, w, k)
         extra["exact_scan"] = exact_scan_measurement(binding, torch, d_sub.contiguous(), d_db, d_q, exact_sub, w, k,
                                                      n_full=4 if args.small else 10)
         if not args.fast:

@@ -21,7 +21,8 @@ Massive-Scale Time Series", arXiv:1610.07328.
 * Sec. 2.1 (DTW by dynamic programming) -> ``dtw``; Sec. 3 (LB_Keogh) -> ``lb_keogh``,
   with the UCR suite's cascade the paper prunes with: ``lb_kim_fl``, ``lb_keogh_kim``,
   ``lb_keogh_rev``
-* Sec. 5.3 (precision of the top-k against the exact DTW top-k) -> ``recall_at_k``
+* Sec. 5.3 (precision of the top-k against the exact DTW top-k) -> ``recall_at_k``;
+  (NDCG of the ranking) -> ``ndcg_at_k``
 """
 from __future__ import annotations
 
@@ -264,6 +265,25 @@ def recall_at_k(returned_ids, exact_ids) -> float:
     if not exact:
         return 1.0
     return sum(1 for i in exact if i in got) / float(len(exact_ids))
+
+
+def ndcg_at_k(returned_ids, gold_ids) -> float:
+    """Sec. 5.3's NDCG of a returned top-k against the gold (exact DTW) top-k, k = len(gold_ids).
+    The printed DCG divides by log2(i) for positions i = 1..k, which is 0 at i = 1, and gives
+    R_i = k - i: read as the standard DCG, sum over result positions i = 1..k of
+    rel / log2(i + 1), with a result's graded relevance k - g + 1 where g (1..k) is its rank in
+    the gold list (k for the gold first, 1 for the gold k-th, 0 outside it); IDCG is the DCG
+    of the gold list itself."""
+    gold = [int(i) for i in gold_ids]
+    k = len(gold)
+    if k == 0:
+        return 1.0
+    rel = {g: k - r for r, g in enumerate(gold) if g >= 0}  # r = g - 1: relevance k .. 1
+    dcg = 0.0
+    for pos, i in enumerate(list(returned_ids)[:k]):
+        dcg += rel.get(int(i), 0) / np.log2(pos + 2.0)
+    idcg = sum((k - r) / np.log2(r + 2.0) for r, g in enumerate(gold) if g >= 0)
+    return dcg / idcg if idcg > 0 else 1.0
 
 
 # ------------------------------------------------------------------ the index

@@ -444,6 +444,36 @@ def test_lb_cascade_band0_is_euclidean():
     assert oracle.lb_keogh_rev(q, c, 0) == pytest.approx(euclid, rel=1e-12)
 
 
+# ------------------------------------------------------------------- Sec. 5.3
+
+def test_ndcg_hand_computed():
+    """Gold [a, b, c] has relevances 3, 2, 1; returned [c, b, a] scores
+    1/log2(2) + 2/log2(3) + 3/log2(4) = 1 + 1.26186 + 1.5 against the ideal
+    3/log2(2) + 2/log2(3) + 1/log2(4) = 3 + 1.26186 + 0.5."""
+    gold = [7, 3, 9]
+    assert oracle.ndcg_at_k([7, 3, 9], gold) == pytest.approx(1.0)
+    want = (1 + 2 / math.log2(3) + 1.5) / (3 + 2 / math.log2(3) + 0.5)
+    assert oracle.ndcg_at_k([9, 3, 7], gold) == pytest.approx(want, rel=1e-12)
+    assert oracle.ndcg_at_k([1, 2, 4], gold) == 0.0
+    # the gold first item alone at the last position: 3 / log2(4)
+    assert oracle.ndcg_at_k([1, 2, 7], gold) == pytest.approx(1.5 / (3 + 2 / math.log2(3) + 0.5), rel=1e-12)
+    assert oracle.ndcg_at_k([5], [5]) == 1.0 and oracle.ndcg_at_k([6], [5]) == 0.0
+
+
+def test_ndcg_orders_and_recall():
+    """Swapping two adjacent returned items lowers NDCG unless both are outside the gold list,
+    and a permutation of the gold list keeps recall 1 while NDCG < 1."""
+    rng = np.random.default_rng(16)
+    gold = list(rng.permutation(50)[:10])
+    base = oracle.ndcg_at_k(gold, gold)
+    assert base == pytest.approx(1.0)
+    for t in range(9):
+        sw = list(gold)
+        sw[t], sw[t + 1] = sw[t + 1], sw[t]
+        assert oracle.ndcg_at_k(sw, gold) < base
+        assert oracle.recall_at_k(sw, gold) == 1.0
+
+
 # --------------------------------------------------------- Algorithms 1 and 2
 
 def test_topk_matches_sort():
@@ -506,3 +536,19 @@ def test_index_rejects_short_series():
     with pytest.raises(ValueError):
         idx.add([np.zeros(52, np.float32)])
     idx.add([np.zeros(53, np.float32)])
+
+
+def test_bench_ndcg_matches_the_oracle():
+    """bench.py reports NDCG with its own code; it must agree with the oracle's definition."""
+    import importlib.util
+    import os
+    spec = importlib.util.spec_from_file_location(
+        "bench_mod", os.path.join(os.path.dirname(os.path.dirname(__file__)), "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    rng = np.random.default_rng(17)
+    for _ in range(30):
+        gold = list(rng.permutation(40)[:10])
+        got = list(rng.choice(np.concatenate([gold, rng.integers(40, 60, 10)]), 10, replace=False))
+        assert bench.ndcg([got], [gold]) == pytest.approx(oracle.ndcg_at_k(got, gold), rel=1e-12)
+        assert bench.recall([got], [gold]) == pytest.approx(oracle.recall_at_k(got, gold), rel=1e-12)
