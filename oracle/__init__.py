@@ -71,6 +71,8 @@ def _load():
             "ssh_oracle_philox4x32_10": (None, [u32p, u32p, u32p]),
             "ssh_oracle_uniform": (ctypes.c_double, [ctypes.c_uint32]),
             "ssh_oracle_filter": (None, [ctypes.c_uint64, ctypes.c_int, f32p]),
+            "ssh_oracle_srp_projection": (None, [ctypes.c_uint64, ctypes.c_int, ctypes.c_int, f32p]),
+            "ssh_oracle_srp_bits": (None, [f32p, ctypes.c_int, ctypes.c_uint64, ctypes.c_int, u32p]),
             "ssh_oracle_num_bits": (ctypes.c_int, [ctypes.c_int] * 3),
             "ssh_oracle_sketch": (None, [f32p, ctypes.c_int, f32p, ctypes.c_int, ctypes.c_int, u8p]),
             "ssh_oracle_window_dot": (ctypes.c_double, [f32p, f32p, ctypes.c_int, ctypes.c_int]),
@@ -125,6 +127,21 @@ def filter_r(seed: int, W: int) -> np.ndarray:
     """Sec. 4.1: the Gaussian filter r (FP32 values)."""
     out = np.zeros(W, dtype=np.float32)
     _load().ssh_oracle_filter(int(seed), int(W), _ptr(out, ctypes.c_float))
+    return out
+
+
+def srp_projection(seed: int, m: int, j: int) -> np.ndarray:
+    """The SRP baseline's projection j for series of length m (FP32 normals)."""
+    out = np.zeros(m, dtype=np.float32)
+    _load().ssh_oracle_srp_projection(int(seed), int(m), int(j), _ptr(out, ctypes.c_float))
+    return out
+
+
+def srp_bits(x, seed: int, nhash: int) -> np.ndarray:
+    """Sign random projections (the paper's SRP baseline, Sec. 5.2): bit j = [r_j . x >= 0]."""
+    x = _f32(x)
+    out = np.zeros(nhash, dtype=np.uint32)
+    _load().ssh_oracle_srp_bits(_ptr(x, ctypes.c_float), len(x), int(seed), int(nhash), _ptr(out, ctypes.c_uint32))
     return out
 
 
@@ -297,9 +314,14 @@ class OracleIndex:
     per-length collections, and a query only sees series of its own length.
     """
 
-    def __init__(self, W: int, delta: int, n: int, K: int, L: int, band: float, seed: int):
+    def __init__(self, W: int, delta: int, n: int, K: int, L: int, band: float, seed: int, family: str = "ssh"):
         if W < 1 or delta < 1 or n < 1 or n > 32 or K < 1 or L < 1 or not band >= 0:
             raise ValueError("invalid SSH parameters")
+        if family not in ("ssh", "srp"):
+            raise ValueError("family is 'ssh' or 'srp'")
+        # "srp": the paper's baseline, K sign random projections of the whole series per
+        # table (hash values (bit, 0) in the same key fold); W, delta and n are unused
+        self.family = family
         self.W, self.delta, self.n, self.K, self.L = W, delta, n, K, L
         self.band = float(np.float32(band))
         self.seed = int(seed)
@@ -311,13 +333,16 @@ class OracleIndex:
         self.next_id = 0
 
     def min_length(self) -> int:
-        return self.W + (self.n - 1) * self.delta
+        return 1 if self.family == "srp" else self.W + (self.n - 1) * self.delta
 
     def tuples(self, kstar, tstar):
         K = self.K
         return [tuple((int(kstar[l * K + i]), int(tstar[l * K + i])) for i in range(K)) for l in range(self.L)]
 
     def hash(self, x):
+        if self.family == "srp":
+            bits = srp_bits(x, self.seed, self.K * self.L)
+            return bits, np.zeros_like(bits)
         h = hash_series(x, self.r, self.delta, self.n, self.seed, self.K, self.L)
         if h is None:
             raise ValueError(f"series of length {len(x)} is shorter than W + (n-1)*delta = {self.min_length()}")

@@ -52,6 +52,7 @@ double ssh_oracle_uniform(uint32_t x) {
 /* Domain tags keep the filter draws and the minhash draws on disjoint counters. */
 #define TAG_FILTER 0x46494C54u /* "FILT" */
 #define TAG_CWS 0x43575331u    /* "CWS1" */
+#define TAG_SRP 0x53525031u    /* "SRP1" */
 
 static void seed_key(uint64_t seed, uint32_t key[2]) {
     key[0] = (uint32_t)(seed & 0xFFFFFFFFu);
@@ -76,6 +77,39 @@ void ssh_oracle_filter(uint64_t seed, int W, float* r_out) {
         double z = (j % 2 == 0) ? radius * cos(angle) : radius * sin(angle);
         r_out[j] = (float)z;
     }
+}
+
+/* The SRP baseline (Sec. 5.2, Table 2): projection j of length m has i.i.d.
+ * normal entries, Box-Muller on the Philox block with counter (i/2, j, SRP1, m)
+ * (cosine branch for even i, sine for odd i), each rounded once to FP32. */
+void ssh_oracle_srp_projection(uint64_t seed, int m, int j, float* r_out) {
+    uint32_t key[2];
+    seed_key(seed, key);
+    const double two_pi = 6.283185307179586476925286766559;
+    for (int i = 0; i < m; ++i) {
+        uint32_t ctr[4] = {(uint32_t)(i / 2), (uint32_t)j, TAG_SRP, (uint32_t)m};
+        uint32_t blk[4];
+        ssh_oracle_philox4x32_10(ctr, key, blk);
+        double u1 = ssh_oracle_uniform(blk[0]);
+        double u2 = ssh_oracle_uniform(blk[1]);
+        double radius = sqrt(-2.0 * log(u1));
+        double angle = two_pi * u2;
+        double z = (i % 2 == 0) ? radius * cos(angle) : radius * sin(angle);
+        r_out[i] = (float)z;
+    }
+}
+
+/* Sign random projections of x over the whole series: bit j = [r_j . x >= 0],
+ * the dot product in FP64, summed in index order. */
+void ssh_oracle_srp_bits(const float* x, int m, uint64_t seed, int nhash, uint32_t* bits_out) {
+    float* r = (float*)malloc(sizeof(float) * (size_t)m);
+    for (int j = 0; j < nhash; ++j) {
+        ssh_oracle_srp_projection(seed, m, j, r);
+        double d = 0.0;
+        for (int i = 0; i < m; ++i) d = d + (double)r[i] * (double)x[i];
+        bits_out[j] = d >= 0.0 ? 1u : 0u;
+    }
+    free(r);
 }
 
 /* ---------------------------------------------------------------- Sketch */

@@ -34,6 +34,9 @@ double ssh_oracle_uniform(uint32_t x);
 /* The random filter r of Sec. 4.1 (entries i.i.d. N(0,1)), drawn from `seed` with
  * Box-Muller on Philox uniforms and rounded once to FP32. */
 void ssh_oracle_filter(uint64_t seed, int W, float* r_out);
+/* SRP baseline: projection j of length m (FP32 normals), and the nhash sign bits of x. */
+void ssh_oracle_srp_projection(uint64_t seed, int m, int j, float* r_out);
+void ssh_oracle_srp_bits(const float* x, int m, uint64_t seed, int nhash, uint32_t* bits_out);
 
 /* Number of sketch bits N_B = floor((m - W) / delta) + 1, or 0 when m < W. */
 int ssh_oracle_num_bits(int m, int W, int delta);

@@ -552,3 +552,44 @@ def test_bench_ndcg_matches_the_oracle():
         got = list(rng.choice(np.concatenate([gold, rng.integers(40, 60, 10)]), 10, replace=False))
         assert bench.ndcg([got], [gold]) == pytest.approx(oracle.ndcg_at_k(got, gold), rel=1e-12)
         assert bench.recall([got], [gold]) == pytest.approx(oracle.recall_at_k(got, gold), rel=1e-12)
+
+
+# ------------------------------------------- Sec. 5.2 baseline: sign random projections
+
+def test_srp_collision_rate_is_one_minus_angle_over_pi():
+    """Charikar's identity for sign random projections: two series agree on a bit with
+    probability 1 - theta / pi, theta their angle; checked over 10^4 projections within 3 sigma."""
+    rng = np.random.default_rng(18)
+    nh = 10_000
+    for _ in range(3):
+        x = rng.standard_normal(48).astype(np.float32)
+        y = (x + rng.uniform(0.3, 2.0) * rng.standard_normal(48)).astype(np.float32)
+        xd, yd = x.astype(np.float64), y.astype(np.float64)
+        theta = math.acos(float(xd @ yd) / math.sqrt(float(xd @ xd) * float(yd @ yd)))
+        p = 1.0 - theta / math.pi
+        agree = float(np.mean(oracle.srp_bits(x, 5, nh) == oracle.srp_bits(y, 5, nh)))
+        assert abs(agree - p) <= 3 * math.sqrt(p * (1 - p) / nh), (agree, p)
+
+
+def test_srp_sign_invariances_and_normal_entries():
+    rng = np.random.default_rng(19)
+    x = rng.standard_normal(100).astype(np.float32)
+    b = oracle.srp_bits(x, 2, 64)
+    assert np.array_equal(oracle.srp_bits(2 * x, 2, 64), b)  # exact scaling by 2 keeps every sign
+    assert np.array_equal(oracle.srp_bits(-x, 2, 64), 1 - b)  # no dot product is exactly 0 here
+    r = np.concatenate([oracle.srp_projection(4, 1000, j) for j in range(100)]).astype(np.float64)
+    assert abs(r.mean()) < 4 / math.sqrt(len(r)) and abs(r.var() - 1) < 4 * math.sqrt(2 / len(r))
+    assert not np.array_equal(oracle.srp_projection(4, 1000, 0), oracle.srp_projection(4, 1000, 1))
+    assert not np.array_equal(oracle.srp_projection(4, 999, 0)[:999], oracle.srp_projection(4, 1000, 0)[:999])
+
+
+def test_srp_index_candidates_are_rows_sharing_a_table_key():
+    rng = np.random.default_rng(20)
+    db = np.cumsum(rng.standard_normal((80, 40)), axis=1).astype(np.float32)
+    ix = oracle.OracleIndex(1, 1, 1, 3, 6, 0.1, 7, family="srp")
+    ix.add(db)
+    for q in db[:5] + 0.3 * rng.standard_normal((5, 40)).astype(np.float32):
+        qb = oracle.srp_bits(q, 7, 18)
+        want = [i for i in range(80) if any(np.array_equal(oracle.srp_bits(db[i], 7, 18)[l * 3:l * 3 + 3],
+                                                             qb[l * 3:l * 3 + 3]) for l in range(6))]
+        assert ix.candidates(q).tolist() == want
