@@ -403,13 +403,16 @@ OPERATING_POINTS = [
 ]
 
 
-def sweep_points(binding, torch, d_sub, d_q, exact, points, band, seed, k, n_plain=20):
+def sweep_points(binding, torch, d_sub, d_q, exact, points, band, seed, k, n_plain=20, srp=False):
     """recall@10, candidate fraction and queries/s of each parameter set (W, delta, n, K, L) on a
-    subset; the chosen point is the fastest with recall@10 >= 0.9 (else the one of highest recall)."""
+    subset; the chosen point is the fastest with recall@10 >= 0.9 (else the one of highest recall).
+    srp: the points are SRP baseline indexes (K, L used; W, delta, n ignored)."""
     n_sub, nq = d_sub.shape[0], d_q.shape[0]
     out = []
     for (W, delta, n, K, L) in points:
-        with binding.SSHIndex(W, delta, n, K, L, band, seed) as ix:
+        make = (lambda: binding.SSHIndex.srp(K, L, band, seed)) if srp else \
+            (lambda: binding.SSHIndex(W, delta, n, K, L, band, seed))
+        with make() as ix:
             ix.add_device(d_sub)  # warm-up build (first use of the shapes)
             build = float("inf")
             for _ in range(2):
@@ -469,6 +472,19 @@ STUDY_POINTS = {
     "delta": [(80, d, 15, 4, 25) for d in (1, 2, 3, 5, 8)],
     "n": [(80, 3, n, 4, 25) for n in (8, 10, 12, 15)],
 }
+
+
+# The paper's SRP baseline (Sec. 5.2) on the same subset: K sign random projections of the
+# whole series per table, 25 tables.
+SRP_POINTS = [(1, 1, 1, K, 25) for K in (16, 8, 4, 2)]
+
+
+def srp_baseline(binding, torch, d_sub, d_q, exact, w, k):
+    """recall@10, NDCG@10, candidate fraction and queries/s of the SRP baseline on the recall subset."""
+    sw = sweep_points(binding, torch, d_sub, d_q, exact, SRP_POINTS, w["band"], w["seed"], k, n_plain=0, srp=True)
+    return {"subset": int(d_sub.shape[0]), "queries": int(d_q.shape[0]),
+            "points": [{key: p[key] for key in ("K", "L", "recall_at_10", "ndcg_at_10", "candidate_fraction",
+                                                 "index_ms", "queries_per_s")} for p in sw["points"]]}
 
 
 def parameter_study(binding, torch, d_sub, d_q, exact, w, k):
@@ -1085,6 +1101,7 @@ def run_gpu(args, w):
         extra["recall_operating_point"] = recall_operating_point(binding, torch, d_sub.contiguous(), d_q,
                                                                  exact_sub, w, k)
         extra["parameter_study"] = parameter_study(binding, torch, d_sub.contiguous(), d_q, exact_sub, w, k)
+        extra["srp_baseline"] = srp_baseline(binding, torch, d_sub.contiguous(), d_q, exact_sub, w, k)
         extra["exact_scan"] = exact_scan_measurement(binding, torch, d_sub.contiguous(), d_db, d_q, exact_sub, w, k,
                                                      n_full=4 if args.small else 10)
         if not args.fast:

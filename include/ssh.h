@@ -77,6 +77,18 @@ const char* ssh_last_error(void);
  */
 ssh_status ssh_create(int W, int delta, int n, int K, int L, float band, uint64_t seed, ssh_index** out);
 
+/* The paper's SRP baseline (Sec. 5.2, Table 2) behind the same index, table and
+ * query API: hash j of a series x of length m is the sign of r_j . x over the
+ * whole series, r_j of i.i.d. normal entries (Philox4x32-10 keyed by seed with
+ * counter (i / 2, j, "SRP1", m), Box-Muller, rounded once to FP32; generated per
+ * length on first use); table l keys the K bits of hashes lK .. lK+K-1 with the
+ * same fold as the SSH pairs (hash value (bit, 0)). Bits are exact: a product
+ * within tau_m ||r_j|| ||x|| of zero (tau_m = max(1e-4, 2 m 2^-24 / (1 - m 2^-24)))
+ * is recomputed in FP64. Any length >= 1 is accepted. Batch plans, the server,
+ * ssh_hash_device and the window add's shared sketch are SSH-only (batch and
+ * server creation and ssh_hash_device return SSH_ENOTSUP; windows are hashed as rows). */
+ssh_status ssh_create_srp(int K, int L, float band, uint64_t seed, ssh_index** out);
+
 /* Release the index and all its device memory. NULL is a no-op. */
 void ssh_destroy(ssh_index* idx);
 

@@ -66,6 +66,8 @@ _SIGS = {
     "ssh_status_str": (ctypes.c_char_p, [ctypes.c_int]),
     "ssh_last_error": (ctypes.c_char_p, []),
     "ssh_create": (ctypes.c_int, [ctypes.c_int] * 5 + [ctypes.c_float, ctypes.c_uint64, ctypes.POINTER(_P)]),
+    "ssh_create_srp": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_float, ctypes.c_uint64,
+                                      ctypes.POINTER(_P)]),
     "ssh_destroy": (None, [_P]),
     "ssh_get_filter": (ctypes.c_int, [_P, _P]),
     "ssh_index_add": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, _I64P]),
@@ -163,6 +165,12 @@ def _stream(stream):
 def ssh_create(W: int, delta: int, n: int, K: int, L: int, band: float, seed: int) -> ctypes.c_void_p:
     h = _P()
     _check(load().ssh_create(W, delta, n, K, L, float(band), int(seed) & (2 ** 64 - 1), ctypes.byref(h)))
+    return h
+
+
+def ssh_create_srp(K: int, L: int, band: float, seed: int) -> ctypes.c_void_p:
+    h = _P()
+    _check(load().ssh_create_srp(K, L, float(band), int(seed) & (2 ** 64 - 1), ctypes.byref(h)))
     return h
 
 
@@ -436,6 +444,15 @@ class SSHIndex:
         self.W, self.delta, self.n, self.K, self.L = W, delta, n, K, L
         self.band, self.seed = band, seed
         self.handle = ssh_create(W, delta, n, K, L, band, seed)
+
+    @classmethod
+    def srp(cls, K: int, L: int, band: float, seed: int = 0) -> "SSHIndex":
+        """The paper's SRP baseline behind the same index API (ssh_create_srp)."""
+        self = cls.__new__(cls)
+        self.W, self.delta, self.n, self.K, self.L = 1, 1, 1, K, L
+        self.band, self.seed = band, seed
+        self.handle = ssh_create_srp(K, L, band, seed)
+        return self
 
     def close(self):
         if self.handle:

@@ -718,8 +718,10 @@ ssh_status ssh_batch_create(ssh_index* const* handles, int nh, int64_t max_queri
     if (!out) return fail_status(SSH_EINVAL, "out is NULL");
     *out = nullptr;
     if (!handles || nh < 1) return fail_status(SSH_EINVAL, "no indexes");
-    for (int h = 0; h < nh; ++h)
+    for (int h = 0; h < nh; ++h) {
         if (!handles[h]) return fail_status(SSH_EINVAL, "handle %d is NULL", h);
+        if (handles[h]->family != 0) return fail_status(SSH_ENOTSUP, "batch plans hash with SSH; index %d is SRP", h);
+    }
     if (max_queries < 1 || max_queries > 65535)
         return fail_status(SSH_EINVAL, "max_queries = %lld outside [1, 65535]", (long long)max_queries);
     if (k < 1 || k > kMaxTopK) return fail_status(SSH_EINVAL, "k = %d outside [1, %d]", k, kMaxTopK);

@@ -102,6 +102,24 @@ void make_filter(uint64_t seed, int W, std::vector<float>& r) {
     }
 }
 
+constexpr uint32_t kTagSrp = 0x53525031u;     // "SRP1"
+
+// The SRP baseline's projection j for series of length m: N(0,1) entries by
+// Box-Muller on the Philox block with counter (i / 2, j, SRP1, m).
+void make_srp_projection(uint64_t seed, int m, int j, float* r) {
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    const double two_pi = 6.283185307179586476925286766559;
+    for (int i = 0; i < m; ++i) {
+        const uint32_t ctr[4] = {(uint32_t)(i / 2), (uint32_t)j, kTagSrp, (uint32_t)m};
+        uint32_t b[4];
+        philox10(ctr, k0, k1, b);
+        const double u1 = unit(b[0]), u2 = unit(b[1]);
+        const double radius = std::sqrt(-2.0 * std::log(u1));
+        const double angle = two_pi * u2;
+        r[i] = (float)((i % 2 == 0) ? radius * std::cos(angle) : radius * std::sin(angle));
+    }
+}
+
 struct Draw {
     double r, beta, lnc;
 };
@@ -200,8 +218,58 @@ double dtw_cells(int m, int rb) { return (double)m * (2.0 * rb + 1.0) - (double)
 
 // Sec. 4.1-4.3 + keys for a.count series, each stage in its own timed region
 // named "<prefix>.<stage>" (units: series).
+// The SRP baseline's projections for length m, generated on the host on first use.
+ssh_status srp_tab(ssh_index* idx, int m, SrpTab** out) {
+    auto it = idx->srp.find(m);
+    if (it == idx->srp.end()) {
+        const int KL = idx->KL;
+        std::vector<float> R((size_t)KL * m), rn(KL);
+        const double u = std::ldexp(1.0, -24), gm = m * u / (1.0 - m * u);
+        const double tau = std::max(1e-4, 2.0 * gm);
+        parallel_for(KL, [&](int64_t j) {
+            make_srp_projection(idx->seed, m, (int)j, R.data() + (size_t)j * m);
+            double nr = 0.0;
+            for (int i = 0; i < m; ++i) nr += (double)R[(size_t)j * m + i] * (double)R[(size_t)j * m + i];
+            rn[j] = std::nextafter((float)(tau * std::sqrt(nr) * (1.0 + 1e-6)), INFINITY);
+        });
+        SrpTab t;
+        cudaError_t e = cudaMalloc(&t.R, R.size() * sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc(&t.rn, rn.size() * sizeof(float));
+        if (e == cudaSuccess) e = cudaMemcpy(t.R, R.data(), R.size() * sizeof(float), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(t.rn, rn.data(), rn.size() * sizeof(float), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            cudaFree(t.R);
+            cudaFree(t.rn);
+            return cuda_status(e, "SRP projections");
+        }
+        it = idx->srp.emplace(m, t).first;
+    }
+    *out = &it->second;
+    return SSH_OK;
+}
+
+ssh_status run_srp(ssh_index* idx, const HashArgs& a, cudaStream_t st, const char* prefix) {
+    SrpTab* t = nullptr;
+    SSH_TRY(srp_tab(idx, a.m, &t));
+    const bool q = prefix[0] == 'q';
+    static const char* names[2][3] = {{"add.srp", "add.srp_fixup", "add.srp_keys"},
+                                      {"query.srp", "query.srp_fixup", "query.srp_keys"}};
+    void* scratch = nullptr;
+    SSH_CUDA(cudaMallocAsync(&scratch, srp_scratch_bytes(a), st));
+    cudaError_t e = cudaSuccess;
+    for (int stage = 0; stage < 3 && e == cudaSuccess; ++stage) {
+        TimedRegion tr(idx, st, names[q][stage], (double)a.count);
+        e = launch_srp_hash(a, t->R, t->rn, scratch, stage, st);
+    }
+    cudaError_t f = cudaFreeAsync(scratch, st);
+    SSH_CUDA(e);
+    SSH_CUDA(f);
+    return SSH_OK;
+}
+
 ssh_status run_hash(ssh_index* idx, const HashArgs& a, cudaStream_t st, const char* prefix) {
     if (a.count <= 0) return SSH_OK;
+    if (idx->family == 1) return run_srp(idx, a, st, prefix);
     static const char* names[2][5] = {{"add.sketch", "add.sketch_fixup", "add.shingle", "add.cws", "add.hash_generic"},
                                       {"query.sketch", "query.sketch_fixup", "query.shingle", "query.cws",
                                        "query.hash_generic"}};
@@ -1007,11 +1075,22 @@ ssh_status ssh_create(int W, int delta, int n, int K, int L, float band, uint64_
     return SSH_OK;
 }
 
+ssh_status ssh_create_srp(int K, int L, float band, uint64_t seed, ssh_index** out) {
+    // the SSH parameters W = delta = n = 1 make every length >= 1 valid and the draw tables tiny
+    SSH_TRY(ssh_create(1, 1, 1, K, L, band, seed, out));
+    (*out)->family = 1;
+    return SSH_OK;
+}
+
 void ssh_destroy(ssh_index* idx) {
     if (!idx) return;
     cudaSetDevice(idx->device);
     cudaDeviceSynchronize();
     for (auto& kv : idx->subs) free_sub(kv.second);
+    for (auto& kv : idx->srp) {
+        cudaFree(kv.second.R);
+        cudaFree(kv.second.rn);
+    }
     for (DevBuf& b : idx->owned) cudaFree(b.p);
     for (DevBuf& b : idx->spare) cudaFree(b.p);
     for (void* p : idx->arena) cudaFree(p);
@@ -1141,7 +1220,7 @@ ssh_status ssh_index_add_windows_device(ssh_index* idx, const float* d_stream, i
     a.keys = s.keys;
     a.key_stride = s.cap;
     a.key_col0 = s.count;
-    if (!a.force_generic && step < g.nb && hash_windows_supported(a)) {
+    if (idx->family == 0 && !a.force_generic && step < g.nb && hash_windows_supported(a)) {
         // overlapping windows share their sketch positions: the stream's bits and
         // shingle ids are computed once (N_B / step times fewer dot products)
         static const char* names[4] = {"add.sketch", "add.sketch_fixup", "add.shingle", "add.cws"};
@@ -1412,6 +1491,7 @@ ssh_status ssh_hash_device(const ssh_index* idx, const float* d_series, int32_t 
     if (!idx || count < 0 || (count > 0 && !d_series)) return fail(SSH_EINVAL, "bad arguments");
     if ((d_sh_ids == nullptr) != (d_sh_counts == nullptr) || (d_kstar == nullptr) != (d_tstar == nullptr))
         return fail(SSH_EINVAL, "shingle ids/counts and kstar/tstar come in pairs");
+    if (idx->family != 0) return fail(SSH_ENOTSUP, "ssh_hash_device computes SSH hashes; this index is SRP");
     SSH_TRY(check_device(idx));
     Geometry g;
     SSH_TRY(geometry(idx, m, &g));

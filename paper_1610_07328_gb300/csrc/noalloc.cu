@@ -57,6 +57,10 @@ extern "C" ssh_status ssh_hash_device_noalloc(const ssh_index* idx, const float*
         set_error("bad arguments");
         return SSH_EINVAL;
     }
+    if (idx->family != 0) {
+        set_error("ssh_hash_device_noalloc computes SSH hashes; this index is SRP");
+        return SSH_ENOTSUP;
+    }
     if ((d_sh_ids == nullptr) != (d_sh_counts == nullptr) || (d_kstar == nullptr) != (d_tstar == nullptr)) {
         set_error("shingle ids/counts and kstar/tstar come in pairs");
         return SSH_EINVAL;

@@ -271,6 +271,9 @@ ssh_status ssh_server_create(ssh_index* const* handles, int nh, int k, int max_b
     if (max_batch < 1 || max_batch > 65535) return fail_status(SSH_EINVAL, "max_batch outside [1, 65535]");
     if (max_slots < 1 || max_slots > 64) return fail_status(SSH_EINVAL, "max_slots outside [1, 64]");
     if (k < 1 || k > kMaxTopK) return fail_status(SSH_EINVAL, "k = %d outside [1, %d]", k, kMaxTopK);
+    for (int h = 0; h < nh; ++h)
+        if (!handles[h] || handles[h]->family != 0)
+            return fail_status(handles[h] ? SSH_ENOTSUP : SSH_EINVAL, "index %d is NULL or SRP (served indexes hash with SSH)", h);
     SSH_TRY(check_device(handles[0]));
     ssh_server* s = new ssh_server();
     s->handles.assign(handles, handles + nh);

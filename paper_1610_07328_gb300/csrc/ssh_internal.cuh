@@ -119,6 +119,12 @@ cudaError_t launch_hash_fast(const HashArgs& a, cudaStream_t st);
 // sets and the minhash. Stages 0 sketch, 1 FP64 fix-up, 2 ids and sets, 3 CWS
 // and keys, over one scratch block of hash_windows_scratch_bytes(a, step) bytes;
 // a.count = windows, a.keys / key_stride / key_col0 as for rows.
+// The SRP baseline's hash (srp.cu): stages 0 bits, 1 FP64 fix-up, 2 keys, over
+// srp_scratch_bytes(a) bytes of scratch; R / rn from the index's SrpTab for a.m.
+size_t srp_scratch_bytes(const HashArgs& a);
+cudaError_t launch_srp_hash(const HashArgs& a, const float* R, const float* rn, void* scratch, int stage,
+                            cudaStream_t st);
+
 bool hash_windows_supported(const HashArgs& a);
 size_t hash_windows_scratch_bytes(const HashArgs& a, int64_t step);
 cudaError_t hash_windows_stage(const HashArgs& a, const float* stream, int64_t step, void* scratch, int stage,
@@ -343,8 +349,17 @@ struct KernelTotals {
     double ms = 0.0, units = 0.0;
 };
 
+// The SRP baseline's projections for one series length m (device): R [KL][m]
+// and rn[j] = tau_m ||r_j||, rounded up.
+struct SrpTab {
+    float* R = nullptr;
+    float* rn = nullptr;
+};
+
 struct ssh_index {
     int W = 0, delta = 0, n = 0, K = 0, L = 0, KL = 0;
+    int family = 0;                   // 0: SSH; 1: the SRP baseline (ssh_create_srp)
+    std::map<int, SrpTab> srp;        // family 1: projections per series length
     bool timing = false;
     std::vector<KernelTimer> pending;
     std::map<std::string, KernelTotals> totals;

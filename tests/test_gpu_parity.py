@@ -715,3 +715,64 @@ def test_windows_of_one_stream_equal_the_oracle_over_the_same_windows(cfg, step,
         oi, od = ref.query(q, 5)
         assert_topk_match(q, ids[i], d[i], oi, od, lambda j: rows[j], rb)
     assert ids[-1][0] == 3 + len(windows) // 3 and d[-1][0] == 0.0
+
+
+@pytest.mark.parametrize("m,K,L", [(128, 8, 10), (512, 12, 20), (77, 4, 6)])
+def test_srp_baseline_matches_the_oracle(m, K, L):
+    """The SRP baseline (ssh_create_srp): every query's candidate set (rows sharing a table key)
+    has the oracle's size, and the top-k equals the oracle's over it."""
+    b = _binding()
+    db = synth.random_walk(500, m, seed=m + 40)
+    qs, _ = synth.perturbed_queries(db, 6, seed=m + 41)
+    ref = oracle.OracleIndex(1, 1, 1, K, L, 0.05, 3, family="srp")
+    ref.add(db)
+    idx = b.SSHIndex.srp(K, L, 0.05, 3)
+    try:
+        idx.add(db)
+        idx.reset_stats()
+        ids, d = idx.query(qs, 5)
+        st = idx.stats()
+    finally:
+        idx.close()
+    assert st["candidates"] == sum(len(ref.candidates(q)) for q in qs)
+    rb = oracle.band_radius(0.05, m)
+    for i, q in enumerate(qs):
+        oi, od = ref.query(q, 5)
+        assert_topk_match(q, ids[i], d[i], oi, od, lambda j: db[j], rb)
+
+
+def test_srp_near_zero_projections_take_the_fp64_path():
+    """Series made orthogonal to projections 0..3 (up to FP32 rounding) put those products at
+    rounding level: the FP64 recomputation decides them, and the candidate sets stay exact."""
+    b = _binding()
+    m, K, L = 96, 4, 3
+    R = np.stack([oracle.srp_projection(9, m, j) for j in range(K * L)]).astype(np.float64)
+    rng = np.random.default_rng(42)
+    rows = []
+    for t in range(200):
+        x = rng.standard_normal(m)
+        for j in range(4):
+            x = x - (R[j] @ x) / (R[j] @ R[j]) * R[j]
+        rows.append(x)
+    db = np.array(rows, np.float32)
+    ref = oracle.OracleIndex(1, 1, 1, K, L, 0.05, 9, family="srp")
+    ref.add(db)
+    idx = b.SSHIndex.srp(K, L, 0.05, 9)
+    try:
+        idx.add(db)
+        ids, d = idx.query(db[:8], 3)
+        st = idx.stats()
+        idx.reset_stats()
+        idx.query(db[8:16], 3)
+        st2 = idx.stats()
+        with pytest.raises(b.SSHError) as e:
+            b.SSHBatch([idx], max_queries=4, k=3)
+        assert e.value.status == b.SSH_ENOTSUP
+    finally:
+        idx.close()
+    assert st["sketch_fp64"] > 0
+    assert st2["candidates"] == sum(len(ref.candidates(q)) for q in db[8:16])
+    rb = oracle.band_radius(0.05, m)
+    for i in range(8):
+        oi, od = ref.query(db[i], 3)
+        assert_topk_match(db[i], ids[i], d[i], oi, od, lambda j: db[j], rb)
