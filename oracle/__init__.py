@@ -81,6 +81,7 @@ def _load():
             "ssh_oracle_cws_log_a": (ctypes.c_double, [ctypes.c_double] * 3 + [ctypes.c_uint32, f64p]),
             "ssh_oracle_cws": (None, [ctypes.c_uint64, ctypes.c_int, u32p, u32p, ctypes.c_int, u32p, u32p]),
             "ssh_oracle_bucket_key": (ctypes.c_uint64, [ctypes.c_uint64, ctypes.c_int, ctypes.c_int, u32p, u32p]),
+            "ssh_oracle_doph": (None, [ctypes.c_uint64, ctypes.c_int, u32p, u32p, ctypes.c_int, u32p, u32p]),
             "ssh_oracle_hash_series": (ctypes.c_int, [f32p, ctypes.c_int, f32p, ctypes.c_int, ctypes.c_int,
                                                       ctypes.c_int, ctypes.c_uint64, ctypes.c_int, ctypes.c_int,
                                                       u32p, u32p]),
@@ -197,6 +198,18 @@ def cws(seed: int, nhash: int, ids, counts):
     ts = np.zeros(nhash, dtype=np.uint32)
     _load().ssh_oracle_cws(int(seed), int(nhash), _ptr(ids, ctypes.c_uint32), _ptr(counts, ctypes.c_uint32),
                            len(ids), _ptr(ks, ctypes.c_uint32), _ptr(ts, ctypes.c_uint32))
+    return ks, ts
+
+
+def doph(seed: int, nhash: int, ids, counts):
+    """Densified one-permutation weighted minhash (a faster variant of Sec. 4.3's weighted
+    minhash): (kstar, tstar) = (shingle id, copy index) of hash functions 0 .. nhash-1."""
+    ids = np.ascontiguousarray(np.asarray(ids, dtype=np.uint32))
+    counts = np.ascontiguousarray(np.asarray(counts, dtype=np.uint32))
+    ks = np.zeros(nhash, dtype=np.uint32)
+    ts = np.zeros(nhash, dtype=np.uint32)
+    _load().ssh_oracle_doph(int(seed), int(nhash), _ptr(ids, ctypes.c_uint32), _ptr(counts, ctypes.c_uint32),
+                            len(ids), _ptr(ks, ctypes.c_uint32), _ptr(ts, ctypes.c_uint32))
     return ks, ts
 
 
@@ -317,10 +330,11 @@ class OracleIndex:
     def __init__(self, W: int, delta: int, n: int, K: int, L: int, band: float, seed: int, family: str = "ssh"):
         if W < 1 or delta < 1 or n < 1 or n > 32 or K < 1 or L < 1 or not band >= 0:
             raise ValueError("invalid SSH parameters")
-        if family not in ("ssh", "srp"):
-            raise ValueError("family is 'ssh' or 'srp'")
+        if family not in ("ssh", "srp", "ssh-doph"):
+            raise ValueError("family is 'ssh', 'srp' or 'ssh-doph'")
         # "srp": the paper's baseline, K sign random projections of the whole series per
-        # table (hash values (bit, 0) in the same key fold); W, delta and n are unused
+        # table (hash values (bit, 0) in the same key fold); W, delta and n are unused.
+        # "ssh-doph": SSH with the densified one-permutation minhash in place of ICWS
         self.family = family
         self.W, self.delta, self.n, self.K, self.L = W, delta, n, K, L
         self.band = float(np.float32(band))
@@ -343,6 +357,12 @@ class OracleIndex:
         if self.family == "srp":
             bits = srp_bits(x, self.seed, self.K * self.L)
             return bits, np.zeros_like(bits)
+        if self.family == "ssh-doph":  # Sec. 4.1-4.2, then the densified one-permutation minhash
+            x = _f32(x)
+            if len(x) < self.min_length():
+                raise ValueError(f"series of length {len(x)} is shorter than {self.min_length()}")
+            ids, counts = shingle(sketch(x, self.r, self.delta), self.n)
+            return doph(self.seed, self.K * self.L, ids, counts)
         h = hash_series(x, self.r, self.delta, self.n, self.seed, self.K, self.L)
         if h is None:
             raise ValueError(f"series of length {len(x)} is shorter than W + (n-1)*delta = {self.min_length()}")

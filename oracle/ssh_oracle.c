@@ -231,6 +231,55 @@ uint64_t ssh_oracle_bucket_key(uint64_t seed, int l, int K, const uint32_t* ksta
     return h;
 }
 
+/* A faster weighted minhash among those the paper cites (Sec. 2.3): densified
+ * one-permutation hashing of the copies. The integer weighted set {(k, S_k)} is
+ * read as the plain set of copies (k, c), c = 1 .. S_k, whose Jaccard similarity
+ * is the weighted Jaccard of the counts. Copy (k, c) has v = mix64(seed ^ D1 ^
+ * (k << 32 | c)), goes to bin floor((v >> 32) * nhash / 2^32) and has value
+ * low32(mix64(v)); each bin keeps its copy of smallest (value, k, c). An empty
+ * bin i takes the bin of the first non-empty j_t = floor((mix64(seed ^ D2 ^
+ * (i << 32 | t)) >> 32) * nhash / 2^32), t = 0, 1, ... (optimal densification),
+ * or, after 64 nhash attempts, the first non-empty bin after i. Hash i is (k, c)
+ * of the copy it ends with; an empty set gives (2^32 - 1, 0) everywhere. */
+#define DOPH_BIN 0xD0F1B1A5C0FFEE01ull
+#define DOPH_FILL 0xDE45E1F1A11B0B02ull
+
+static uint32_t doph_scale(uint64_t v, int nhash) { return (uint32_t)(((v >> 32) * (uint64_t)nhash) >> 32); }
+
+void ssh_oracle_doph(uint64_t seed, int nhash, const uint32_t* ids, const uint32_t* counts, int nnz,
+                     uint32_t* kstar, uint32_t* tstar) {
+    uint64_t* bins = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)nhash);
+    for (int i = 0; i < nhash; ++i) bins[i] = UINT64_MAX;
+    for (int e = 0; e < nnz; ++e) {
+        for (uint32_t c = 1; c <= counts[e]; ++c) {
+            uint64_t pack = ((uint64_t)ids[e] << 32) | (uint64_t)c;
+            uint64_t v = mix64(seed ^ DOPH_BIN ^ pack);
+            uint32_t b = doph_scale(v, nhash);
+            uint64_t key = ((uint64_t)(uint32_t)mix64(v) << 32) | ((uint64_t)ids[e] << 16) | (uint64_t)c;
+            if (key < bins[b]) bins[b] = key;
+        }
+    }
+    for (int i = 0; i < nhash; ++i) {
+        uint64_t key = bins[i];
+        if (key == UINT64_MAX && nnz > 0) {
+            long long tries = 64LL * nhash;
+            for (long long t = 0; t < tries && key == UINT64_MAX; ++t) {
+                uint32_t j = doph_scale(mix64(seed ^ DOPH_FILL ^ (((uint64_t)i << 32) | (uint64_t)t)), nhash);
+                key = bins[j];
+            }
+            for (int d = 1; d < nhash && key == UINT64_MAX; ++d) key = bins[(i + d) % nhash];
+        }
+        if (key == UINT64_MAX) {
+            kstar[i] = 0xFFFFFFFFu;
+            tstar[i] = 0u;
+        } else {
+            kstar[i] = (uint32_t)((key >> 16) & 0xFFFFu);
+            tstar[i] = (uint32_t)(key & 0xFFFFu);
+        }
+    }
+    free(bins);
+}
+
 int ssh_oracle_hash_series(const float* x, int m, const float* r, int W, int delta, int n,
                            uint64_t seed, int K, int L, uint32_t* kstar, uint32_t* tstar) {
     int nb = ssh_oracle_num_bits(m, W, delta);

@@ -73,6 +73,9 @@ void ssh_oracle_cws(uint64_t seed, int nhash, const uint32_t* ids, const uint32_
  * splitmix64-finalizer fold; used only to compare with the library's keys, the
  * oracle's own tables compare the K-tuples themselves). */
 uint64_t ssh_oracle_bucket_key(uint64_t seed, int l, int K, const uint32_t* kstar, const uint32_t* tstar);
+/* Densified one-permutation weighted minhash of a weighted set (ids < 2^16, counts < 2^16). */
+void ssh_oracle_doph(uint64_t seed, int nhash, const uint32_t* ids, const uint32_t* counts, int nnz,
+                     uint32_t* kstar, uint32_t* tstar);
 
 /* Sec. 4.1-4.3 for one series: sketch, shingle, weighted minhash. kstar/tstar hold
  * K*L entries. Returns the number of distinct shingles, or -1 if the series is too
