@@ -487,6 +487,51 @@ def srp_baseline(binding, torch, d_sub, d_q, exact, w, k):
                                                  "index_ms", "queries_per_s")} for p in sw["points"]]}
 
 
+def minhash_variants(binding, torch, d_db, d_sub, d_q, exact, w, k):
+    """SSH_OPT_MINHASH 0 (ICWS) against 1 (densified one-permutation hashing): the index build of
+    the whole workload (N series, borrowed; best of 3) with its minhash kernel's time, and
+    recall@10 / NDCG@10 / candidate fraction on the recall subset at n = 15, 10, 8."""
+    out = {}
+    for mh, name in ((0, "icws"), (1, "doph")):
+        entry = {}
+        with binding.SSHIndex(w["W"], w["delta"], w["n"], w["K"], w["L"], w["band"], w["seed"]) as ix:
+            ix.set_minhash(mh)
+            best = float("inf")
+            for rep in range(4):
+                ix.clear()
+                if rep == 3:
+                    ix.reset_stats()
+                    ix.set_kernel_timing(True)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record()
+                ix.add_device(d_db, borrow=True)
+                e1.record()
+                e1.synchronize()
+                if rep < 3:
+                    best = min(best, e0.elapsed_time(e1))
+            kt = ix.kernel_times()
+            ix.set_kernel_timing(False)
+        entry["index_ms"] = best
+        entry["series_hashed_per_s_index_phase"] = d_db.shape[0] / (best / 1000.0)
+        if "add.cws" in kt:
+            entry["minhash_kernel_ms"] = kt["add.cws"]["total_ms"] / max(kt["add.cws"]["calls"], 1)
+        pts = [(w["W"], w["delta"], n, w["K"], w["L"]) for n in (15, 10, 8)]
+        sw = []
+        for (W, delta, n, K, L) in pts:
+            with binding.SSHIndex(W, delta, n, K, L, w["band"], w["seed"]) as ix:
+                ix.set_minhash(mh)
+                ix.add_device(d_sub)
+                ids, ms, st = _timed_query(torch, ix, d_q, k)
+                sw.append({"n": n, "recall_at_10": recall(ids.cpu().numpy(), exact),
+                           "ndcg_at_10": ndcg(ids.cpu().numpy(), exact),
+                           "candidate_fraction": st["candidates"] / max(st["queries"], 1) / d_sub.shape[0],
+                           "queries_per_s": d_q.shape[0] / (ms / 1000.0)})
+        entry["subset_points"] = sw
+        out[name] = entry
+    return out
+
+
 def parameter_study(binding, torch, d_sub, d_q, exact, w, k):
     """recall@10, NDCG@10, candidate fraction, index build time and queries/s as W, delta and n vary."""
     out = {}
@@ -1102,6 +1147,7 @@ def run_gpu(args, w):
                                                                  exact_sub, w, k)
         extra["parameter_study"] = parameter_study(binding, torch, d_sub.contiguous(), d_q, exact_sub, w, k)
         extra["srp_baseline"] = srp_baseline(binding, torch, d_sub.contiguous(), d_q, exact_sub, w, k)
+        extra["minhash_variants"] = minhash_variants(binding, torch, d_db, d_sub.contiguous(), d_q, exact_sub, w, k)
         extra["exact_scan"] = exact_scan_measurement(binding, torch, d_sub.contiguous(), d_db, d_q, exact_sub, w, k,
                                                      n_full=4 if args.small else 10)
         if not args.fast:

@@ -263,14 +263,24 @@ void ssh_server_destroy(ssh_server* s);
  * envelope against the query) on the candidates that pass, before their DTW
  * (it prunes more but builds each candidate's envelope, which costs more than
  * the DTW it saves at the band radii measured, up to 102). Batch plans use 1.
- * Same results in every mode: all are lower bounds of the banded DTW. */
+ * Same results in every mode: all are lower bounds of the banded DTW.
+ * SSH_OPT_MINHASH (default 0): the weighted minhash of Sec. 4.3's last step. 0 is
+ * Ioffe's consistent weighted sampling (ICWS); 1 is densified one-permutation
+ * hashing of the set's copies (k, c), c = 1 .. S_k, one of the faster variants
+ * the paper cites: each copy goes to one of the K*L bins by one hash, a bin keeps
+ * its smallest copy and empty bins borrow by optimal densification; its collision
+ * probability per hash is the same weighted Jaccard, at O(copies + K L) work per
+ * series instead of O(distinct shingles x K L). Hashes and keys differ from
+ * ICWS's. Settable only while the index is empty (else SSH_EBUSY); needs a
+ * compiled sketch shape (adds return SSH_ENOTSUP otherwise). */
 typedef enum ssh_option {
     SSH_OPT_LB_PRUNE = 1,
     SSH_OPT_KERNEL_TIMING = 2,
     SSH_OPT_HASH_KERNEL = 3,
     SSH_OPT_CWS_FP64 = 4,
     SSH_OPT_EXACT_SCAN = 5,
-    SSH_OPT_LB_CASCADE = 6
+    SSH_OPT_LB_CASCADE = 6,
+    SSH_OPT_MINHASH = 7
 } ssh_option;
 ssh_status ssh_set_option(ssh_index* idx, ssh_option opt, int64_t value);
 

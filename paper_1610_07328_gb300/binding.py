@@ -23,6 +23,7 @@ SSH_OPT_HASH_KERNEL = 3
 SSH_OPT_CWS_FP64 = 4
 SSH_OPT_EXACT_SCAN = 5
 SSH_OPT_LB_CASCADE = 6
+SSH_OPT_MINHASH = 7
 
 _lib = None
 _lock = threading.Lock()
@@ -523,6 +524,10 @@ class SSHIndex:
     def set_exact_scan(self, on: bool):
         """Rank every stored series of the query's length (exact top-k, no hashing)."""
         ssh_set_option(self.handle, SSH_OPT_EXACT_SCAN, 1 if on else 0)
+
+    def set_minhash(self, kind: int):
+        """0 ICWS (default), 1 densified one-permutation hashing (only on an empty index)."""
+        ssh_set_option(self.handle, SSH_OPT_MINHASH, int(kind))
 
     def set_lb_cascade(self, mode):
         """0 LB_Keogh alone, 1 with the LB_Kim endpoints (default), 2 + reversed LB_Keogh;

@@ -400,6 +400,10 @@ ssh_status build_plan(ssh_batch* b) {
     for (const ssh_batch::HostClass& hc : b->cls) {
         HashArgs a = hc.a;
         a.count = Q;
+        if (a.minhash != 0 && (a.force_generic || !hash_fast_supported(a))) {
+            e = cudaErrorNotSupported;  // the one-permutation minhash runs in the split pipeline only
+            break;
+        }
         if (!a.force_generic && hash_fast_supported(a)) hbytes = std::max(hbytes, hash_fast_scratch_bytes(a));
     }
     if (e == cudaSuccess) e = cudaMalloc(&b->hscratch, hbytes);

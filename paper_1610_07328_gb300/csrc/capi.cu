@@ -276,6 +276,9 @@ ssh_status run_hash(ssh_index* idx, const HashArgs& a, cudaStream_t st, const ch
     const int w = (prefix[0] == 'q') ? 1 : 0;
     const double units = (double)a.count;
     if (a.force_generic || !hash_fast_supported(a)) {
+        if (a.minhash != 0)
+            return fail(SSH_ENOTSUP, "the one-permutation minhash needs a compiled sketch shape (W %d, delta %d)",
+                        a.W, a.delta);
         TimedRegion tr(idx, st, names[w][4], units);
         SSH_CUDA(launch_hash_generic(a, st));
         return SSH_OK;
@@ -382,6 +385,7 @@ HashArgs base_hash_args(const ssh_index* idx, int m, const Geometry& g) {
     a.tab_stride = tab_stride_of(idx->KL);
     a.force_generic = idx->hash_kernel == 1;
     a.force_fp64 = idx->cws_fp64;
+    a.minhash = idx->minhash;
     a.kla = idx->d_kla;
     a.p32 = idx->d_p32;
     a.p64 = idx->d_p64;
@@ -1413,6 +1417,13 @@ ssh_status ssh_set_option(ssh_index* idx, ssh_option opt, int64_t value) {
         case SSH_OPT_CWS_FP64:
             idx->cws_fp64 = value != 0;
             return SSH_OK;
+        case SSH_OPT_MINHASH: {
+            if (value < 0 || value > 1) return fail(SSH_EINVAL, "SSH_OPT_MINHASH takes 0 or 1");
+            for (const auto& kv : idx->subs)
+                if (kv.second.count > 0) return fail(SSH_EBUSY, "SSH_OPT_MINHASH changes only an empty index");
+            idx->minhash = (int)value;
+            return SSH_OK;
+        }
         case SSH_OPT_LB_CASCADE:
             if (value < 0 || value > 2) return fail(SSH_EINVAL, "SSH_OPT_LB_CASCADE takes 0, 1 or 2");
             idx->lb_cascade = (int)value;

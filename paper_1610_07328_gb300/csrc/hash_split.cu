@@ -565,6 +565,100 @@ __global__ void __launch_bounds__(256, 4) cws_kernel(HashArgs a, const uint32_t*
     if (n64c && a.stats) atomicAdd(&a.stats[kStatCws64], n64c);
 }
 
+// Densified one-permutation weighted minhash of the copies (k, c), c = 1 .. S_k:
+// one warp per series, the nhash = K L bins in shared memory (64-bit atomicMin of
+// value << 32 | k << 16 | c), then each empty bin takes the bin of the first
+// non-empty one of its pseudo-random sequence (after 64 K L tries, the next
+// non-empty bin). Integer-only, so the hashes equal the definition exactly.
+constexpr uint64_t kDophBin = 0xD0F1B1A5C0FFEE01ull;
+constexpr uint64_t kDophFill = 0xDE45E1F1A11B0B02ull;
+constexpr int kDophPerLane = 8;  // bins per lane: K L <= 256
+
+__device__ __forceinline__ uint32_t doph_scale(uint64_t v, int nh) {
+    return (uint32_t)(((v >> 32) * (uint64_t)nh) >> 32);
+}
+
+__global__ void __launch_bounds__(256) doph_kernel(HashArgs a, const uint32_t* sets, const int2* sizes) {
+    extern __shared__ __align__(16) unsigned char dsm[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    const int KL = a.KL, S = a.S;
+    const size_t per_warp = (size_t)KL * 16;
+    unsigned long long* bins = reinterpret_cast<unsigned long long*>(dsm + (size_t)warp * per_warp);
+    uint32_t* kst = reinterpret_cast<uint32_t*>(bins + KL);
+    uint32_t* tst = kst + KL;
+    const int64_t nwarps = (int64_t)gridDim.x * wpb;
+    int64_t r0, r1;
+    row_range(a, &r0, &r1);
+    for (int64_t row = r0 + (int64_t)blockIdx.x * wpb + warp; row < r1; row += nwarps) {
+        for (int j = lane; j < KL; j += 32) bins[j] = ~0ull;
+        __syncwarp();
+        const int2 sz = __ldg(sizes + row);
+        const int n1 = sz.x, nnz = sz.x + sz.y;
+        for (int e = lane; e < nnz; e += 32) {
+            const uint32_t v = __ldg(sets + row * S + e);
+            const uint32_t k = (e < n1) ? v : set_id(v), cnt = (e < n1) ? 1u : set_count(v);
+            for (uint32_t c = 1; c <= cnt; ++c) {
+                const uint64_t h = mix64(a.seed ^ kDophBin ^ (((uint64_t)k << 32) | c));
+                const uint64_t key = ((uint64_t)(uint32_t)mix64(h) << 32) | ((uint64_t)k << 16) | c;
+                atomicMin(&bins[doph_scale(h, KL)], (unsigned long long)key);
+            }
+        }
+        __syncwarp();
+        // each bin's owner publishes its copy (k, c) (k = all ones: empty) ...
+        for (int i = lane; i < KL; i += 32) {
+            const unsigned long long key = bins[i];
+            kst[i] = (key == ~0ull) ? 0xFFFFFFFFu : (uint32_t)((key >> 16) & 0xFFFFu);
+            tst[i] = (key == ~0ull) ? 0u : (uint32_t)(key & 0xFFFFu);
+        }
+        __syncwarp();
+        // ... then empty bins borrow from the published non-empty ones (into registers, so
+        // no borrowed value is visible to another bin's probes), and store after a sync
+        uint32_t rk[kDophPerLane], rt[kDophPerLane];
+#pragma unroll
+        for (int q = 0; q < kDophPerLane; ++q) {
+            const int i = lane + 32 * q;
+            rk[q] = 0xFFFFFFFFu;
+            rt[q] = 0u;
+            if (i >= KL) continue;
+            uint32_t k = kst[i], c = tst[i];
+            if (k == 0xFFFFFFFFu && nnz > 0) {
+                const uint32_t tries = 64u * (uint32_t)KL;
+                for (uint32_t t = 0; t < tries && k == 0xFFFFFFFFu; ++t) {
+                    const uint32_t j =
+                        doph_scale(mix64(a.seed ^ kDophFill ^ (((uint64_t)(uint32_t)i << 32) | (uint64_t)t)), KL);
+                    k = kst[j];
+                    c = tst[j];
+                }
+                for (int d = 1; d < KL && k == 0xFFFFFFFFu; ++d) {
+                    k = kst[(i + d) % KL];
+                    c = tst[(i + d) % KL];
+                }
+            }
+            rk[q] = k;
+            rt[q] = c;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < kDophPerLane; ++q) {
+            const int i = lane + 32 * q;
+            if (i < KL) {
+                kst[i] = rk[q];
+                tst[i] = rt[q];
+            }
+        }
+        __syncwarp();
+        if (a.kstar_out)
+            for (int j = lane; j < KL; j += 32) {
+                a.kstar_out[row * KL + j] = kst[j];
+                a.tstar_out[row * KL + j] = tst[j];
+            }
+        if (a.keys)
+            for (int l = lane; l < a.L; l += 32)
+                a.keys[(int64_t)l * a.key_stride + a.key_col0 + row] = bucket_key(a.seed, l, a.K, kst, tst);
+        __syncwarp();
+    }
+}
+
 int sms_of_device() {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -624,7 +718,25 @@ cudaError_t launch_shingle(const HashArgs& a, const uint32_t* bits, uint32_t* se
     return launch_shingle_t<false>(a, bits, sets, sizes, nullptr, 0, st);
 }
 
+cudaError_t launch_doph(const HashArgs& a, const uint32_t* sets, const int2* sizes, cudaStream_t st) {
+    if (a.KL > 32 * kDophPerLane) return cudaErrorInvalidValue;
+    const int wpb = warps_for((size_t)a.KL * 16);
+    if (wpb < 1) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)wpb * a.KL * 16;
+    cudaError_t e = ensure_dynamic_smem((const void*)doph_kernel, smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, doph_kernel, wpb * 32, smem);
+    int64_t grid = (int64_t)sms_of_device() * (per_sm > 0 ? per_sm : 1);
+    const int64_t need = (a.count + wpb - 1) / wpb;
+    if (grid > need) grid = need;
+    doph_kernel<<<(unsigned)std::max<int64_t>(grid, 1), wpb * 32, smem, st>>>(a, sets, sizes);
+    note_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t launch_cws(const HashArgs& a, const uint32_t* sets, const int2* sizes, cudaStream_t st) {
+    if (a.minhash == 1) return launch_doph(a, sets, sizes, st);
     const CwsLayout lay = cws_layout(a.S, a.KL);
     const int wpb = warps_for((size_t)lay.total);
     if (wpb < 1) return cudaErrorInvalidValue;

@@ -83,6 +83,10 @@ extern "C" ssh_status ssh_hash_device_noalloc(const ssh_index* idx, const float*
     cudaStream_t st = (cudaStream_t)stream;
     const long long l0 = g_launches.load();
     ssh_status status = SSH_OK;
+    if ((a.force_generic || !hash_fast_supported(a)) && a.minhash != 0) {
+        set_error("the one-permutation minhash needs a compiled sketch shape");
+        return SSH_ENOTSUP;
+    }
     if (a.force_generic || !hash_fast_supported(a)) {
         // shapes without a specialised pipeline: the single-kernel path needs no scratch
         cudaError_t e = launch_hash_generic(a, st);

@@ -86,6 +86,7 @@ struct HashArgs {
     int rank_stride;         // KL rounded up to a multiple of 64 (row padding holds 0xFFFF)
     int force_generic;       // 1: use the generic kernel even when a specialised one exists
     int force_fp64;          // 1: decide every minhash by the FP64 recomputation (a test knob)
+    int minhash;             // 0: ICWS (Sec. 4.3); 1: densified one-permutation hashing of the copies
     const uint2* kla;        // [KL][2^n] per rank: (shingle id, ln a at count 1 rounded once to FP32, as bits)
     const float4* p32;       // [2^n][KL] (r, 1/r, beta, ln c) rounded to FP32
     const double* p64;       // [KL][2^n][3] (r, beta, ln c) in FP64
@@ -359,6 +360,7 @@ struct SrpTab {
 struct ssh_index {
     int W = 0, delta = 0, n = 0, K = 0, L = 0, KL = 0;
     int family = 0;                   // 0: SSH; 1: the SRP baseline (ssh_create_srp)
+    int minhash = 0;                  // SSH_OPT_MINHASH: 0 ICWS, 1 densified one-permutation hashing
     std::map<int, SrpTab> srp;        // family 1: projections per series length
     bool timing = false;
     std::vector<KernelTimer> pending;

@@ -63,11 +63,12 @@ def gpu_hash(idx, x: np.ndarray):
                 keys=keys.cpu().numpy().view(np.uint64), nb=nb)
 
 
-def check_hash_parity(cfg, x, rows=None, generic=False, force_fp64=False):
+def check_hash_parity(cfg, x, rows=None, generic=False, force_fp64=False, minhash=0):
     idx = _index(cfg)
     try:
         idx.set_hash_kernel(generic)
         idx.set_cws_fp64(force_fp64)
+        idx.set_minhash(minhash)
         g = gpu_hash(idx, x)
         r = oracle.filter_r(cfg["seed"], cfg["W"])
         assert np.array_equal(idx.filter, r)
@@ -79,7 +80,7 @@ def check_hash_parity(cfg, x, rows=None, generic=False, force_fp64=False):
             k = int(g["nnz"][i])
             assert k == len(sid), f"nnz of row {i}"
             assert np.array_equal(g["ids"][i, :k], sid) and np.array_equal(g["cnt"][i, :k], scnt), f"shingles {i}"
-            ks, ts = oracle.cws(cfg["seed"], KL, sid, scnt)
+            ks, ts = (oracle.doph if minhash else oracle.cws)(cfg["seed"], KL, sid, scnt)
             assert np.array_equal(g["ks"][i], ks), f"kstar of row {i}"
             assert np.array_equal(g["ts"][i], ts), f"tstar of row {i}"
             for l in range(cfg["L"]):
@@ -776,3 +777,37 @@ def test_srp_near_zero_projections_take_the_fp64_path():
     for i in range(8):
         oi, od = ref.query(db[i], 3)
         assert_topk_match(db[i], ids[i], d[i], oi, od, lambda j: db[j], rb)
+
+
+@pytest.mark.parametrize("cfg,m", [(CFG1, 128), (CFG2, 512), (CFG3, 1024)])
+def test_doph_minhash_parity(cfg, m):
+    """SSH_OPT_MINHASH 1: the densified one-permutation minhash of every series equals the
+    oracle's, (k*, t*) and bucket keys bit for bit (random walks and repeated-shingle-heavy
+    ECG-like beats)."""
+    x = synth.random_walk(150, m, seed=m + 50) if m != 1024 else synth.ecg_like(80, m, seed=51)
+    check_hash_parity(cfg, x, minhash=1)
+
+
+def test_doph_end_to_end_and_option_rules():
+    b = _binding()
+    cfg = CFG1
+    db = synth.random_walk(800, 128, seed=52)
+    qs, _ = synth.perturbed_queries(db, 8, seed=53)
+    ref = oracle.OracleIndex(**cfg, family="ssh-doph")
+    ref.add(db)
+    with _index(cfg) as idx:
+        idx.set_minhash(1)
+        idx.add(db)
+        ids, d = idx.query(qs, 5)
+        with pytest.raises(b.SSHError) as e:
+            idx.set_minhash(0)  # the stored keys are one-permutation keys
+        assert e.value.status == b.SSH_EBUSY
+    rb = oracle.band_radius(cfg["band"], 128)
+    for i, q in enumerate(qs):
+        oi, od = ref.query(q, 5)
+        assert_topk_match(q, ids[i], d[i], oi, od, lambda j: db[j], rb)
+    with b.SSHIndex(40, 3, 10, 4, 8, 0.05, 0) as idx:  # no compiled sketch shape for W = 40
+        idx.set_minhash(1)
+        with pytest.raises(b.SSHError) as e:
+            idx.add(synth.random_walk(5, 128, seed=54))
+        assert e.value.status == b.SSH_ENOTSUP
