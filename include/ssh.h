@@ -51,7 +51,7 @@ typedef enum ssh_status {
     SSH_ELENGTH = 4,  /* a series is too short, too long, or a query length has no sub-index */
     SSH_EBUSY = 5,    /* admission refused: not enough free device memory */
     SSH_ETIMEOUT = 6, /* a bounded device wait gave up */
-    SSH_ENOTSUP = 7   /* a parameter combination this build does not implement */
+    SSH_ENOTSUP = 7   /* a parameter combination the library does not implement */
 } ssh_status;
 
 /* Name of a status code ("SSH_OK", ...). Never NULL. */
@@ -65,7 +65,7 @@ const char* ssh_last_error(void);
  * uses 20 tables of one hash each, here there are L tables keyed by K hashes each).
  *   W      filter length, 1 <= W <= 8192 (Sec. 4.1)
  *   delta  filter step, >= 1 (Sec. 4.1)
- *   n      shingle length in bits, 1 <= n <= 16 in this build (Sec. 4.2);
+ *   n      shingle length in bits, 1 <= n <= 16 (the draws are tabulated per shingle id) (Sec. 4.2);
  *          17..32 return SSH_ENOTSUP, anything else SSH_EINVAL
  *   K, L   hashes per table and number of tables, K*L <= 4096
  *   band   Sakoe-Chiba band as a fraction of the series length: the DTW radius

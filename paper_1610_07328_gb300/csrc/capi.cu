@@ -539,7 +539,7 @@ ssh_status validate_lengths(ssh_index* idx, const int32_t* lengths, int64_t coun
         SSH_TRY(geometry(idx, lengths[i], &g));
         const int rb = band_radius(idx->band, lengths[i]);
         if (dtw_plan(lengths[i], rb).S == 0)
-            return fail(SSH_ENOTSUP, "DTW radius %d (length %d) is wider than this build covers", rb, lengths[i]);
+            return fail(SSH_ENOTSUP, "DTW radius %d (length %d) is wider than the compiled DTW tilings cover", rb, lengths[i]);
     }
     return SSH_OK;
 }
@@ -1577,7 +1577,7 @@ static ssh_status pairwise(const float* d_a, const int64_t* d_a_idx, const float
         SSH_CUDA(launch_lb_rev(ps, m, rb, d_out, nullptr, 1.f, nullptr, nullptr, st));
     } else {
         cudaError_t e = launch_dtw_plan(ps, m, rb, dtw_tuned_plan(m, rb, st), d_out, st);
-        if (e == cudaErrorNotSupported) return fail(SSH_ENOTSUP, "DTW radius %d is wider than this build covers", rb);
+        if (e == cudaErrorNotSupported) return fail(SSH_ENOTSUP, "DTW radius %d is wider than the compiled DTW tilings cover", rb);
         SSH_CUDA(e);
     }
     SSH_CUDA(cudaStreamSynchronize(st));
