@@ -283,6 +283,16 @@ __global__ void __launch_bounds__(256) lb_rev_kernel(PairSet ps, int m, int rb, 
 // the loop is unrolled by the window period U = S/2 + 1 so the slide is a
 // renaming of registers, not moves.
 
+// (r0, r1) = (d0 * d0 + c0, d1 * d1 + c1) with one paired FP32 FMA (sm_100+),
+// each half rounded once exactly as fmaf: two DTW cells in one issue slot.
+__device__ __forceinline__ void sq_add2(float& r0, float& r1, float d0, float d1, float c0, float c1) {
+    unsigned long long dd, cc, rr;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(dd) : "f"(d0), "f"(d1));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(cc) : "f"(c0), "f"(c1));
+    asm("fma.rn.f32x2 %0, %1, %1, %2;" : "=l"(rr) : "l"(dd), "l"(cc));
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r0), "=f"(r1) : "l"(rr));
+}
+
 __device__ __forceinline__ float min3f(float a, float b, float c) {
     float d;
     asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
@@ -392,26 +402,40 @@ __global__ void __launch_bounds__(256) dtw_wave_kernel(PairSet ps, int m, int rb
                 // wave tau = 2s: odd slots 2a+1, cell (A - a, B + a), c = cw[a+1], q = qw[a]
                 float right = __shfl_down_sync(kFull, D[0], 1);
                 if (g == G - 1) right = INF;
+                // the cells of a wave are independent: slots 2a+1 and 2a+3 share one paired FMA
 #pragma unroll
-                for (int a = 0; a < H; ++a) {
+                for (int a = 0; a < H; a += 2) {
                     const int pp = 2 * a + 1;
-                    const float cv = creg[(a + 1 + U - u) % U];
-                    const float qv = qreg[(a + u) % U];
                     const float ur = (pp + 1 < S) ? D[pp + 1] : right;
-                    const float d = cv - qv;
-                    D[pp] = fmaf(d, d, min3f(ur, D[pp - 1], D[pp]));
+                    const float d = creg[(a + 1 + U - u) % U] - qreg[(a + u) % U];
+                    const float mn = min3f(ur, D[pp - 1], D[pp]);
+                    if (a + 1 < H) {
+                        const int p1 = pp + 2;
+                        const float ur1 = (p1 + 1 < S) ? D[p1 + 1] : right;
+                        const float d1 = creg[(a + 2 + U - u) % U] - qreg[(a + 1 + u) % U];
+                        const float mn1 = min3f(ur1, D[p1 - 1], D[p1]);
+                        sq_add2(D[pp], D[p1], d, d1, mn, mn1);
+                    } else {
+                        D[pp] = fmaf(d, d, mn);
+                    }
                 }
                 // wave tau = 2s + 1: even slots 2a, cell (A + 1 - a, B + a), c = cw[a], q = qw[a]
                 float left = __shfl_up_sync(kFull, D[S - 1], 1);
                 if (g == 0) left = INF;
 #pragma unroll
-                for (int a = 0; a < H; ++a) {
+                for (int a = 0; a < H; a += 2) {
                     const int pp = 2 * a;
-                    const float cv = creg[(a + U - u) % U];
-                    const float qv = qreg[(a + u) % U];
                     const float lf = (pp > 0) ? D[pp - 1] : left;
-                    const float d = cv - qv;
-                    D[pp] = fmaf(d, d, min3f(D[pp + 1], lf, D[pp]));
+                    const float d = creg[(a + U - u) % U] - qreg[(a + u) % U];
+                    const float mn = min3f(D[pp + 1], lf, D[pp]);
+                    if (a + 1 < H) {
+                        const int p1 = pp + 2;
+                        const float d1 = creg[(a + 1 + U - u) % U] - qreg[(a + 1 + u) % U];
+                        const float mn1 = min3f(D[p1 + 1], D[p1 - 1], D[p1]);
+                        sq_add2(D[pp], D[p1], d, d1, mn, mn1);
+                    } else {
+                        D[pp] = fmaf(d, d, mn);
+                    }
                 }
                 D[PMASK] = fmaxf(D[PMASK], mflag);
             }
