@@ -487,7 +487,9 @@ ssh_status enqueue_pipeline(ssh_batch* b) {
     for (int c = 0; c < C; ++c) {
         const ssh_batch::HostClass& hc = b->cls[c];
         SSH_CUDA(launch_envelope(d.q_ptr, Q, hc.m, hc.rb, b->upper, b->lower, st, d.cls_begin + c, b->max_m));
-        PairSet ps{b->seg_begin, Q, d.q_ptr, b->pair_b, nullptr, kLbGridPairs, d.cls_begin + c, b->max_m,
+        // the pair counts are on the device: size the grid for kLbGridPairs pairs per
+        // segment at one pair per warp (the launcher plans about 8 per warp)
+        PairSet ps{b->seg_begin, Q, d.q_ptr, b->pair_b, nullptr, 8 * kLbGridPairs, d.cls_begin + c, b->max_m,
                    std::min<int64_t>(kGridSegs, Q)};
         SSH_CUDA(launch_lb_keogh(ps, b->upper, b->lower, hc.m, b->lb, st, true));  // with the LB_Kim endpoints
     }

@@ -158,7 +158,22 @@ __global__ void __launch_bounds__(kLbWarps * 32) lb_keogh_kernel(PairSet ps, con
         for (int64_t p = b + (int64_t)blockIdx.x * per_cta + warp; p < e; p += (int64_t)gridDim.x * per_cta) {
             const float* c = ps.pair_b[p];
             float acc = 0.f;
-            for (int i = lane; i < m; i += 32) {
+            int i = lane;
+            // four loads in flight per lane, then their terms in order
+            for (; i + 96 < m; i += 128) {
+                float v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) v[u] = __ldg(c + i + 32 * u);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int j = i + 32 * u;
+                    const float du = v[u] - env[j];
+                    const float dl = v[u] - env[m + j];
+                    const float d = du > 0.f ? du : (dl < 0.f ? dl : 0.f);
+                    acc = fmaf(d, d, acc);
+                }
+            }
+            for (; i < m; i += 32) {
                 const float v = __ldg(c + i);
                 const float du = v - env[i];
                 const float dl = v - env[m + i];
@@ -763,7 +778,8 @@ cudaError_t launch_envelope(const float* const* seg_a, int64_t nseg, int m, int 
 cudaError_t launch_lb_keogh(const PairSet& ps, const float* upper, const float* lower, int m, float* out,
                             cudaStream_t st, bool kim) {
     if (ps.nseg <= 0 || ps.max_seg_pairs <= 0) return cudaSuccess;
-    int64_t gx = (ps.max_seg_pairs + kLbWarps - 1) / kLbWarps;
+    // about 8 pairs per warp: the staged envelope serves 64 pairs of its block
+    int64_t gx = (ps.max_seg_pairs + kLbWarps * 8 - 1) / (kLbWarps * 8);
     if (gx > 65535) gx = 65535;
     const size_t smem = 2 * (size_t)m * sizeof(float);
     const void* fn = kim ? (const void*)lb_keogh_kernel<true> : (const void*)lb_keogh_kernel<false>;

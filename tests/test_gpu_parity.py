@@ -811,3 +811,31 @@ def test_doph_end_to_end_and_option_rules():
         with pytest.raises(b.SSHError) as e:
             idx.add(synth.random_walk(5, 128, seed=54))
         assert e.value.status == b.SSH_ENOTSUP
+
+
+def test_limits_and_empty_calls():
+    """k at its maximum (1024) returns every candidate in order and fills the rest with
+    (-1, +inf); k above it is refused; empty adds and empty query batches are no-ops; the
+    option values outside their ranges are refused."""
+    b = _binding()
+    cfg = CFG1
+    db = synth.random_walk(300, 128, seed=60)
+    with _index(cfg) as idx:
+        assert idx.add(np.zeros((0, 128), np.float32)) == 0 and len(idx) == 0
+        idx.add(db)
+        ids, d = idx.query(db[:2], 1024)
+        for i in range(2):
+            real = ids[i] >= 0
+            n = int(real.sum())
+            assert real[:n].all() and not real[n:].any() and np.isinf(d[i, n:]).all()
+            pairs = list(zip(d[i, :n].tolist(), ids[i, :n].tolist()))
+            assert pairs == sorted(pairs) and ids[i, 0] == i and d[i, 0] == 0.0
+        with pytest.raises(b.SSHError) as e:
+            idx.query(db[:1], 1025)
+        assert e.value.status == b.SSH_EINVAL
+        ids0, d0 = idx.query(np.zeros((0, 128), np.float32), 5)
+        assert ids0.shape == (0, 5)
+        for opt, bad in ((b.SSH_OPT_LB_CASCADE, 3), (b.SSH_OPT_MINHASH, 2), (b.SSH_OPT_HASH_KERNEL, 2)):
+            with pytest.raises(b.SSHError) as e:
+                b.ssh_set_option(idx.handle, opt, bad)
+            assert e.value.status == b.SSH_EINVAL
