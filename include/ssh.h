@@ -271,8 +271,9 @@ void ssh_server_destroy(ssh_server* s);
  * its smallest copy and empty bins borrow by optimal densification; its collision
  * probability per hash is the same weighted Jaccard, at O(copies + K L) work per
  * series instead of O(distinct shingles x K L). Hashes and keys differ from
- * ICWS's. Settable only while the index is empty (else SSH_EBUSY); needs a
- * compiled sketch shape (adds return SSH_ENOTSUP otherwise). */
+ * ICWS's. Settable only while the index is empty (else SSH_EBUSY) and for
+ * K*L <= 256 (else SSH_ENOTSUP); needs a compiled sketch shape (adds return
+ * SSH_ENOTSUP otherwise). */
 typedef enum ssh_option {
     SSH_OPT_LB_PRUNE = 1,
     SSH_OPT_KERNEL_TIMING = 2,

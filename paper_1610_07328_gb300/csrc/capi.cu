@@ -1419,6 +1419,8 @@ ssh_status ssh_set_option(ssh_index* idx, ssh_option opt, int64_t value) {
             return SSH_OK;
         case SSH_OPT_MINHASH: {
             if (value < 0 || value > 1) return fail(SSH_EINVAL, "SSH_OPT_MINHASH takes 0 or 1");
+            if (value == 1 && idx->KL > 256)
+                return fail(SSH_ENOTSUP, "the one-permutation minhash covers K*L <= 256 (this index: %d)", idx->KL);
             for (const auto& kv : idx->subs)
                 if (kv.second.count > 0) return fail(SSH_EBUSY, "SSH_OPT_MINHASH changes only an empty index");
             idx->minhash = (int)value;
