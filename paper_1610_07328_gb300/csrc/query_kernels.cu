@@ -805,8 +805,10 @@ cudaError_t launch_lb_rev(const PairSet& ps, int m, int rb, float* out, const ui
     int warps = 8;
     while (warps > 1 && lb_rev_smem(m, rb, warps) > 200 * 1024) --warps;
     const size_t smem = lb_rev_smem(m, rb, warps);
-    if (smem > 227 * 1024) return cudaErrorInvalidValue;
     const bool mark = U != nullptr;
+    // a series too long for one warp's envelope buffers: the optional pruning pass is
+    // skipped (the survivors all go to DTW, same results); a direct request fails
+    if (smem > 227 * 1024) return mark ? cudaSuccess : cudaErrorInvalidValue;
     const void* fn = mark ? (const void*)lb_rev_kernel<true> : (const void*)lb_rev_kernel<false>;
     cudaError_t e = ensure_dynamic_smem(fn, smem);
     if (e != cudaSuccess) return e;
