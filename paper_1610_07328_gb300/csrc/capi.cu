@@ -530,16 +530,26 @@ int64_t run_end(const int32_t* lengths, int64_t i, int64_t count) {
     return j;
 }
 
+// A run of consecutive series of one length: series [i, j) of a call, length m.
+struct LengthRun {
+    int64_t i, j;
+    int m;
+};
+
 // Every length of a call must be valid before anything is added (each run of
-// equal lengths is checked once).
-ssh_status validate_lengths(ssh_index* idx, const int32_t* lengths, int64_t count) {
-    for (int64_t i = 0; i < count; i = run_end(lengths, i, count)) {
+// equal lengths is checked once); `runs` (may be NULL) receives the runs, so the
+// lengths are scanned once per call.
+ssh_status validate_lengths(ssh_index* idx, const int32_t* lengths, int64_t count,
+                            std::vector<LengthRun>* runs = nullptr) {
+    for (int64_t i = 0, j; i < count; i = j) {
+        j = run_end(lengths, i, count);
         Geometry g;
         if (lengths[i] <= 0) return fail(SSH_ELENGTH, "series %lld has length %d", (long long)i, lengths[i]);
         SSH_TRY(geometry(idx, lengths[i], &g));
         const int rb = band_radius(idx->band, lengths[i]);
         if (dtw_plan(lengths[i], rb).S == 0)
             return fail(SSH_ENOTSUP, "DTW radius %d (length %d) is wider than the compiled DTW tilings cover", rb, lengths[i]);
+        if (runs) runs->push_back(LengthRun{i, j, lengths[i]});
     }
     return SSH_OK;
 }
@@ -561,12 +571,12 @@ SubIndex& sub_for(ssh_index* idx, int m, const Geometry& g) {
 // call whose first id is id0; `dev` points at series i0, the series back to
 // back in device memory that stays valid while the index uses it. The
 // sub-indexes touched are added to `touched`; their tables are rebuilt later.
-ssh_status hash_range(ssh_index* idx, const float* dev, const int32_t* lengths, int64_t i0, int64_t i1, int64_t id0,
-                      cudaStream_t st, std::vector<int>& touched) {
-    int64_t i = i0, run_off = 0;
-    while (i < i1) {
-        const int64_t j = run_end(lengths, i, i1);
-        const int m = lengths[i];
+ssh_status hash_runs(ssh_index* idx, const float* dev, const std::vector<LengthRun>& runs, int64_t id0,
+                     cudaStream_t st, std::vector<int>& touched) {
+    int64_t run_off = 0;
+    for (const LengthRun& r : runs) {
+        const int64_t i = r.i, j = r.j;
+        const int m = r.m;
         const int64_t nrun = j - i;
         Geometry g;
         SSH_TRY(geometry(idx, m, &g));
@@ -587,9 +597,18 @@ ssh_status hash_range(ssh_index* idx, const float* dev, const int32_t* lengths, 
         s.count += nrun;
         idx->host_stats.series_hashed += nrun;
         run_off += (int64_t)m * nrun;
-        i = j;
     }
     return SSH_OK;
+}
+
+ssh_status hash_range(ssh_index* idx, const float* dev, const int32_t* lengths, int64_t i0, int64_t i1, int64_t id0,
+                      cudaStream_t st, std::vector<int>& touched) {
+    std::vector<LengthRun> runs;
+    for (int64_t i = i0, j; i < i1; i = j) {
+        j = run_end(lengths, i, i1);
+        runs.push_back(LengthRun{i, j, lengths[i]});
+    }
+    return hash_runs(idx, dev, runs, id0, st, touched);
 }
 
 // Rebuild the tables of the touched sub-indexes and mark the index ready after
@@ -611,9 +630,10 @@ ssh_status finish_add(ssh_index* idx, const std::vector<int>& touched, int64_t c
 // Algorithm 1 for the series of one call, already in device memory.
 ssh_status add_series(ssh_index* idx, const float* dev, const int32_t* lengths, int64_t count, cudaStream_t st,
                       int64_t* first_id) {
-    SSH_TRY(validate_lengths(idx, lengths, count));
+    std::vector<LengthRun> runs;
+    SSH_TRY(validate_lengths(idx, lengths, count, &runs));
     std::vector<int> touched;
-    SSH_TRY(hash_range(idx, dev, lengths, 0, count, idx->next_id, st, touched));
+    SSH_TRY(hash_runs(idx, dev, runs, idx->next_id, st, touched));
     return finish_add(idx, touched, count, st, first_id, false);
 }
 
