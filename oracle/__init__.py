@@ -289,12 +289,14 @@ def hash_series(x, r, delta: int, n: int, seed: int, K: int, L: int):
 
 
 def recall_at_k(returned_ids, exact_ids) -> float:
-    """Sec. 5.3 precision: |returned top-k  ∩  exact top-k| / k."""
+    """Sec. 5.3 precision: |returned top-k  ∩  exact top-k| / |exact top-k|. Entries of -1 are
+    empty slots (fewer than k series to return); the exact list then holds min(k, N) ids, and
+    a result that returns all of them scores 1 (as an empty exact list does)."""
     exact = [int(i) for i in exact_ids if int(i) >= 0]
     got = {int(i) for i in returned_ids if int(i) >= 0}
     if not exact:
         return 1.0
-    return sum(1 for i in exact if i in got) / float(len(exact_ids))
+    return sum(1 for i in exact if i in got) / float(len(exact))
 
 
 def ndcg_at_k(returned_ids, gold_ids) -> float:

@@ -474,6 +474,22 @@ def test_ndcg_orders_and_recall():
         assert oracle.recall_at_k(sw, gold) == 1.0
 
 
+def test_recall_at_k_hand_worked():
+    """Sec. 5.3 precision on hand-worked lists, with empty (-1) slots on either side: the
+    denominator is the number of exact neighbours that exist, the numerator the returned ids
+    among them (order and -1 slots of the result do not count)."""
+    cases = [
+        ([3, 7, -1, -1, -1], [5, 3, 9, -1, -1], 1 / 3),   # 3 series exist, one found
+        ([9, 5, 3, -1, -1], [5, 3, 9, -1, -1], 1.0),      # all three found, in another order
+        ([4, 8, 2, -1], [1, 2, 3, 4], 0.5),               # 2 of 4, one wrong, one slot empty
+        ([-1, -1, -1, -1], [1, 2, 3, 4], 0.0),            # nothing returned
+        ([7, 8], [-1, -1], 1.0),                          # nothing to find
+        ([2, 2, 1], [1, 2, 3], 2 / 3),                    # a repeated id counts once
+    ]
+    for got, gold, want in cases:
+        assert oracle.recall_at_k(got, gold) == pytest.approx(want, abs=1e-15), (got, gold)
+
+
 # --------------------------------------------------------- Algorithms 1 and 2
 
 def test_topk_matches_sort():
@@ -552,6 +568,12 @@ def test_bench_ndcg_matches_the_oracle():
         got = list(rng.choice(np.concatenate([gold, rng.integers(40, 60, 10)]), 10, replace=False))
         assert bench.ndcg([got], [gold]) == pytest.approx(oracle.ndcg_at_k(got, gold), rel=1e-12)
         assert bench.recall([got], [gold]) == pytest.approx(oracle.recall_at_k(got, gold), rel=1e-12)
+        # short lists: empty (-1) slots at the end of either list
+        gold_s = gold[:int(rng.integers(0, 10))]
+        gold_s = gold_s + [-1] * (10 - len(gold_s))
+        got_s = got[:int(rng.integers(0, 10))]
+        got_s = got_s + [-1] * (10 - len(got_s))
+        assert bench.recall([got_s], [gold_s]) == pytest.approx(oracle.recall_at_k(got_s, gold_s), rel=1e-12)
 
 
 # ------------------------------------------- Sec. 5.2 baseline: sign random projections
