@@ -43,8 +43,6 @@ TINY = dict(name="plain SSH tiny", N=1000, m=128, W=32, delta=3, n=8, K=4, L=16,
             recall_subset=1000)
 
 FP32_LANES_PER_SM = 128
-NUM_SMS = 152
-MAX_SM_MHZ = 2070.0
 
 
 def workload_desc(w):
@@ -54,12 +52,15 @@ def workload_desc(w):
 
 
 def peaks():
+    """HBM copy bandwidth and the maximum SM clock measured on the GB300s
+    (MEASURED_PEAKS.json), else the recipe's fallback figures."""
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
         with open(path) as f:
             p = json.load(f)
-        return dict(hbm_gbs=float(p["hbm_gbs"]), source="measured")
-    return dict(hbm_gbs=6800.0, source="fallback")
+        return dict(hbm_gbs=float(p["hbm_gbs"]), sm_max_mhz=float(p.get("sm_max_mhz") or 2070.0),
+                    source="measured")
+    return dict(hbm_gbs=6800.0, sm_max_mhz=2070.0, source="fallback")
 
 
 def l2_read_gbs(torch, dev, binding):
@@ -83,9 +84,21 @@ def l2_read_gbs(torch, dev, binding):
     return x.numel() * 4 * passes / (best / 1000.0) / 1e9
 
 
+_FP32_PEAK = {}
+
+
+def set_fp32_peak(num_sms, sm_max_mhz):
+    _FP32_PEAK.update(sms=int(num_sms), mhz=float(sm_max_mhz))
+
+
 def fp32_peak_tflops():
-    # 152 SMs x 128 FP32 lanes x 2 FLOP (FMA) x 2.07 GHz maximum SM clock
-    return NUM_SMS * FP32_LANES_PER_SM * 2 * MAX_SM_MHZ * 1e6 / 1e12
+    """The device's SM count x 128 FP32 lanes x 2 FLOP (FMA) x the measured maximum SM clock."""
+    return _FP32_PEAK["sms"] * FP32_LANES_PER_SM * 2 * _FP32_PEAK["mhz"] * 1e6 / 1e12
+
+
+def fp32_peak_source():
+    return "derived: %d SMs x %d FP32 lanes x 2 x %.0f MHz" % (_FP32_PEAK["sms"], FP32_LANES_PER_SM,
+                                                                _FP32_PEAK["mhz"])
 
 
 # ------------------------------------------------------------------ clocks
@@ -138,6 +151,23 @@ class ClockSampler:
                     reasons.add(name)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def h2d_copy_gbs(torch, h_src, d_dst):
+    """Host-to-device copy bandwidth from pinned memory: one copy of the whole series buffer,
+    timed with CUDA events on the current stream, best of 3 after one warm-up."""
+    st = torch.cuda.current_stream()
+    d_dst.copy_(h_src, non_blocking=True)
+    best = float("inf")
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(st)
+        d_dst.copy_(h_src, non_blocking=True)
+        e1.record(st)
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return h_src.numel() * h_src.element_size() / (best / 1000.0) / 1e9
 
 
 def gpu_bus_id(torch, dev):
@@ -235,26 +265,46 @@ def oracle_sample_all_cores(w, n_sample: int, n_queries: int, timeout: float = 3
 
 
 def run_reference(args, w):
+    """The oracle as it stands, on the host cores, each step a bounded sample of the workload:
+    index an n_s-series slice and answer all nq queries on that slice's index. The query phase
+    of the full step grows with N (candidate sets grow in proportion to the index), so a step
+    over n_s series costs n_s/N of the full step under that model; value = n_s / step time."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    n_sample, n_q = (1000, 2) if not args.small else (200, 2)
-    vals = []
-    secs = 0.0
+    import oracle
+    n_s = 1000 if not args.small else 200
+    n_slices = 5
+    slices = []
+    all_rows = synth.random_walk(n_slices * n_s, w["m"], seed=w["seed"])
+    for s in range(n_slices):
+        db = all_rows[s * n_s:(s + 1) * n_s]
+        qs, _ = synth.perturbed_queries(db, w["nq"], seed=1 + s)
+        slices.append((db, qs))
+    step_s = []
     for s in range(args.warmup + args.steps):
-        r = oracle_sample(w, n_sample, n_q, row0=(s % 5) * n_sample)
+        db, qs = slices[s % n_slices]
+        t0 = time.perf_counter()
+        idx = oracle.OracleIndex(w["W"], w["delta"], w["n"], w["K"], w["L"], w["band"], w["seed"])
+        idx.add(db)
+        for q in qs:
+            idx.query(q, w["k"])
+        dt = time.perf_counter() - t0
         if s >= args.warmup:
-            vals.append(r["value"])
-            secs += r["seconds"]
-    value = statistics.mean(vals)
-    sample = r["sample"] + f"; each step a different {n_sample}-series slice"
+            step_s.append(dt)
+    ms_per_step = 1000.0 * statistics.mean(step_s)
+    value = n_s / (ms_per_step / 1000.0)
+    sample = (f"each step: the oracle indexes a {n_s}-series slice of the workload (one of {n_slices}) and answers "
+              f"{w['nq']} perturbed queries on it, one core")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "series/s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * w["N"] / value,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload_desc(w), "parallelism": "single process, CPU oracle"},
+        "config": {"workload": f"sample of {workload_desc(w)}: {n_s} series + {w['nq']} queries per step",
+                   "parallelism": "single process, CPU oracle"},
         "cpu_baseline": {"value": value, "unit": "series/s", "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "series/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "extrapolated_full_step_ms": 1000.0 * w["N"] / value,
     }
     print(json.dumps(line), flush=True)
 
@@ -374,10 +424,12 @@ def exact_topk_gpu(binding, torch, d_q, d_db, rows, m, rb, k):
 
 
 def recall(ids, exact):
+    """Mean recall@k: returned ids found in the exact top-k over the exact list's valid (>= 0) ids."""
     r = []
     for a, b in zip(ids, exact):
         got = {int(x) for x in a if x >= 0}
-        r.append(sum(1 for x in b if int(x) in got) / len(b))
+        gold = [int(x) for x in b if x >= 0]
+        r.append(sum(1 for x in gold if x in got) / len(gold) if gold else 1.0)
     return float(np.mean(r))
 
 
@@ -1042,6 +1094,7 @@ def run_gpu(args, w):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
+    set_fp32_peak(torch.cuda.get_device_properties(dev).multi_processor_count, peaks()["sm_max_mhz"])
     N, m, nq, k = w["N"], w["m"], w["nq"], w["k"]
 
     # inputs: each rank holds its own N-series shard (weak scaling), pinned on the host and resident on the GPU
@@ -1176,7 +1229,7 @@ def run_gpu(args, w):
     h_db_np = h_db.numpy()
     h_q_np2 = h_q.numpy()
     qlen = qlengths
-    e2e_steps = max(2, min(args.steps, 5))
+    e2e_steps = args.steps
     # warm-up: the first host add allocates the index's 2 GB staging copy, later
     # adds reuse it (ssh_index_clear keeps the buffer for the next add)
     for _ in range(max(1, min(args.warmup, 2))):
@@ -1197,6 +1250,7 @@ def run_gpu(args, w):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_ms = float(t.item())
     idx.close()
+    h2d_peak = h2d_copy_gbs(torch, h_db, d_db)
 
     pk = peaks()
     roofs = kernel_rooflines(w, times, pk)
@@ -1205,7 +1259,7 @@ def run_gpu(args, w):
     d = roofs[dominant]
     roofline = {"kernel": dominant, "bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"],
                 "unit": d["unit"], "frac": d["frac"], "traffic": traffic_for(dominant),
-                "peak_source": pk["source"] if d["unit"] == "GB/s" else "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
+                "peak_source": pk["source"] if d["unit"] == "GB/s" else fp32_peak_source()}
     l2b = traffic_for(dominant, "l2_read_bytes_per_launch")
     if l2b:
         # the minhash kernel's binding resource: its L2 reads (rank-row gathers) per launch from the
@@ -1240,6 +1294,10 @@ def run_gpu(args, w):
         "e2e": {"value": N * world / (e2e_ms / 1000.0), "unit": "series/s",
                 "h2d_bytes_per_step": N * m * 4 + nq * m * 4,
                 "d2h_bytes_per_step": nq * k * 12, "steps": e2e_steps, "warmup": max(1, min(args.warmup, 2)),
+                "ms_per_step": e2e_ms,
+                "h2d_gbs": (N * m * 4 + nq * m * 4) / (e2e_ms / 1000.0) / 1e9,
+                "h2d_peak_gbs": h2d_peak, "h2d_frac": (N * m * 4 + nq * m * 4) / (e2e_ms / 1000.0) / 1e9 / h2d_peak,
+                "h2d_peak_source": "measured here: one pinned host-to-device copy of the series (best of 3)",
                 "api": "ssh_index_clear + ssh_index_add(host) + ssh_query(host)"},
         "clocks": clocks,
         "setup_s": {"inputs": gen_s},
@@ -1263,10 +1321,180 @@ def run_gpu(args, w):
         except Exception as e:  # reported, never fatal to the line
             line["cpu_baseline"]["all_cores"] = {"error": repr(e)[:200]}
     if rank == 0:
-        print(json.dumps(line), flush=True)
+        detail = args.detail_out or os.path.join(ROOT, "gpurun_out", "bench_detail_n%d.json" % world)
+        try:
+            os.makedirs(os.path.dirname(detail), exist_ok=True)
+            with open(detail, "w") as f:
+                json.dump(line, f, indent=1)
+        except OSError as e:  # the headline below still carries every contract key
+            detail = "not written: %r" % (e,)
+        print(json.dumps(headline(line, detail)), flush=True)
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+
+
+# ------------------------------------------------- fixed cases for ncu captures
+#
+#   python bench.py --profile-case hash 200000
+#       hashes 200,000 random walks of length 512 with the scale parameters (W=80, delta=3,
+#       n=15, K=4, L=25) through ssh_hash_device twice: the sketch, FP64 fix-up, shingle and
+#       minhash kernels run once per call.
+#   python bench.py --profile-case dtw 512:25 [reps]
+#       banded DTW of 100 queries against 2,000,000 / m random candidates each (rows of a
+#       random-walk table larger than L2) through ssh_dtw_device; prints the fastest call.
+#   python bench.py --profile-case tables 262144
+#       an index of 262,144 random walks of length 512 with the scale parameters, added twice.
+#   python bench.py --profile-case batch 50000 1024
+#       five per-length indexes (m = 128 .. 2048, W = m/8, delta=3, n=15, K=4, L=25) of 50,000
+#       random walks each and three batches of 1,024 mixed-length queries through one plan.
+
+def profile_hash(n: int) -> None:
+    import torch
+    from paper_1610_07328_gb300 import binding
+    m = 512
+    x = torch.from_numpy(synth.random_walk(n, m, seed=0)).cuda()
+    with binding.SSHIndex(80, 3, 15, 4, 25, 0.05, 0) as idx:
+        keys = torch.empty((25, n), dtype=torch.int64, device="cuda")
+        for _ in range(2):
+            binding.ssh_hash_device(idx.handle, x, m, n, d_keys=keys)
+        torch.cuda.synchronize()
+        print("hashed", n, "series twice;", idx.stats())
+
+
+def profile_dtw(spec: str, reps: int) -> None:
+    import torch
+    from paper_1610_07328_gb300 import binding
+    for case in spec.split(","):
+        m, rb = (int(v) for v in case.split(":"))
+        nb = max(20000, 400_000_000 // (4 * m))
+        b = torch.from_numpy(synth.random_walk(nb, m, seed=1)).cuda()
+        a = torch.from_numpy(synth.random_walk(100, m, seed=2)).cuda()
+        cand = max(200, 2_000_000 // m)
+        rng = np.random.default_rng(0)
+        ai = torch.from_numpy(np.repeat(np.arange(100), cand).astype(np.int64)).cuda()
+        bi = torch.from_numpy(rng.integers(0, nb, 100 * cand).astype(np.int64)).cuda()
+        out = torch.empty(100 * cand, device="cuda")
+        best = float("inf")
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            binding.ssh_dtw_device(a, ai, b, bi, m, rb, out)
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        cells = 100 * cand * (m * (2 * rb + 1) - rb * (rb + 1))
+        print(f"m={m} rb={rb} pairs={100 * cand} call_ms={best:.3f} cells={cells}")
+
+
+def profile_batch(n: int, nq: int) -> None:
+    import torch
+    from paper_1610_07328_gb300 import binding
+    lens = (128, 256, 512, 1024, 2048)
+    hosts = {m: synth.random_walk(n, m, seed=40 + m) for m in lens}
+    idxs = [binding.SSHIndex(m // 8, 3, 15, 4, 25, 0.05, 0) for m in lens]
+    data = {m: torch.from_numpy(hosts[m]).cuda() for m in lens}
+    for ix, m in zip(idxs, lens):
+        ix.add_device(data[m], borrow=True)
+    rng = np.random.default_rng(4)
+    qlens = rng.choice(np.array(lens, np.int32), size=nq)
+    qs = [synth.perturbed_queries(hosts[m], 1, seed=1000 + i)[0][0] for i, m in enumerate(qlens)]
+    d_q = torch.from_numpy(np.concatenate(qs)).cuda()
+    ids = torch.empty((nq, 10), dtype=torch.int64, device="cuda")
+    dd = torch.empty((nq, 10), dtype=torch.float32, device="cuda")
+    with binding.SSHBatch(idxs, max_queries=nq, k=10) as bt:
+        for _ in range(3):
+            bt.query(d_q, qlens, ids, dd)
+        torch.cuda.synchronize()
+        print("batches done;", bt.stats())
+    for ix in idxs:
+        ix.close()
+
+
+def profile_tables(n: int) -> None:
+    import torch
+    from paper_1610_07328_gb300 import binding
+    x = torch.from_numpy(synth.random_walk(n, 512, seed=0)).cuda()
+    with binding.SSHIndex(80, 3, 15, 4, 25, 0.05, 0) as idx:
+        for _ in range(2):
+            idx.clear()
+            idx.add_device(x, borrow=True)
+        torch.cuda.synchronize()
+        print("built twice;", len(idx), "rows")
+
+
+
+def run_profile_case(argv):
+    if len(argv) >= 2 and argv[0] == "hash":
+        profile_hash(int(argv[1]))
+    elif len(argv) >= 2 and argv[0] == "tables":
+        profile_tables(int(argv[1]))
+    elif len(argv) >= 3 and argv[0] == "batch":
+        profile_batch(int(argv[1]), int(argv[2]))
+    elif len(argv) >= 2 and argv[0] == "dtw":
+        profile_dtw(argv[1], int(argv[2]) if len(argv) > 2 else 3)
+    else:
+        raise SystemExit("unknown --profile-case %r" % (argv,))
+
+
+def _r(x, nd=4):
+    """Round a float for the headline (significant digits), leave other values alone."""
+    if isinstance(x, float) and math.isfinite(x) and x != 0.0:
+        return float("%.*g" % (nd, x))
+    return x
+
+
+def headline(line, detail_path):
+    """The one short JSON line printed last: the contract keys plus the few figures that the
+    detail file (every block of the run) summarises."""
+    keep = ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+            "scaling", "vs_baseline", "dtype", "data", "gpu_launches", "clocks")
+    h = {k: line[k] for k in keep if k in line}
+    h["value"] = float(line["value"])
+    c = line["config"]
+    h["config"] = {k: c[k] for k in ("workload", "parallelism", "l2") if k in c}
+    r = line["roofline"]
+    h["roofline"] = {k: _r(r[k]) for k in ("kernel", "bound", "achieved", "peak", "unit", "frac", "traffic")}
+    if r.get("binding"):
+        b = r["binding"]
+        h["roofline"]["binding"] = {"resource": b["resource"], "achieved": _r(b["achieved"]), "peak": _r(b["peak"]),
+                                    "frac": _r(b["frac"])}
+    kr = line.get("kernels", {})
+    if "add.hash_pipeline" in kr:
+        h["hash_pipeline_hbm_frac"] = _r(kr["add.hash_pipeline"]["frac"])
+    if "query.dtw" in kr:
+        h["dtw_fp32_frac"] = _r(kr["query.dtw"].get("frac"))
+    if "cpu_baseline" in line:
+        cb = line["cpu_baseline"]
+        h["cpu_baseline"] = {"value": _r(cb["value"]), "unit": cb["unit"], "cores": cb["cores"], "kind": cb["kind"],
+                             "sample": cb["sample"]}
+        if isinstance(cb.get("all_cores"), dict) and "value" in cb["all_cores"]:
+            h["cpu_baseline"]["all_cores"] = {"value": _r(cb["all_cores"]["value"]),
+                                              "cores": cb["all_cores"]["cores"]}
+    e = line["e2e"]
+    h["e2e"] = {k: _r(e[k]) for k in ("value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step", "steps",
+                                      "h2d_gbs", "h2d_peak_gbs", "h2d_frac") if k in e}
+    h["queries_per_s"] = _r(line["queries_per_s"])
+    h["latency_ms"] = {"p50": _r(line["latency_ms"]["p50"]), "p99": _r(line["latency_ms"]["p99"])}
+    for k in ("recall_at_10", "ndcg_at_10"):
+        if k in line:
+            h[k] = _r(line[k])
+    rop = line.get("recall_operating_point", {}).get("chosen")
+    if rop:
+        h["at_recall_0_9"] = {"queries_per_s": _r(rop["queries_per_s"]), "recall_at_10": _r(rop["recall_at_10"]),
+                              "params": "W=%d delta=%d n=%d K=%d L=%d" % (rop["W"], rop["delta"], rop["n"],
+                                                                          rop["K"], rop["L"])}
+    if "batched" in line:
+        b = line["batched"]
+        h["batched_queries_per_s"] = _r(b["batched_queries_per_s"])
+        if b.get("at_recall"):
+            h["batched_at_recall_queries_per_s"] = _r(b["at_recall"]["batched_queries_per_s"])
+    if "served" in line:
+        s = line["served"]["rates"]
+        h["served_p50_p99_ms"] = {str(x["offered_qps"]): [_r(x["p50_ms"], 3), _r(x["p99_ms"], 3)] for x in s}
+    h["detail"] = os.path.relpath(detail_path, ROOT) if os.path.isabs(detail_path) else detail_path
+    return h
 
 
 def main():
@@ -1282,7 +1510,15 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the mixed-length batch-plan measurement")
     ap.add_argument("--no-served", action="store_true", help="skip the serving-loop measurement")
     ap.add_argument("--no-subsequence", action="store_true", help="skip the sliding-window index measurement")
+    ap.add_argument("--detail-out", default=None,
+                    help="where the full measurement JSON goes (default gpurun_out/bench_detail_nN.json)")
+    ap.add_argument("--profile-case", nargs="+", default=None,
+                    help="run one fixed small case for an ncu capture (hash N | dtw m:rb[,m:rb] [reps] | "
+                         "tables N | batch N nq) and exit")
     args = ap.parse_args()
+    if args.profile_case:
+        run_profile_case(args.profile_case)
+        return
     w = TINY if args.small else SCALE
     if args.impl == "reference":
         run_reference(args, w)
