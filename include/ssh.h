@@ -297,6 +297,9 @@ typedef struct ssh_stats {
     int64_t kernel_launches;   /* kernels launched by calls on this index */
     int64_t lb2_pruned;        /* of lb_pruned: candidates that passed LB_Keogh and were pruned by the
                                   reversed LB_Keogh (SSH_OPT_LB_CASCADE) */
+    int64_t lb2_skipped;       /* queries whose requested reversed LB_Keogh pass (SSH_OPT_LB_CASCADE 2)
+                                  did not run because the candidate envelopes of one series length do not
+                                  fit in shared memory; their survivors all went to DTW (same results) */
 } ssh_stats;
 ssh_status ssh_get_stats(const ssh_index* idx, ssh_stats* out);
 ssh_status ssh_reset_stats(ssh_index* idx);

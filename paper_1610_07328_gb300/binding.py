@@ -38,7 +38,7 @@ class SSHError(RuntimeError):
 class ssh_stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in (
         "series_hashed", "sketch_fp64", "cws_fp64", "queries", "candidates", "dtw_computed", "lb_pruned",
-        "kernel_launches", "lb2_pruned")]
+        "kernel_launches", "lb2_pruned", "lb2_skipped")]
 
     def as_dict(self):
         return {n: int(getattr(self, n)) for n, _ in self._fields_}

@@ -529,12 +529,14 @@ ssh_status capture(ssh_batch* b) {
         cudaGraphExecDestroy(b->exec);
         b->exec = nullptr;
     }
-    const long long l0 = g_launches.load();
+    const long long l0 = t_launches;
     SSH_CUDA(cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal));
     ssh_status s = enqueue_pipeline(b);
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(b->st, &g);
-    g_launches.fetch_sub(g_launches.load() - l0);  // counted per replay instead
+    const long long captured = t_launches - l0;  // counted per replay instead
+    t_launches -= captured;
+    g_launches.fetch_sub(captured);
     if (s != SSH_OK) {
         if (g) cudaGraphDestroy(g);
         return s;

@@ -28,6 +28,7 @@ namespace ssh {
 
 static thread_local char g_err[512] = "";
 std::atomic<long long> g_launches{0};
+thread_local long long t_launches = 0;
 
 void set_error(const char* fmt, ...) {
     va_list ap;
@@ -199,7 +200,7 @@ struct TimedRegion {
     long long launches0;
     cudaEvent_t start = nullptr;
     TimedRegion(ssh_index* i, cudaStream_t s, const char* n, double u)
-        : idx(i), st(s), name(n), units(u), launches0(g_launches.load()) {
+        : idx(i), st(s), name(n), units(u), launches0(t_launches) {
         if (idx->timing && cudaEventCreate(&start) == cudaSuccess) cudaEventRecord(start, st);
     }
     ~TimedRegion() {
@@ -210,7 +211,7 @@ struct TimedRegion {
             return;
         }
         cudaEventRecord(stop, st);
-        idx->pending.push_back(KernelTimer{name, start, stop, (int)(g_launches.load() - launches0), units});
+        idx->pending.push_back(KernelTimer{name, start, stop, (int)(t_launches - launches0), units});
     }
 };
 
@@ -567,9 +568,11 @@ SubIndex& sub_for(ssh_index* idx, int m, const Geometry& g) {
     return s;
 }
 
-// Algorithm 1 (sketch, shingle, minhash and row keys) for series [i0, i1) of a
-// call whose first id is id0; `dev` points at series i0, the series back to
-// back in device memory that stays valid while the index uses it. The
+// Algorithm 1 (sketch, shingle, minhash and row keys) for a list of runs of
+// equal-length series of a call whose first id is id0 (run r holds the call's
+// series [r.i, r.j), all of length r.m). `dev` holds the runs' series back to
+// back, contiguously from runs[0].i on (run k starts after the floats of runs
+// 0..k-1), in device memory that stays valid while the index uses it. The
 // sub-indexes touched are added to `touched`; their tables are rebuilt later.
 ssh_status hash_runs(ssh_index* idx, const float* dev, const std::vector<LengthRun>& runs, int64_t id0,
                      cudaStream_t st, std::vector<int>& touched) {
@@ -829,7 +832,9 @@ ssh_status query_group(ssh_index* idx, SubIndex& s, const std::vector<const floa
                 sub.abandon = U;
                 sub.abandon_shrink = shrink;
                 // UCR cascade: the reversed LB_Keogh clears the survivors it proves too far
-                if (e == cudaSuccess && rev) {
+                if (e == cudaSuccess && rev && !lb_rev_fits(m, rb)) {
+                    idx->host_stats.lb2_skipped += nq;  // requested, but the envelopes do not fit
+                } else if (e == cudaSuccess && rev) {
                     TimedRegion tr(idx, st, "query.lb_rev", 0.0);
                     e = launch_lb_rev(sub, m, rb, nullptr, U, shrink, fb, ftotal + 2, st);
                 }
@@ -1202,9 +1207,9 @@ struct LaunchCount {
     ssh_stats* st;
     long long l0;
     explicit LaunchCount(const ssh_index* idx)
-        : st(idx ? const_cast<ssh_stats*>(&idx->host_stats) : nullptr), l0(g_launches.load()) {}
+        : st(idx ? const_cast<ssh_stats*>(&idx->host_stats) : nullptr), l0(t_launches) {}
     ~LaunchCount() {
-        if (st) st->kernel_launches += g_launches.load() - l0;
+        if (st) __atomic_fetch_add(&st->kernel_launches, (int64_t)(t_launches - l0), __ATOMIC_RELAXED);
     }
 };
 

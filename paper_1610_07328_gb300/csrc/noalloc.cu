@@ -81,7 +81,7 @@ extern "C" ssh_status ssh_hash_device_noalloc(const ssh_index* idx, const float*
     a.tstar_out = d_tstar;
     if (count == 0) return SSH_OK;
     cudaStream_t st = (cudaStream_t)stream;
-    const long long l0 = g_launches.load();
+    const long long l0 = t_launches;  // this thread's launches: calls on other threads do not count here
     ssh_status status = SSH_OK;
     if ((a.force_generic || !hash_fast_supported(a)) && a.minhash != 0) {
         set_error("the one-permutation minhash needs a compiled sketch shape");
@@ -94,14 +94,17 @@ extern "C" ssh_status ssh_hash_device_noalloc(const ssh_index* idx, const float*
     } else {
         const size_t need = hash_fast_scratch_bytes(a);
         if (need > kNoAllocScratchBytes) {
-            // the scratch grows linearly with the series count: report the largest count that fits
-            HashArgs one = a;
-            one.count = 1;
-            const size_t per = hash_fast_scratch_bytes(one);
-            HashArgs two = a;
-            two.count = 2;
-            const size_t step = hash_fast_scratch_bytes(two) - per;
-            const long long fit = step ? (long long)((kNoAllocScratchBytes - (per - step)) / step) : 0;
+            // the largest count that fits: the scratch size never decreases as the count grows
+            // (each sub-buffer grows with it, rounded up to 256 bytes), so bisect on it
+            long long lo = 0, hi = (long long)count;  // fits(lo) holds, fits(hi) does not
+            while (hi - lo > 1) {
+                const long long mid = lo + (hi - lo) / 2;
+                HashArgs t = a;
+                t.count = mid;
+                if (hash_fast_scratch_bytes(t) <= kNoAllocScratchBytes) lo = mid;
+                else hi = mid;
+            }
+            const long long fit = lo;
             set_error("ssh_hash_device_noalloc: %lld series of length %d need %zu bytes of scratch; the fixed "
                       "scratch holds %zu bytes (at most %lld series of this length per call)",
                       (long long)count, m, need, kNoAllocScratchBytes, fit);
@@ -116,6 +119,8 @@ extern "C" ssh_status ssh_hash_device_noalloc(const ssh_index* idx, const float*
         if (e == cudaSuccess) e = hash_fast_cws(a, b, st);
         if (e != cudaSuccess) status = cuda_status(e, "no-alloc hash pipeline");
     }
-    const_cast<ssh_index*>(idx)->host_stats.kernel_launches += g_launches.load() - l0;
+    // the index is shared by concurrent callers: add this call's launches atomically
+    __atomic_fetch_add(&const_cast<ssh_index*>(idx)->host_stats.kernel_launches, (int64_t)(t_launches - l0),
+                       __ATOMIC_RELAXED);
     return status;
 }

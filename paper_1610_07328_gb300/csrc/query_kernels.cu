@@ -799,6 +799,8 @@ size_t lb_rev_smem(int m, int rb, int warps) {
     return ((size_t)((m + 3) & ~3) + (size_t)warps * 4 * mpa) * sizeof(float);
 }
 
+bool lb_rev_fits(int m, int rb) { return lb_rev_smem(m, rb, 1) <= 227 * 1024; }
+
 cudaError_t launch_lb_rev(const PairSet& ps, int m, int rb, float* out, const uint32_t* U, float shrink,
                           const float** pair_mut, unsigned long long* pruned, cudaStream_t st) {
     if (ps.nseg <= 0 || ps.max_seg_pairs <= 0) return cudaSuccess;
@@ -806,8 +808,8 @@ cudaError_t launch_lb_rev(const PairSet& ps, int m, int rb, float* out, const ui
     while (warps > 1 && lb_rev_smem(m, rb, warps) > 200 * 1024) --warps;
     const size_t smem = lb_rev_smem(m, rb, warps);
     const bool mark = U != nullptr;
-    // a series too long for one warp's envelope buffers: the optional pruning pass is
-    // skipped (the survivors all go to DTW, same results); a direct request fails
+    // a series too long for one warp's envelope buffers: callers of the optional pruning
+    // pass check lb_rev_fits first (and count the skip); a direct request fails
     if (smem > 227 * 1024) return mark ? cudaSuccess : cudaErrorInvalidValue;
     const void* fn = mark ? (const void*)lb_rev_kernel<true> : (const void*)lb_rev_kernel<false>;
     cudaError_t e = ensure_dynamic_smem(fn, smem);

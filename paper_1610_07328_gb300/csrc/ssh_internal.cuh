@@ -38,9 +38,15 @@ ssh_status check_device(const ssh_index* idx);
         if (_e != cudaSuccess) return ::ssh::cuda_status(_e, #expr); \
     } while (0)
 
-// Kernel launches made by this library in the calling process (all threads).
+// Kernel launches made by this library in the calling process (all threads),
+// and by the calling thread alone (per-call counts take differences of the
+// latter, so calls on other threads do not inflate them).
 extern std::atomic<long long> g_launches;
-inline void note_launch(int n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+extern thread_local long long t_launches;
+inline void note_launch(int n = 1) {
+    g_launches.fetch_add(n, std::memory_order_relaxed);
+    t_launches += n;
+}
 
 // ------------------------------------------------------------- constants
 
@@ -221,6 +227,8 @@ cudaError_t launch_lb_keogh(const PairSet& ps, const float* upper, const float* 
 // Reversed LB_Keogh (the candidate's envelope, the query's samples). With U (per
 // segment bound bits): clears pair_mut[p] of pairs whose LB * shrink > U and
 // counts them in *pruned; without: writes out[slot].
+// Whether the reversed LB_Keogh pass fits in shared memory at this (m, r_b).
+bool lb_rev_fits(int m, int rb);
 cudaError_t launch_lb_rev(const PairSet& ps, int m, int rb, float* out, const uint32_t* U, float shrink,
                           const float** pair_mut, unsigned long long* pruned, cudaStream_t st);
 

@@ -8,6 +8,8 @@ array and starts from whatever the previous call left there.
 This file is named to be collected last, so a run that stops at the first
 failure has already run every other test.
 """
+import re
+
 import numpy as np
 import pytest
 
@@ -75,3 +77,12 @@ def test_noalloc_rejects_counts_beyond_the_fixed_scratch():
         assert e.value.status == binding.SSH_EINVAL
         assert "scratch" in str(e.value) and "at most" in str(e.value)
         assert (keys.cpu().numpy() == 0).all()  # nothing ran
+        # the limit the message reports is exact: that many series fit, one more does not
+        fit = int(re.search(r"at most (\d+) series", str(e.value)).group(1))
+        assert 0 < fit < N
+        binding.ssh_hash_device_noalloc(idx.handle, d_x[:fit], m, fit, d_keys=keys[:, :fit].contiguous())
+        torch.cuda.synchronize()
+        with pytest.raises(binding.SSHError) as e2:
+            binding.ssh_hash_device_noalloc(idx.handle, d_x[:fit + 1], m, fit + 1,
+                                            d_keys=keys[:, :fit + 1].contiguous())
+        assert e2.value.status == binding.SSH_EINVAL
