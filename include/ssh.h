@@ -226,9 +226,22 @@ typedef struct ssh_server_stats {
     double mean_batch;          /* queries per batch */
     int64_t inserts_submitted, inserts_applied, insert_errors, insert_batches;
     double insert_latency_ms_sum; /* submit-to-applied time summed over insert calls */
+    int64_t max_inflight_device;  /* most batches executing on the GPU at once (a launch counts the
+                                     other slots whose batch had not finished on the device) */
+    int64_t deferred;           /* queries put back in the queue because their batch's candidates
+                                   would have grown the pair buffers past the free-memory reserve */
+    int64_t refused;            /* queries answered SSH_EBUSY: alone in a batch, their candidates
+                                   still needed more pair memory than the reserve admits */
 } ssh_server_stats;
+/* reserve_bytes: device memory kept free, both when slots are created and when a
+ * slot's candidate (pair) buffers grow; a batch that would breach it is split
+ * (its queries requeued, later batches admitted at half the size) and a single
+ * query that still does not fit completes with SSH_EBUSY. */
 ssh_status ssh_server_create(ssh_index* const* handles, int nh, int k, int max_batch, int max_slots,
                              int64_t reserve_bytes, ssh_server** out);
+/* ssh_server_create with the first pair capacity of every slot (0: the batch plan default). */
+ssh_status ssh_server_create_ex(ssh_index* const* handles, int nh, int k, int max_batch, int max_slots,
+                                int64_t reserve_bytes, int64_t max_pairs, ssh_server** out);
 double ssh_server_now(const ssh_server* s);
 ssh_status ssh_server_submit(ssh_server* s, const float* queries, const int32_t* lengths, int64_t n,
                              const double* arrival_s, int64_t* tickets);

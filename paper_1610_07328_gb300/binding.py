@@ -54,7 +54,8 @@ class ssh_server_stats(ctypes.Structure):
                 ("errors", ctypes.c_int64), ("batches", ctypes.c_int64), ("max_inflight", ctypes.c_int64),
                 ("mean_batch", ctypes.c_double), ("inserts_submitted", ctypes.c_int64),
                 ("inserts_applied", ctypes.c_int64), ("insert_errors", ctypes.c_int64),
-                ("insert_batches", ctypes.c_int64), ("insert_latency_ms_sum", ctypes.c_double)]
+                ("insert_batches", ctypes.c_int64), ("insert_latency_ms_sum", ctypes.c_double),
+                ("max_inflight_device", ctypes.c_int64), ("deferred", ctypes.c_int64), ("refused", ctypes.c_int64)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
@@ -87,6 +88,8 @@ _SIGS = {
     "ssh_batch_destroy": (None, [_P]),
     "ssh_server_create": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int64,
                                          ctypes.POINTER(_P)]),
+    "ssh_server_create_ex": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                            ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(_P)]),
     "ssh_server_now": (ctypes.c_double, [_P]),
     "ssh_server_submit": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, _P, _P]),
     "ssh_server_insert": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64]),
@@ -300,14 +303,15 @@ class SSHBatch:
 class SSHServer:
     """Owning wrapper around an ssh_server (serving loop with continuous batching)."""
 
-    def __init__(self, indexes, k: int, max_batch: int = 256, max_slots: int = 4, reserve_bytes: int = 1 << 30):
+    def __init__(self, indexes, k: int, max_batch: int = 256, max_slots: int = 4, reserve_bytes: int = 1 << 30,
+                 max_pairs: int = 0):
         self.k = k
         self.indexes = list(indexes)  # kept alive for the server's lifetime
         arr = (ctypes.c_void_p * len(self.indexes))(*[ix.handle.value if isinstance(ix.handle, ctypes.c_void_p)
                                                        else ix.handle for ix in self.indexes])
         out = _P()
-        _check(load().ssh_server_create(ctypes.cast(arr, ctypes.c_void_p), len(self.indexes), k, max_batch, max_slots,
-                                        reserve_bytes, ctypes.byref(out)))
+        _check(load().ssh_server_create_ex(ctypes.cast(arr, ctypes.c_void_p), len(self.indexes), k, max_batch,
+                                           max_slots, reserve_bytes, max_pairs, ctypes.byref(out)))
         self.handle = out
 
     def now(self) -> float:

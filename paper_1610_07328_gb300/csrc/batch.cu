@@ -659,12 +659,23 @@ bool batch_done(ssh_batch* b) { return cudaEventQuery(b->ev_done) != cudaErrorNo
 // Wait for the launched batch; a batch whose candidates overflowed the pair
 // buffers is run again with grown buffers. Captures the graph after a
 // plan's first (direct) batch. Results: batch_outputs, rows in caller order.
-ssh_status batch_finish(ssh_batch* b) {
+ssh_status batch_finish(ssh_batch* b, int64_t reserve_bytes) {
     SSH_CUDA(cudaEventSynchronize(b->ev_done));
     for (int attempt = 0; b->h_status->overflow; ++attempt) {
         if (attempt == 1) return fail_status(SSH_ENOMEM, "batch candidates exceed the pair buffers");
         const int64_t need = (int64_t)b->h_status->pairs;
-        SSH_TRY(alloc_pairs(b, need + need / 4 + 1024));
+        const int64_t cap = need + need / 4 + 1024;
+        if (reserve_bytes >= 0) {
+            // admission by free memory: the old buffers are freed before the new ones are made
+            size_t free_b = 0, total_b = 0;
+            SSH_CUDA(cudaMemGetInfo(&free_b, &total_b));
+            const int64_t grow = (cap - b->pcap) * kBatchPairBytes;
+            if ((int64_t)free_b - grow < reserve_bytes)
+                return fail_status(SSH_EBUSY, "%lld candidate pairs need %lld more bytes of pair buffers; %lld free, "
+                                   "%lld reserved", (long long)need, (long long)grow, (long long)free_b,
+                                   (long long)reserve_bytes);
+        }
+        SSH_TRY(alloc_pairs(b, cap));
         if (b->exec) cudaGraphExecDestroy(b->exec);
         b->exec = nullptr;
         SSH_TRY(batch_launch(b));
@@ -714,7 +725,7 @@ size_t batch_device_bytes(const ssh_batch* b) {
     const size_t Q = (size_t)b->qcap;
     return plan_view(nullptr, b->qcap, C).bytes + C * sizeof(ClassDev) + (size_t)b->Lmax * Q * 8 +
            Q * (size_t)b->max_words * 4 + Q * 8 * 6 + Q * (size_t)b->max_m * 8 + Q * 4 * 2 + Q * 8 +
-           Q * (size_t)b->k * 12 + Q * 4 + (size_t)b->pcap * 44;
+           Q * (size_t)b->k * 12 + Q * 4 + (size_t)b->pcap * kBatchPairBytes;
 }
 
 }  // namespace ssh

@@ -810,13 +810,13 @@ ssh_status query_group(ssh_index* idx, SubIndex& s, const std::vector<const floa
         SSH_TRY(sc.get(&fcount, nq));
         SSH_TRY(sc.get(&fbegin, nq + 1));
         SSH_TRY(sc.get(&cursor, nq));
-        SSH_TRY(sc.get(&ftotal, 3));
+        SSH_TRY(sc.get(&ftotal, 5));  // pairs of the two passes, reversed-LB prunes, DTW blocks of the two passes
         SSH_TRY(sc.get(&fb, C));
         SSH_TRY(sc.get(&fslot, C));
         unsigned long long* h_tot = idx->h_pinned;
-        h_tot[0] = h_tot[1] = h_tot[2] = 0;
+        h_tot[0] = h_tot[1] = h_tot[2] = h_tot[3] = h_tot[4] = 0;
         const bool rev = idx->lb_cascade == 2;
-        SSH_CUDA(cudaMemsetAsync(ftotal + 2, 0, sizeof(unsigned long long), st));
+        SSH_CUDA(cudaMemsetAsync(ftotal + 2, 0, 3 * sizeof(unsigned long long), st));
         ssh_status fst = SSH_OK;
         size_t tslot[2] = {SIZE_MAX, SIZE_MAX};  // the two DTW timings: cells are known after the sync
         for (int mode = 0; mode < 2 && fst == SSH_OK; ++mode) {
@@ -828,6 +828,7 @@ ssh_status query_group(ssh_index* idx, SubIndex& s, const std::vector<const floa
             if (e == cudaSuccess) e = launch_filter(f, st);
             // every filtered segment is no longer than its candidate segment: size the DTW grid by max_c
             PairSet sub{fbegin, nq, d_qptr, fb, fslot, max_c};
+            sub.blocks_done = ftotal + 3 + mode;  // the cells actually computed (abandoned pairs stop early)
             if (mode == 1) {  // survivors: stop at the bound U of the seeds' k-th distance
                 sub.abandon = U;
                 sub.abandon_shrink = shrink;
@@ -850,7 +851,7 @@ ssh_status query_group(ssh_index* idx, SubIndex& s, const std::vector<const floa
         }
         if (fst == SSH_OK) {
             // read at the end of the query with the results
-            cudaError_t e = cudaMemcpyAsync(h_tot, ftotal, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
+            cudaError_t e = cudaMemcpyAsync(h_tot, ftotal, 5 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
             if (e != cudaSuccess) fst = cuda_status(e, "rerank counts");
         }
         if (fst != SSH_OK) {
@@ -879,10 +880,11 @@ ssh_status query_group(ssh_index* idx, SubIndex& s, const std::vector<const floa
         const unsigned long long rev = pruned_counts[2];
         idx->host_stats.dtw_computed += (int64_t)(pruned_counts[0] + pruned_counts[1] - rev);
         idx->host_stats.lb2_pruned += (int64_t)rev;
+        // DTW units: the cells computed, a pair's blocks of wavefront steps times its cells per block
+        const double cells_per_block = dtw_cells(m, rb) / (double)dtw_plan_blocks(m, rb, dplan);
         for (int mode = 0; mode < 2; ++mode)
             if (pruned_slots[mode] != SIZE_MAX)
-                idx->pending[pruned_slots[mode]].units =
-                    (double)(pruned_counts[mode] - (mode == 1 ? rev : 0ull)) * dtw_cells(m, rb);
+                idx->pending[pruned_slots[mode]].units = (double)pruned_counts[3 + mode] * cells_per_block;
     }
     idx->host_stats.lb_pruned = idx->host_stats.candidates - idx->host_stats.dtw_computed;
     SSH_CUDA(e);

@@ -474,6 +474,7 @@ __global__ void __launch_bounds__(256) dtw_wave_kernel(PairSet ps, int m, int rb
                         if (t == p_f) res = D[t];
                 }
                 if (g == g_f) out[ps.pair_slot ? ps.pair_slot[p] : p] = res;
+                if (ps.blocks_done && g == 0) atomicAdd(ps.blocks_done, (unsigned long long)lblk);
             }
             need = lane_in_group && (fin || ab);
         }
@@ -823,6 +824,12 @@ cudaError_t launch_lb_rev(const PairSet& ps, int m, int rb, float* out, const ui
         lb_rev_kernel<false><<<grid, warps * 32, smem, st>>>(ps, m, rb, out, U, shrink, pair_mut, pruned);
     note_launch();
     return cudaGetLastError();
+}
+
+int64_t dtw_plan_blocks(int m, int rb, const DtwPlan& pl) {
+    const int U = pl.S / 2 + 1;
+    const int s_end = (2 * (m - 1) + rb) >> 1;
+    return (s_end + U) / U;
 }
 
 cudaError_t launch_dtw_plan(const PairSet& ps, int m, int rb, const DtwPlan& pl, float* out, cudaStream_t st) {

@@ -7,7 +7,12 @@
 // queries are waiting it packs up to max_batch of them into the slot, copies
 // them to the device and launches the slot's batch without waiting, so the
 // batches of several slots overlap on the GPU while new arrivals queue up.
-// Completed slots hand their rows back to the requests. Inserts are applied
+// Completed slots hand their rows back to the requests. Candidate buffers are
+// admitted by free device memory: a batch whose candidates outgrow its slot's
+// pair buffers grows them only while reserve_bytes of device memory stay free;
+// otherwise its queries go back to the front of the queue and later batches
+// are admitted at half the size (doubling again after each batch that fits),
+// and a single query that still does not fit is answered SSH_EBUSY. Inserts are applied
 // between batches: the worker stops admitting queries, lets the slots drain,
 // appends the waiting series to the indexes (Algorithm 1) and resumes; the
 // plans then rewrite their table descriptors in place. A request's latency is
@@ -77,6 +82,8 @@ struct ssh_server {
     std::vector<ssh_index*> handles;
     std::vector<int32_t> known_lengths;
     int k = 0, max_batch = 0, max_len = 0;
+    int batch_cap = 0;          // queries admitted per batch now (max_batch, halved by refused growth)
+    int64_t reserve_bytes = 0;  // device memory kept free when pair buffers grow
     std::vector<Slot> slots;
     Clock::time_point t0;
     std::mutex mu;
@@ -103,8 +110,19 @@ bool length_known(const ssh_server* s, int32_t m) {
 
 // Deliver a finished slot's rows to its requests (called by the worker, lock not held).
 void complete_slot(ssh_server* s, Slot& sl) {
-    ssh_status status = batch_finish(sl.b);
+    ssh_status status = batch_finish(sl.b, s->reserve_bytes);
     const int64_t n = (int64_t)sl.reqs.size();
+    if (status == SSH_EBUSY && n > 1) {
+        // memory admission refused the growth: requeue the batch in order, admit smaller ones
+        std::lock_guard<std::mutex> lock(s->mu);
+        for (int64_t i = n - 1; i >= 0; --i) s->pending.push_front(std::move(sl.reqs[i]));
+        s->batch_cap = std::max<int>(1, (int)(n / 2));
+        s->st.deferred += n;
+        sl.reqs.clear();
+        sl.running = false;
+        return;
+    }
+    if (status == SSH_OK) s->batch_cap = std::min(s->max_batch, 2 * s->batch_cap);
     if (status == SSH_OK) {
         const int64_t* d_ids;
         const float* d_dists;
@@ -134,7 +152,10 @@ void complete_slot(ssh_server* s, Slot& sl) {
         }
         s->st.queries_done += n;
         s->st.batches += 1;
-        if (status != SSH_OK) {
+        if (status == SSH_EBUSY) {
+            s->st.refused += n;  // one query whose candidates do not fit the admitted memory
+            s->worker_error = ssh_last_error();
+        } else if (status != SSH_OK) {
             s->st.errors += n;
             s->worker_error = ssh_last_error();
         }
@@ -202,7 +223,7 @@ void worker_loop(ssh_server* s) {
             // 3. admit waiting queries into free slots
             for (Slot& sl : s->slots) {
                 if (sl.running || s->pending.empty()) continue;
-                const int64_t n = std::min<int64_t>((int64_t)s->pending.size(), s->max_batch);
+                const int64_t n = std::min<int64_t>((int64_t)s->pending.size(), s->batch_cap);
                 sl.reqs.clear();
                 sl.lengths.clear();
                 int64_t off = 0;
@@ -221,6 +242,9 @@ void worker_loop(ssh_server* s) {
                                                 batch_stream(sl.b));
                 if (e != cudaSuccess) status = cuda_status(e, "server query copy");
                 if (status == SSH_OK) status = batch_prepare(sl.b, sl.d_q, sl.lengths.data(), n);
+                int on_device = 0;  // batches of other slots still executing on the GPU
+                for (Slot& o : s->slots)
+                    if (&o != &sl && o.running && !batch_done(o.b)) ++on_device;
                 if (status == SSH_OK) status = batch_launch(sl.b);
                 sl.running = true;
                 if (status != SSH_OK) {
@@ -244,6 +268,8 @@ void worker_loop(ssh_server* s) {
                 int r2 = 0;
                 for (Slot& q : s->slots) r2 += q.running;
                 s->st.max_inflight = std::max<int64_t>(s->st.max_inflight, r2);
+                if (sl.running)
+                    s->st.max_inflight_device = std::max<int64_t>(s->st.max_inflight_device, on_device + 1);
             }
         }
         // 4. idle: wait briefly for arrivals or completions
@@ -265,7 +291,13 @@ extern "C" {
 
 ssh_status ssh_server_create(ssh_index* const* handles, int nh, int k, int max_batch, int max_slots,
                              int64_t reserve_bytes, ssh_server** out) {
+    return ssh_server_create_ex(handles, nh, k, max_batch, max_slots, reserve_bytes, 0, out);
+}
+
+ssh_status ssh_server_create_ex(ssh_index* const* handles, int nh, int k, int max_batch, int max_slots,
+                                int64_t reserve_bytes, int64_t max_pairs, ssh_server** out) {
     if (!out) return fail_status(SSH_EINVAL, "out is NULL");
+    if (reserve_bytes < 0 || max_pairs < 0) return fail_status(SSH_EINVAL, "reserve_bytes and max_pairs must be >= 0");
     *out = nullptr;
     if (!handles || nh < 1) return fail_status(SSH_EINVAL, "no indexes");
     if (max_batch < 1 || max_batch > 65535) return fail_status(SSH_EINVAL, "max_batch outside [1, 65535]");
@@ -279,6 +311,8 @@ ssh_status ssh_server_create(ssh_index* const* handles, int nh, int k, int max_b
     s->handles.assign(handles, handles + nh);
     s->k = k;
     s->max_batch = max_batch;
+    s->batch_cap = max_batch;
+    s->reserve_bytes = reserve_bytes;
     s->t0 = Clock::now();
     for (ssh_index* h : s->handles)
         for (auto& kv : h->subs)
@@ -295,7 +329,7 @@ ssh_status ssh_server_create(ssh_index* const* handles, int nh, int k, int max_b
             (int64_t)free_b - (int64_t)batch_device_bytes(s->slots[0].b) < reserve_bytes)
             break;
         Slot sl;
-        status = ssh_batch_create(handles, nh, max_batch, k, 0, &sl.b);
+        status = ssh_batch_create(handles, nh, max_batch, k, max_pairs, &sl.b);
         if (status != SSH_OK) {
             if (i > 0) status = SSH_OK;  // keep the slots made so far
             break;

@@ -217,6 +217,9 @@ struct PairSet {
     // warp's pairs once all of them certainly exceed it (distance reported +inf)
     const uint32_t* abandon = nullptr;
     float abandon_shrink = 1.f; // relative FP32 rounding margin of a path cost (1 - 4 (m + 3) 2^-24)
+    // optional device counter: every pair adds the blocks of wavefront steps it ran
+    // (all of them when it finishes, fewer when it is abandoned); see dtw_plan_blocks
+    unsigned long long* blocks_done = nullptr;
 };
 
 cudaError_t launch_envelope(const float* const* seg_a, int64_t nseg, int m, int rb, float* upper, float* lower,
@@ -240,6 +243,9 @@ DtwPlan dtw_plan(int m, int rb);
 // counts (the first call for a (m, rb) runs the timing on `st` and waits for it).
 DtwPlan dtw_tuned_plan(int m, int rb, cudaStream_t st);
 cudaError_t launch_dtw(const PairSet& ps, int m, int rb, float* out, cudaStream_t st);
+// Blocks of wavefront steps a complete DTW of one pair takes under a plan: the
+// cells a pair computed are blocks_done / dtw_plan_blocks of its m(2r+1) - r(r+1).
+int64_t dtw_plan_blocks(int m, int rb, const DtwPlan& pl);
 cudaError_t launch_dtw_plan(const PairSet& ps, int m, int rb, const DtwPlan& pl, float* out, cudaStream_t st);
 
 // Raise (never lower) a kernel's dynamic shared memory limit on the current
@@ -298,7 +304,13 @@ cudaError_t launch_topk_output(const TopkOut& o, const uint64_t* keys, const int
 ssh_status batch_prepare(ssh_batch* b, const float* d_queries, const int32_t* lengths, int64_t nq);
 ssh_status batch_launch(ssh_batch* b);
 bool batch_done(ssh_batch* b);
-ssh_status batch_finish(ssh_batch* b);
+// Wait for the launched batch; on pair-buffer overflow grow the buffers and run
+// it again. reserve_bytes >= 0: grow only while that much device memory stays
+// free after the growth, else return SSH_EBUSY (nothing ranked; the plan stays
+// valid for smaller batches). reserve_bytes < 0: grow unconditionally.
+ssh_status batch_finish(ssh_batch* b, int64_t reserve_bytes = -1);
+// Device bytes of one candidate pair in a plan's pair buffers.
+constexpr int64_t kBatchPairBytes = 44;
 ssh_status batch_refresh(ssh_batch* b);
 void batch_outputs(const ssh_batch* b, const int64_t** ids, const float** dists, const int32_t** which);
 cudaStream_t batch_stream(const ssh_batch* b);

@@ -48,6 +48,10 @@ def test_server_rows_are_the_same_alone_and_in_a_mix():
             t0 = srv.submit(q0, np.array([256], np.int32))
             ids0, d0, which0, lat0 = srv.wait(t0[0])
             assert which0 == LENS.index(256) and lat0 > 0
+            # warm-up: every slot runs its first batch directly and captures its graph
+            wq, _ = synth.perturbed_queries(dbs[512], 48, seed=98)
+            for t in srv.submit(wq, np.full(48, 512, np.int32)):
+                srv.wait(t)
             # a mix of 150 queries of all lengths in three waves, q0 at a random place of the second
             qs, ls = [], []
             for t in range(150):
@@ -78,7 +82,11 @@ def test_server_rows_are_the_same_alone_and_in_a_mix():
             st = srv.stats()
             assert st["queries_done"] == 152 and st["errors"] == 0
             assert st["batches"] >= 10 and 1.0 <= st["mean_batch"] <= 16.0
-            assert st["slots"] >= 1 and st["max_inflight"] >= 1
+            assert st["slots"] == 3 and st["max_inflight"] >= 2
+            # continuous batching: a batch was launched while another slot's batch was still
+            # executing on the GPU, and every row above equals its row alone
+            assert st["max_inflight_device"] >= 2, st
+            assert st["deferred"] == 0 and st["refused"] == 0
     finally:
         for ix in idxs:
             ix.close()
@@ -107,3 +115,54 @@ def test_server_inserts_become_visible_and_unknown_lengths_are_refused():
     finally:
         for ix in idxs:
             ix.close()
+
+
+def test_server_admits_candidate_buffers_by_free_memory():
+    """Pair buffers grow only while the reserve of free device memory holds. With a reserve of
+    the whole device no growth is admitted: a batch whose candidates overflow its slot's 64
+    pairs is requeued and split, a single query that still does not fit is answered SSH_EBUSY
+    (never SSH_ENOMEM), and queries whose candidates fit are served in smaller batches with the
+    same rows as the group path. Without a reserve the same queries are served by growing."""
+    from paper_1610_07328_gb300 import binding
+    many = synth.random_walk(256, 128, seed=61)   # n = 8, one hash per table: most rows are candidates
+    few = synth.random_walk(20, 256, seed=62)     # at most 20 candidates per query
+    ix_many = binding.SSHIndex(16, 3, 8, 1, 8, 0.05, 0)
+    ix_few = binding.SSHIndex(32, 3, 15, 4, 25, 0.05, 0)
+    k = 4
+    try:
+        ix_many.add(many)
+        ix_few.add(few)
+        idxs = [ix_many, ix_few]
+        q_many, _ = synth.perturbed_queries(many, 8, seed=63)
+        q_few, _ = synth.perturbed_queries(few, 4, seed=64)
+        total = torch.cuda.mem_get_info()[1]
+        with binding.SSHServer(idxs, k=k, max_batch=8, max_slots=2, reserve_bytes=total, max_pairs=64) as srv:
+            assert srv.stats()["slots"] == 1  # the reserve admits no second slot either
+            tickets = srv.submit(q_many, np.full(8, 128, np.int32))
+            srv.flush(60.0)
+            got = {}
+            while len(got) < 8:
+                tk, _, _, _, status = srv.collect(64, 1.0)
+                got.update(zip(tk.tolist(), status.tolist()))
+            assert sorted(got) == sorted(tickets.tolist())
+            assert all(v == binding.SSH_EBUSY for v in got.values()), got
+            st = srv.stats()
+            assert st["refused"] == 8 and st["errors"] == 0 and st["deferred"] >= 8
+            # queries whose candidates fit the admitted buffers are served (in smaller batches)
+            t_few = srv.submit(q_few, np.full(4, 256, np.int32))
+            rows = [srv.wait(t, 30.0) for t in t_few]
+            for i, q in enumerate(q_few):
+                gi, gd = _group_rows(binding, idxs, q, 256, k)
+                assert np.array_equal(rows[i][0], gi) and np.array_equal(rows[i][1], gd)
+                assert rows[i][2] == 1
+        with binding.SSHServer(idxs, k=k, max_batch=8, max_slots=2, reserve_bytes=0, max_pairs=64) as srv:
+            t_many = srv.submit(q_many, np.full(8, 128, np.int32))
+            rows = [srv.wait(t, 30.0) for t in t_many]
+            for i, q in enumerate(q_many):
+                gi, gd = _group_rows(binding, idxs, q, 128, k)
+                assert np.array_equal(rows[i][0], gi) and np.array_equal(rows[i][1], gd)
+            st = srv.stats()
+            assert st["deferred"] == 0 and st["refused"] == 0 and st["errors"] == 0
+    finally:
+        ix_many.close()
+        ix_few.close()
