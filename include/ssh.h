@@ -392,6 +392,16 @@ ssh_status ssh_hash_device_noalloc(const ssh_index* idx, const float* d_series, 
 ssh_status ssh_dtw_device(const float* d_a, const int64_t* d_a_idx, const float* d_b, const int64_t* d_b_idx,
                           int64_t npairs, int32_t m, int32_t rb, float* d_out, void* stream);
 
+/* ssh_dtw_device with an explicit tiling instead of the one the library's autotuner
+ * picks for (m, rb): S band slots per lane (8, 14 or 26) and the kernel variant
+ * (0: paired square-adds; 1: paired differences too, S = 14 or 26). Every tiling
+ * computes each cell from the same three values in the same order, so all give
+ * the same distances bit for bit. SSH_ENOTSUP for a tiling that is not compiled
+ * or needs more than 32 lanes per pair at this radius. */
+ssh_status ssh_dtw_device_tiled(const float* d_a, const int64_t* d_a_idx, const float* d_b, const int64_t* d_b_idx,
+                                int64_t npairs, int32_t m, int32_t rb, int32_t S, int32_t variant, float* d_out,
+                                void* stream);
+
 /* Sec. 3 LB_Keogh for `npairs` pairs: d_out[p] = LB_Keogh of row d_b_idx[p] of d_b
  * against the envelope (radius rb) of row d_a_idx[p] of d_a. */
 ssh_status ssh_lb_keogh_device(const float* d_a, const int64_t* d_a_idx, const float* d_b, const int64_t* d_b_idx,

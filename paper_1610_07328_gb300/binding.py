@@ -106,6 +106,8 @@ _SIGS = {
     "ssh_hash_device": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int64, _P] + [_P] * 7),
     "ssh_hash_device_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int64, _P] + [_P] * 7),
     "ssh_dtw_device": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _P, _P]),
+    "ssh_dtw_device_tiled": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                            ctypes.c_int32, ctypes.c_int32, _P, _P]),
     "ssh_lb_keogh_device": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _P, _P]),
     "ssh_lb_bound_device": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                            ctypes.c_int32, _P, _P]),
@@ -421,6 +423,13 @@ def ssh_hash_device_noalloc(h, d_series, m: int, count: int, d_bits=None, d_sh_i
 def ssh_dtw_device(d_a, d_a_idx, d_b, d_b_idx, m: int, rb: int, d_out, stream=None) -> None:
     _check(load().ssh_dtw_device(_dev_ptr(d_a), _dev_ptr(d_a_idx), _dev_ptr(d_b), _dev_ptr(d_b_idx),
                                  d_a_idx.numel(), m, rb, _dev_ptr(d_out), _stream(stream)))
+
+
+def ssh_dtw_device_tiled(d_a, d_a_idx, d_b, d_b_idx, m: int, rb: int, S: int, variant: int, d_out,
+                         stream=None) -> None:
+    """ssh_dtw_device with the tiling (S slots per lane, kernel variant) given explicitly."""
+    _check(load().ssh_dtw_device_tiled(_dev_ptr(d_a), _dev_ptr(d_a_idx), _dev_ptr(d_b), _dev_ptr(d_b_idx),
+                                       d_a_idx.numel(), m, rb, S, variant, _dev_ptr(d_out), _stream(stream)))
 
 
 def ssh_lb_keogh_device(d_a, d_a_idx, d_b, d_b_idx, m: int, rb: int, d_out, stream=None) -> None:

@@ -227,7 +227,7 @@ using namespace ssh;
 struct ssh_batch {
     struct HostClass {
         int h = 0, m = 0, rb = 0, L = 0;
-        DtwPlan plan{0, 0, 0};
+        DtwPlan plan{0, 0, 0, 0};
         HashArgs a;
     };
     std::vector<ssh_index*> handles;

@@ -778,7 +778,7 @@ ssh_status query_group(ssh_index* idx, SubIndex& s, const std::vector<const floa
     const int rb = s.rb;
     unsigned long long* pruned_counts = nullptr;  // pinned: DTW pairs of the seed and survivor passes
     size_t pruned_slots[2] = {SIZE_MAX, SIZE_MAX};
-    const DtwPlan dplan = (C > 0) ? dtw_tuned_plan(m, rb, st) : DtwPlan{0, 0, 0};
+    const DtwPlan dplan = (C > 0) ? dtw_tuned_plan(m, rb, st) : DtwPlan{0, 0, 0, 0};
     if (C > 0 && !idx->lb_prune) {
         {
             TimedRegion tr(idx, st, "query.dtw", (double)C * dtw_cells(m, rb));
@@ -1555,7 +1555,8 @@ ssh_status ssh_hash_device(const ssh_index* idx, const float* d_series, int32_t 
 
 // lb: -1 DTW, 0 LB_Keogh, 1 LB_Keogh with the LB_Kim endpoints, 2 reversed LB_Keogh
 static ssh_status pairwise(const float* d_a, const int64_t* d_a_idx, const float* d_b, const int64_t* d_b_idx,
-                           int64_t npairs, int32_t m, int32_t rb, float* d_out, cudaStream_t st, int lb) {
+                           int64_t npairs, int32_t m, int32_t rb, float* d_out, cudaStream_t st, int lb,
+                           const DtwPlan* forced = nullptr) {
     if (npairs < 0 || m < 1 || rb < 0 || rb >= m || (npairs > 0 && (!d_a || !d_a_idx || !d_b || !d_b_idx || !d_out)))
         return fail(SSH_EINVAL, "bad arguments");
     if (npairs == 0) return SSH_OK;
@@ -1605,7 +1606,7 @@ static ssh_status pairwise(const float* d_a, const int64_t* d_a_idx, const float
     } else if (lb == 2) {
         SSH_CUDA(launch_lb_rev(ps, m, rb, d_out, nullptr, 1.f, nullptr, nullptr, st));
     } else {
-        cudaError_t e = launch_dtw_plan(ps, m, rb, dtw_tuned_plan(m, rb, st), d_out, st);
+        cudaError_t e = launch_dtw_plan(ps, m, rb, forced ? *forced : dtw_tuned_plan(m, rb, st), d_out, st);
         if (e == cudaErrorNotSupported) return fail(SSH_ENOTSUP, "DTW radius %d is wider than the compiled DTW tilings cover", rb);
         SSH_CUDA(e);
     }
@@ -1616,6 +1617,17 @@ static ssh_status pairwise(const float* d_a, const int64_t* d_a_idx, const float
 ssh_status ssh_dtw_device(const float* d_a, const int64_t* d_a_idx, const float* d_b, const int64_t* d_b_idx,
                           int64_t npairs, int32_t m, int32_t rb, float* d_out, void* stream) {
     return pairwise(d_a, d_a_idx, d_b, d_b_idx, npairs, m, rb, d_out, (cudaStream_t)stream, -1);
+}
+
+ssh_status ssh_dtw_device_tiled(const float* d_a, const int64_t* d_a_idx, const float* d_b, const int64_t* d_b_idx,
+                                int64_t npairs, int32_t m, int32_t rb, int32_t S, int32_t variant, float* d_out,
+                                void* stream) {
+    if (rb < 0 || rb >= m) return fail(SSH_EINVAL, "bad arguments");
+    const DtwPlan pl = dtw_plan_for(rb, S, variant);
+    if (pl.S == 0)
+        return fail(SSH_ENOTSUP, "no compiled DTW tiling with S = %d, variant %d at radius %d", (int)S, (int)variant,
+                    (int)rb);
+    return pairwise(d_a, d_a_idx, d_b, d_b_idx, npairs, m, rb, d_out, (cudaStream_t)stream, -1, &pl);
 }
 
 ssh_status ssh_lb_keogh_device(const float* d_a, const int64_t* d_a_idx, const float* d_b, const int64_t* d_b_idx,

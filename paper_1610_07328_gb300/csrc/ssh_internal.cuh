@@ -235,10 +235,16 @@ bool lb_rev_fits(int m, int rb);
 cudaError_t launch_lb_rev(const PairSet& ps, int m, int rb, float* out, const uint32_t* U, float shrink,
                           const float** pair_mut, unsigned long long* pruned, cudaStream_t st);
 
+// A DTW tiling: S band slots per lane, G lanes per pair, the slot forced to +inf,
+// and the kernel variant (0: paired FMAs; 1: paired differences and FMAs, S = 2 mod 4).
 struct DtwPlan {
     int S, G, pmask;
+    int variant = 0;
 };
 DtwPlan dtw_plan(int m, int rb);
+bool dtw_tiling_compiled(int S, int variant);
+// The plan of slot count S and variant at radius rb (S == 0: not compiled or too wide).
+DtwPlan dtw_plan_for(int rb, int S, int variant);
 // The tiling used for (m, rb): timed once per process over the candidate slot
 // counts (the first call for a (m, rb) runs the timing on `st` and waits for it).
 DtwPlan dtw_tuned_plan(int m, int rb, cudaStream_t st);

@@ -198,6 +198,40 @@ def test_dtw_parity(m, rb):
     np.testing.assert_allclose(got, want, rtol=RTOL, atol=0)
 
 
+TILINGS = [(8, 0), (14, 0), (26, 0), (14, 1), (26, 1)]
+
+
+@pytest.mark.parametrize("m,rb", [(128, 6), (512, 25), (1024, 102), (2048, 102), (1024, 51), (64, 63),
+                                  (100, 0), (37, 5), (300, 140), (13, 1)])
+def test_dtw_every_tiling_matches_the_oracle_and_each_other(m, rb):
+    """Every compiled tiling (slots per lane S, kernel variant) computes each cell from the same
+    three values with the same operations, so all give identical distances, within 1e-5 of the
+    oracle; a tiling that needs more than 32 lanes per pair is refused."""
+    b = _binding()
+    A = synth.random_walk(6, m, seed=m + 3)
+    B = synth.random_walk(30, m, seed=m + 4)
+    ai, bi = _pairs(len(A), len(B), 90, seed=m + 5)
+    want = np.array([oracle.dtw(A[i], B[j], rb) for i, j in zip(ai, bi)])
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    dai, dbi = torch.from_numpy(ai).cuda(), torch.from_numpy(bi).cuda()
+    results = {}
+    for S, variant in TILINGS:
+        out = torch.full((len(ai),), -1.0, dtype=torch.float32, device="cuda")
+        if (2 * rb + 2 + S - 1) // S > 32:
+            with pytest.raises(b.SSHError) as e:
+                b.ssh_dtw_device_tiled(dA, dai, dB, dbi, m, rb, S, variant, out)
+            assert e.value.status == b.SSH_ENOTSUP
+            continue
+        b.ssh_dtw_device_tiled(dA, dai, dB, dbi, m, rb, S, variant, out)
+        results[(S, variant)] = out.cpu().numpy()
+        np.testing.assert_allclose(results[(S, variant)], want, rtol=RTOL, atol=0, err_msg=str((S, variant)))
+    first = next(iter(results.values()))
+    for key, got in results.items():
+        assert np.array_equal(got, first), key
+    with pytest.raises(b.SSHError):
+        b.ssh_dtw_device_tiled(dA, dai, dB, dbi, m, rb, 10, 1, torch.empty(len(ai), device="cuda"))
+
+
 def test_dtw_identity_and_band0():
     b = _binding()
     m = 512
