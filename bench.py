@@ -153,6 +153,18 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
+def host_rss_bytes():
+    """Resident set size of this process (Linux /proc), 0 where unavailable."""
+    try:
+        with open("/proc/self/status") as f:
+            for line in f:
+                if line.startswith("VmRSS:"):
+                    return int(line.split()[1]) * 1024
+    except OSError:
+        pass
+    return 0
+
+
 def h2d_copy_gbs(torch, h_src, d_dst):
     """Host-to-device copy bandwidth from pinned memory: one copy of the whole series buffer,
     timed with CUDA events on the current stream, best of 3 after one warm-up."""
@@ -1110,7 +1122,12 @@ def run_gpu(args, w):
     d_dists = torch.empty((nq, k), dtype=torch.float32, device=dev)
     gen_s = time.perf_counter() - t_gen
 
+    rss0 = host_rss_bytes()
+    t_create = time.perf_counter()
     idx = binding.SSHIndex(w["W"], w["delta"], w["n"], w["K"], w["L"], w["band"], w["seed"])
+    torch.cuda.synchronize()
+    create_s = time.perf_counter() - t_create
+    create_rss = host_rss_bytes() - rss0
     stream = torch.cuda.current_stream()
 
     lengths = np.full(N, m, np.int32)
@@ -1301,6 +1318,9 @@ def run_gpu(args, w):
                 "api": "ssh_index_clear + ssh_index_add(host) + ssh_query(host)"},
         "clocks": clocks,
         "setup_s": {"inputs": gen_s},
+        "ssh_create": {"seconds": create_s, "host_rss_growth_bytes": create_rss,
+                       "what": "ssh_create at n=%d, K*L=%d: filter on the host, draw tables built on the GPU"
+                               % (w["n"], w["K"] * w["L"])},
         **extra,
     }
     if rank == 0 and world == 1 and not args.no_batched:
@@ -1476,6 +1496,8 @@ def headline(line, detail_path):
     h["e2e"] = {k: _r(e[k]) for k in ("value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step", "steps",
                                       "h2d_gbs", "h2d_peak_gbs", "h2d_frac") if k in e}
     h["queries_per_s"] = _r(line["queries_per_s"])
+    if "ssh_create" in line:
+        h["ssh_create_s"] = _r(line["ssh_create"]["seconds"])
     h["latency_ms"] = {"p50": _r(line["latency_ms"]["p50"]), "p99": _r(line["latency_ms"]["p99"])}
     for k in ("recall_at_10", "ndcg_at_10"):
         if k in line:

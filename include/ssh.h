@@ -65,15 +65,19 @@ const char* ssh_last_error(void);
  * uses 20 tables of one hash each, here there are L tables keyed by K hashes each).
  *   W      filter length, 1 <= W <= 8192 (Sec. 4.1)
  *   delta  filter step, >= 1 (Sec. 4.1)
- *   n      shingle length in bits, 1 <= n <= 16 (the draws are tabulated per shingle id) (Sec. 4.2);
- *          17..32 return SSH_ENOTSUP, anything else SSH_EINVAL
+ *   n      shingle length in bits, 1 <= n <= 32 (Sec. 4.2); anything else SSH_EINVAL.
+ *          For n <= 16 the minhash draws of every (hash, shingle id) are tabulated
+ *          on the device; for 17..32 they are computed in FP64 as each series is
+ *          hashed (exact, slower; the one-permutation minhash option needs n <= 16)
  *   K, L   hashes per table and number of tables, K*L <= 4096
  *   band   Sakoe-Chiba band as a fraction of the series length: the DTW radius
  *          is floor(band * m) (clamped to m-1); band >= 0
  *   seed   seeds the filter r and every minhash draw (Philox4x32-10)
- * The filter and the minhash draw tables are generated on the host and copied
- * to the current CUDA device, which becomes the index's device.
- * On success *out owns about K*L*2^n*40 bytes of device memory.
+ * The filter is generated on the host; the Sec. 4.3 draw tables are built on the
+ * current CUDA device (which becomes the index's device) by kernels, from draws
+ * whose logarithm is a fixed sequence of FP64 operations (the same bits on any
+ * machine). On success *out owns about 90 bytes of device memory per (hash,
+ * shingle id) for n <= 16 (290 MB at K*L = 100, n = 15), and under 1 MB for n > 16.
  */
 ssh_status ssh_create(int W, int delta, int n, int K, int L, float band, uint64_t seed, ssh_index** out);
 
@@ -285,8 +289,8 @@ void ssh_server_destroy(ssh_server* s);
  * probability per hash is the same weighted Jaccard, at O(copies + K L) work per
  * series instead of O(distinct shingles x K L). Hashes and keys differ from
  * ICWS's. Settable only while the index is empty (else SSH_EBUSY) and for
- * K*L <= 256 (else SSH_ENOTSUP); needs a compiled sketch shape (adds return
- * SSH_ENOTSUP otherwise). */
+ * K*L <= 256 and n <= 16 (else SSH_ENOTSUP); needs a compiled sketch shape (adds
+ * return SSH_ENOTSUP otherwise). */
 typedef enum ssh_option {
     SSH_OPT_LB_PRUNE = 1,
     SSH_OPT_KERNEL_TIMING = 2,
@@ -394,10 +398,10 @@ ssh_status ssh_dtw_device(const float* d_a, const int64_t* d_a_idx, const float*
 
 /* ssh_dtw_device with an explicit tiling instead of the one the library's autotuner
  * picks for (m, rb): S band slots per lane (8, 14 or 26) and the kernel variant
- * (0: paired square-adds; 1: paired differences too, S = 14 or 26). Every tiling
- * computes each cell from the same three values in the same order, so all give
- * the same distances bit for bit. SSH_ENOTSUP for a tiling that is not compiled
- * or needs more than 32 lanes per pair at this radius. */
+ * (0, the only one built). Every tiling computes each cell from the same three
+ * values in the same order, so all give the same distances bit for bit.
+ * SSH_ENOTSUP for a tiling that is not compiled or needs more than 32 lanes per
+ * pair at this radius. */
 ssh_status ssh_dtw_device_tiled(const float* d_a, const int64_t* d_a_idx, const float* d_b, const int64_t* d_b_idx,
                                 int64_t npairs, int32_t m, int32_t rb, int32_t S, int32_t variant, float* d_out,
                                 void* stream);

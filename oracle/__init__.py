@@ -79,6 +79,7 @@ def _load():
             "ssh_oracle_shingle": (ctypes.c_int, [u8p, ctypes.c_int, ctypes.c_int, u32p, u32p]),
             "ssh_oracle_cws_draw": (None, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, f64p, f64p, f64p]),
             "ssh_oracle_cws_log_a": (ctypes.c_double, [ctypes.c_double] * 3 + [ctypes.c_uint32, f64p]),
+            "ssh_oracle_ln": (ctypes.c_double, [ctypes.c_double]),
             "ssh_oracle_cws": (None, [ctypes.c_uint64, ctypes.c_int, u32p, u32p, ctypes.c_int, u32p, u32p]),
             "ssh_oracle_bucket_key": (ctypes.c_uint64, [ctypes.c_uint64, ctypes.c_int, ctypes.c_int, u32p, u32p]),
             "ssh_oracle_doph": (None, [ctypes.c_uint64, ctypes.c_int, u32p, u32p, ctypes.c_int, u32p, u32p]),
@@ -176,6 +177,11 @@ def shingle(bits, n: int):
     nnz = _load().ssh_oracle_shingle(_ptr(b, ctypes.c_uint8) if nb else None, nb, int(n),
                                      _ptr(ids, ctypes.c_uint32), _ptr(counts, ctypes.c_uint32))
     return ids[:nnz].copy(), counts[:nnz].copy()
+
+
+def ln(x: float) -> float:
+    """The oracle's natural logarithm (a fixed sequence of FP64 operations; Sec. 4.3 draws)."""
+    return _load().ssh_oracle_ln(float(x))
 
 
 def cws_draw(seed: int, j: int, k: int):

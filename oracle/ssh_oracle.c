@@ -166,6 +166,50 @@ int ssh_oracle_shingle(const uint8_t* bits, int nb, int n, uint32_t* ids_out, ui
 
 /* --------------------------------------------------- Weighted minhash (ICWS) */
 
+/* Natural logarithm of a positive normal double as a fixed sequence of IEEE
+ * round-to-nearest operations, so that every machine (and a GPU doing the same
+ * operations) gets the same bits: x = 2^e f with f in [sqrt(1/2), sqrt(2))
+ * (exact, by the exponent bits), ln f = 2 atanh(s) with s = (f - 1) / (f + 1)
+ * and the atanh series s + s^3/3 + ... + s^23/23 (|s| <= 0.1716, so the first
+ * omitted term is below 2^-60 of the sum), and ln x = e ln2_hi + (ln f + e ln2_lo)
+ * with Cody and Waite's split of ln 2 (the hi part has 11 trailing zero bits,
+ * so e ln2_hi is exact). Accurate to a few ulp. Returns NaN outside its domain. */
+#define LN2_HI 6.93147180369123816490e-01 /* 0x3FE62E42FEE00000 */
+#define LN2_LO 1.90821492927058770002e-10 /* 0x3DEA39EF35793C76 */
+
+double ssh_oracle_ln(double x) {
+    uint64_t bits;
+    memcpy(&bits, &x, sizeof bits);
+    int ex = (int)((bits >> 52) & 0x7FF);
+    if (!(x > 0.0) || ex == 0 || ex == 0x7FF) return NAN;
+    int e = ex - 1023;
+    uint64_t fb = (bits & 0x000FFFFFFFFFFFFFull) | 0x3FF0000000000000ull; /* f in [1, 2) */
+    double f;
+    memcpy(&f, &fb, sizeof f);
+    if (f > 1.41421356237309504880) { /* f / 2, exact */
+        fb = (fb & 0x000FFFFFFFFFFFFFull) | 0x3FE0000000000000ull;
+        memcpy(&f, &fb, sizeof f);
+        e += 1;
+    }
+    double s = (f - 1.0) / (f + 1.0);
+    double z = s * s;
+    double p = 1.0 / 23.0;
+    p = 1.0 / 21.0 + z * p;
+    p = 1.0 / 19.0 + z * p;
+    p = 1.0 / 17.0 + z * p;
+    p = 1.0 / 15.0 + z * p;
+    p = 1.0 / 13.0 + z * p;
+    p = 1.0 / 11.0 + z * p;
+    p = 1.0 / 9.0 + z * p;
+    p = 1.0 / 7.0 + z * p;
+    p = 1.0 / 5.0 + z * p;
+    p = 1.0 / 3.0 + z * p;
+    double s2 = s + s;
+    double lnf = s2 + s2 * (z * p);
+    double de = (double)e;
+    return de * LN2_HI + (lnf + de * LN2_LO);
+}
+
 void ssh_oracle_cws_draw(uint64_t seed, uint32_t j, uint32_t k, double* r, double* c, double* beta) {
     uint32_t key[2];
     seed_key(seed, key);
@@ -179,15 +223,15 @@ void ssh_oracle_cws_draw(uint64_t seed, uint32_t j, uint32_t k, double* r, doubl
     double u3 = ssh_oracle_uniform(b0[2]);
     double u4 = ssh_oracle_uniform(b0[3]);
     double u5 = ssh_oracle_uniform(b1[0]);
-    *r = -log(u1 * u2);    /* Gamma(2,1) as the sum of two Exp(1) */
-    *c = -log(u3 * u4);    /* Gamma(2,1) */
-    *beta = u5;            /* U(0,1) */
+    *r = -ssh_oracle_ln(u1 * u2);    /* Gamma(2,1) as the sum of two Exp(1) */
+    *c = -ssh_oracle_ln(u3 * u4);    /* Gamma(2,1) */
+    *beta = u5;                      /* U(0,1) */
 }
 
 double ssh_oracle_cws_log_a(double r, double c, double beta, uint32_t S, double* t_out) {
-    double ln_s = log((double)S);
+    double ln_s = ssh_oracle_ln((double)S);
     double t = floor(ln_s / r + beta);
-    double ln_a = log(c) - r * ((t - beta) + 1.0);
+    double ln_a = ssh_oracle_ln(c) - r * ((t - beta) + 1.0);
     *t_out = t;
     return ln_a;
 }

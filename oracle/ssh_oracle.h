@@ -54,12 +54,19 @@ double ssh_oracle_window_dot(const float* x, const float* r, int W, int start);
  * returns how many there are (0 when nb < n). ids_out/counts_out hold nb entries. */
 int ssh_oracle_shingle(const uint8_t* bits, int nb, int n, uint32_t* ids_out, uint32_t* counts_out);
 
+/* Natural logarithm used by the weighted-minhash draws: a fixed sequence of IEEE
+ * FP64 operations (exponent split, atanh series, Cody-Waite ln 2), so the draws
+ * are the same bits on every machine. Positive normal x; NaN otherwise. */
+double ssh_oracle_ln(double x);
+
 /* The random draws of one weighted-minhash function j for one shingle id k (Ioffe
  * 2010, "Improved Consistent Sampling"): r ~ Gamma(2,1), c ~ Gamma(2,1),
- * beta ~ U(0,1), all from Philox keyed on (seed) with counter (k, j, tag, block). */
+ * beta ~ U(0,1), all from Philox keyed on (seed) with counter (k, j, tag, block):
+ * r = -ln(u1 u2), c = -ln(u3 u4), beta = u5 with ln = ssh_oracle_ln. */
 void ssh_oracle_cws_draw(uint64_t seed, uint32_t j, uint32_t k, double* r, double* c, double* beta);
 
-/* ln a for one (j, k, S): t = floor(ln S / r + beta), ln a = ln c - r * ((t - beta) + 1).
+/* ln a for one (j, k, S): t = floor(ln S / r + beta), ln a = ln c - r * ((t - beta) + 1),
+ * every logarithm by ssh_oracle_ln.
  * Writes t to *t_out. */
 double ssh_oracle_cws_log_a(double r, double c, double beta, uint32_t S, double* t_out);
 

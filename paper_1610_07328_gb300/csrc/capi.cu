@@ -60,7 +60,6 @@ static ssh_status fail(ssh_status s, const char* fmt, ...) {
 namespace {
 
 constexpr uint32_t kTagFilter = 0x46494C54u;  // "FILT"
-constexpr uint32_t kTagCws = 0x43575331u;     // "CWS1"
 
 void philox10(const uint32_t in[4], uint32_t k0, uint32_t k1, uint32_t out[4]) {
     uint32_t c0 = in[0], c1 = in[1], c2 = in[2], c3 = in[3];
@@ -119,33 +118,6 @@ void make_srp_projection(uint64_t seed, int m, int j, float* r) {
         const double angle = two_pi * u2;
         r[i] = (float)((i % 2 == 0) ? radius * std::cos(angle) : radius * std::sin(angle));
     }
-}
-
-struct Draw {
-    double r, beta, lnc;
-};
-
-// Sec. 4.3 (Ioffe's ICWS): r ~ Gamma(2,1), c ~ Gamma(2,1), beta ~ U(0,1) for hash j, shingle k.
-inline Draw cws_draw(uint64_t seed, uint32_t j, uint32_t k) {
-    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
-    const uint32_t c0[4] = {k, j, kTagCws, 0u};
-    const uint32_t c1[4] = {k, j, kTagCws, 1u};
-    uint32_t a[4], b[4];
-    philox10(c0, k0, k1, a);
-    philox10(c1, k0, k1, b);
-    const double u1 = unit(a[0]), u2 = unit(a[1]), u3 = unit(a[2]), u4 = unit(a[3]), u5 = unit(b[0]);
-    Draw d;
-    d.r = -std::log(u1 * u2);
-    const double c = -std::log(u3 * u4);
-    d.beta = u5;
-    d.lnc = std::log(c);
-    return d;
-}
-
-// ln a of a shingle seen s times: t = floor(ln s / r + beta), ln a = ln c - r ((t - beta) + 1).
-inline double log_a(const Draw& d, double lns) {
-    const double t = std::floor(lns / d.r + d.beta);
-    return d.lnc - d.r * ((t - d.beta) + 1.0);
 }
 
 template <typename F>
@@ -987,7 +959,6 @@ ssh_status ssh_create(int W, int delta, int n, int K, int L, float band, uint64_
     if (W < 1 || W > kMaxW) return fail(SSH_EINVAL, "W = %d outside [1, %d]", W, kMaxW);
     if (delta < 1) return fail(SSH_EINVAL, "delta = %d < 1", delta);
     if (n < 1 || n > 32) return fail(SSH_EINVAL, "n = %d outside [1, 32]", n);
-    if (n > kMaxShingleBits) return fail(SSH_ENOTSUP, "n = %d > %d needs draws computed on the fly (not built)", n, kMaxShingleBits);
     if (K < 1 || L < 1 || (int64_t)K * L > kMaxKL) return fail(SSH_EINVAL, "K*L = %lld outside [1, %d]", (long long)K * L, kMaxKL);
     if (!(band >= 0.0f) || std::isinf(band)) return fail(SSH_EINVAL, "band must be finite and >= 0");
 
@@ -1033,68 +1004,16 @@ ssh_status ssh_create(int W, int delta, int n, int K, int L, float band, uint64_
     const double tau = std::max(1e-4, 2.0 * gw);
     idx->tau_norm = std::nextafter((float)(tau * std::sqrt(nr) * (1.0 + 1e-6)), INFINITY);
 
-    // Sec. 4.3 draw tables for every (hash j, shingle k)
-    const int KL = idx->KL;
-    const int64_t nk = (int64_t)1 << n;
-    const int KLr = rank_stride_of(KL), KLp = tab_stride_of(KL);
-    std::vector<uint16_t> rank((size_t)nk * KLr, (uint16_t)0xFFFF);
-    std::vector<uint2> kla((size_t)KL * nk);  // per rank: (shingle id, fl32 ln a at count 1)
-    std::vector<float4> p32((size_t)nk * KL);
-    std::vector<double> p64((size_t)KL * nk * 3);
-    // ln a rounded once to FP32 for small counts, and their t (255: compute it in FP64)
-    std::vector<float> lav((size_t)nk * kTabCounts * KLp, 0.f);
-    std::vector<uint8_t> tsm((size_t)nk * (kTabCounts - 1) * KLp, (uint8_t)255);
-    parallel_for(KL, [&](int64_t j) {
-        std::vector<std::pair<double, uint32_t>> la1(nk);
-        for (int64_t k = 0; k < nk; ++k) {
-            const Draw d = cws_draw(seed, (uint32_t)j, (uint32_t)k);
-            p32[(size_t)k * KL + j] = make_float4((float)d.r, (float)(1.0 / d.r), (float)d.beta, (float)d.lnc);
-            double* q = &p64[((size_t)j * nk + k) * 3];
-            q[0] = d.r;
-            q[1] = d.beta;
-            q[2] = d.lnc;
-            la1[k] = {log_a(d, std::log(1.0)), (uint32_t)k};
-            for (int c = 1; c <= kTabCounts; ++c) {
-                const double lns = std::log((double)c);
-                lav[((size_t)k * kTabCounts + (c - 1)) * KLp + j] = (float)log_a(d, lns);
-                if (c >= 2) {
-                    const double t = std::floor(lns / d.r + d.beta);
-                    tsm[((size_t)k * (kTabCounts - 1) + (c - 2)) * KLp + j] =
-                        (t >= 0.0 && t < 255.0) ? (uint8_t)t : (uint8_t)255;
-                }
-            }
+    // Sec. 4.3 draw tables for every (hash j, shingle k), built on the GPU (draws.cu)
+    {
+        ssh_status ts = build_draw_tables(idx, idx->hstream);
+        if (ts != SSH_OK) {
+            ssh_destroy(idx);
+            return ts;
         }
-        std::sort(la1.begin(), la1.end());  // (value, id): equal values keep the smaller id first
-        for (int64_t rnk = 0; rnk < nk; ++rnk) {
-            rank[(size_t)la1[rnk].second * KLr + j] = (uint16_t)rnk;
-            const uint32_t k = la1[rnk].second;
-            float v = lav[(size_t)k * kTabCounts * KLp + j];
-            uint32_t bitsv;
-            memcpy(&bitsv, &v, 4);
-            kla[(size_t)j * nk + rnk] = make_uint2(k, bitsv);
-        }
-    });
-    std::vector<float> lns32(kMaxCount + 1);
-    std::vector<double> lns64(kMaxCount + 1);
-    for (int s = 0; s <= kMaxCount; ++s) {
-        lns64[s] = std::log((double)s);
-        lns32[s] = (float)lns64[s];
     }
-
-    auto up = [&](void** dst, const void* src, size_t bytes) -> cudaError_t {
-        cudaError_t err = cudaMalloc(dst, bytes);
-        if (err != cudaSuccess) return err;
-        return cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
-    };
-    e = up(reinterpret_cast<void**>(&idx->d_r), idx->h_r.data(), W * sizeof(float));
-    if (e == cudaSuccess) e = up(reinterpret_cast<void**>(&idx->d_rank), rank.data(), rank.size() * 2);
-    if (e == cudaSuccess) e = up(reinterpret_cast<void**>(&idx->d_kla), kla.data(), kla.size() * sizeof(uint2));
-    if (e == cudaSuccess) e = up(reinterpret_cast<void**>(&idx->d_p32), p32.data(), p32.size() * sizeof(float4));
-    if (e == cudaSuccess) e = up(reinterpret_cast<void**>(&idx->d_p64), p64.data(), p64.size() * sizeof(double));
-    if (e == cudaSuccess) e = up(reinterpret_cast<void**>(&idx->d_lav), lav.data(), lav.size() * sizeof(float));
-    if (e == cudaSuccess) e = up(reinterpret_cast<void**>(&idx->d_tsm), tsm.data(), tsm.size());
-    if (e == cudaSuccess) e = up(reinterpret_cast<void**>(&idx->d_lns32), lns32.data(), lns32.size() * sizeof(float));
-    if (e == cudaSuccess) e = up(reinterpret_cast<void**>(&idx->d_lns64), lns64.data(), lns64.size() * sizeof(double));
+    e = cudaMalloc(reinterpret_cast<void**>(&idx->d_r), W * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemcpy(idx->d_r, idx->h_r.data(), W * sizeof(float), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMalloc(&idx->d_stats, kNumStatSlots * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(idx->d_stats, 0, kNumStatSlots * sizeof(unsigned long long));
     if (e != cudaSuccess) {
@@ -1448,6 +1367,9 @@ ssh_status ssh_set_option(ssh_index* idx, ssh_option opt, int64_t value) {
             if (value < 0 || value > 1) return fail(SSH_EINVAL, "SSH_OPT_MINHASH takes 0 or 1");
             if (value == 1 && idx->KL > 256)
                 return fail(SSH_ENOTSUP, "the one-permutation minhash covers K*L <= 256 (this index: %d)", idx->KL);
+            if (value == 1 && idx->n > kMaxShingleBits)
+                return fail(SSH_ENOTSUP, "the one-permutation minhash covers n <= %d (this index: %d)",
+                            kMaxShingleBits, idx->n);
             for (const auto& kv : idx->subs)
                 if (kv.second.count > 0) return fail(SSH_EBUSY, "SSH_OPT_MINHASH changes only an empty index");
             idx->minhash = (int)value;

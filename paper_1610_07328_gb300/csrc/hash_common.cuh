@@ -28,6 +28,121 @@ __device__ __forceinline__ uint64_t bucket_key(uint64_t seed, int l, int K, cons
     return h;
 }
 
+// ---------------------------------------------- Sec. 4.3 draws on the device
+
+// Philox4x32-10 (Salmon et al., SC'11): the counter-based generator of every draw.
+__host__ __device__ __forceinline__ void philox4x32_10(const uint32_t in[4], uint32_t k0, uint32_t k1,
+                                                       uint32_t out[4]) {
+    uint32_t c0 = in[0], c1 = in[1], c2 = in[2], c3 = in[3];
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        if (round) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint64_t m0 = (uint64_t)0xD2511F53u * c0;
+        const uint64_t m1 = (uint64_t)0xCD9E8D57u * c2;
+        const uint32_t n0 = (uint32_t)(m1 >> 32) ^ c1 ^ k0;
+        const uint32_t n2 = (uint32_t)(m0 >> 32) ^ c3 ^ k1;
+        c1 = (uint32_t)m1;
+        c3 = (uint32_t)m0;
+        c0 = n0;
+        c2 = n2;
+    }
+    out[0] = c0;
+    out[1] = c1;
+    out[2] = c2;
+    out[3] = c3;
+}
+
+// ((x >> 9) + 1/2) 2^-23: exact in FP32 and FP64, never 0 or 1.
+__device__ __forceinline__ double unit23(uint32_t x) {
+    return __dmul_rn(__dadd_rn((double)(x >> 9), 0.5), 1.0 / 8388608.0);
+}
+
+// Natural logarithm of a positive normal double as one fixed sequence of IEEE
+// round-to-nearest operations (so every machine computes the same bits): the
+// exponent split x = 2^e f, f in [sqrt(1/2), sqrt(2)); ln f = 2 atanh(s),
+// s = (f - 1) / (f + 1), by the series s + s^3/3 + ... + s^23/23 in Horner form;
+// ln x = e ln2_hi + (ln f + e ln2_lo) with Cody and Waite's two-part ln 2.
+// NaN for zero, negative, subnormal, infinite or NaN x.
+__device__ __forceinline__ double ln_fixed(double x) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+    const int ex = (int)((bits >> 52) & 0x7FF);
+    if (!(x > 0.0) || ex == 0 || ex == 0x7FF) return __longlong_as_double(0x7FF8000000000000ll);
+    int e = ex - 1023;
+    unsigned long long fb = (bits & 0x000FFFFFFFFFFFFFull) | 0x3FF0000000000000ull;
+    double f = __longlong_as_double((long long)fb);
+    if (f > 1.41421356237309504880) {
+        fb = (fb & 0x000FFFFFFFFFFFFFull) | 0x3FE0000000000000ull;
+        f = __longlong_as_double((long long)fb);
+        e += 1;
+    }
+    const double s = __ddiv_rn(__dsub_rn(f, 1.0), __dadd_rn(f, 1.0));
+    const double z = __dmul_rn(s, s);
+    double p = 1.0 / 23.0;
+    p = __dadd_rn(1.0 / 21.0, __dmul_rn(z, p));
+    p = __dadd_rn(1.0 / 19.0, __dmul_rn(z, p));
+    p = __dadd_rn(1.0 / 17.0, __dmul_rn(z, p));
+    p = __dadd_rn(1.0 / 15.0, __dmul_rn(z, p));
+    p = __dadd_rn(1.0 / 13.0, __dmul_rn(z, p));
+    p = __dadd_rn(1.0 / 11.0, __dmul_rn(z, p));
+    p = __dadd_rn(1.0 / 9.0, __dmul_rn(z, p));
+    p = __dadd_rn(1.0 / 7.0, __dmul_rn(z, p));
+    p = __dadd_rn(1.0 / 5.0, __dmul_rn(z, p));
+    p = __dadd_rn(1.0 / 3.0, __dmul_rn(z, p));
+    const double s2 = __dadd_rn(s, s);
+    const double lnf = __dadd_rn(s2, __dmul_rn(s2, __dmul_rn(z, p)));
+    const double de = (double)e;
+    constexpr double kLn2Hi = 6.93147180369123816490e-01;  // 0x3FE62E42FEE00000
+    constexpr double kLn2Lo = 1.90821492927058770002e-10;  // 0x3DEA39EF35793C76
+    return __dadd_rn(__dmul_rn(de, kLn2Hi), __dadd_rn(lnf, __dmul_rn(de, kLn2Lo)));
+}
+
+constexpr uint32_t kTagCwsDraw = 0x43575331u;  // "CWS1"
+
+// Ioffe's ICWS draws of hash j for shingle k: r = -ln(u1 u2), c = -ln(u3 u4)
+// (Gamma(2,1) each), beta = u5 (U(0,1)), from the Philox blocks with counters
+// (k, j, CWS1, 0) and (k, j, CWS1, 1) under the key (seed low, seed high).
+__device__ __forceinline__ void cws_draw_dev(uint64_t seed, uint32_t j, uint32_t k, double* r, double* beta,
+                                             double* lnc) {
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    const uint32_t c0[4] = {k, j, kTagCwsDraw, 0u};
+    const uint32_t c1[4] = {k, j, kTagCwsDraw, 1u};
+    uint32_t x[4], y[4];
+    philox4x32_10(c0, k0, k1, x);
+    philox4x32_10(c1, k0, k1, y);
+    *r = -ln_fixed(__dmul_rn(unit23(x[0]), unit23(x[1])));
+    const double c = -ln_fixed(__dmul_rn(unit23(x[2]), unit23(x[3])));
+    *beta = unit23(y[0]);
+    *lnc = ln_fixed(c);
+}
+
+// FP64 minhash of hash j with the draws computed here (no tables; any n <= 32):
+// t = floor(ln S / r + beta), ln a = ln c - r ((t - beta) + 1), the smallest ln a
+// wins, equal values go to the smaller id (ids ascending).
+__device__ inline void cws_fp64_otf(const HashArgs& a, int j, const uint32_t* cid, const uint32_t* ccnt, int nnz,
+                                    uint32_t* kout, uint32_t* tout) {
+    double best = __longlong_as_double(0x7FF0000000000000ll);
+    uint32_t bk = 0, bt = 0;
+#pragma unroll 1
+    for (int e = 0; e < nnz; ++e) {
+        const uint32_t k = cid[e];
+        double r, beta, lnc;
+        cws_draw_dev(a.seed, (uint32_t)j, k, &r, &beta, &lnc);
+        const double lns = a.lns64[ccnt[e]];
+        const double t = floor(__dadd_rn(__ddiv_rn(lns, r), beta));
+        const double la = __dsub_rn(lnc, __dmul_rn(r, __dadd_rn(__dsub_rn(t, beta), 1.0)));
+        if (la < best) {
+            best = la;
+            bk = k;
+            bt = (uint32_t)t;
+        }
+    }
+    *kout = bk;
+    *tout = bt;
+}
+
 // FP64 recomputation of one hash j over the whole weighted set (ids ascending),
 // in the order of the definition: t = floor(ln S / r + beta),
 // ln a = ln c - r ((t - beta) + 1); the smallest ln a wins, ties to the smaller id.

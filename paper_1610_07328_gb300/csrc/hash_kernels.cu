@@ -17,7 +17,9 @@
 //    FP32 together with a guaranteed error interval (relative width >= 1e-6,
 //    directed rounding); if the winner's interval overlaps another candidate's,
 //    or a floor() is within its error of an integer step, the whole hash is
-//    recomputed in FP64 exactly as the definition orders the operations.
+//    recomputed in FP64 exactly as the definition orders the operations;
+//  - for n > kMaxShingleBits there are no tables: each hash is the FP64 argmin
+//    with its draws computed here (Philox, ln_fixed), the definition itself.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -188,7 +190,13 @@ __global__ void __launch_bounds__(kMaxWarpsPerCta * 32) hash_kernel(HashArgs a, 
     const size_t nk = (size_t)1 << n;
     for (int j0 = 0; j0 < KL; j0 += 32) {
         const int j = j0 + lane;
-        if (j < KL) {
+        if (j < KL && n > kMaxShingleBits) {
+            // no draw tables for shingles this long: every draw in FP64 here, exactly as defined
+            uint32_t ks, ts;
+            cws_fp64_otf(a, j, cid, ccnt, nnz, &ks, &ts);
+            kst[j] = ks;
+            tst[j] = ts;
+        } else if (j < KL) {
             uint32_t rmin = 0xFFFFFFFFu;
             bool hasA = false;
             CwsTrack tr;

@@ -481,278 +481,6 @@ __global__ void __launch_bounds__(256) dtw_wave_kernel(PairSet ps, int m, int rb
     }
 }
 
-// ---------------------------------------------------------------------------
-// The same wavefront with the differences paired as well (variant 1). The two
-// cells of one paired FMA lie on one anti-diagonal, so their differences are
-// (c[x] - q[y], c[x-1] - q[y+1]): one sub.f32x2 when (c[x], c[x-1]) and
-// (q[y], q[y+1]) sit in register pairs. The query is staged in shared memory
-// as the pairs (q[y], q[y+1]) (kPad outside [0, m), so no bounds test), and the
-// candidate window keeps (cw[t], cw[t+1]) pairs: the pair that enters at a step
-// is the new sample and the previous step's new sample (one register copy).
-// Per two cells: one paired subtract, two 3-input mins, one paired FMA. Each
-// cell computes fma(d, d, min3(...)) on the same three values as variant 0, so
-// the distances are bit-identical. S = 2 mod 4 (H = S/2 odd): the query pairs
-// of even and odd steps form two families that each slide by one pair every
-// two steps, so both rotate with the same period U = H + 1 as the candidate.
-
-__device__ __forceinline__ unsigned long long pk2(float lo, float hi) {
-    unsigned long long v;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(v) : "f"(lo), "f"(hi));
-    return v;
-}
-__device__ __forceinline__ float lo2(unsigned long long v) {
-    float lo, hi;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-    return lo;
-}
-__device__ __forceinline__ unsigned long long sub2(unsigned long long a, unsigned long long b) {
-    unsigned long long r;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-// (r0, r1) = (d0 * d0 + c0, d1 * d1 + c1) for packed d and c (each half rounded as fmaf)
-__device__ __forceinline__ void sq_add2p(float& r0, float& r1, unsigned long long dd, float c0, float c1) {
-    unsigned long long cc = pk2(c0, c1), rr;
-    asm("fma.rn.f32x2 %0, %1, %1, %2;" : "=l"(rr) : "l"(dd), "l"(cc));
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(r0), "=f"(r1) : "l"(rr));
-}
-
-// Query pairs a pair-variant launch stages: pair k of the shared array holds
-// (q[qbase + k], q[qbase + k + 1]) for k in [0, npair).
-struct PairQ {
-    int qbase, npair;
-};
-__host__ __device__ inline PairQ pair_q_layout(int m, int rb, int S, int G) {
-    const int H = S / 2, U = H + 1;
-    const int PAD = G * S - (2 * rb + 1);
-    const int s_end = (2 * (m - 1) + rb) >> 1;
-    const int nblk = (s_end + U) / U;
-    const int s0 = s_end + 1 - nblk * U;
-    const int b_lo = -rb + (1 - PAD) / 2;             // b_off of lane 0
-    const int b_hi = (G - 1) * H - rb + (1 - PAD) / 2; // b_off of lane G - 1
-    PairQ p;
-    p.qbase = s0 + b_lo;
-    p.npair = (s_end + b_hi + H - 1) - p.qbase + 1;
-    return p;
-}
-
-template <int S, int PMASK>
-__global__ void __launch_bounds__(256) dtw_pair_kernel(PairSet ps, int m, int rb, int G, float* out) {
-    static_assert(S % 4 == 2, "the pair variant needs H = S/2 odd");
-    constexpr int H = S / 2;
-    constexpr int U = H + 1;   // even
-    constexpr int QF = U / 2;  // query pairs per family
-    extern __shared__ __align__(16) unsigned long long qq_s[];
-    __shared__ unsigned long long s_next;
-    const int lane = threadIdx.x & 31;
-    const int gpw = 32 / G;
-    const int grp = lane / G, g = lane - grp * G;
-    const bool lane_in_group = grp < gpw;
-    const unsigned gbits = (G == 32) ? 0xFFFFFFFFu : (((1u << G) - 1u) << (grp * G));
-    const int PAD = G * S - (2 * rb + 1);
-    const int gmask = (PAD - 1) / S;
-    const float mflag = (g == gmask) ? __int_as_float(0x7F800000) : __int_as_float(0xFF800000);
-    const float INF = __int_as_float(0x7F800000);
-    const int tau_f = 2 * (m - 1) + rb;
-    const int s_end = tau_f >> 1;
-    const int nblk = (s_end + U) / U;
-    const int s0 = s_end + 1 - nblk * U;
-    const int of = rb + PAD;
-    const int g_f = of / S, p_f = of - g_f * S;
-    const int a_off = -g * H + (PAD - 1) / 2;
-    const int b_off = g * H - rb + (1 - PAD) / 2;
-    const PairQ pq = pair_q_layout(m, rb, S, G);
-    const int qo = b_off - pq.qbase;  // shared pair index of q[B(s)] is s + qo
-    const int64_t s_lo = ps.seg_range ? ps.seg_range[0] : 0, s_hi = ps.seg_range ? ps.seg_range[1] : ps.nseg;
-    for (int64_t seg = s_lo + blockIdx.y; seg < s_hi; seg += gridDim.y) {
-        const int64_t sb = ps.seg_begin[seg], se = ps.seg_begin[seg + 1];
-        const int64_t per_cta = (int64_t)(blockDim.x >> 5) * gpw;
-        const int64_t share = max(per_cta, (se - sb + gridDim.x - 1) / gridDim.x);
-        const int64_t b0 = sb + (int64_t)blockIdx.x * share;
-        const int64_t b1 = min(se, b0 + share);
-        if (b0 >= b1) continue;  // uniform over the block
-        const float* qg = ps.seg_a[seg];
-        __syncthreads();
-        for (int k = threadIdx.x; k < pq.npair; k += blockDim.x) {
-            const int y = pq.qbase + k;
-            const float v0 = (y >= 0 && y < m) ? qg[y] : kPad;
-            const float v1 = (y + 1 >= 0 && y + 1 < m) ? qg[y + 1] : kPad;
-            qq_s[k] = pk2(v0, v1);
-        }
-        if (threadIdx.x == 0) s_next = (unsigned long long)b0;
-        __syncthreads();
-        float bound = INF;
-        if (ps.abandon) {
-            const uint32_t ub = ps.abandon[seg];
-            if (ub != 0xFFFFFFFFu) bound = __uint_as_float(ub);
-        }
-
-        int64_t p = -1;
-        int lblk = 0;
-        const float* c = qg;
-        float D[S];
-        unsigned long long cp[U];            // (cw[t], cw[t+1]) of pair t at cp[(t + U - u) % U]
-        unsigned long long qf0[QF], qf1[QF]; // query pairs of even / odd steps
-        bool need = lane_in_group;
-        while (true) {
-            unsigned long long v = ~0ull;
-            if (need && g == 0) {
-                v = atomicAdd(&s_next, 1ull);
-                while (v < (unsigned long long)b1 && ps.pair_b[v] == nullptr) v = atomicAdd(&s_next, 1ull);
-            }
-            v = __shfl_sync(kFull, v, lane_in_group ? grp * G : lane);
-            if (need) {
-                p = (v < (unsigned long long)b1) ? (int64_t)v : -1;
-                if (p >= 0) {
-                    c = ps.pair_b[p];
-                    lblk = 0;
-#pragma unroll
-                    for (int t = 0; t < S; ++t) D[t] = 0.f;
-                    if (g == gmask) D[PMASK] = INF;
-                    // candidate pairs t = 1 .. H at step s0: (c[A(s0) + 1 - t], c[A(s0) - t])
-#pragma unroll
-                    for (int t = 1; t < U; ++t) {
-                        const int ci = s0 + a_off + 1 - t;
-                        const float x0 = (ci >= 0 && ci < m) ? __ldg(c + ci) : kPad;
-                        const float x1 = (ci - 1 >= 0 && ci - 1 < m) ? __ldg(c + ci - 1) : kPad;
-                        cp[t] = pk2(x0, x1);
-                    }
-                    cp[0] = 0ull;
-                    // query pairs of both families but their newest: (q[B(s0 + f) + 2i], ...)
-#pragma unroll
-                    for (int i = 0; i < QF - 1; ++i) {
-                        qf0[i] = qq_s[s0 + qo + 2 * i];
-                        qf1[i] = qq_s[s0 + 1 + qo + 2 * i];
-                    }
-                } else {
-                    c = qg;
-                }
-            }
-            if (!__any_sync(kFull, p >= 0)) break;
-            const int sbase = s0 + lblk * U;
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int s = sbase + u;
-                const int k = u >> 1;
-                unsigned long long* qf = (u & 1) ? qf1 : qf0;
-                {   // the entering candidate pair (c[A(s) + 1], c[A(s)]) and query pair (q[B(s) + H - 1], ..)
-                    const int ci = s + a_off + 1;
-                    const float cn = (ci >= 0 && ci < m) ? __ldg(c + ci) : kPad;
-                    cp[(U - u) % U] = pk2(cn, lo2(cp[(U - u + 1) % U]));
-                    qf[(QF - 1 + k) % QF] = qq_s[s + qo + H - 1];
-                }
-                // wave tau = 2s: odd slots 2a+1 (cw[a+1] - qw[a]), paired with 2a+3
-                float right = __shfl_down_sync(kFull, D[0], 1);
-                if (g == G - 1) right = INF;
-#pragma unroll
-                for (int a = 0; a < H; a += 2) {
-                    const int pp = 2 * a + 1;
-                    const unsigned long long qa = qf[(a / 2 + k) % QF];
-                    if (a + 1 < H) {
-                        const int p1 = pp + 2;
-                        const unsigned long long dd = sub2(cp[(a + 1 + U - u) % U], qa);
-                        const float mn = min3f(D[pp + 1], D[pp - 1], D[pp]);
-                        const float ur1 = (p1 + 1 < S) ? D[p1 + 1] : right;
-                        const float mn1 = min3f(ur1, D[p1 - 1], D[p1]);
-                        sq_add2p(D[pp], D[p1], dd, mn, mn1);
-                    } else {
-                        const float d = lo2(cp[(a + 1 + U - u) % U]) - lo2(qa);
-                        const float ur = (pp + 1 < S) ? D[pp + 1] : right;
-                        D[pp] = fmaf(d, d, min3f(ur, D[pp - 1], D[pp]));
-                    }
-                }
-                // wave tau = 2s + 1: even slots 2a (cw[a] - qw[a]), paired with 2a+2
-                float left = __shfl_up_sync(kFull, D[S - 1], 1);
-                if (g == 0) left = INF;
-#pragma unroll
-                for (int a = 0; a < H; a += 2) {
-                    const int pp = 2 * a;
-                    const unsigned long long qa = qf[(a / 2 + k) % QF];
-                    const float lf = (pp > 0) ? D[pp - 1] : left;
-                    if (a + 1 < H) {
-                        const int p1 = pp + 2;
-                        const unsigned long long dd = sub2(cp[(a + U - u) % U], qa);
-                        const float mn = min3f(D[pp + 1], lf, D[pp]);
-                        const float mn1 = min3f(D[p1 + 1], D[p1 - 1], D[p1]);
-                        sq_add2p(D[pp], D[p1], dd, mn, mn1);
-                    } else {
-                        const float d = lo2(cp[(a + U - u) % U]) - lo2(qa);
-                        D[pp] = fmaf(d, d, min3f(D[pp + 1], lf, D[pp]));
-                    }
-                }
-                D[PMASK] = fmaxf(D[PMASK], mflag);
-            }
-            ++lblk;
-            bool over = false;
-            if (bound < INF) {  // uniform over the block
-                float lm = INF;
-#pragma unroll
-                for (int t = 0; t < S; ++t)
-                    if (g * S + t >= PAD) lm = fminf(lm, D[t]);
-                const unsigned bal = __ballot_sync(kFull, lm * ps.abandon_shrink > bound);
-                over = (bal & gbits) == gbits;
-            }
-            const bool fin = p >= 0 && lblk == nblk;
-            const bool ab = p >= 0 && !fin && over;
-            if (fin || ab) {
-                float res = INF;
-                if (fin) {
-#pragma unroll
-                    for (int t = 0; t < S; ++t)
-                        if (t == p_f) res = D[t];
-                }
-                if (g == g_f) out[ps.pair_slot ? ps.pair_slot[p] : p] = res;
-                if (ps.blocks_done && g == 0) atomicAdd(ps.blocks_done, (unsigned long long)lblk);
-            }
-            need = lane_in_group && (fin || ab);
-        }
-    }
-}
-
-template <int S>
-cudaError_t launch_pair(const PairSet& ps, int m, int rb, int G, int pmask, float* out, cudaStream_t st) {
-    const int threads = 256;
-    const int per_cta = (threads / 32) * (32 / G);
-    int64_t gx = (ps.max_seg_pairs + per_cta - 1) / per_cta;
-    if (gx < 1) gx = 1;
-    if (gx > 65535) gx = 65535;
-    dim3 grid((unsigned)gx, (unsigned)(ps.grid_y ? ps.grid_y : std::min<int64_t>(ps.nseg, 65535)));
-    const size_t smem = (size_t)pair_q_layout(m, rb, S, G).npair * sizeof(unsigned long long);
-#define SSH_PAIR_CASE(PM)                                                                                   \
-    case PM: {                                                                                              \
-        cudaError_t e = ensure_dynamic_smem((const void*)dtw_pair_kernel<S, PM>, smem);                    \
-        if (e != cudaSuccess) return e;                                                                     \
-        dtw_pair_kernel<S, PM><<<grid, threads, smem, st>>>(ps, m, rb, G, out);                             \
-        note_launch();                                                                                      \
-        return cudaGetLastError();                                                                          \
-    }
-    switch (pmask) {
-        SSH_PAIR_CASE(0)
-        SSH_PAIR_CASE(2)
-        SSH_PAIR_CASE(4)
-        SSH_PAIR_CASE(6)
-        SSH_PAIR_CASE(8)
-        SSH_PAIR_CASE(10)
-        SSH_PAIR_CASE(12)
-        default:
-            break;
-    }
-    if constexpr (S > 14) {
-        switch (pmask) {
-            SSH_PAIR_CASE(14)
-            SSH_PAIR_CASE(16)
-            SSH_PAIR_CASE(18)
-            SSH_PAIR_CASE(20)
-            SSH_PAIR_CASE(22)
-            SSH_PAIR_CASE(24)
-            default:
-                break;
-        }
-    }
-#undef SSH_PAIR_CASE
-    return cudaErrorInvalidValue;
-}
-
 template <int S>
 cudaError_t launch_wave(const PairSet& ps, int m, int rb, int G, int pmask, float* out, cudaStream_t st) {
     const int threads = 256;
@@ -996,11 +724,7 @@ __global__ void tune_pairs_kernel(const float* a, const float* b, int m, int64_t
 // Pick the slot count S per lane and the lanes per pair G for radius rb:
 // G = ceil((2 rb + 2) / S) lanes cover the band plus the one forced-inf slot,
 // and the cost per pair is proportional to S / (pairs per warp).
-bool dtw_tiling_compiled(int S, int variant) {
-    if (variant == 0) return S == 8 || S == 14 || S == 26;
-    if (variant == 1) return S == 14 || S == 26;
-    return false;
-}
+bool dtw_tiling_compiled(int S, int variant) { return variant == 0 && (S == 8 || S == 14 || S == 26); }
 
 DtwPlan dtw_plan_for(int rb, int S, int variant) {
     if (!dtw_tiling_compiled(S, variant)) return DtwPlan{0, 0, 0, 0};
@@ -1120,11 +844,6 @@ int64_t dtw_plan_blocks(int m, int rb, const DtwPlan& pl) {
 
 cudaError_t launch_dtw_plan(const PairSet& ps, int m, int rb, const DtwPlan& pl, float* out, cudaStream_t st) {
     if (ps.nseg <= 0 || ps.max_seg_pairs <= 0) return cudaSuccess;
-    if (pl.variant == 1) {
-        if (pl.S == 14) return launch_pair<14>(ps, m, rb, pl.G, pl.pmask, out, st);
-        if (pl.S == 26) return launch_pair<26>(ps, m, rb, pl.G, pl.pmask, out, st);
-        return cudaErrorNotSupported;
-    }
     if (pl.S == 8) return launch_wave<8>(ps, m, rb, pl.G, pl.pmask, out, st);
     if (pl.S == 14) return launch_wave<14>(ps, m, rb, pl.G, pl.pmask, out, st);
     if (pl.S == 26) return launch_wave<26>(ps, m, rb, pl.G, pl.pmask, out, st);
@@ -1192,14 +911,12 @@ DtwPlan dtw_tuned_plan(int m, int rb, cudaStream_t st) {
         if (it != cache.end()) return it->second;
     }
     std::vector<DtwPlan> cands;
-    for (int variant = 0; variant < 2; ++variant)
-        for (int S : {8, 14, 26}) {
-            if (!dtw_tiling_compiled(S, variant)) continue;
-            const int G = (2 * rb + 2 + S - 1) / S;
-            if (G > 32) continue;
-            const int PAD = G * S - (2 * rb + 1);
-            cands.push_back(DtwPlan{S, G, (PAD - 1) % S, variant});
-        }
+    for (int S : {8, 14, 26}) {
+        const int G = (2 * rb + 2 + S - 1) / S;
+        if (G > 32) continue;
+        const int PAD = G * S - (2 * rb + 1);
+        cands.push_back(DtwPlan{S, G, (PAD - 1) % S, 0});
+    }
     DtwPlan best = dtw_plan(m, rb);
     if (cands.size() > 1) {
         const double cells = (double)m * (2.0 * rb + 1.0) - (double)rb * (rb + 1.0);

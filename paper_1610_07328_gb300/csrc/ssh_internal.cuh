@@ -119,6 +119,9 @@ struct HashArgs {
 };
 
 bool hash_fast_supported(const HashArgs& a);
+// Sec. 4.3 draw tables of an index (and its ln s tables), built on the GPU on
+// `st` (draws.cu); for n > kMaxShingleBits only ln s (draws are computed on the fly).
+ssh_status build_draw_tables(ssh_index* idx, cudaStream_t st);
 cudaError_t launch_hash_fast(const HashArgs& a, cudaStream_t st);
 
 // Windows of one stream (row k = samples [k step, k step + m)): the sketch bits
@@ -236,7 +239,7 @@ cudaError_t launch_lb_rev(const PairSet& ps, int m, int rb, float* out, const ui
                           const float** pair_mut, unsigned long long* pruned, cudaStream_t st);
 
 // A DTW tiling: S band slots per lane, G lanes per pair, the slot forced to +inf,
-// and the kernel variant (0: paired FMAs; 1: paired differences and FMAs, S = 2 mod 4).
+// and the kernel variant (0, the wavefront with paired square-adds, is the one built).
 struct DtwPlan {
     int S, G, pmask;
     int variant = 0;

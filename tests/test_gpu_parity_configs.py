@@ -217,3 +217,60 @@ def test_reversed_lb_skip_is_counted():
         for t in range(5):
             if ids2[i, t] != oi[t]:  # a near tie at this tolerance
                 assert abs(oracle.dtw(q, db[ids2[i, t]], rb) - od[t]) <= 2 * tol * od[t]
+
+
+# --------------------------------------------- shingles longer than the draw tables
+
+def _unpack_bits(words, nb):
+    return np.array([(int(words[i // 32]) >> (31 - i % 32)) & 1 for i in range(nb)], np.uint8)
+
+
+@pytest.mark.parametrize("n", [17, 20, 32])
+def test_long_shingles_hash_and_query_match_the_oracle(n):
+    """n > 16: no draw tables; every minhash is the FP64 argmin with its Philox draws computed
+    in the kernel. Sketch bits, shingle sets, (k*, t*) and keys are bit-exact with the oracle,
+    and queries equal the oracle's Algorithm 2."""
+    b = _binding()
+    cfg = dict(W=16, delta=2, n=n, K=2, L=8, band=0.05, seed=3)
+    m, N = 128, 300
+    x = synth.random_walk(N, m, seed=70 + n)
+    nb = (m - cfg["W"]) // cfg["delta"] + 1
+    S = nb - n + 1
+    KL = cfg["K"] * cfg["L"]
+    r = oracle.filter_r(cfg["seed"], cfg["W"])
+    with _index(cfg) as idx:
+        d_x = torch.from_numpy(x).cuda()
+        bits = torch.zeros((N, (nb + 31) // 32), dtype=torch.int32, device="cuda")
+        ids = torch.zeros((N, S), dtype=torch.int32, device="cuda")
+        cnt = torch.zeros((N, S), dtype=torch.int32, device="cuda")
+        nnz = torch.zeros(N, dtype=torch.int32, device="cuda")
+        ks = torch.zeros((N, KL), dtype=torch.int32, device="cuda")
+        ts = torch.zeros((N, KL), dtype=torch.int32, device="cuda")
+        keys = torch.zeros((cfg["L"], N), dtype=torch.int64, device="cuda")
+        b.ssh_hash_device(idx.handle, d_x, m, N, bits, ids, cnt, nnz, ks, ts, keys)
+        torch.cuda.synchronize()
+        u32 = lambda t: t.cpu().numpy().view(np.uint32)
+        g_bits, g_ids, g_cnt, g_ks, g_ts = u32(bits), u32(ids), u32(cnt), u32(ks), u32(ts)
+        g_nnz, g_keys = nnz.cpu().numpy(), keys.cpu().numpy().view(np.uint64)
+        for i in range(0, N, 7):
+            ob = oracle.sketch(x[i], r, cfg["delta"])
+            assert np.array_equal(_unpack_bits(g_bits[i], nb), ob), i
+            sid, scnt = oracle.shingle(ob, n)
+            k = int(g_nnz[i])
+            assert k == len(sid) and np.array_equal(g_ids[i, :k], sid) and np.array_equal(g_cnt[i, :k], scnt), i
+            oks, ots = oracle.cws(cfg["seed"], KL, sid, scnt)
+            assert np.array_equal(g_ks[i], oks) and np.array_equal(g_ts[i], ots), i
+            for l in range(cfg["L"]):
+                assert int(g_keys[l, i]) == oracle.bucket_key(cfg["seed"], l, cfg["K"], oks, ots), (l, i)
+        # Algorithm 2 end to end
+        idx.add(x)
+        qs, _ = synth.perturbed_queries(x, 6, seed=80 + n)
+        q_ids, q_d = idx.query(qs, 5)
+        st = idx.stats()
+    ref = oracle.OracleIndex(**cfg)
+    ref.add(x)
+    rb = oracle.band_radius(cfg["band"], m)
+    for i, q in enumerate(qs):
+        oi, od = ref.query(q, 5)
+        assert_topk_match(q, q_ids[i], q_d[i], oi, od, lambda j: x[j], rb)
+    assert st["candidates"] == sum(len(ref.candidates(q)) for q in qs)

@@ -173,6 +173,25 @@ def _draws(seed, j, k):
     return oracle.cws_draw(seed, j, k)
 
 
+def test_oracle_ln_is_the_natural_logarithm():
+    """The draws' logarithm (a fixed FP64 operation sequence, so every machine and the GPU get
+    the same bits) is the natural logarithm: within 4 ulp of the C library's log over the
+    whole range the draws use (u1 u2 >= 2^-48 up to the largest count), exact at 1, ln(2^k)
+    = k ln 2, and NaN outside its domain."""
+    rng = np.random.default_rng(41)
+    xs = np.concatenate([rng.uniform(2.0 ** -48, 1.0, 4000), np.exp(rng.uniform(-33.3, 11.1, 4000)),
+                         np.arange(1, 2000, dtype=np.float64), [2.0 ** -48, 1 - 2.0 ** -24, 65535.0,
+                                                                  math.sqrt(2), math.sqrt(0.5), 0.5, 2.0]])
+    for x in xs:
+        got, want = oracle.ln(float(x)), math.log(float(x))
+        assert abs(got - want) <= 4 * math.ulp(want) or (want == 0.0 and got == 0.0), (x, got, want)
+    assert oracle.ln(1.0) == 0.0
+    for k in (-40, -1, 1, 7, 30):
+        assert abs(oracle.ln(2.0 ** k) - k * math.log(2.0)) <= 2 * math.ulp(k * math.log(2.0))
+    for bad in (0.0, -1.0, float("inf"), float("nan"), 5e-324):
+        assert math.isnan(oracle.ln(bad))
+
+
 def test_cws_single_element_set():
     """A one-element set hashes to that element; t* brackets the weight: y* <= S < y* e^r
     with y* = exp(r (t* - beta)) (Ioffe 2010, the consistent-sampling interval)."""
