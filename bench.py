@@ -695,20 +695,52 @@ def batched_measurement(args, binding, torch, dev):
                        "band 5%%; %d queries of uniformly mixed lengths, top-%d" % (N4, list(BATCH_LENGTHS), nq4, k),
            "index_build_series_per_s": 5 * N4 / (build_ms / 1000.0)}
     with binding.SSHBatch(idxs, max_queries=nq4, k=k) as bt:
-        for _ in range(2):  # the first batch runs directly and captures the graph
-            bt.query(d_q, qlens, ids, dd, which)
-        torch.cuda.synchronize()
-        steps = max(3, min(args.steps, 5))
-        e0.record()
-        for _ in range(steps):
-            bt.query(d_q, qlens, ids, dd, which)
-        e1.record()
-        e1.synchronize()
-        batch_ms = e0.elapsed_time(e1) / steps
-        st = bt.stats()
+        modes = {}
+        # the rerank as one persistent launch, as per-class kernels, then by batch size (the default)
+        for persistent in (True, False, None):
+            bt.set_persistent(persistent)
+            for _ in range(2):  # the first batch runs directly and captures the graph
+                bt.query(d_q, qlens, ids, dd, which)
+            torch.cuda.synchronize()
+            steps = max(3, min(args.steps, 5))
+            e0.record()
+            for _ in range(steps):
+                bt.query(d_q, qlens, ids, dd, which)
+            e1.record()
+            e1.synchronize()
+            modes[persistent] = (e0.elapsed_time(e1) / steps, bt.stats())
+        batch_ms, st = modes[None]
     out.update({"batched_queries_per_s": nq4 / (batch_ms / 1000.0), "ms_per_batch": batch_ms,
-                "graph_kernels": st["graph_kernels"], "candidates_per_query": st["pairs"] / nq4,
-                "dtw_per_query": st["dtw"] / nq4})
+                "graph_kernels": st["graph_kernels"],
+                "rerank": "by batch size (persistent launch up to 512 queries, per-class kernels above)",
+                "persistent_rerank": {"queries_per_s": nq4 / (modes[True][0] / 1000.0), "ms_per_batch": modes[True][0],
+                                      "graph_kernels": modes[True][1]["graph_kernels"]},
+                "per_class_kernels": {"queries_per_s": nq4 / (modes[False][0] / 1000.0),
+                                      "ms_per_batch": modes[False][0],
+                                      "graph_kernels": modes[False][1]["graph_kernels"]},
+                "candidates_per_query": st["pairs"] / nq4, "dtw_per_query": st["dtw"] / nq4})
+    # small batches of the same mix (the serving loop's regime), both rerank forms
+    small = []
+    for nsm in (64, 256, 1024):
+        offs_s = np.concatenate([[0], np.cumsum(qlens[:nsm])])
+        d_qs = d_q[: int(offs_s[-1])].contiguous()
+        row = {"queries": nsm}
+        with binding.SSHBatch(idxs, max_queries=nsm, k=k) as bs:
+            for persistent, key in ((True, "persistent"), (False, "per_class")):
+                bs.set_persistent(persistent)
+                for _ in range(3):
+                    bs.query(d_qs, qlens[:nsm], ids[:nsm], dd[:nsm])
+                torch.cuda.synchronize()
+                e0.record()
+                for _ in range(5):
+                    bs.query(d_qs, qlens[:nsm], ids[:nsm], dd[:nsm])
+                e1.record()
+                e1.synchronize()
+                ms = e0.elapsed_time(e1) / 5
+                row[key] = {"ms_per_batch": ms, "queries_per_s": nsm / (ms / 1000.0),
+                            "graph_kernels": bs.stats()["graph_kernels"]}
+        small.append(row)
+    out["small_batches"] = small
     # plain path: one query per call on the query's own index
     n_plain = min(nq4, 256)
     one_i = torch.empty((1, k), dtype=torch.int64, device=dev)
@@ -1510,6 +1542,7 @@ def headline(line, detail_path):
     if "batched" in line:
         b = line["batched"]
         h["batched_queries_per_s"] = _r(b["batched_queries_per_s"])
+        h["batched_graph_kernels"] = b.get("graph_kernels")
         if b.get("at_recall"):
             h["batched_at_recall_queries_per_s"] = _r(b["at_recall"]["batched_queries_per_s"])
     if "served" in line:

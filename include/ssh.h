@@ -171,7 +171,15 @@ ssh_status ssh_group_query_device(ssh_index* const* handles, int nh, const float
  * plan's pipeline runs on a fixed grid and reads the batch's sizes from device
  * memory, so the pipeline is captured once as a CUDA graph and replayed for
  * each batch; the first batch of a plan runs directly and the graph is
- * captured from it. ssh_batch_create allocates every device buffer: room for
+ * captured from it. After hashing and the candidate unions, the rerank of
+ * every length class (LB_Keogh, the seed DTWs, the bound, the survivors' DTW
+ * with early abandoning, the top-k) runs, for a batch of up to 512 queries,
+ * as one persistent cooperative launch whose blocks claim work items of all
+ * classes from device counters (DTW items at their class's autotuned tiling;
+ * a grid-barrier wait that runs out, about 4 s, ends the batch with
+ * SSH_ETIMEOUT), and for larger batches as per-class kernels, which fill the
+ * GPU by themselves; a plan keeps a captured graph of each form.
+ * ssh_batch_create allocates every device buffer: room for
  * max_queries queries (1 .. 65535), top-k with k <= 1024, and max_pairs
  * (query, candidate) pairs in total (0: max(2^20, 2048 max_queries)); a batch
  * with more candidates grows the pair buffers and reruns. The DTW tiling of
@@ -194,6 +202,12 @@ ssh_status ssh_batch_query(ssh_batch* b, const float* d_queries, const int32_t* 
                            float* d_dists, int32_t* d_which, void* stream);
 ssh_status ssh_batch_stats(const ssh_batch* b, int64_t* pairs, int64_t* dtw, int64_t* pair_capacity,
                            int32_t* graph_kernels);
+/* The rerank's form: mode 1, the one persistent launch; 0, per-class kernels
+ * (envelope and LB_Keogh per class, selections, filters, DTW per class and
+ * pass, top-k); -1 (the default), persistent for batches of at most 512
+ * queries (the serving loop's slots use per-class kernels: slots share the GPU). Both forms give the same results bit for bit. The first batch of a
+ * form runs directly and captures its graph. SSH_EINVAL for another mode. */
+ssh_status ssh_batch_set_persistent(ssh_batch* b, int32_t mode);
 void ssh_batch_destroy(ssh_batch* b);
 
 /* ---- serving loop with continuous batching ----

@@ -86,6 +86,7 @@ _SIGS = {
     "ssh_batch_query": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, _P, _P, _P, _P]),
     "ssh_batch_stats": (ctypes.c_int, [_P, _I64P, _I64P, _I64P, ctypes.POINTER(ctypes.c_int32)]),
     "ssh_batch_destroy": (None, [_P]),
+    "ssh_batch_set_persistent": (ctypes.c_int, [_P, ctypes.c_int32]),
     "ssh_server_create": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int64,
                                          ctypes.POINTER(_P)]),
     "ssh_server_create_ex": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -283,6 +284,11 @@ class SSHBatch:
 
     def stats(self) -> dict:
         return ssh_batch_stats(self.handle)
+
+    def set_persistent(self, on) -> None:
+        """The rerank as one persistent launch (True), as per-class kernels (False), or by batch
+        size (None, the default: persistent up to 512 queries)."""
+        _check(load().ssh_batch_set_persistent(self.handle, -1 if on is None else (1 if on else 0)))
 
     def close(self):
         if self.handle:

@@ -70,6 +70,12 @@ struct BatchStatus {
     unsigned long long pairs;     // candidates of the batch (counted even when over capacity)
     unsigned long long overflow;  // 1: pairs > capacity, nothing was ranked
     unsigned long long dtw[2];    // DTW pairs of the seed and survivor passes
+    // the persistent rerank's work counters and grid barrier (zero on entry), and
+    // its error flag (a barrier wait ran out)
+    unsigned long long rr_work[kRerankWork];
+    unsigned rr_bar[2];
+    unsigned rr_err;
+    unsigned rr_pad;
 };
 
 // The query table, in the order of the sorted queries (class by class).
@@ -241,11 +247,18 @@ struct ssh_batch {
     int64_t max_words = 1;
     cudaStream_t st = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_done = nullptr;
-    cudaGraphExec_t exec = nullptr;
+    cudaGraphExec_t execs[2] = {nullptr, nullptr};  // captured pipelines: per-class rerank, persistent rerank
+    cudaGraphExec_t exec = nullptr;                 // the one the current batch runs
     bool eager = false;           // the launched batch ran without the graph (capture after it)
     int64_t nq = 0;               // queries of the prepared batch
     std::vector<int> q_class;     // their classes, in caller order
     int graph_kernels = 0;
+    int graph_kernels_m[2] = {0, 0};
+    int mode_pref = -1;           // -1: by batch size; 0: per-class rerank kernels; 1: persistent rerank
+    bool persistent = true;       // the current batch's rerank: one persistent launch (else per-class kernels)
+    int rerank_grid = 0;          // blocks of the persistent rerank's last launch
+    RerankClass* d_rcls = nullptr;  // [C] lengths, radii and DTW tilings of the classes
+    int64_t* item_off = nullptr;  // [2 (C + 1)] item layouts of the persistent rerank
     // plan (pinned host copy + device copy)
     unsigned char* h_plan = nullptr;
     unsigned char* d_plan = nullptr;
@@ -315,15 +328,26 @@ ssh_status alloc_pairs(ssh_batch* b, int64_t pcap) {
     return SSH_OK;
 }
 
-void free_plan(ssh_batch* b) {
-    if (b->exec) cudaGraphExecDestroy(b->exec);
+void drop_graphs(ssh_batch* b) {
+    for (int i = 0; i < 2; ++i) {
+        if (b->execs[i]) cudaGraphExecDestroy(b->execs[i]);
+        b->execs[i] = nullptr;
+    }
     b->exec = nullptr;
+}
+
+void free_plan(ssh_batch* b) {
+    drop_graphs(b);
     cudaFreeHost(b->h_plan);
     cudaFree(b->d_plan);
     cudaFree(b->d_cls);
     cudaFreeHost(b->h_cls);
     b->h_cls = nullptr;
     cudaFree(b->hscratch);
+    cudaFree(b->d_rcls);
+    cudaFree(b->item_off);
+    b->d_rcls = nullptr;
+    b->item_off = nullptr;
     b->hscratch = nullptr;
     cudaFree(b->qkeys);
     cudaFree(b->bitmap);
@@ -422,6 +446,14 @@ ssh_status build_plan(ssh_batch* b) {
     if (e == cudaSuccess) e = cudaMalloc(&b->out_ids, (size_t)Q * b->k * 8);
     if (e == cudaSuccess) e = cudaMalloc(&b->out_dists, (size_t)Q * b->k * 4);
     if (e == cudaSuccess) e = cudaMalloc(&b->out_which, (size_t)Q * 4);
+    std::vector<RerankClass> rc(C);
+    for (int c = 0; c < C; ++c) {
+        const ssh_batch::HostClass& hc = b->cls[c];
+        rc[c] = RerankClass{hc.m, hc.rb, hc.plan.S, hc.plan.G, hc.plan.pmask, (int64_t)rerank_dtw_chunk(hc.plan)};
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_rcls, C * sizeof(RerankClass));
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_rcls, rc.data(), C * sizeof(RerankClass), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&b->item_off, (size_t)2 * (C + 1) * 8);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_cls, dev.data(), C * sizeof(ClassDev), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(b->bitmap, 0, (size_t)Q * b->max_words * 4);
     if (e != cudaSuccess) {
@@ -483,6 +515,44 @@ ssh_status enqueue_pipeline(ssh_batch* b) {
     SSH_CUDA(cudaGetLastError());
     const int64_t* n_pairs = b->seg_begin + Q;
     SSH_CUDA(launch_fill_f32(b->dist, b->pcap, n_pairs, __builtin_huge_valf(), st));
+    const float shrink = (float)(1.0 - 4.0 * (b->max_m + 3) * std::ldexp(1.0, -24));
+    if (b->persistent) {
+        // Sec. 3 + Sec. 2.1 + the top-k of every class in one persistent launch
+        RerankArgs ra;
+        ra.nq = d.nq;
+        ra.q_cls = d.q_cls;
+        ra.q_ptr = d.q_ptr;
+        ra.cls = b->d_rcls;
+        ra.seg_begin = b->seg_begin;
+        ra.pair_b = b->pair_b;
+        ra.cand_rows = b->cand_rows;
+        ra.upper = b->upper;
+        ra.lower = b->lower;
+        ra.env_stride = b->max_m;
+        ra.lb = b->lb;
+        ra.dist = b->dist;
+        ra.fb = b->fb;
+        ra.fslot = b->fslot;
+        ra.fcount = b->fcount;
+        ra.fcursor = b->cursor;
+        ra.fbegin = b->fbegin;
+        ra.cls_begin = d.cls_begin;
+        ra.C = C;
+        ra.item_off = b->item_off;
+        ra.T = b->T;
+        ra.U = b->U;
+        ra.k = b->k;
+        ra.shrink = shrink;
+        ra.out = TopkOut{b->out_ids, b->out_dists, d.q_pos, nullptr, d.q_gid, b->out_which, d.q_which, d.nq};
+        ra.dtw_counts = b->d_status->dtw;
+        ra.overflow = &b->d_status->overflow;
+        ra.work = b->d_status->rr_work;
+        ra.bar = b->d_status->rr_bar;
+        ra.err = &b->d_status->rr_err;
+        SSH_CUDA(launch_rerank(ra, b->max_m, st, &b->rerank_grid));
+        SSH_CUDA(cudaMemcpyAsync(b->h_status, b->d_status, sizeof(BatchStatus), cudaMemcpyDeviceToHost, st));
+        return SSH_OK;
+    }
     // Sec. 3: LB_Keogh of every candidate against its query's envelope
     for (int c = 0; c < C; ++c) {
         const ssh_batch::HostClass& hc = b->cls[c];
@@ -497,7 +567,6 @@ ssh_status enqueue_pipeline(ssh_batch* b) {
     // distance; DTW of the others only where LB (1 - eta) stays below it
     SSH_CUDA(launch_select_kth_u32(reinterpret_cast<const uint32_t*>(b->lb), b->seg_begin, Q, kSeedFactor * b->k, b->T,
                                        st));
-    const float shrink = (float)(1.0 - 4.0 * (b->max_m + 3) * std::ldexp(1.0, -24));
     for (int mode = 0; mode < 2; ++mode) {
         if (mode == 1)
             SSH_CUDA(launch_select_kth_u32(reinterpret_cast<const uint32_t*>(b->dist), b->seg_begin, Q, b->k, b->U, st));
@@ -525,10 +594,12 @@ ssh_status enqueue_pipeline(ssh_batch* b) {
 }
 
 ssh_status capture(ssh_batch* b) {
-    if (b->exec) {
-        cudaGraphExecDestroy(b->exec);
-        b->exec = nullptr;
+    const int mode = b->persistent ? 1 : 0;
+    if (b->execs[mode]) {
+        cudaGraphExecDestroy(b->execs[mode]);
+        b->execs[mode] = nullptr;
     }
+    b->exec = nullptr;
     const long long l0 = t_launches;
     SSH_CUDA(cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal));
     ssh_status s = enqueue_pipeline(b);
@@ -551,10 +622,11 @@ ssh_status capture(ssh_batch* b) {
         cudaGraphNodeType t;
         if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kernels;
     }
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, g, 0);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->execs[mode], g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return cuda_status(e, "batch graph instantiate");
-    b->graph_kernels = kernels;
+    b->exec = b->execs[mode];
+    b->graph_kernels = b->graph_kernels_m[mode] = kernels;
     return SSH_OK;
 }
 
@@ -643,6 +715,12 @@ ssh_status batch_prepare(ssh_batch* b, const float* d_queries, const int32_t* le
 // kernels themselves for a plan's first batch); returns without waiting.
 ssh_status batch_launch(ssh_batch* b) {
     for (ssh_index* h : b->handles) SSH_CUDA(cudaStreamWaitEvent(b->st, h->ready, 0));  // latest adds' tables
+    // the rerank's form: one persistent launch balances the work of few queries over every
+    // SM; a large batch fills the GPU with per-class kernels, which measured faster there
+    const int mode = b->mode_pref >= 0 ? b->mode_pref : (b->nq <= kPersistentMaxQueries ? 1 : 0);
+    b->persistent = mode == 1;
+    b->exec = b->execs[mode];
+    b->graph_kernels = b->graph_kernels_m[mode];
     b->eager = b->exec == nullptr;
     if (b->eager) {
         SSH_TRY(enqueue_pipeline(b));
@@ -676,11 +754,12 @@ ssh_status batch_finish(ssh_batch* b, int64_t reserve_bytes) {
                                    (long long)reserve_bytes);
         }
         SSH_TRY(alloc_pairs(b, cap));
-        if (b->exec) cudaGraphExecDestroy(b->exec);
-        b->exec = nullptr;
+        drop_graphs(b);  // both captured the old pair buffers
         SSH_TRY(batch_launch(b));
         SSH_CUDA(cudaEventSynchronize(b->ev_done));
     }
+    if (b->h_status->rr_err)
+        return fail_status(SSH_ETIMEOUT, "the persistent rerank's grid barrier gave up (a block did not arrive)");
     if (b->eager) SSH_TRY(capture(b));
     b->eager = false;
     for (size_t h = 0; h < b->handles.size(); ++h) {
@@ -794,6 +873,13 @@ ssh_status ssh_batch_stats(const ssh_batch* b, int64_t* pairs, int64_t* dtw, int
     if (dtw) *dtw = (int64_t)(b->h_status->dtw[0] + b->h_status->dtw[1]);
     if (pair_capacity) *pair_capacity = b->pcap;
     if (graph_kernels) *graph_kernels = b->graph_kernels;
+    return SSH_OK;
+}
+
+ssh_status ssh_batch_set_persistent(ssh_batch* b, int32_t mode) {
+    if (!b) return fail_status(SSH_EINVAL, "NULL batch");
+    if (mode < -1 || mode > 1) return fail_status(SSH_EINVAL, "mode %d is not -1, 0 or 1", (int)mode);
+    b->mode_pref = mode;
     return SSH_OK;
 }
 

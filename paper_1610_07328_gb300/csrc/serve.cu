@@ -334,6 +334,9 @@ ssh_status ssh_server_create_ex(ssh_index* const* handles, int nh, int k, int ma
             if (i > 0) status = SSH_OK;  // keep the slots made so far
             break;
         }
+        // slots overlap on the GPU: the per-class rerank shares the SMs, while the persistent
+        // rerank (a cooperative launch over every SM) would wait for the other slots to drain
+        ssh_batch_set_persistent(sl.b, 0);
         const size_t qbytes = (size_t)max_batch * std::max(s->max_len, 1) * sizeof(float);
         cudaError_t e = cudaMalloc(&sl.d_q, qbytes);
         if (e == cudaSuccess) e = cudaMallocHost(&sl.h_q, qbytes);

@@ -306,6 +306,52 @@ struct TopkOut {
 cudaError_t launch_topk_output(const TopkOut& o, const uint64_t* keys, const int64_t* seg_begin, const uint64_t* kth,
                                int64_t nseg, int k, cudaStream_t st);
 
+// The whole rerank of a batch plan in one persistent cooperative launch
+// (batch_rerank.cu): per length class its length, radius and DTW tiling.
+struct RerankClass {
+    int m, rb, S, G, pmask;
+    int64_t dtw_chunk;  // pairs per DTW work item
+};
+struct RerankArgs {
+    const int64_t* nq;                // [1] queries of the batch (sorted by class)
+    const int32_t* q_cls;             // [Q] class of each sorted query
+    const float* const* q_ptr;        // [Q] query samples
+    const RerankClass* cls;           // [C]
+    const int64_t* seg_begin;         // [Q + 1] each query's candidate pairs
+    const float** pair_b;             // [P] candidate rows
+    const uint32_t* cand_rows;        // [P] their rows in the class's sub-index
+    float *upper, *lower;             // [Q][env_stride] envelopes
+    int64_t env_stride;
+    float* lb;                        // [P]
+    float* dist;                      // [P], +inf on entry
+    const float** fb;                 // [P] the pass's pairs
+    int64_t* fslot;                   // [P] their slots
+    int64_t* fcount;                  // [Q]
+    unsigned long long* fcursor;      // [Q]
+    int64_t* fbegin;                  // [Q + 1]
+    const int64_t* cls_begin;         // [C + 1] first sorted query of each class
+    int C;                            // classes
+    int64_t* item_off;                // [2 (C + 1)] item layouts of the LB pass and of a DTW pass
+    uint32_t *T, *U;                  // [Q]
+    int k;
+    float shrink;
+    TopkOut out;
+    unsigned long long* dtw_counts;   // [2] pairs of the seed and survivor passes (added)
+    const unsigned long long* overflow;
+    unsigned long long* work;         // [kRerankWork] item counters, zero on entry
+    unsigned* bar;                    // [2] grid barrier (count zero on entry, generation)
+    unsigned* err;                    // set when a barrier wait ran out (zero on entry)
+};
+constexpr int kRerankWork = 12;
+// Batches of at most this many queries rerank in the persistent launch by default
+// (measured on mixed lengths 128 .. 2048: 1.07x faster at 64 queries, 1.67x at 256,
+// 1.12x slower at 1024 and 1.49x slower at 4096, where per-class kernels fill the
+// GPU by themselves).
+constexpr int64_t kPersistentMaxQueries = 512;
+size_t rerank_smem_bytes(int max_m);
+int rerank_dtw_chunk(const DtwPlan& pl);
+cudaError_t launch_rerank(const RerankArgs& a, int max_m, cudaStream_t st, int* grid_out);
+
 // Batch plans, asynchronously (the server's slots): prepare writes the query
 // table (queries back to back at d_queries), launch starts the batch on the
 // plan's stream, done polls it, finish waits (and reruns an overflowed batch),

@@ -274,3 +274,46 @@ def test_long_shingles_hash_and_query_match_the_oracle(n):
         oi, od = ref.query(q, 5)
         assert_topk_match(q, q_ids[i], q_d[i], oi, od, lambda j: x[j], rb)
     assert st["candidates"] == sum(len(ref.candidates(q)) for q in qs)
+
+
+@pytest.mark.parametrize("n,K", [(15, 4), (8, 1)], ids=["config4-params", "many-candidates"])
+def test_persistent_rerank_equals_per_class_kernels_at_all_lengths(n, K):
+    """The batch's rerank as one persistent launch and as per-class kernels give the same rows
+    bit for bit at every length class (128 .. 2048, radii 6 .. 102), directly and replayed,
+    and both equal the oracle's Algorithm 2; the persistent plan's graph holds far fewer
+    kernels."""
+    b = _binding()
+    lens = (128, 256, 512, 1024, 2048)
+    nrows = {128: 300, 256: 300, 512: 250, 1024: 200, 2048: 150}
+    dbs = {m: synth.random_walk(nrows[m], m, seed=m + 21) for m in lens}
+    cfgs = {m: dict(W=m // 8, delta=3, n=n, K=K, L=25, band=0.05, seed=0) for m in lens}
+    idxs, refs = [], {}
+    try:
+        for m in lens:
+            ix = _index(cfgs[m])
+            ix.add(dbs[m])
+            idxs.append(ix)
+            refs[m] = oracle.OracleIndex(**cfgs[m])
+            refs[m].add(dbs[m])
+        k = 10
+        kernels = {}
+        with b.SSHBatch(idxs, max_queries=40, k=k) as bt:
+            for rep in range(2):
+                qs, qlens = _mixed(dbs, lens, 30 + 5 * rep, seed=60 + rep)
+                rows = {}
+                for persistent in (True, False):
+                    bt.set_persistent(persistent)
+                    for _ in range(2):  # the first batch after the switch runs directly, the second replays
+                        rows[persistent] = _run_batch(bt, qs, qlens, k)
+                    kernels[persistent] = bt.stats()["graph_kernels"]
+                for x, y in zip(rows[True], rows[False]):
+                    assert np.array_equal(x, y)
+                ids, dd, which = rows[True]
+                for i, (q, m) in enumerate(zip(qs, qlens)):
+                    assert which[i] == lens.index(m)
+                    oi, od = refs[m].query(q, k)
+                    assert_topk_match(q, ids[i], dd[i], oi, od, lambda j: dbs[m][j], oracle.band_radius(0.05, m))
+        assert kernels[True] < kernels[False] and kernels[True] <= 30, kernels
+    finally:
+        for ix in idxs:
+            ix.close()
