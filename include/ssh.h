@@ -438,7 +438,11 @@ ssh_status ssh_lb_keogh_device(const float* d_a, const int64_t* d_a_idx, const f
 ssh_status ssh_lb_bound_device(const float* d_a, const int64_t* d_a_idx, const float* d_b, const int64_t* d_b_idx,
                                int64_t npairs, int32_t m, int32_t rb, int32_t kind, float* d_out, void* stream);
 
-/* Measurement helper, not part of the method: reads the `bytes` bytes at d_buf
+/* ---- measurement-only export ----
+ *
+ * Not part of the method and not used by any other entry point: it gives the
+ * benchmark the L2 read bandwidth that bounds the minhash kernel's gathers.
+ * Reads the `bytes` bytes at d_buf
  * (16-byte aligned, bytes a multiple of 16) `passes` times in one kernel launch
  * on `stream`, with loads that bypass L1, and returns once the launch is enqueued.
  * A buffer that fits in L2 gives the L2 read bandwidth when the caller times the

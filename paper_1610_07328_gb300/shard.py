@@ -30,13 +30,15 @@ def merge_topk(ids: np.ndarray, dists: np.ndarray, k: int) -> tuple[np.ndarray, 
     flat_d = dists.transpose(1, 0, 2).reshape(nq, r * kk).astype(np.float64)
     flat_d = np.where(flat_i < 0, np.inf, flat_d)
     id_key = np.where(flat_i < 0, np.iinfo(np.int64).max, flat_i)
+    # every row at once: order by (distance, id), empty slots last, keep the first k
+    order = np.lexsort((id_key, flat_d), axis=-1)[:, :k]
+    top_i = np.take_along_axis(flat_i, order, axis=1).astype(np.int64)
+    top_d = np.take_along_axis(flat_d, order, axis=1)
     out_i = np.full((nq, k), -1, np.int64)
     out_d = np.full((nq, k), np.inf, np.float32)
-    for q in range(nq):
-        order = np.lexsort((id_key[q], flat_d[q]))[:k]
-        keep = flat_i[q, order] >= 0
-        out_i[q, :keep.sum()] = flat_i[q, order][keep]
-        out_d[q, :keep.sum()] = flat_d[q, order][keep]
+    w = top_i.shape[1]
+    out_i[:, :w] = np.where(top_i >= 0, top_i, -1)
+    out_d[:, :w] = np.where(top_i >= 0, top_d, np.inf).astype(np.float32)
     return out_i, out_d
 
 
