@@ -319,7 +319,9 @@ ssh_status ssh_set_option(ssh_index* idx, ssh_option opt, int64_t value);
 /* Counters since the last ssh_reset_stats (all cumulative). */
 typedef struct ssh_stats {
     int64_t series_hashed;     /* series and queries hashed (Sec. 4.1-4.3) */
-    int64_t sketch_fp64;       /* sketch windows recomputed in FP64 (|r.x| near 0) */
+    int64_t sketch_fp64;       /* sketch windows near the sign boundary (|r.x| <= tau ||r|| ||x||), decided
+                                  apart from the FP32 pass: by an error-bounded compensated FP32 dot product,
+                                  else in FP64 */
     int64_t cws_fp64;          /* minhashes recomputed in FP64 (near ties / floor steps) */
     int64_t queries;           /* queries answered */
     int64_t candidates;        /* sum over queries of |R| (Alg. 2 union) */

@@ -202,8 +202,63 @@ __global__ void __launch_bounds__(kSketchWarps * 32, 3)
     if (n_inplace && a.stats) atomicAdd(&a.stats[kStatSketch64], n_inplace);
 }
 
-// One thread per listed window: FP64 in the definition's order (the FP32 x FP32
-// products are exact in FP64, so an FMA equals the separate multiply and add).
+// Sign of the FP64 dot product r . x (W terms, FP32 inputs, summed in order as
+// the definition does) from FP32 arithmetic where an error bound settles it:
+// Ogita, Rump & Oishi's Dot2 ("Accurate sum and dot product", SIAM J. Sci.
+// Comput. 26(6), 2005: TwoProduct by FMA, TwoSum, the errors summed apart)
+// returns res with |res - r.x| <= u |r.x| + g^2 sum |r_i x_i| (u = 2^-24,
+// g = W u / (1 - W u)), and the FP64 chain errs by at most
+// g64 sum |r_i x_i| (g64 = W 2^-53 / (1 - W 2^-53)). When |res| exceeds both
+// with a margin, r.x and its FP64 value are nonzero and have the sign of res.
+// Returns 1 (bit 1), 0 (bit 0) or -1 (not settled: recompute in FP64). Terms
+// whose error-free product could underflow (a nonzero factor below 2^-50) are
+// left to FP64 too.
+struct Dot2 {
+    float p = 0.f, s = 0.f, sabs = 0.f;
+    bool tiny = false;
+    __device__ __forceinline__ void add(float rj, float xj) {
+        const float ar = fabsf(rj), ax = fabsf(xj);
+        tiny |= (ar != 0.f && ar < 8.8817842e-16f) || (ax != 0.f && ax < 8.8817842e-16f);  // 2^-50
+        const float h = __fmul_rn(rj, xj);
+        const float e = __fmaf_rn(rj, xj, -h);  // rj xj = h + e exactly
+        const float q = __fadd_rn(p, h);        // TwoSum(p, h) = q + f exactly
+        const float z = __fsub_rn(q, p);
+        const float f = __fadd_rn(__fsub_rn(p, __fsub_rn(q, z)), __fsub_rn(h, z));
+        p = q;
+        s = __fadd_rn(s, __fadd_rn(f, e));
+        sabs = __fmaf_ru(ar, ax, sabs);  // an upper bound of sum |r_j x_j|
+    }
+};
+
+__device__ __forceinline__ int dot2_sign(const float* r, const float* x, int W) {
+    Dot2 d;
+    int j = 0;
+    for (; j + 8 <= W; j += 8) {  // groups of 8: the loads are issued together
+        float rv[8], xv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            rv[u] = __ldg(r + j + u);
+            xv[u] = __ldg(x + j + u);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) d.add(rv[u], xv[u]);
+    }
+    for (; j < W; ++j) d.add(__ldg(r + j), __ldg(x + j));
+    const float p = d.p, s = d.s, sabs = d.sabs;
+    const bool tiny = d.tiny;
+    const float res = __fadd_rn(p, s);
+    // 2 (g^2 + g64) <= 2.002 (W u)^2 + 2.221e-16 W for W <= 8192 (W u <= 5e-4); FP32 rounding of
+    // the factor is covered by the slack in its constants
+    const float wu = (float)W * 5.9604645e-08f;
+    const float fac = 2.01f * wu * wu + 2.3e-16f * (float)W;
+    const float bound = __fadd_ru(__fmul_ru(fac, sabs), __fmul_ru(fabsf(res), 2.384185791015625e-07f));
+    if (tiny || !(fabsf(res) > bound)) return -1;
+    return res > 0.f ? 1 : 0;
+}
+
+// One thread per listed window: the sign by dot2_sign, else FP64 in the
+// definition's order (the FP32 x FP32 products are exact in FP64, so an FMA
+// equals the separate multiply and add).
 __global__ void sketch_fixup_kernel(HashArgs a, uint32_t* bits, const unsigned long long* fix,
                                     const unsigned long long* nfix, unsigned long long cap) {
     const unsigned long long n = min(*nfix, cap);
@@ -213,6 +268,11 @@ __global__ void sketch_fixup_kernel(HashArgs a, uint32_t* bits, const unsigned l
         const int64_t row = (int64_t)(v >> 16);
         const int i = (int)(v & 0xFFFFu);
         const float* xw = row_ptr(a, row) + i * a.delta;
+        const int sg = dot2_sign(a.r, xw, a.W);
+        if (sg >= 0) {
+            if (sg) atomicOr(&bits[row * a.nwords + (i >> 5)], 1u << (31 - (i & 31)));
+            continue;
+        }
         double d = 0.0;
         int j = 0;
         // groups of 8: the loads are issued together, the FMAs stay in the definition's order
@@ -836,6 +896,11 @@ __global__ void stream_fixup_kernel(HashArgs a, const float* s, uint32_t* bits, 
          t += (unsigned long long)gridDim.x * blockDim.x) {
         const int64_t j = (int64_t)fix[t];
         const float* xw = s + j;
+        const int sg = dot2_sign(a.r, xw, a.W);
+        if (sg >= 0) {
+            if (sg) atomicOr(&bits[j >> 5], 1u << (31 - (j & 31)));
+            continue;
+        }
         double d = 0.0;
         for (int q = 0; q < a.W; ++q) d = fma((double)__ldg(a.r + q), (double)__ldg(xw + q), d);
         if (d >= 0.0) atomicOr(&bits[j >> 5], 1u << (31 - (j & 31)));
