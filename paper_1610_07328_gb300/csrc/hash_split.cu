@@ -27,6 +27,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <cstring>
 
 #include "hash_common.cuh"
 #include "ssh_internal.cuh"
@@ -83,10 +84,25 @@ __host__ __device__ inline int sketch_xb(int m, int W, int DELTA, int R, int LPS
 
 // The filter as a by-value kernel parameter: it sits in the constant bank and
 // every FMA reads its tap from there, leaving the registers to the windows.
-template <int W>
+// v2[j] packs the taps that sample t meets in two neighbouring windows k, k+1
+// of a lane (j = t - k DELTA): r[j] (0 past the filter) in the low half and
+// r[j - DELTA] (0 before it) in the high half, for one paired FMA.
+template <int W, int DELTA>
 struct FilterParam {
     float v[W];
+    unsigned long long v2[W + DELTA];
 };
+
+#ifndef SSH_SKETCH_PAIRED
+#define SSH_SKETCH_PAIRED 1
+#endif
+
+// (d.lo, d.hi) = (a.lo * b.lo + c.lo, a.hi * b.hi + c.hi), each half rounded once as fmaf.
+__device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsigned long long b, unsigned long long c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
 
 // Provisional bits go to `bits`; windows needing FP64 go to fix[0..cap) as
 // (row << 16 | window), counted in *nfix. If the list is full the window is
@@ -98,7 +114,7 @@ struct FilterParam {
 // FMAs.
 template <int W, int DELTA, int R, int SPW>
 __global__ void __launch_bounds__(kSketchWarps * 32, 3)
-    sketch_kernel(HashArgs a, const FilterParam<W> rp, uint32_t* bits, unsigned long long* fix,
+    sketch_kernel(HashArgs a, const FilterParam<W, DELTA> rp, uint32_t* bits, unsigned long long* fix,
                   unsigned long long fix_cap, unsigned long long* nfix) {
     constexpr int STRIP = W + (R - 1) * DELTA;
     constexpr int LPS = 32 / SPW;
@@ -142,10 +158,41 @@ __global__ void __launch_bounds__(kSketchWarps * 32, 3)
             // the R dot products and the energy of the lane's strip of STRIP samples,
             // which holds every window of the lane: ||x_window||^2 <= strip energy
             float acc[R];
-#pragma unroll
-            for (int k = 0; k < R; ++k) acc[k] = 0.f;
             float e = 0.f;
             const float* xs = x + ll * R * DELTA;
+            // windows 2p and 2p + 1 in one paired FMA per sample: each half gets the
+            // same FMAs in the same order as alone (the zero taps only add +-0 to a
+            // sum, which changes no nonzero value and no sign test). Up to 10 windows
+            // per lane: more leave too few registers for the pairs.
+            if constexpr (SSH_SKETCH_PAIRED && R <= 10) {
+            constexpr int NP = R / 2;
+            unsigned long long acc2[NP > 0 ? NP : 1];
+#pragma unroll
+            for (int q = 0; q < NP; ++q) acc2[q] = 0ull;
+            float acc_odd = 0.f;
+#pragma unroll
+            for (int t = 0; t < STRIP; ++t) {
+                const float xv = xs[t];
+                e = fmaf(xv, xv, e);
+                unsigned long long xx;
+                asm("mov.b64 %0, {%1, %1};" : "=l"(xx) : "f"(xv));
+#pragma unroll
+                for (int q = 0; q < NP; ++q) {
+                    const int j = t - 2 * q * DELTA;
+                    if (j >= 0 && j < W + DELTA) acc2[q] = ffma2(rp.v2[j], xx, acc2[q]);
+                }
+                if constexpr ((R & 1) != 0) {
+                    const int j = t - (R - 1) * DELTA;
+                    if (j >= 0 && j < W) acc_odd = fmaf(rp.v[j], xv, acc_odd);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < NP; ++q)
+                asm("mov.b64 {%0, %1}, %2;" : "=f"(acc[2 * q]), "=f"(acc[2 * q + 1]) : "l"(acc2[q]));
+            if constexpr ((R & 1) != 0) acc[R - 1] = acc_odd;
+            } else {
+#pragma unroll
+            for (int k = 0; k < R; ++k) acc[k] = 0.f;
 #pragma unroll
             for (int t = 0; t < STRIP; ++t) {
                 const float xv = xs[t];
@@ -155,6 +202,7 @@ __global__ void __launch_bounds__(kSketchWarps * 32, 3)
                     const int j = t - k * DELTA;
                     if (j >= 0 && j < W) acc[k] = fmaf(rp.v[j], xv, acc[k]);
                 }
+            }
             }
             // e carries at most STRIP roundings of relative 2^-24 each: inflate it past them
             const float e_up = __fmul_ru(e, 1.0f + (float)(2 * STRIP + 64) * 5.9604645e-08f);
@@ -739,9 +787,16 @@ cudaError_t launch_sketch_t(const HashArgs& a, uint32_t* bits, unsigned long lon
     int64_t grid = (int64_t)sms_of_device() * (per_sm > 0 ? per_sm : 1);
     const int64_t need = ((a.count + SPW - 1) / SPW + kSketchWarps - 1) / kSketchWarps;
     if (grid > need) grid = need;
-    FilterParam<W> rp;
+    FilterParam<W, DELTA> rp;
     if (!a.r_host) return cudaErrorInvalidValue;
     for (int j = 0; j < W; ++j) rp.v[j] = a.r_host[j];
+    for (int j = 0; j < W + DELTA; ++j) {
+        const float lo = j < W ? a.r_host[j] : 0.f, hi = j >= DELTA ? a.r_host[j - DELTA] : 0.f;
+        uint32_t ul, uh;
+        memcpy(&ul, &lo, 4);
+        memcpy(&uh, &hi, 4);
+        rp.v2[j] = ((unsigned long long)uh << 32) | ul;
+    }
     sketch_kernel<W, DELTA, R, SPW><<<(unsigned)grid, kSketchWarps * 32, smem, st>>>(a, rp, bits, fix, cap, nfix);
     note_launch();
     return cudaGetLastError();
