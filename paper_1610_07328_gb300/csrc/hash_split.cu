@@ -353,7 +353,7 @@ __device__ __forceinline__ uint32_t set_count(uint32_t v) { return v >> 16; }
 // position inserted the id first), and, when the caller asked for the sorted
 // set, the set itself for ranking.
 struct ShingleLayout {
-    int tbits, tab, pos, cid, total;
+    int tbits, tab, pos, stage, cid, total;
 };
 
 __host__ __device__ inline ShingleLayout shingle_layout(int S, bool sorted_out) {
@@ -363,6 +363,7 @@ __host__ __device__ inline ShingleLayout shingle_layout(int S, bool sorted_out) 
     int off = 0;
     L.tab = off; off += a16(4 << L.tbits);
     L.pos = off; off += a16(4 * S);
+    L.stage = off; off += a16(4 * S);  // the repeated shingles before they follow the count-1 ones
     L.cid = off; off += sorted_out ? a16(4 * S) : 0;
     L.total = off;
     return L;
@@ -390,6 +391,7 @@ __global__ void __launch_bounds__(256) shingle_kernel(HashArgs a, const uint32_t
     unsigned char* wb = smem + (size_t)warp * lay.total;
     uint32_t* tab = reinterpret_cast<uint32_t*>(wb + lay.tab);
     uint32_t* pos = reinterpret_cast<uint32_t*>(wb + lay.pos);
+    uint32_t* stage = reinterpret_cast<uint32_t*>(wb + lay.stage);
     uint32_t* cid = reinterpret_cast<uint32_t*>(wb + lay.cid);
     const uint32_t tmask = (1u << lay.tbits) - 1u;
     const int tshift = 32 - lay.tbits;
@@ -436,22 +438,10 @@ __global__ void __launch_bounds__(256) shingle_kernel(HashArgs a, const uint32_t
             hi = lo;
         }
         __syncwarp();
-        int n1 = 0, nm = 0;
-        for (int t = 0; t < rounds; ++t) {
-            const int i = lane + 32 * t;
-            bool one = false, more = false;
-            if (i < S) {
-                const uint32_t p = pos[i];
-                if (p & kOwner) {
-                    one = set_count(tab[p & ~kOwner]) == 1u;
-                    more = !one;
-                }
-            }
-            n1 += __popc(__ballot_sync(kFull, one));
-            nm += __popc(__ballot_sync(kFull, more));
-        }
+        // one pass over the positions: owners write count-1 ids at once and stage the
+        // repeated ones (they follow the count-1 ids), and clear their slots
         uint32_t* out = sets + row * S;
-        int o1 = 0, om = n1;
+        int o1 = 0, om = 0;
         for (int t = 0; t < rounds; ++t) {
             const int i = lane + 32 * t;
             bool one = false, more = false;
@@ -460,18 +450,26 @@ __global__ void __launch_bounds__(256) shingle_kernel(HashArgs a, const uint32_t
                 const uint32_t p = pos[i];
                 if (p & kOwner) {
                     v = tab[p & ~kOwner];
+                    tab[p & ~kOwner] = 0u;
                     one = set_count(v) == 1u;
                     more = !one;
                 }
             }
             const unsigned b1 = __ballot_sync(kFull, one), bm = __ballot_sync(kFull, more);
-            const int e = one ? o1 + __popc(b1 & lt) : om + __popc(bm & lt);
-            if (one || more) {
-                out[e] = one ? set_id(v) : v;
+            if (one) {
+                const int e = o1 + __popc(b1 & lt);
+                out[e] = set_id(v);
                 if (sorted_out) cid[e] = v;
             }
+            if (more) stage[om + __popc(bm & lt)] = v;
             o1 += __popc(b1);
             om += __popc(bm);
+        }
+        __syncwarp();
+        const int n1 = o1, nm = om;
+        for (int e = lane; e < nm; e += 32) {
+            out[n1 + e] = stage[e];
+            if (sorted_out) cid[n1 + e] = stage[e];
         }
         __syncwarp();
         const int nnz = n1 + nm;
@@ -489,13 +487,6 @@ __global__ void __launch_bounds__(256) shingle_kernel(HashArgs a, const uint32_t
         if (lane == 0) {
             sizes[row] = make_int2(n1, nm);
             if (a.nnz_out) a.nnz_out[row] = nnz;
-        }
-        for (int t = 0; t < rounds; ++t) {
-            const int i = lane + 32 * t;
-            if (i < S) {
-                const uint32_t p = pos[i];
-                if (p & kOwner) tab[p & ~kOwner] = 0u;
-            }
         }
         __syncwarp();
     }
