@@ -122,12 +122,13 @@ __global__ void bin_scatter_kernel(const uint64_t* keys, int64_t row0, int64_t n
 //
 // Bins of about 16 rows number 2^B (B up to 24): one scatter into all of them
 // writes every entry to a random place. Large tables are partitioned in two
-// passes instead: pass 1 scatters by the top b1 = B/2 key bits through
-// per-block shared-memory histograms, so each block writes contiguous runs per
-// bucket; pass 2 takes one bucket (a few thousand entries, which stay in L2)
-// per block and places its entries into the bucket's 2^(B-b1) bins.
+// passes instead: pass 1 scatters by the top b1 = min(12, B - 7) key bits
+// through per-block shared-memory histograms over chunks of 4,096 rows, so each
+// block writes contiguous runs per bucket; pass 2 takes one bucket (1-2K
+// entries at the usual sizes) per block and places its entries into the
+// bucket's 2^(B-b1) bins in shared memory before writing them out.
 
-constexpr int kPartThreads = 256;
+constexpr int kPartThreads = 512;
 constexpr int kPartItems = 8;                             // rows per thread of pass 1
 constexpr int kPartChunk = kPartThreads * kPartItems;     // rows per block of pass 1
 
@@ -274,34 +275,80 @@ __global__ void __launch_bounds__(kPartThreads) part_scatter_kernel(const uint64
 
 // Pass 2: bucket d of table l into its 2^b2 bins (bins[l][(d << b2) + e] = bin
 // start; the bucket's block also writes bins[l][2^B] = n when it is the last).
-// Each thread holds kRegionItems entries of a tile in registers: their loads
-// are issued together, counted, and placed from the same registers.
-constexpr int kRegionItems = 8;
+// A bucket of at most kRegionTile entries (all of them at the usual sizes) is
+// read once into registers, counted, placed in shared memory at its bin's
+// position and written out with consecutive threads on consecutive addresses.
+// A larger bucket is taken a tile at a time: one pass counts, a second places
+// each entry straight into the output through the shared bin cursors.
+constexpr int kRegionThreads = 256;
+constexpr int kRegionItems = 12;
+constexpr int kRegionTile = kRegionThreads * kRegionItems;
 
-__global__ void __launch_bounds__(kPartThreads) part_region_kernel(const uint64_t* tk, const uint32_t* tr, int64_t n,
-                                                                   const uint32_t* bstart, int b1, int b2,
-                                                                   int64_t out_stride, uint32_t* bins,
-                                                                   uint64_t* skeys, uint32_t* srows) {
-    extern __shared__ uint32_t sm[];
-    uint32_t* h = sm;                      // [2^b2]
-    uint32_t* part = sm + (1 << b2);       // [blockDim.x]
+size_t region_smem(int b2) {
+    return (size_t)kRegionTile * 12 + ((size_t)(1 << b2) + kRegionThreads) * sizeof(uint32_t);
+}
+
+__global__ void __launch_bounds__(kRegionThreads) part_region_kernel(const uint64_t* tk, const uint32_t* tr, int64_t n,
+                                                                     const uint32_t* bstart, int b1, int b2,
+                                                                     int64_t out_stride, uint32_t* bins,
+                                                                     uint64_t* skeys, uint32_t* srows) {
+    extern __shared__ __align__(16) unsigned char rsm[];
     const int d = blockIdx.x, l = blockIdx.y, nb = 1 << b1, n2 = 1 << b2;
+    uint64_t* pkey = reinterpret_cast<uint64_t*>(rsm);                                   // [kRegionTile]
+    uint32_t* prow = reinterpret_cast<uint32_t*>(pkey + kRegionTile);                    // [kRegionTile]
+    uint32_t* h = prow + kRegionTile;                                                    // [2^b2]
+    uint32_t* part = h + n2;                                                             // [blockDim.x]
     const uint32_t* bs = bstart + (int64_t)l * (nb + 1);
     const int64_t s0 = bs[d], s1 = bs[d + 1];
     const uint64_t* tkl = tk + (int64_t)l * n;
     const uint32_t* trl = tr + (int64_t)l * n;
     const int shift = 64 - b1 - b2;
     const uint32_t mask = (uint32_t)n2 - 1u;
-    constexpr int kTile = kPartThreads * kRegionItems;
     for (int i = threadIdx.x; i < n2; i += blockDim.x) h[i] = 0u;
     __syncthreads();
+    uint32_t* bl = bins + (int64_t)l * (((int64_t)nb << b2) + 1);
+    uint64_t* sk = skeys + (int64_t)l * out_stride;
+    uint32_t* sr = srows + (int64_t)l * out_stride;
     uint64_t key[kRegionItems];
     uint32_t row[kRegionItems];
-    // counts (the first tile stays in registers for the placement)
-    for (int64_t t0 = s0; t0 < s1; t0 += kTile) {
+    if (s1 - s0 <= kRegionTile) {
+        const int cnt = (int)(s1 - s0);
+        uint32_t rnk[kRegionItems];
 #pragma unroll
         for (int u = 0; u < kRegionItems; ++u) {
-            const int64_t i = t0 + u * kPartThreads + threadIdx.x;
+            const int i = u * kRegionThreads + threadIdx.x;
+            if (i < cnt) {
+                key[u] = tkl[s0 + i];
+                row[u] = trl[s0 + i];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kRegionItems; ++u)
+            if (u * kRegionThreads + (int)threadIdx.x < cnt) rnk[u] = atomicAdd(&h[(uint32_t)(key[u] >> shift) & mask], 1u);
+        __syncthreads();
+        block_exclusive_scan(h, n2, part);
+        for (int i = threadIdx.x; i < n2; i += blockDim.x) bl[((int64_t)d << b2) + i] = (uint32_t)s0 + h[i];
+        if (d == nb - 1 && threadIdx.x == 0) bl[(int64_t)nb << b2] = (uint32_t)s1;
+#pragma unroll
+        for (int u = 0; u < kRegionItems; ++u) {
+            if (u * kRegionThreads + (int)threadIdx.x < cnt) {
+                const uint32_t at = h[(uint32_t)(key[u] >> shift) & mask] + rnk[u];  // < cnt
+                pkey[at] = key[u];
+                prow[at] = row[u];
+            }
+        }
+        __syncthreads();
+        for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
+            sk[s0 + j] = pkey[j];
+            sr[s0 + j] = prow[j];
+        }
+        return;
+    }
+    // counts (the first tile stays in registers for the placement)
+    for (int64_t t0 = s0; t0 < s1; t0 += kRegionTile) {
+#pragma unroll
+        for (int u = 0; u < kRegionItems; ++u) {
+            const int64_t i = t0 + u * kRegionThreads + threadIdx.x;
             uint64_t kk = 0;
             if (i < s1) kk = tkl[i];
             if (t0 == s0) key[u] = kk;
@@ -310,19 +357,16 @@ __global__ void __launch_bounds__(kPartThreads) part_region_kernel(const uint64_
     }
     __syncthreads();
     block_exclusive_scan(h, n2, part);
-    uint32_t* bl = bins + (int64_t)l * (((int64_t)nb << b2) + 1);
     for (int i = threadIdx.x; i < n2; i += blockDim.x) {
         bl[((int64_t)d << b2) + i] = (uint32_t)s0 + h[i];
         h[i] += (uint32_t)s0;  // now the placement cursors
     }
     if (d == nb - 1 && threadIdx.x == 0) bl[(int64_t)nb << b2] = (uint32_t)s1;
     __syncthreads();
-    uint64_t* sk = skeys + (int64_t)l * out_stride;
-    uint32_t* sr = srows + (int64_t)l * out_stride;
-    for (int64_t t0 = s0; t0 < s1; t0 += kTile) {
+    for (int64_t t0 = s0; t0 < s1; t0 += kRegionTile) {
 #pragma unroll
         for (int u = 0; u < kRegionItems; ++u) {
-            const int64_t i = t0 + u * kPartThreads + threadIdx.x;
+            const int64_t i = t0 + u * kRegionThreads + threadIdx.x;
             if (i < s1) {
                 if (t0 != s0) key[u] = tkl[i];
                 row[u] = trl[i];
@@ -330,7 +374,7 @@ __global__ void __launch_bounds__(kPartThreads) part_region_kernel(const uint64_
         }
 #pragma unroll
         for (int u = 0; u < kRegionItems; ++u) {
-            const int64_t i = t0 + u * kPartThreads + threadIdx.x;
+            const int64_t i = t0 + u * kRegionThreads + threadIdx.x;
             if (i < s1) {
                 const uint32_t pos = atomicAdd(&h[(uint32_t)(key[u] >> shift) & mask], 1u);
                 sk[pos] = key[u];
@@ -377,11 +421,13 @@ cudaError_t build_tables(const uint64_t* keys, int64_t row0, int64_t n, int L, i
             if (e == cudaSuccess)
                 part_scatter_kernel<<<g1, kPartThreads, smem1, st>>>(keys, row0, n, cap, b1, nblk, counts, bstart,
                                                                     tk, tr);
-            const size_t smem2 = ((size_t)(1 << b2) + kPartThreads) * sizeof(uint32_t);
-            part_region_kernel<<<dim3((unsigned)nb, (unsigned)L), kPartThreads, smem2, st>>>(
-                tk, tr, n, bstart, b1, b2, out_stride, bins, skeys, srows);
+            const size_t smem2 = region_smem(b2);
+            if (e == cudaSuccess) e = ensure_dynamic_smem((const void*)part_region_kernel, smem2);
+            if (e == cudaSuccess)
+                part_region_kernel<<<dim3((unsigned)nb, (unsigned)L), kRegionThreads, smem2, st>>>(
+                    tk, tr, n, bstart, b1, b2, out_stride, bins, skeys, srows);
             note_launch(5);
-            e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaGetLastError();
         }
         cudaFreeAsync(counts, st);
         cudaFreeAsync(bstart, st);

@@ -659,15 +659,13 @@ def test_exact_scan_equals_brute_force_topk(prune):
         assert_topk_match(q, ids[i], d[i], oi, od, lambda j: db[j], rb)
 
 
-def test_large_tables_two_pass_partition_candidates():
-    """Tables of >= 65,536 rows are binned in two passes. The candidate set of every query must be
-    the union over tables of the rows whose bucket key equals the query's (computed here from the
-    keys ssh_hash_device returns), and a stored series must find itself at distance 0."""
+def _check_large_table_candidates(db, src):
+    """Every query's candidate count must equal the size of the union over tables of the rows
+    whose bucket key equals the query's (computed here from the keys ssh_hash_device returns),
+    and the stored series db[src[:3]] must find themselves at distance 0."""
     b = _binding()
-    cfg = CFG1
-    N, m = 70_000, 128
-    db = synth.random_walk(N, m, seed=71)
-    with _index(cfg) as idx:
+    N, m = db.shape
+    with _index(CFG1) as idx:
         idx.add(db)
         L = idx.L
         d_db = torch.from_numpy(db).cuda()
@@ -675,8 +673,6 @@ def test_large_tables_two_pass_partition_candidates():
         b.ssh_hash_device(idx.handle, d_db, m, N, d_keys=keys)
         torch.cuda.synchronize()
         keys = keys.cpu().numpy()
-        rng = np.random.default_rng(5)
-        src = rng.integers(0, N, 6)
         qs = np.concatenate([db[src[:3]], synth.perturbed_queries(db, 3, seed=9)[0]])
         qkeys = torch.zeros((L, len(qs)), dtype=torch.int64, device="cuda")
         b.ssh_hash_device(idx.handle, torch.from_numpy(qs).cuda(), m, len(qs), d_keys=qkeys)
@@ -690,7 +686,23 @@ def test_large_tables_two_pass_partition_candidates():
             ids, d = idx.query(qs[i:i + 1], 3)
             assert idx.stats()["candidates"] == int(want.sum())
             if i < 3:
-                assert ids[0, 0] == src[i] and d[0, 0] == 0.0
+                assert d[0, 0] == 0.0 and np.array_equal(db[ids[0, 0]], db[src[i]])
+
+
+def test_large_tables_two_pass_partition_candidates():
+    """Tables of >= 65,536 rows are binned in two passes (buckets of the top key bits, then the
+    bins inside each bucket, placed in shared memory)."""
+    db = synth.random_walk(70_000, 128, seed=71)
+    _check_large_table_candidates(db, np.random.default_rng(5).integers(0, len(db), 6))
+
+
+def test_large_tables_with_an_oversized_bucket():
+    """5,000 copies of one series share its bucket key in every table, so that bucket holds more
+    entries than a block places in shared memory and the second pass takes its tile-by-tile path;
+    the candidate sets must still be the exact key matches."""
+    db = synth.random_walk(70_000, 128, seed=72)
+    db[10_000:15_000] = db[3]
+    _check_large_table_candidates(db, np.array([3, 12_345, 40_000, 0, 0, 0]))
 
 
 def test_read_probe_runs_and_rejects_bad_sizes():
