@@ -798,8 +798,11 @@ ssh_status query_group(ssh_index* idx, SubIndex& s, const std::vector<const floa
             FilterArgs f{seg_begin, nq, max_c, lb, T, U, shrink, mode, fcount, cursor, fbegin, ftotal + mode, pair_b, fb,
                          fslot};
             if (e == cudaSuccess) e = launch_filter(f, st);
-            // every filtered segment is no longer than its candidate segment: size the DTW grid by max_c
-            PairSet sub{fbegin, nq, d_qptr, fb, fslot, max_c};
+            // every filtered segment is no longer than its candidate segment, and a seed segment holds
+            // about kSeedFactor * k pairs: size the DTW grid by that (a block whose share is empty
+            // exits at once; a longer segment gives each block a larger share, see dtw_wave_kernel)
+            const int64_t seg_pairs = mode == 0 ? std::min<int64_t>(max_c, (int64_t)kSeedFactor * k) : max_c;
+            PairSet sub{fbegin, nq, d_qptr, fb, fslot, seg_pairs};
             sub.blocks_done = ftotal + 3 + mode;  // the cells actually computed (abandoned pairs stop early)
             if (mode == 1) {  // survivors: stop at the bound U of the seeds' k-th distance
                 sub.abandon = U;
