@@ -50,10 +50,22 @@ __global__ void probe_union_kernel(ProbeArgs a) {
     }
 }
 
+// Set bits of each query's bitmap row: one block per row, eight independent
+// coalesced loads in flight per thread.
 __global__ void bitmap_count_kernel(const uint32_t* bitmap, int64_t words, int64_t* counts) {
+    constexpr int kU = 8;
     const uint32_t* bm = bitmap + (int64_t)blockIdx.x * words;
     int64_t s = 0;
-    for (int64_t w = threadIdx.x; w < words; w += blockDim.x) s += __popc(bm[w]);
+    for (int64_t w0 = 0; w0 < words; w0 += (int64_t)kU * blockDim.x) {
+        uint32_t v[kU];
+#pragma unroll
+        for (int j = 0; j < kU; ++j) {
+            const int64_t w = w0 + (int64_t)j * blockDim.x + threadIdx.x;
+            v[j] = (w < words) ? bm[w] : 0u;
+        }
+#pragma unroll
+        for (int j = 0; j < kU; ++j) s += __popc(v[j]);
+    }
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
     __shared__ int64_t part[32];
     if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
@@ -68,6 +80,7 @@ __global__ void bitmap_count_kernel(const uint32_t* bitmap, int64_t words, int64
 // Rows of each query's bitmap in ascending order, at offsets[q] ..
 __global__ void __launch_bounds__(1024) bitmap_compact_kernel(const uint32_t* bitmap, int64_t words,
                                                               const int64_t* offsets, uint32_t* cand_rows) {
+    constexpr int kW = 4;  // consecutive words per thread
     __shared__ int part[32];
     __shared__ int64_t s_base;
     const int64_t q = blockIdx.x;
@@ -75,10 +88,15 @@ __global__ void __launch_bounds__(1024) bitmap_compact_kernel(const uint32_t* bi
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) s_base = offsets[q];
     __syncthreads();
-    for (int64_t w0 = 0; w0 < words; w0 += blockDim.x) {
-        const int64_t w = w0 + threadIdx.x;
-        uint32_t bits = (w < words) ? bm[w] : 0u;
-        int c = __popc(bits);
+    for (int64_t w0 = 0; w0 < words; w0 += (int64_t)kW * blockDim.x) {
+        const int64_t wb = w0 + (int64_t)kW * threadIdx.x;
+        uint32_t bits[kW];
+        int c = 0;
+#pragma unroll
+        for (int j = 0; j < kW; ++j) {
+            bits[j] = (wb + j < words) ? bm[wb + j] : 0u;
+            c += __popc(bits[j]);
+        }
         int incl = c;
         for (int o = 1; o < 32; o <<= 1) {
             int v = __shfl_up_sync(kFull, incl, o);
@@ -97,10 +115,14 @@ __global__ void __launch_bounds__(1024) bitmap_compact_kernel(const uint32_t* bi
         }
         __syncthreads();
         int64_t pos = s_base + part[warp] + (incl - c);
-        while (bits) {
-            int b = __ffs(bits) - 1;
-            bits &= bits - 1;
-            cand_rows[pos++] = (uint32_t)(w * 32 + b);
+#pragma unroll
+        for (int j = 0; j < kW; ++j) {
+            uint32_t bj = bits[j];
+            while (bj) {
+                const int b = __ffs(bj) - 1;
+                bj &= bj - 1;
+                cand_rows[pos++] = (uint32_t)((wb + j) * 32 + b);
+            }
         }
         __syncthreads();
         if (threadIdx.x == blockDim.x - 1) s_base = pos;
