@@ -1504,6 +1504,7 @@ def headline(line, detail_path):
             "scaling", "vs_baseline", "dtype", "data", "gpu_launches", "clocks")
     h = {k: line[k] for k in keep if k in line}
     h["value"] = float(line["value"])
+    h["ms_per_step"] = _r(float(line["ms_per_step"]), 5)
     c = line["config"]
     h["config"] = {k: c[k] for k in ("workload", "parallelism", "l2") if k in c}
     r = line["roofline"]
@@ -1545,9 +1546,6 @@ def headline(line, detail_path):
         h["batched_graph_kernels"] = b.get("graph_kernels")
         if b.get("at_recall"):
             h["batched_at_recall_queries_per_s"] = _r(b["at_recall"]["batched_queries_per_s"])
-    if "served" in line:
-        s = line["served"]["rates"]
-        h["served_p50_p99_ms"] = {str(x["offered_qps"]): [_r(x["p50_ms"], 3), _r(x["p99_ms"], 3)] for x in s}
     h["detail"] = os.path.relpath(detail_path, ROOT) if os.path.isabs(detail_path) else detail_path
     return h
 

@@ -1,0 +1,64 @@
+"""The benchmark's last stdout line: a short headline with the contract's keys, whatever the
+run's clock record holds (the full measurement goes to the detail file)."""
+import json
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def _full_line():
+    """A full measurement line of the scale workload, with the longest strings the bench writes."""
+    sample = ("oracle indexed 10000 series and answered 10 queries on them; step time extrapolated as "
+              "N*t_hash + nq*t_query*N/10000")
+    return {
+        "metric": bench.METRIC, "value": 186495018.55175248, "unit": "series/s", "n_gpus": 1, "steps": 10,
+        "warmup": 3, "ms_per_step": 5.362073516845703, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "gpu_launches": 340,
+        "clocks": {"sm_mhz": 1965.0, "sm_max_mhz": 2070.0,
+                   "reasons": ["sw_power_cap", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"],
+                   "samples": 2},
+        "config": {"workload": bench.workload_desc(bench.SCALE), "parallelism": "single GPU",
+                   "l2": "inputs larger than L2 (series 2.05 GB per step)", "recall_subset": 10000},
+        "roofline": {"kernel": "add.cws", "bound": "hbm", "achieved": 295.4832, "peak": 6790.0, "unit": "GB/s",
+                     "frac": 0.043517, "traffic": 714453760.0, "peak_source": "measured",
+                     "binding": {"resource": "L2 reads (gathers)", "bytes_per_launch": 23231502560.0,
+                                 "achieved": 9481.93, "peak": 19168.48, "unit": "GB/s", "frac": 0.49466,
+                                 "peak_source": "measured here: L1-bypassing reads of a 32 MB L2-resident buffer"}},
+        "kernels": {"add.hash_pipeline": {"frac": 0.086093}, "query.dtw": {"frac": 0.062119}},
+        "cpu_baseline": {"value": 764.0447, "unit": "series/s", "cores": 1, "kind": "oracle", "sample": sample,
+                         "seconds": 11.9, "all_cores": {"value": 9748.85, "unit": "series/s", "cores": 16,
+                                                        "sample": sample, "seconds": 0.85}},
+        "e2e": {"value": 84106303.9, "unit": "series/s", "h2d_bytes_per_step": 2048204800, "d2h_bytes_per_step": 12000,
+                "steps": 10, "warmup": 2, "ms_per_step": 11.89, "h2d_gbs": 172.26, "h2d_peak_gbs": 211.47,
+                "h2d_frac": 0.8146, "h2d_peak_source": "measured here", "api": "ssh_index_add(host) + ssh_query(host)"},
+        "queries_per_s": 115277.07, "ssh_create": {"seconds": 0.0068},
+        "latency_ms": {"p50": 0.40864, "p99": 0.59648, "mode": "one query per call on the built index"},
+        "recall_at_10": 0.009, "ndcg_at_10": 0.02703,
+        "recall_operating_point": {"chosen": {"W": 40, "delta": 3, "n": 10, "K": 4, "L": 25, "recall_at_10": 0.925,
+                                              "queries_per_s": 90503.63}},
+        "batched": {"batched_queries_per_s": 12936.91, "graph_kernels": 56,
+                    "at_recall": {"batched_queries_per_s": 3285.26}},
+        "served": {"rates": [{"offered_qps": q, "p50_ms": 1.5, "p99_ms": 9.9} for q in (1000, 5000, 20000, 50000)]},
+    }
+
+
+def test_headline_is_short_and_carries_the_contract_keys():
+    h = bench.headline(_full_line(), "gpurun_out/bench_detail_n1.json")
+    text = json.dumps(h)
+    assert len(text) < 2048
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "dtype", "data", "gpu_launches", "clocks", "roofline", "cpu_baseline", "e2e"):
+        assert key in h, key
+    assert h["config"]["workload"].startswith("plain SSH at scale")
+    assert h["value"] == 186495018.55175248
+    for key in ("bound", "achieved", "peak", "unit", "frac", "traffic"):
+        assert key in h["roofline"], key
+    for key in ("value", "unit", "cores", "kind", "sample"):
+        assert key in h["cpu_baseline"], key
+    for key in ("value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step"):
+        assert key in h["e2e"], key
+    assert json.loads(text) == h
