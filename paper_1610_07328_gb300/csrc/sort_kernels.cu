@@ -4,8 +4,9 @@
 // Tables: one most-significant-digit radix pass per table. The top B bits of
 // each 64-bit bucket key pick one of 2^B bins (B chosen so a bin holds about
 // 16 rows); a histogram, an exclusive scan and a scatter place every (key, row)
-// in its bin. Equal keys always share a bin, so a probe scans the query key's
-// bin and compares full keys; the order inside a bin is not used.
+// in its bin (large tables take two passes, below). Equal keys always share a
+// bin, so a probe scans the query key's bin and compares full keys; the order
+// inside a bin is not used.
 // Selections: per-segment radix select of the k-th smallest key.
 #include <cuda_runtime.h>
 #include <stdint.h>
