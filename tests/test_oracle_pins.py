@@ -382,6 +382,32 @@ def test_dtw_identity_symmetry_band0_monotone():
             prev = d
 
 
+def test_dtw_and_lb_keogh_closed_forms_on_steps_and_constants():
+    """Closed forms of the banded DTW (Sec. 2.1) and LB_Keogh (Sec. 3) that depend on the band.
+    Two unit steps, q = 0 before sample k and 1 from it, c the same with k2 (1 <= k, k2 <= m-1):
+    rows i in [min(k, k2), |k2 - k| - rb + min(k, k2)) can reach no column of the other series'
+    level inside the band, so DTW = max(0, |k2 - k| - rb), and a path meeting that count exists;
+    the envelope of q misses c on exactly those samples, so LB_Keogh is tight there. Constant
+    series a, b: every path has at least m cells of cost (a - b)^2 and the diagonal has m."""
+    rng = np.random.default_rng(12)
+    for _ in range(300):
+        m = int(rng.integers(2, 60))
+        k, k2 = (int(v) for v in rng.integers(1, m, 2))
+        rb = int(rng.integers(0, m))
+        q = np.where(np.arange(m) < k, 0.0, 1.0).astype(np.float32)
+        c = np.where(np.arange(m) < k2, 0.0, 1.0).astype(np.float32)
+        want = float(max(0, abs(k2 - k) - rb))
+        assert oracle.dtw(q, c, rb) == want
+        assert oracle.dtw(c, q, rb) == want
+        assert oracle.lb_keogh(q, c, rb) == want
+    for m in (1, 5, 17, 64):
+        a = np.full(m, 2.5, np.float32)
+        b = np.full(m, -1.0, np.float32)
+        for rb in range(m):
+            assert oracle.dtw(a, b, rb) == m * 3.5 ** 2
+            assert oracle.lb_keogh(a, b, rb) == m * 3.5 ** 2
+
+
 def test_band_radius_floor():
     assert oracle.band_radius(0.05, 128) == 6
     assert oracle.band_radius(0.05, 512) == 25
