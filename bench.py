@@ -660,6 +660,34 @@ def exact_scan_measurement(binding, torch, d_sub, d_db, d_q, exact_sub, w, k, n_
     return out
 
 
+def dtw_full_load_measurement(binding, torch, d_db, d_q, w, rows=40_000, nq=10):
+    """The banded DTW kernel at full load: an exact scan with LB pruning off ranks every one of
+    `rows` stored series for each of `nq` queries, so one DTW launch runs rows * nq complete
+    pairs (no abandoning); its CUDA-event time gives cells/s and the FP32 fraction at 3 FLOP
+    per cell. The query path's own DTW passes are short (seeds, then survivors cut by the bound)
+    and are reported apart as query.dtw."""
+    try:
+        with binding.SSHIndex(w["W"], w["delta"], w["n"], w["K"], w["L"], w["band"], w["seed"]) as ix:
+            ix.add_device(d_db[:rows].contiguous(), borrow=True)
+            ix.set_exact_scan(True)
+            ix.set_lb_prune(False)
+            q = d_q[:nq].contiguous()
+            _timed_query(torch, ix, q, w["k"], reps=1)
+            ix.set_kernel_timing(True)
+            ix.reset_stats()
+            _timed_query(torch, ix, q, w["k"], reps=3)
+            t = ix.kernel_times()["query.dtw"]
+            ix.set_kernel_timing(False)
+        ms = t["total_ms"] / t["calls"]
+        cells = t["units"] / t["calls"]
+        tflops = 3.0 * cells / (ms * 1e-3) / 1e12
+        return {"pairs_per_launch": rows * nq, "cells_per_launch": cells, "ms_per_launch": ms,
+                "cells_per_s": cells / (ms * 1e-3), "tflops": tflops, "peak_tflops": fp32_peak_tflops(),
+                "frac": tflops / fp32_peak_tflops(), "peak_source": fp32_peak_source()}
+    except Exception as e:  # a measurement block: report, never lose the bench line
+        return {"error": "%s: %s" % (type(e).__name__, e)}
+
+
 BATCH_LENGTHS = (128, 256, 512, 1024, 2048)
 
 
@@ -1250,6 +1278,7 @@ def run_gpu(args, w):
         extra["parameter_study"] = parameter_study(binding, torch, d_sub.contiguous(), d_q, exact_sub, w, k)
         extra["srp_baseline"] = srp_baseline(binding, torch, d_sub.contiguous(), d_q, exact_sub, w, k)
         extra["minhash_variants"] = minhash_variants(binding, torch, d_db, d_sub.contiguous(), d_q, exact_sub, w, k)
+        extra["dtw_full_load"] = dtw_full_load_measurement(binding, torch, d_db, d_q, w)
         extra["exact_scan"] = exact_scan_measurement(binding, torch, d_sub.contiguous(), d_db, d_q, exact_sub, w, k,
                                                      n_full=4 if args.small else 10)
         if not args.fast:
@@ -1518,6 +1547,8 @@ def headline(line, detail_path):
         h["hash_pipeline_hbm_frac"] = _r(kr["add.hash_pipeline"]["frac"])
     if "query.dtw" in kr:
         h["dtw_fp32_frac"] = _r(kr["query.dtw"].get("frac"))
+    if isinstance(line.get("dtw_full_load"), dict) and "frac" in line["dtw_full_load"]:
+        h["dtw_fp32_frac_full_load"] = _r(line["dtw_full_load"]["frac"])
     if "cpu_baseline" in line:
         cb = line["cpu_baseline"]
         h["cpu_baseline"] = {"value": _r(cb["value"]), "unit": cb["unit"], "cores": cb["cores"], "kind": cb["kind"],

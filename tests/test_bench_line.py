@@ -43,6 +43,7 @@ def _full_line():
         "batched": {"batched_queries_per_s": 12936.91, "graph_kernels": 56,
                     "at_recall": {"batched_queries_per_s": 3285.26}},
         "served": {"rates": [{"offered_qps": q, "p50_ms": 1.5, "p99_ms": 9.9} for q in (1000, 5000, 20000, 50000)]},
+        "dtw_full_load": {"frac": 0.27123, "tflops": 21.71, "cells_per_s": 7.24e12},
     }
 
 
