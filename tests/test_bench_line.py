@@ -63,3 +63,33 @@ def test_headline_is_short_and_carries_the_contract_keys():
     for key in ("value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step"):
         assert key in h["e2e"], key
     assert json.loads(text) == h
+
+
+def test_algorithmic_bytes_per_series_follow_the_sketch_geometry():
+    """Per-series bytes of the hash kernels at the scale shape (m=512, W=80, delta=3, n=15, L=25):
+    N_B = floor((m - W) / delta) + 1 = 145 sign bits (5 words), S = N_B - n + 1 = 131 shingles."""
+    w = bench.SCALE
+    assert bench.algorithmic(w, "sketch") == ("hbm", 4 * 512 + 4 * 5)
+    assert bench.algorithmic(w, "shingle") == ("hbm", 4 * 5 + 4 * 131)
+    assert bench.algorithmic(w, "cws") == ("hbm", 4 * 131 + 8 * 25)
+    assert bench.algorithmic(w, "table_sort") == ("hbm", 20)
+    assert bench.algorithmic(w, "dtw") == ("alu", 3)
+    assert bench.algorithmic(w, "probe_union") == (None, None)
+
+
+def test_kernel_rooflines_divide_algorithmic_work_by_the_event_time():
+    bench.set_fp32_peak(152, 2070.0)
+    times = {"add.cws": {"total_ms": 3 * 2.45, "calls": 3, "launches": 3, "units": 3e6},
+             "query.dtw": {"total_ms": 2.0, "calls": 2, "launches": 2, "units": 2e9},
+             "query.probe_union": {"total_ms": 0.5, "calls": 2, "launches": 4, "units": 50.0}}
+    out = bench.kernel_rooflines(bench.SCALE, times, {"hbm_gbs": 6790.0})
+    cws = out["add.cws"]
+    assert cws["avg_ms"] == 2.45 and cws["units_per_call"] == 1e6
+    assert abs(cws["achieved"] - 1e6 * 724 / 2.45e-3 / 1e9) < 1e-9
+    assert abs(cws["frac"] - cws["achieved"] / 6790.0) < 1e-12
+    dtw = out["query.dtw"]
+    assert dtw["unit"] == "TFLOP/s" and abs(dtw["achieved"] - 3.0) < 1e-12
+    assert abs(dtw["peak"] - 152 * 128 * 2 * 2070e6 / 1e12) < 1e-9
+    assert out["query.probe_union"]["achieved"] is None
+    pipe = out["add.hash_pipeline"]  # only the minhash was timed here: the series read + keys written
+    assert abs(pipe["achieved"] - 1e6 * (4 * 512 + 8 * 25) / 2.45e-3 / 1e9) < 1e-9
