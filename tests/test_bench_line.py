@@ -93,3 +93,24 @@ def test_kernel_rooflines_divide_algorithmic_work_by_the_event_time():
     assert out["query.probe_union"]["achieved"] is None
     pipe = out["add.hash_pipeline"]  # only the minhash was timed here: the series read + keys written
     assert abs(pipe["achieved"] - 1e6 * (4 * 512 + 8 * 25) / 2.45e-3 / 1e9) < 1e-9
+
+
+def test_reference_arm_prints_its_contract_line():
+    """`bench.py --impl reference` times the CPU oracle on a slice of the workload per step and
+    prints one JSON line last, with the step it actually timed as ms_per_step."""
+    import subprocess
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "0"], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    last = r.stdout.strip().splitlines()[-1]
+    assert len(last) < 2048
+    line = json.loads(last)
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC
+    assert line["value"] > 0 and line["unit"] == "series/s" and line["steps"] == 1 and line["warmup"] == 0
+    series, queries = 1000, 100
+    assert "%d series + %d queries per step" % (series, queries) in line["config"]["workload"]
+    assert abs(line["value"] - series / (line["ms_per_step"] / 1000.0)) <= 1e-6 * line["value"]
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"] and cb["sample"]
+    assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
